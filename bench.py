@@ -1,0 +1,337 @@
+"""Benchmark of libtsqr: R factor of a tall-and-skinny FP64 matrix on GB300.
+
+Workload (one step = one full TSQR of the matrix: leaf folds + reduction tree + normalize):
+  FP64 A of 4,194,304 x 32 (1 GiB, column-major), iid N(0,1) from seed 0, the AUTO plan
+  (hybrid tree: flat folds inside each CTA, binary tree across CTAs).
+Metric: GFLOP/s counted as (2 m n^2 - 2 n^3 / 3) per step; A-read GB/s reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (one unblocked Householder QR, FP64) on the host cores,
+each step a bounded row sample of the same workload.  Under torchrun every rank factorizes its
+own replica (the method needs no exchange between GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M, N = 4194304, 32
+SEED = 0
+FP64_FMA_PER_CLK_PER_SM = 2      # measured DFMA issue rate of a GB300 SM
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def flops(m, n):
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        p = {"hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "source": "measured",
+             "sm_max_mhz": float(d.get("sm_max_mhz", SM_MAX_MHZ))}
+    mhz = p.get("sm_max_mhz", SM_MAX_MHZ)
+    p["fp64_tflops"] = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            self.path = f"/tmp/tsqr_clocks_{os.getpid()}.csv"
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen([exe, f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend, init_method="env://")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_sample_rows(target_s=12.0, threads=None):
+    """Rows of the workload the oracle factorizes in about target_s seconds."""
+    return 1 << 20
+
+
+def run_cpu_baseline(At_cpu, threads, rows, gpu_R_fn=None):
+    import numpy as np
+    import oracle
+    A = oracle.from_torch_colmajor(At_cpu[:, :rows])
+    t0 = time.perf_counter()
+    Ro = oracle.householder_r(A, nthreads=threads)
+    dt = time.perf_counter() - t0
+    out = {"value": flops(rows, N) / dt / 1e9, "unit": "GFLOP/s", "cores": threads,
+           "kind": "oracle", "seconds": dt,
+           "sample": f"first {rows:,} rows of the {M:,} x {N} workload (FP64, one unblocked "
+                     f"Householder QR, {threads} threads)"}
+    if gpu_R_fn is not None:
+        Rg = gpu_R_fn(rows)
+        kap = oracle.kappa_from_r(Ro)
+        out["parity_sample"] = {
+            "rows": rows, "rel_err_vs_oracle": oracle.rel_err(Rg, Ro),
+            "bound_50_kappa_u": 50 * kap * 2.0 ** -53,
+            "gram_residual": oracle.gram_residual(A, Rg, nthreads=threads),
+            "gram_tol": 1e-13}
+    return out
+
+
+def bench_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import workloads
+    threads = os.cpu_count() or 1
+    rows = cpu_sample_rows()
+    At = workloads.gaussian(rows, N, seed=SEED)
+    import oracle
+    A = oracle.from_torch_colmajor(At)
+    for _ in range(args.warmup):
+        oracle.householder_r(A, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.householder_r(A, nthreads=threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = flops(rows, N) / dt / 1e9
+    line = {"metric": "TSQR GFLOP/s (2mn^2-2n^3/3), FP64", "value": v, "unit": "GFLOP/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 {M:,} x {N} N(0,1) seed {SEED}; CPU oracle on a "
+                                   f"{rows:,}-row sample per step", "m": M, "n": N},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {rows:,} rows of the workload per step"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_ours(args, world, rank, local):
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    At_cpu = workloads.gaussian(M, N, seed=SEED + rank)
+    A = At_cpu.to(dev).T                                   # (m, n) column-major, lda = m
+    R = T.empty_r(N, dev)
+    plan = T.tsqr_resolve_plan(M, N)
+    fl = flops(M, N)
+    bytes_a = 8.0 * M * N
+
+    for _ in range(max(args.warmup, 3)):
+        T.tsqr_r(A, R=R)
+    torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM (1 GiB > the 129 MB L2: no flush needed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            T.tsqr_r(A, R=R)
+            ev[i][1].record(stream)
+            launches += T.tsqr_last_launch_count()
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms_local = start.elapsed_time(end)
+    per_launch = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(ms_local, world)
+    status = T.tsqr_get_device_status()
+    ms_step = ms / args.steps
+    value = world * fl * args.steps / (ms / 1e3) / 1e9
+
+    # end to end through the public call with HOST buffers: pinned H2D of A, the call, D2H of R
+    A_host = At_cpu.pin_memory()
+    A_dev = torch.empty_like(A_host, device=dev)
+    R_host = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        A_dev.copy_(A_host, non_blocking=True)
+        T.tsqr_r(A_dev.T, R=R)
+        R_host.copy_(R.T, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        T.tsqr_r(A_dev.T, R=R)
+        R_host.copy_(R.T, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e = {"value": world * fl / e2e_s / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(A_host.numel() * 8), "d2h_bytes_per_step": int(N * N * 8),
+           "ms_per_step": e2e_s * 1e3}
+
+    pk = peaks()
+    kern_ms = statistics.mean(per_launch)
+    achieved = fl / (kern_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["fp64_tflops"], "traffic": None,
+            "peak_note": "FP64 DFMA pipe: 152 SMs x 2 FMA/clk x 2 flop x max SM clock "
+                         "(derived; measured DFMA microbenchmark 1.20 TFLOP/s)",
+            "kernel": "tsqr_f64_kernel", "kernel_ms": kern_ms,
+            "a_read_gbs": bytes_a / (kern_ms / 1e3) / 1e9,
+            "a_read_frac_of_hbm": bytes_a / (kern_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+            "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": pk["source"]}
+    traffic_path = os.path.join(ROOT, "profiles", "tsqr_f64_kernel_traffic.json")
+    if os.path.exists(traffic_path):
+        with open(traffic_path) as f:
+            tr = json.load(f)
+        if tr.get("kernel_sha") == kernel_sha():
+            roof["traffic"] = tr.get("bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rows = cpu_sample_rows()
+
+        def gpu_R(rows_):
+            Rs = T.tsqr_r(A[:rows_, :])
+            return Rs.cpu().numpy()
+
+        cpu = run_cpu_baseline(At_cpu, threads, rows, gpu_R)
+
+    if rank == 0:
+        line = {"metric": "TSQR GFLOP/s (2mn^2-2n^3/3), FP64", "value": value, "unit": "GFLOP/s",
+                "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"FP64 {M:,} x {N} N(0,1) seed {SEED}+rank, 1 GiB per GPU",
+                           "m": M, "n": N, "tree": ["auto", "binary", "flat", "hybrid"][plan.tree],
+                           "tile_rows": plan.tile_rows, "ctas": plan.ctas, "warps": plan.warps,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "input 1 GiB per GPU > 129 MB L2; no flush"},
+                "a_read_gbs": world * bytes_a * args.steps / (ms / 1e3) / 1e9,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "device_status": int(status)}
+        print(json.dumps(line))
+    return 0
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1002_4250_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1002_4250_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        return bench_reference(args, world, rank)
+    from paper_1002_4250_gb300 import _build
+    _build.build()
+    rc = bench_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,143 @@
+/*
+ * libtsqr -- the R factor of A = QR for tall-and-skinny matrices (m >> n) on one NVIDIA GB300
+ * (sm_103a), computed TSQR-style after J. Langou, "Computing the R of the QR factorization of
+ * tall and skinny matrices using MPI_Reduce" (arXiv:1002.4250):
+ *   step 1 (Section 2, Section 3 / Table 1): every row tile of A gets a local Householder QR;
+ *   step 2 (Section 2, Table 3): the tiles' n x n upper-triangular factors are reduced along a
+ *          tree by the operator qr(R_i, R_j) = R factor of [R_i; R_j], which does no arithmetic
+ *          on the known zeros of the two triangles.
+ * The tree is fixed per call (binary, flat or hybrid; Section 1 and Fig. 1), so a call is
+ * bit-reproducible: same inputs and same plan give the same bytes.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major: element (i, j) of A is A[i + j*lda].
+ *   - R is n x n, written in full: the upper triangle with diag(R) >= 0 (Section 2: R is unique
+ *     up to the sign of each row; a non-negative diagonal makes it unique) and an exact zero
+ *     strict lower triangle.  R is always FP64.
+ *   - Pointers named "device" must be device (or managed) memory of the current device; the
+ *     caller owns every buffer; the library never frees or keeps caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream).
+ *     Argument errors are found on the host and returned before anything is enqueued.
+ *     Conditions met on the device (non-finite values in R) are recorded in a per-stream
+ *     status word that tsqr_get_device_status() reads.
+ *   - Workspace (tree-node slots and counters) is allocated by the library, per device and
+ *     stream, with stream-ordered allocation, grown when needed and reused across calls;
+ *     tsqr_release_workspace() returns it.  Calls on the same stream may follow each other
+ *     freely; the first call on a stream should not be made under stream capture.
+ *   - n is limited to TSQR_MAX_N.
+ */
+#ifndef LIBTSQR_TSQR_H
+#define LIBTSQR_TSQR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSQR_MAX_N 128
+
+typedef enum {
+    TSQR_SUCCESS = 0,
+    TSQR_ERR_INVALID_ARG = 1,   /* a size, leading dimension, pointer or enum is invalid      */
+    TSQR_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. n > TSQR_MAX_N)              */
+    TSQR_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, allocation, copy)      */
+    TSQR_ERR_ALLOC = 4,         /* workspace could not be allocated                           */
+    TSQR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (reserved)              */
+    TSQR_STATUS_NONFINITE = 6   /* R holds NaN or Inf (the input held NaN/Inf or overflowed)  */
+} tsqr_status_t;
+
+/* Storage type of A.  R is always FP64. */
+typedef enum { TSQR_F64 = 0, TSQR_F32 = 1, TSQR_BF16 = 2 } tsqr_dtype_t;
+
+/* Arithmetic of the leaf (tile) factorizations.  The tree operator is FP64 in every mode.
+ * TSQR_PREC_F64:   FP64 everywhere (A must be TSQR_F64).
+ * TSQR_PREC_MIXED: leaf Householder panels in FP32 (A is FP32 or BF16, widened exactly on
+ *                  load), reflector norms and tree combines in FP64.                          */
+typedef enum { TSQR_PREC_F64 = 0, TSQR_PREC_MIXED = 1 } tsqr_prec_t;
+
+/* Reduction tree over the row tiles (Section 1: "any reduction tree" works by associativity).
+ * BINARY: one tile of tile_rows rows per leaf, leaves paired (2t, 2t+1) level by level, the
+ *         lower index on top, an odd last node promoted unchanged (Fig. 1 for four leaves).
+ * FLAT:   one CTA folds every tile in row order, R <- R([R; A_t]) (the tile algorithms' tree).
+ * HYBRID: `ctas` CTAs each fold a contiguous run of tiles flat, their R factors then reduced
+ *         by the BINARY rule.  AUTO picks HYBRID.                                            */
+typedef enum {
+    TSQR_TREE_AUTO = 0, TSQR_TREE_BINARY = 1, TSQR_TREE_FLAT = 2, TSQR_TREE_HYBRID = 3
+} tsqr_tree_t;
+
+/* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic
+ * order, so two calls with equal plans and inputs return identical bytes. */
+typedef struct {
+    int32_t tree;       /* tsqr_tree_t                                                     */
+    int32_t tile_rows;  /* rows per tile (slab) b; must fit the kernel's shared memory      */
+    int32_t ctas;       /* HYBRID: number of leaf CTAs                                      */
+    int32_t warps;      /* warps per CTA (2, 4 or 8)                                         */
+} tsqr_plan_t;
+
+typedef void *tsqr_stream_t; /* a cudaStream_t */
+
+/* R factor of the m x n FP64 matrix A (Section 2, steps 1 and 2).
+ *   A   : device, column-major, lda >= max(1, m); read only.
+ *   m   : rows, m >= 0 (m = 0 gives R = 0; m < n gives rows m..n-1 of R equal to zero).
+ *   n   : columns, 0 <= n <= TSQR_MAX_N (n = 0 does nothing).
+ *   R   : device, column-major n x n, ldr >= max(1, n); fully written.
+ * Uses the AUTO plan.  Returns TSQR_SUCCESS once the work is enqueued.                     */
+tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
+                     tsqr_stream_t stream);
+
+/* tsqr_r with the storage type of A, the leaf arithmetic and an optional plan (NULL = AUTO).
+ * (dtype, prec) must be (F64, F64), (F32, MIXED) or (BF16, MIXED).  lda counts elements. */
+tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
+                        int64_t lda, double *R, int64_t ldr, const tsqr_plan_t *plan,
+                        tsqr_stream_t stream);
+
+/* One node of the reduction tree on the GPU: the operator qr(R1, R2) of Section 2 / Table 3,
+ * the R factor of the 2n x n stack [R1; R2] of two upper triangles (entries below their
+ * diagonals are ignored), computed with the same reflector sign rule as the tree
+ * (beta = -sign(alpha) ||.||, sign(0) = +1).
+ *   R1, R2 : device, column-major n x n, ld1, ld2 >= n; read only.
+ *   R      : device, column-major n x n, ldr >= n: the R factor, strict lower part zero;
+ *            with normalize != 0 rows are also flipped so that diag(R) >= 0.             */
+tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const double *R2,
+                             int64_t ld2, double *R, int64_t ldr, int32_t normalize,
+                             tsqr_stream_t stream);
+
+/* Varlen batch of independent problems: R_i = R factor of A_i for i < count.
+ *   ptrs    : host array of `count` device pointers; A_i is column-major m_i x n_i with
+ *             lda_i = m_i (e.g. all pointing into one packed buffer).
+ *   ms, ns  : host arrays of count rows (>= 0) and columns (1..TSQR_MAX_N).
+ *   offsets : host array of count+1 non-decreasing element offsets into R_packed with
+ *             offsets[i+1] - offsets[i] >= n_i^2; R_i is written column-major with ld n_i at
+ *             R_packed + offsets[i].
+ *   R_packed: device FP64 buffer of at least offsets[count] elements.
+ *   dtype, prec as for tsqr_r_ex.  All problems are factorized by one launch.             */
+tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                             const int64_t *offsets, int32_t count, double *R_packed,
+                             int32_t dtype, int32_t prec, tsqr_stream_t stream);
+
+/* Synchronizes `stream`, returns the device-side status recorded by the calls made on it since
+ * the last query (TSQR_SUCCESS or TSQR_STATUS_NONFINITE) and clears it.  TSQR_ERR_CUDA if the
+ * stream reports an error. */
+tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream);
+
+/* Frees every workspace the library holds (all devices and streams) after synchronizing
+ * the devices it used.  Safe to call at any time no call is in flight. */
+void tsqr_release_workspace(void);
+
+/* Static description of a status code. */
+const char *tsqr_status_string(int32_t status);
+
+/* The plan AUTO (or `plan`) resolves to for an (m, n, dtype, prec) problem on the current
+ * device, written to *out.  Host only; enqueues nothing. */
+tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t prec,
+                                const tsqr_plan_t *plan, tsqr_plan_t *out);
+
+/* Number of kernel launches the last successful call on this host thread enqueued. */
+int32_t tsqr_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBTSQR_TSQR_H */

@@ -1,0 +1,217 @@
+"""libtsqr: the R factor of A = QR for tall-and-skinny matrices on one GB300 (sm_103a).
+
+A thin ctypes binding of the C ABI in ``include/tsqr.h``.  Every function marshals arguments
+and calls the library; all computation runs in libtsqr's CUDA kernels.  There is no CPU
+fallback: the first call raises ImportError if ``_build/libtsqr.so`` is missing (build it
+with ``__graft_entry__.build()`` or ``python paper_1002_4250_gb300/_build.py``).
+
+Two layers:
+
+* ``capi`` -- the C functions themselves (``capi.tsqr_r(A_ptr, m, n, lda, R_ptr, ldr, stream)``
+  and so on), taking raw device pointers and sizes;
+* functions of the same names taking torch CUDA tensors: a column-major m x n matrix is a
+  tensor of logical shape (m, n) with strides (1, lda) -- e.g. ``At.T`` for a contiguous
+  (n, m) tensor ``At`` -- and R comes back as a logical (n, n) FP64 tensor with column-major
+  storage.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsqr.so")
+
+SUCCESS, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, STATUS_NONFINITE = range(7)
+F64, F32, BF16 = 0, 1, 2
+PREC_F64, PREC_MIXED = 0, 1
+TREE_AUTO, TREE_BINARY, TREE_FLAT, TREE_HYBRID = 0, 1, 2, 3
+MAX_N = 128
+_TREES = {"auto": TREE_AUTO, "binary": TREE_BINARY, "flat": TREE_FLAT, "hybrid": TREE_HYBRID}
+
+
+class Plan(ctypes.Structure):
+    """tsqr_plan_t: tree, tile_rows, ctas, warps (zeros mean "choose")."""
+    _fields_ = [("tree", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("ctas", ctypes.c_int32), ("warps", ctypes.c_int32)]
+
+
+_capi = None
+
+
+def _load():
+    """Load and bind libtsqr.so.  Raises ImportError when the library has not been built:
+    there is no CPU fallback."""
+    global _capi
+    if _capi is not None:
+        return _capi
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libtsqr is not built ({LIB_PATH} missing); run `python -c \"import __graft_entry__ "
+            "as g; g.build()\"` -- there is no CPU fallback")
+    capi = ctypes.CDLL(LIB_PATH)
+    _p, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    capi.tsqr_r.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
+    capi.tsqr_r.restype = _i32
+    capi.tsqr_r_ex.argtypes = [_p, _i32, _i32, _i64, _i64, _i64, _p, _i64, ctypes.POINTER(Plan), _p]
+    capi.tsqr_r_ex.restype = _i32
+    capi.tsqr_qr_uppers.argtypes = [_i64, _p, _i64, _p, _i64, _p, _i64, _i32, _p]
+    capi.tsqr_qr_uppers.restype = _i32
+    capi.tsqr_r_batched.argtypes = [ctypes.POINTER(_p), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_i64), _i32, _p, _i32, _i32, _p]
+    capi.tsqr_r_batched.restype = _i32
+    capi.tsqr_get_device_status.argtypes = [_p]
+    capi.tsqr_get_device_status.restype = _i32
+    capi.tsqr_release_workspace.argtypes = []
+    capi.tsqr_release_workspace.restype = None
+    capi.tsqr_status_string.argtypes = [_i32]
+    capi.tsqr_status_string.restype = ctypes.c_char_p
+    capi.tsqr_resolve_plan.argtypes = [_i64, _i64, _i32, _i32, ctypes.POINTER(Plan), ctypes.POINTER(Plan)]
+    capi.tsqr_resolve_plan.restype = _i32
+    capi.tsqr_last_launch_count.argtypes = []
+    capi.tsqr_last_launch_count.restype = _i32
+
+    _capi = capi
+    return capi
+
+
+def __getattr__(name):
+    if name == "capi":
+        return _load()
+    raise AttributeError(name)
+
+
+#: every symbol include/tsqr.h declares
+ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
+               "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
+               "tsqr_last_launch_count")
+
+
+class TsqrError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        msg = _load().tsqr_status_string(int(status)).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else msg)
+
+
+def check(status: int, what: str = "") -> None:
+    if status != SUCCESS:
+        raise TsqrError(status, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor_dims(A, what="A"):
+    """(m, n, lda) of a logical (m, n) CUDA tensor stored column-major (strides (1, lda))."""
+    if A.dim() != 2 or not A.is_cuda:
+        raise ValueError(f"{what} must be a 2-D CUDA tensor")
+    m, n = A.shape
+    s0, s1 = A.stride()
+    if n > 1 and m > 1 and s0 != 1:
+        raise ValueError(f"{what} must be column-major (strides (1, lda)); got strides {A.stride()}")
+    lda = s1 if n > 1 else max(m, 1)
+    return m, n, max(lda, m, 1)
+
+
+def colmajor(A):
+    """Column-major copy of a logical (m, n) tensor (for callers holding row-major data)."""
+    return A.T.contiguous().T
+
+
+def empty_r(n: int, device=None):
+    """A logical (n, n) FP64 tensor with column-major storage, for R."""
+    import torch
+    return torch.empty((n, n), dtype=torch.float64, device=device).T
+
+
+def make_plan(tree="auto", tile_rows=0, ctas=0, warps=0) -> Plan:
+    return Plan(_TREES[tree] if isinstance(tree, str) else int(tree), int(tile_rows), int(ctas),
+                int(warps))
+
+
+def tsqr_r(A, R=None, stream=None):
+    """R factor (logical (n, n), diag >= 0) of the column-major FP64 CUDA tensor A (m, n)."""
+    import torch
+    if A.dtype != torch.float64:
+        raise ValueError("tsqr_r takes FP64 input; use tsqr_r_ex for FP32/BF16")
+    m, n, lda = _colmajor_dims(A)
+    if R is None:
+        R = empty_r(n, A.device)
+    check(_load().tsqr_r(A.data_ptr(), m, n, lda, R.data_ptr(), max(R.stride(1), n, 1),
+                      _stream_ptr(stream)), "tsqr_r")
+    return R
+
+
+_DT = {}
+
+
+def _dtype_code(t):
+    import torch
+    if not _DT:
+        _DT.update({torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16})
+    if t not in _DT:
+        raise ValueError(f"unsupported dtype {t}")
+    return _DT[t]
+
+
+def tsqr_r_ex(A, prec=None, plan: Plan | None = None, R=None, stream=None):
+    """tsqr_r for FP64 / FP32 / BF16 input with an optional plan (see ``make_plan``)."""
+    m, n, lda = _colmajor_dims(A)
+    dt = _dtype_code(A.dtype)
+    if prec is None:
+        prec = PREC_F64 if dt == F64 else PREC_MIXED
+    if R is None:
+        R = empty_r(n, A.device)
+    pp = ctypes.byref(plan) if plan is not None else None
+    check(_load().tsqr_r_ex(A.data_ptr(), dt, int(prec), m, n, lda, R.data_ptr(),
+                         max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_r_ex")
+    return R
+
+
+def tsqr_qr_uppers(R1, R2, normalize=False, R=None, stream=None):
+    """The tree operator qr(R1, R2) (Table 3) on two logical (n, n) column-major FP64 tensors."""
+    n = R1.shape[0]
+    _, _, ld1 = _colmajor_dims(R1, "R1")
+    _, _, ld2 = _colmajor_dims(R2, "R2")
+    if R is None:
+        R = empty_r(n, R1.device)
+    check(_load().tsqr_qr_uppers(n, R1.data_ptr(), ld1, R2.data_ptr(), ld2, R.data_ptr(),
+                              max(R.stride(1), n, 1), 1 if normalize else 0, _stream_ptr(stream)),
+          "tsqr_qr_uppers")
+    return R
+
+
+def tsqr_r_batched(ptrs, ms, ns, offsets, R_packed, dtype=F64, prec=PREC_F64, stream=None):
+    """Varlen batch through one launch; ptrs/ms/ns/offsets are host sequences (see tsqr.h)."""
+    count = len(ms)
+    P = (ctypes.c_void_p * max(count, 1))(*[int(p) for p in ptrs])
+    M = (ctypes.c_int64 * max(count, 1))(*[int(x) for x in ms])
+    N = (ctypes.c_int32 * max(count, 1))(*[int(x) for x in ns])
+    O = (ctypes.c_int64 * (count + 1))(*[int(x) for x in offsets])
+    check(_load().tsqr_r_batched(P, M, N, O, count, R_packed.data_ptr(), int(dtype), int(prec),
+                              _stream_ptr(stream)), "tsqr_r_batched")
+    return R_packed
+
+
+def tsqr_get_device_status(stream=None) -> int:
+    return int(_load().tsqr_get_device_status(_stream_ptr(stream)))
+
+
+def tsqr_release_workspace() -> None:
+    _load().tsqr_release_workspace()
+
+
+def tsqr_resolve_plan(m, n, dtype=F64, prec=PREC_F64, plan: Plan | None = None) -> Plan:
+    out = Plan()
+    check(_load().tsqr_resolve_plan(int(m), int(n), int(dtype), int(prec),
+                                 ctypes.byref(plan) if plan is not None else None,
+                                 ctypes.byref(out)), "tsqr_resolve_plan")
+    return out
+
+
+def tsqr_last_launch_count() -> int:
+    return int(_load().tsqr_last_launch_count())

@@ -1,0 +1,347 @@
+// The C ABI of libtsqr (include/tsqr.h): argument checks, plan selection, workspace and
+// launches.  Every step of the computation runs in the kernels; this file only plans and
+// enqueues.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "tsqr.h"
+#include "tsqr_internal.h"
+
+using namespace tsqr;
+
+namespace {
+
+thread_local int g_last_launches = 0;
+
+struct Workspace {
+    void *base = nullptr;   // counters + slots (grown on demand)
+    size_t bytes = 0;
+    int *status = nullptr;  // device status word (lives as long as the workspace entry)
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+struct DeviceInfo {
+    int sms = 0;
+    size_t smem_block_optin = 0;
+    size_t smem_sm = 0;
+};
+
+DeviceInfo device_info(int dev) {
+    static std::mutex mu;
+    static std::map<int, DeviceInfo> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    DeviceInfo d;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) d.sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+        d.smem_block_optin = (size_t)v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess)
+        d.smem_sm = (size_t)v;
+    cache[dev] = d;
+    return d;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct F64Plan {
+    int tree = TSQR_TREE_HYBRID;
+    int warps = 4;
+    int h = 0, hs = 0, ldS = 0;
+    int64_t nslabs = 0;
+    int nleaves = 0;
+    size_t smem = 0;
+    TreeShape shape{};
+    int64_t nodes = 0;
+};
+
+tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
+    std::memset(t, 0, sizeof(*t));
+    int64_t c = leaves, off = 0;
+    int l = 0;
+    for (;;) {
+        if (l >= kMaxLevels) return TSQR_ERR_UNSUPPORTED;
+        t->count[l] = (int)c;
+        t->offset[l] = (int)off;
+        off += c;
+        ++l;
+        if (c == 1) break;
+        c = (c + 1) / 2;
+    }
+    t->levels = l;
+    *nodes = off;
+    return TSQR_SUCCESS;
+}
+
+int ld_for(int hs) { return (hs % 2 == 0) ? hs + 1 : hs; }
+
+// Largest slab height (a multiple of `warps`, >= n) whose shared memory fits `budget` bytes.
+int max_slab_rows(int n, int warps, size_t budget) {
+    int lo = 0;
+    for (int hs = warps * (int)((n + warps - 1) / warps); hs <= 1 << 16; hs += warps) {
+        if (f64_smem_bytes(n, hs, ld_for(hs), warps) > budget) break;
+        lo = hs;
+    }
+    return lo;
+}
+
+tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    if (di.sms <= 0) return TSQR_ERR_CUDA;
+    p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
+    if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
+    p->warps = (n <= 64) ? 4 : 8;
+    if (over && over->warps) {
+        if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
+        p->warps = over->warps;
+    }
+    const int W = p->warps;
+    const size_t reserve = 1024;
+    const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
+    const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
+    if (over && over->tile_rows < 0) return TSQR_ERR_INVALID_ARG;
+    const int64_t mm = std::max<int64_t>(m, 1);
+    if (p->tree == TSQR_TREE_BINARY || (over && over->tile_rows > 0)) {
+        const int64_t b = (over && over->tile_rows > 0) ? over->tile_rows : 256;
+        if (b > (1 << 16)) return TSQR_ERR_UNSUPPORTED;
+        p->h = (int)b;
+        p->hs = (int)round_up(std::max<int64_t>(b, n), W);
+    } else {
+        int hs = max_slab_rows(n, W, two_per_sm);
+        if (hs < n) hs = max_slab_rows(n, W, one_per_sm);
+        if (hs < n) return TSQR_ERR_UNSUPPORTED;
+        // a slab taller than the matrix only multiplies zeros
+        hs = (int)std::min<int64_t>(hs, round_up(std::max<int64_t>(mm, n), W));
+        p->h = hs;
+        p->hs = hs;
+    }
+    p->ldS = ld_for(p->hs);
+    p->smem = f64_smem_bytes(n, p->hs, p->ldS, W);
+    if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
+    p->nslabs = (mm + p->h - 1) / p->h;
+    int64_t leaves;
+    if (p->tree == TSQR_TREE_FLAT) {
+        leaves = 1;
+    } else if (p->tree == TSQR_TREE_BINARY) {
+        leaves = p->nslabs;
+    } else {
+        if (over && over->ctas < 0) return TSQR_ERR_INVALID_ARG;
+        if (over && over->ctas > 0) {
+            leaves = over->ctas;
+        } else {
+            if (f64_prepare(p->smem) != cudaSuccess) return TSQR_ERR_CUDA;
+            const int per_sm = std::max(1, f64_blocks_per_sm(W, p->smem));
+            leaves = (int64_t)di.sms * per_sm;
+        }
+        leaves = std::min<int64_t>(leaves, p->nslabs);
+    }
+    if (leaves < 1 || leaves > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
+    p->nleaves = (int)leaves;
+    return build_tree(leaves, &p->shape, &p->nodes);
+}
+
+// Workspace for (current device, stream): at least `bytes` bytes plus a status word.
+tsqr_status_t get_workspace(cudaStream_t stream, size_t bytes, Workspace **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace &w = g_ws[{dev, stream}];
+    if (!w.status) {
+        if (cudaMallocAsync((void **)&w.status, 256, stream) != cudaSuccess) return TSQR_ERR_ALLOC;
+        if (cudaMemsetAsync(w.status, 0, sizeof(int), stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    }
+    if (bytes > w.bytes) {
+        if (w.base) cudaFreeAsync(w.base, stream);
+        w.base = nullptr;
+        w.bytes = 0;
+        const size_t nb = align_up(bytes, 1 << 20);
+        if (cudaMallocAsync(&w.base, nb, stream) != cudaSuccess) return TSQR_ERR_ALLOC;
+        w.bytes = nb;
+    }
+    *out = &w;
+    return TSQR_SUCCESS;
+}
+
+tsqr_status_t zero_r(double *R, int64_t n, int64_t ldr, cudaStream_t stream) {
+    if (cudaMemset2DAsync(R, (size_t)ldr * sizeof(double), 0, (size_t)n * sizeof(double),
+                          (size_t)n, stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    return TSQR_SUCCESS;
+}
+
+tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
+                      const tsqr_plan_t *over, cudaStream_t stream) {
+    g_last_launches = 0;
+    if (n == 0) return TSQR_SUCCESS;
+    if (m == 0) return zero_r(R, n, ldr, stream);
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, over, &p);
+    if (st != TSQR_SUCCESS) return st;
+    if (f64_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = (size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, cnt_bytes + slot_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    F64Args a;
+    a.A = A;
+    a.m = m;
+    a.lda = lda;
+    a.n = (int)n;
+    a.h = p.h;
+    a.hs = p.hs;
+    a.ldS = p.ldS;
+    a.nslabs = p.nslabs;
+    a.nleaves = p.nleaves;
+    a.tree = p.shape;
+    a.counters = (unsigned int *)ws->base;
+    a.slots = (double *)((char *)ws->base + cnt_bytes);
+    a.R = R;
+    a.ldr = ldr;
+    a.status = ws->status;
+    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (f64_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    g_last_launches = 1;
+    return TSQR_SUCCESS;
+}
+
+bool bad_dims(int64_t m, int64_t n, int64_t lda, int64_t ldr) {
+    return m < 0 || n < 0 || lda < std::max<int64_t>(1, m) || ldr < std::max<int64_t>(1, n);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tsqr_status_string(int32_t s) {
+    switch (s) {
+        case TSQR_SUCCESS: return "success";
+        case TSQR_ERR_INVALID_ARG: return "invalid argument";
+        case TSQR_ERR_UNSUPPORTED: return "unsupported size or configuration";
+        case TSQR_ERR_CUDA: return "CUDA runtime error";
+        case TSQR_ERR_ALLOC: return "workspace allocation failed";
+        case TSQR_ERR_TIMEOUT: return "bounded device wait timed out";
+        case TSQR_STATUS_NONFINITE: return "R holds NaN or Inf";
+        default: return "unknown status";
+    }
+}
+
+int32_t tsqr_last_launch_count(void) { return g_last_launches; }
+
+tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
+                     tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
+    return run_f64(A, m, n, lda, R, ldr, nullptr, (cudaStream_t)stream);
+}
+
+tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
+                        int64_t lda, double *R, int64_t ldr, const tsqr_plan_t *plan,
+                        tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
+    if (dtype < TSQR_F64 || dtype > TSQR_BF16 || prec < TSQR_PREC_F64 || prec > TSQR_PREC_MIXED)
+        return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
+    if (dtype == TSQR_F64 && prec == TSQR_PREC_F64)
+        return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
+    if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
+    return TSQR_ERR_UNSUPPORTED;
+}
+
+tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const double *R2,
+                             int64_t ld2, double *R, int64_t ldr, int32_t normalize,
+                             tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (n < 0 || ld1 < std::max<int64_t>(1, n) || ld2 < std::max<int64_t>(1, n) ||
+        ldr < std::max<int64_t>(1, n))
+        return TSQR_ERR_INVALID_ARG;
+    if (n == 0) return TSQR_SUCCESS;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (!R1 || !R2 || !R) return TSQR_ERR_INVALID_ARG;
+    const int W = (n <= 64) ? 4 : 8;
+    const int hs = (int)round_up(n, W);
+    const int ldS = ld_for(hs);
+    const size_t smem = f64_smem_bytes((int)n, hs, ldS, W);
+    if (f64_prepare(smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    Workspace *ws = nullptr;
+    tsqr_status_t st = get_workspace((cudaStream_t)stream, 0, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    if (f64_combine_launch((int)n, R1, ld1, R2, ld2, R, ldr, normalize ? 1 : 0, W, ldS, hs, smem,
+                           ws->status, (cudaStream_t)stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    g_last_launches = 1;
+    return TSQR_SUCCESS;
+}
+
+tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                             const int64_t *offsets, int32_t count, double *R_packed,
+                             int32_t dtype, int32_t prec, tsqr_stream_t stream) {
+    g_last_launches = 0;
+    (void)ptrs; (void)ms; (void)ns; (void)offsets; (void)R_packed; (void)dtype; (void)prec;
+    (void)stream;
+    if (count < 0) return TSQR_ERR_INVALID_ARG;
+    if (count == 0) return TSQR_SUCCESS;
+    return TSQR_ERR_UNSUPPORTED;
+}
+
+tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TSQR_ERR_CUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    int flags = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find({dev, s});
+        if (it == g_ws.end() || !it->second.status) return TSQR_SUCCESS;
+        if (cudaMemcpy(&flags, it->second.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        if (cudaMemset(it->second.status, 0, sizeof(int)) != cudaSuccess) return TSQR_ERR_CUDA;
+    }
+    return (flags & kStatusNonfiniteBit) ? TSQR_STATUS_NONFINITE : TSQR_SUCCESS;
+}
+
+void tsqr_release_workspace(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_ws) {
+        cudaSetDevice(kv.first.first);
+        cudaDeviceSynchronize();
+        if (kv.second.base) cudaFree(kv.second.base);
+        if (kv.second.status) cudaFree(kv.second.status);
+    }
+    g_ws.clear();
+    cudaSetDevice(cur);
+}
+
+tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t prec,
+                                const tsqr_plan_t *plan, tsqr_plan_t *out) {
+    if (!out || m < 0 || n < 1) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (dtype != TSQR_F64 || prec != TSQR_PREC_F64) return TSQR_ERR_UNSUPPORTED;
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, plan, &p);
+    if (st != TSQR_SUCCESS) return st;
+    out->tree = p.tree;
+    out->tile_rows = p.h;
+    out->ctas = p.nleaves;
+    out->warps = p.warps;
+    return TSQR_SUCCESS;
+}
+
+}  // extern "C"

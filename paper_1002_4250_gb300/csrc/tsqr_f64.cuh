@@ -1,0 +1,75 @@
+// FP64 TSQR device code: the shared-memory fold R <- R([R; S]) that serves both as the leaf
+// (S = a row slab of A, Section 2 step 1 fused with a flat tree, Section 1) and as the tree
+// operator qr(R1, R2) (S = R2, an upper triangle; Section 2, Table 3), plus the cross-CTA
+// binary reduction tree (Fig. 1) with the "last child to arrive combines" rule.
+//
+// Cost model this is written for (measured on GB300): one warp-wide FP64 instruction occupies a
+// sub-partition's FP64 unit for ~64 cycles whether 1 or 32 lanes are active, FP64 latency is
+// ~65 cycles, sqrt ~620 and divide ~375 cycles; everything that is not FP64 (shared-memory
+// traffic, integer work, shuffles, barriers) is nearly free by comparison.  Hence:
+//   * the bulk pass spreads its (row, column) items evenly over all 32 lanes, whatever the
+//     shrinking width of the trailing triangle, and fuses the update by reflector j with the
+//     dot products for reflector j+1 (one sweep, two FMAs per item);
+//   * partial dot products are summed along fixed, index-determined orders (bit-reproducible);
+//   * the per-column scalar work (norm, sqrt, divides) is done once per CTA by one warp.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsqr {
+
+constexpr int kMaxN = 128;
+constexpr int kMaxLevels = 48;
+constexpr int kSegStride = 32 + kMaxN;  // segment slots per warp (lanes + column boundaries)
+
+// Binary reduction tree over `count[0]` leaves: level l has count[l] nodes; node t of level
+// l+1 has children 2t and 2t+1 of level l (an odd last child is promoted unchanged).  Node
+// (l, t) has the global id offset[l] + t.
+struct TreeShape {
+    int levels;
+    int count[kMaxLevels];
+    int offset[kMaxLevels];
+};
+
+struct F64Args {
+    const double *A;
+    int64_t m, lda;
+    int n;
+    int h;          // rows of a slab (tile) of A; a slab occupies rows [0, h) of S
+    int hs;         // rows of S in shared memory: >= max(h, n), a multiple of the warp count
+    int ldS;        // leading dimension of S in shared memory (doubles)
+    int64_t nslabs; // ceil(m / h)
+    int nleaves;    // CTAs of the leaf phase; leaf c folds slabs [c*nslabs/nleaves, ...)
+    TreeShape tree;
+    double *slots;          // one n x n column-major slot per tree node (workspace)
+    unsigned int *counters; // one arrival counter per tree node (workspace, zeroed per call)
+    double *R;              // output, column-major n x n, ld ldr
+    int64_t ldr;
+    int *status;            // device status word (TSQR_STATUS_NONFINITE is or-ed in)
+};
+
+// Shared-memory carve-up (offsets in doubles), identical on host and device.
+struct SmemLayout {
+    int S, Rp, f, seg, tot, npart, scal, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int warps) {
+    SmemLayout L;
+    int o = 0;
+    L.S = o;      o += ldS * n;
+    L.Rp = o;     o += n * (n + 1) / 2 + 1;
+    L.f = o;      o += n + 1;
+    L.seg = o;    o += warps * kSegStride;
+    L.tot = o;    o += kSegStride;
+    L.npart = o;  o += warps;
+    L.scal = o;   o += 4;
+    L.total = o;
+    (void)hs;
+    return L;
+}
+
+// Packed upper triangle, row-major: row j holds R(j, j..n-1) at rowoff(j).
+__host__ __device__ inline int rowoff(int n, int j) { return j * n - (j * (j - 1)) / 2; }
+
+}  // namespace tsqr

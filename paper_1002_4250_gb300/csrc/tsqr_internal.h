@@ -1,0 +1,24 @@
+// Declarations shared by the host API and the kernels of libtsqr (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tsqr_f64.cuh"
+
+namespace tsqr {
+
+constexpr int kStatusNonfiniteBit = 1;
+
+// FP64 path (tsqr_f64.cu)
+size_t f64_smem_bytes(int n, int hs, int ldS, int warps);
+cudaError_t f64_prepare(size_t smem_bytes);
+int f64_blocks_per_sm(int warps, size_t smem_bytes);
+cudaError_t f64_launch(const F64Args &a, int warps, size_t smem_bytes, cudaStream_t stream);
+cudaError_t f64_combine_launch(int n, const double *R1, int64_t ld1, const double *R2,
+                               int64_t ld2, double *R, int64_t ldr, int normalize, int warps,
+                               int ldS, int hs, size_t smem_bytes, int *status,
+                               cudaStream_t stream);
+
+}  // namespace tsqr

@@ -1,0 +1,204 @@
+"""GPU parity of libtsqr's FP64 path against the CPU oracle (element by element), through the
+C ABI.  Acceptance (FP64): ||R^T R - A^T A||_F / ||A||_F^2 <= 1e-13 and every entry within
+50 kappa(A) u ||R_oracle||_F of the oracle's R (the oracle is one unblocked Householder QR of
+all of A with diag(R) >= 0)."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_4250_gb300 as T
+    return T
+
+
+def _gpu(At):
+    """Logical column-major CUDA view of the (n, m) host storage At."""
+    return At.cuda().T
+
+
+def _to_np(R):
+    return R.detach().cpu().numpy()
+
+
+def _assert_parity(oracle, A_np, R_gpu, R_ref=None, gram_tol=1e-13, G=None, nthreads=8):
+    R = _to_np(R_gpu)
+    if R_ref is None:
+        R_ref = oracle.householder_r(A_np, nthreads=nthreads)
+    n = R.shape[0]
+    assert np.all(np.tril(R, -1) == 0), "strict lower triangle must be zero"
+    assert np.all(np.diag(R) >= 0), "diag(R) >= 0"
+    kap = oracle.kappa_from_r(R_ref) if n > 0 else 1.0
+    tol = 50 * kap * U * max(np.linalg.norm(R_ref), 1e-300)
+    np.testing.assert_allclose(R, R_ref, rtol=0, atol=tol)
+    res = oracle.gram_residual(A_np, R, G=G, nthreads=nthreads)
+    assert res <= gram_tol, f"gram residual {res:.3e}"
+    return res
+
+
+PLANS = [("binary", 256, 0), ("binary", 100, 0), ("flat", 0, 0), ("hybrid", 0, 0),
+         ("hybrid", 64, 5)]
+
+
+@pytest.mark.parametrize("tree,b,ctas", PLANS)
+@pytest.mark.parametrize("m,n", [(10000, 16), (2531, 1), (2531, 2), (1999, 3), (4097, 8),
+                                 (3001, 32), (1500, 64), (777, 128)])
+def test_parity_trees_and_widths(oracle, T, tree, b, ctas, m, n):
+    At = workloads.gaussian(m, n, seed=m + n)
+    A = oracle.from_torch_colmajor(At)
+    R = T.tsqr_r_ex(_gpu(At), plan=T.make_plan(tree, tile_rows=b, ctas=ctas))
+    _assert_parity(oracle, A, R)
+
+
+def test_config_small_binary_256(oracle, T):
+    """10,000 x 16, N(0,1) from seed 0, tiles 256 x 16, binary tree (40 tiles, the last of
+    16 rows); also equal to the oracle's own TSQR with the same tree."""
+    At = workloads.gaussian(10000, 16, seed=0)
+    A = oracle.from_torch_colmajor(At)
+    plan = T.make_plan("binary", tile_rows=256)
+    assert T.tsqr_resolve_plan(10000, 16, plan=plan).ctas == 40
+    R = T.tsqr_r_ex(_gpu(At), plan=plan)
+    _assert_parity(oracle, A, R)
+    Rt = oracle.tsqr_r(A, b=256, tree="binary")
+    kap = oracle.kappa_from_r(Rt)
+    assert oracle.rel_err(_to_np(R), Rt) <= 50 * kap * U
+
+
+@pytest.mark.parametrize("lda_pad", [0, 1, 3, 8])
+def test_leading_dimension(oracle, T, lda_pad):
+    import torch
+    m, n = 3333, 12
+    At = workloads.gaussian(m, n, seed=5)
+    big = torch.zeros(n, m + lda_pad, dtype=torch.float64)
+    big[:, :m] = At
+    Ag = big.cuda().T[:m, :]          # strides (1, m + lda_pad)
+    assert Ag.stride() == (1, m + lda_pad)
+    R = T.tsqr_r(Ag)
+    _assert_parity(oracle, oracle.from_torch_colmajor(At), R)
+
+
+def test_output_leading_dimension(oracle, T):
+    import torch
+    m, n = 2000, 10
+    At = workloads.gaussian(m, n, seed=6)
+    Rbig = torch.full((n, 17), 7.0, dtype=torch.float64, device="cuda")  # ldr = 17
+    Rv = Rbig.T[:n, :]
+    T.tsqr_r(_gpu(At), R=Rv)
+    torch.cuda.synchronize()
+    _assert_parity(oracle, oracle.from_torch_colmajor(At), Rv)
+    assert torch.all(Rbig.T[n:, :] == 7.0), "rows beyond n of the ldr padding must be untouched"
+
+
+@pytest.mark.parametrize("m,n", [(0, 5), (1, 1), (1, 6), (3, 7), (7, 7), (8, 7)])
+def test_tiny_and_wide(oracle, T, m, n):
+    import torch
+    if m == 0:
+        Ag = torch.zeros(n, 1, dtype=torch.float64, device="cuda").T[:0, :]
+        assert np.all(_to_np(T.tsqr_r(Ag)) == 0)
+        return
+    At = workloads.gaussian(m, n, seed=9)
+    Ro = oracle.householder_r(oracle.from_torch_colmajor(At))
+    Rn = _to_np(T.tsqr_r(_gpu(At)))
+    np.testing.assert_allclose(Rn, Ro, rtol=0, atol=1e-13 * max(1.0, np.abs(Ro).max()))
+
+
+def test_planted_r0_and_conditioning(oracle, T):
+    """kappa = 1e8 conditioned input (G diag(sigma) V^T), 262,144 x 32."""
+    At = workloads.conditioned(262144, 32, 1e8, seed=0)
+    A = oracle.from_torch_colmajor(At)
+    R = T.tsqr_r(_gpu(At))
+    _assert_parity(oracle, A, R)
+
+
+def test_bit_reproducible(T):
+    import torch
+    At = workloads.gaussian(200000, 32, seed=1)
+    Ag = _gpu(At)
+    for tree in ("hybrid", "binary", "flat"):
+        p = T.make_plan(tree)
+        a = T.tsqr_r_ex(Ag, plan=p).clone()
+        b = T.tsqr_r_ex(Ag, plan=p).clone()
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), tree
+
+
+def test_tree_independence(T, oracle):
+    """Section 2: the tree changes neither the result (beyond rounding) nor its stability."""
+    At = workloads.gaussian(100000, 24, seed=2)
+    A = oracle.from_torch_colmajor(At)
+    Ro = oracle.householder_r(A, nthreads=8)
+    for plan in [("binary", 256, 0), ("binary", 1000, 0), ("flat", 0, 0), ("hybrid", 0, 0),
+                 ("hybrid", 128, 7)]:
+        R = T.tsqr_r_ex(_gpu(At), plan=T.make_plan(*plan))
+        _assert_parity(oracle, A, R, R_ref=Ro)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 16, 31, 32, 64, 100, 128])
+def test_operator_matches_oracle_raw(oracle, T, n):
+    """qr(R1, R2) on the GPU vs the oracle's operator, before any sign fix: both use the
+    same reflector sign rule, so the raw factors agree entry by entry."""
+    import torch
+    rng = np.random.default_rng(n)
+    R1 = np.triu(rng.standard_normal((n, n))) + np.diag(np.abs(rng.standard_normal(n)) + 1)
+    R2 = np.triu(rng.standard_normal((n, n)))
+    # entries below the diagonals must be ignored
+    R1g = torch.from_numpy(R1 + np.tril(np.full((n, n), 9.0), -1)).cuda().T.contiguous().T
+    R2g = torch.from_numpy(R2 + np.tril(np.full((n, n), -5.0), -1)).cuda().T.contiguous().T
+    Rg = _to_np(T.tsqr_qr_uppers(R1g, R2g, normalize=False))
+    Ro, _, _ = oracle.qr_uppers(R1, R2)
+    Ro = np.triu(Ro)
+    kap = np.linalg.cond(np.vstack([R1, R2]))
+    np.testing.assert_allclose(Rg, Ro, rtol=0, atol=50 * kap * U * np.linalg.norm(Ro))
+    Rn = _to_np(T.tsqr_qr_uppers(R1g, R2g, normalize=True))
+    np.testing.assert_allclose(Rn, oracle.sign_fix(Ro), rtol=0,
+                               atol=50 * kap * U * np.linalg.norm(Ro))
+
+
+def test_nonfinite_input_is_reported(T):
+    import torch
+    At = workloads.gaussian(5000, 8, seed=3)
+    At[3, 1234] = float("nan")
+    T.tsqr_get_device_status()  # clear
+    R = T.tsqr_r(_gpu(At))
+    assert T.tsqr_get_device_status() == T.STATUS_NONFINITE
+    assert torch.isnan(R).any()
+    R = T.tsqr_r(_gpu(workloads.gaussian(5000, 8, seed=3)))
+    assert T.tsqr_get_device_status() == T.SUCCESS
+
+
+def test_zero_and_rank_deficient(oracle, T):
+    import torch
+    m, n = 3000, 6
+    At = workloads.gaussian(m, n, seed=4)
+    At[2] = 0.0               # a zero column
+    At[4] = At[1] * 3.0       # a dependent column
+    A = oracle.from_torch_colmajor(At)
+    R = _to_np(T.tsqr_r(_gpu(At)))
+    # R is not unique past a zero pivot: check the invariant R^T R = A^T A instead
+    assert oracle.gram_residual(A, R) <= 1e-13
+    assert np.all(np.isfinite(R))
+    Z = torch.zeros(n, m, dtype=torch.float64)
+    assert np.all(_to_np(T.tsqr_r(_gpu(Z))) == 0)
+
+
+def test_launch_count(T):
+    T.tsqr_r(_gpu(workloads.gaussian(50000, 16, seed=7)))
+    assert T.tsqr_last_launch_count() == 1
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e8])
+def test_full_size_4m_x_32(oracle, T, kappa):
+    """The benchmark's workload at full size, in the launch configuration the bench times."""
+    m, n = 4194304, 32
+    At = workloads.gaussian(m, n, seed=0) if kappa == 1.0 else workloads.conditioned(m, n, kappa, seed=0)
+    A = oracle.from_torch_colmajor(At)
+    R = T.tsqr_r(_gpu(At))
+    _assert_parity(oracle, A, R, nthreads=16)
