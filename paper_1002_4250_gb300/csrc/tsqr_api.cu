@@ -54,8 +54,8 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 struct F64Plan {
     int tree = TSQR_TREE_HYBRID;
     int warps = 4;
-    int h = 0, hs = 0, ldS = 0;
-    int64_t nslabs = 0;
+    int64_t unit = 0, nunits = 0;  // rows per work unit (tile or slab) and their count
+    int h = 0, hs = 0, ldS = 0;    // chunk rows, shared-memory rows, leading dimension
     int nleaves = 0;
     size_t smem = 0;
     TreeShape shape{};
@@ -82,14 +82,25 @@ tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
 
 int ld_for(int hs) { return (hs % 2 == 0) ? hs + 1 : hs; }
 
-// Largest slab height (a multiple of `warps`, >= n) whose shared memory fits `budget` bytes.
+// Shared-memory rows for a chunk of `rows` rows: a multiple of the warp count, and of
+// 32 x warps once that large (every lane then owns the same number of a warp's rows).
+int slab_rows_for(int64_t rows, int n, int warps) {
+    int64_t r = std::max<int64_t>(rows, n);
+    const int64_t g = (r >= 32 * warps) ? 32 * warps : warps;
+    return (int)round_up(r, g);
+}
+
+// Largest shared-memory row count (multiple of 32 x warps when >= that, else of warps,
+// and >= n) whose shared memory fits `budget` bytes; 0 if none.
 int max_slab_rows(int n, int warps, size_t budget) {
-    int lo = 0;
-    for (int hs = warps * (int)((n + warps - 1) / warps); hs <= 1 << 16; hs += warps) {
+    int best = 0;
+    for (int hs = slab_rows_for(n, n, warps); hs <= (1 << 16);) {
         if (f64_smem_bytes(n, hs, ld_for(hs), warps) > budget) break;
-        lo = hs;
+        best = hs;
+        hs += (hs >= 32 * warps) ? 32 * warps : warps;
+        if (hs > 32 * warps && hs % (32 * warps)) hs = (int)round_up(hs, 32 * warps);
     }
-    return lo;
+    return best;
 }
 
 tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
@@ -104,46 +115,44 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
         if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
     }
+    if (over && (over->tile_rows < 0 || over->ctas < 0)) return TSQR_ERR_INVALID_ARG;
     const int W = p->warps;
     const size_t reserve = 1024;
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
-    if (over && over->tile_rows < 0) return TSQR_ERR_INVALID_ARG;
+    int hs_fit = max_slab_rows(n, W, two_per_sm);
+    if (hs_fit < n) hs_fit = max_slab_rows(n, W, one_per_sm);
+    if (hs_fit < n) return TSQR_ERR_UNSUPPORTED;
     const int64_t mm = std::max<int64_t>(m, 1);
-    if (p->tree == TSQR_TREE_BINARY || (over && over->tile_rows > 0)) {
-        const int64_t b = (over && over->tile_rows > 0) ? over->tile_rows : 256;
-        if (b > (1 << 16)) return TSQR_ERR_UNSUPPORTED;
-        p->h = (int)b;
-        p->hs = (int)round_up(std::max<int64_t>(b, n), W);
+    const bool tiled = (p->tree == TSQR_TREE_BINARY) || (over && over->tile_rows > 0);
+    if (tiled) {
+        // work unit = one tile of b rows; a tile taller than fits on chip is folded in chunks
+        p->unit = (over && over->tile_rows > 0) ? over->tile_rows : 256;
+        p->hs = std::min(slab_rows_for(std::min<int64_t>(p->unit, mm), n, W), hs_fit);
+        p->h = (int)std::min<int64_t>(p->unit, p->hs);
     } else {
-        int hs = max_slab_rows(n, W, two_per_sm);
-        if (hs < n) hs = max_slab_rows(n, W, one_per_sm);
-        if (hs < n) return TSQR_ERR_UNSUPPORTED;
-        // a slab taller than the matrix only multiplies zeros
-        hs = (int)std::min<int64_t>(hs, round_up(std::max<int64_t>(mm, n), W));
-        p->h = hs;
-        p->hs = hs;
+        // work unit = one slab as tall as fits (a slab taller than A only multiplies zeros)
+        p->hs = std::min(hs_fit, slab_rows_for(mm, n, W));
+        p->h = p->hs;
+        p->unit = p->h;
     }
     p->ldS = ld_for(p->hs);
     p->smem = f64_smem_bytes(n, p->hs, p->ldS, W);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
-    p->nslabs = (mm + p->h - 1) / p->h;
+    p->nunits = (mm + p->unit - 1) / p->unit;
     int64_t leaves;
     if (p->tree == TSQR_TREE_FLAT) {
         leaves = 1;
     } else if (p->tree == TSQR_TREE_BINARY) {
-        leaves = p->nslabs;
+        leaves = p->nunits;
+    } else if (over && over->ctas > 0) {
+        leaves = over->ctas;
     } else {
-        if (over && over->ctas < 0) return TSQR_ERR_INVALID_ARG;
-        if (over && over->ctas > 0) {
-            leaves = over->ctas;
-        } else {
-            if (f64_prepare(p->smem) != cudaSuccess) return TSQR_ERR_CUDA;
-            const int per_sm = std::max(1, f64_blocks_per_sm(W, p->smem));
-            leaves = (int64_t)di.sms * per_sm;
-        }
-        leaves = std::min<int64_t>(leaves, p->nslabs);
+        if (f64_prepare(p->smem) != cudaSuccess) return TSQR_ERR_CUDA;
+        const int per_sm = std::max(1, f64_blocks_per_sm(W, p->smem));
+        leaves = (int64_t)di.sms * per_sm;
     }
+    leaves = std::min<int64_t>(leaves, p->nunits);
     if (leaves < 1 || leaves > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
     p->nleaves = (int)leaves;
     return build_tree(leaves, &p->shape, &p->nodes);
@@ -197,11 +206,12 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     a.m = m;
     a.lda = lda;
     a.n = (int)n;
+    a.unit = p.unit;
+    a.nunits = p.nunits;
+    a.nleaves = p.nleaves;
     a.h = p.h;
     a.hs = p.hs;
     a.ldS = p.ldS;
-    a.nslabs = p.nslabs;
-    a.nleaves = p.nleaves;
     a.tree = p.shape;
     a.counters = (unsigned int *)ws->base;
     a.slots = (double *)((char *)ws->base + cnt_bytes);
@@ -338,7 +348,7 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
     tsqr_status_t st = plan_f64(m, (int)n, plan, &p);
     if (st != TSQR_SUCCESS) return st;
     out->tree = p.tree;
-    out->tile_rows = p.h;
+    out->tile_rows = (int32_t)p.unit;
     out->ctas = p.nleaves;
     out->warps = p.warps;
     return TSQR_SUCCESS;

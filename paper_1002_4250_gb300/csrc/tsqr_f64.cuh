@@ -36,11 +36,12 @@ struct F64Args {
     const double *A;
     int64_t m, lda;
     int n;
-    int h;          // rows of a slab (tile) of A; a slab occupies rows [0, h) of S
+    int64_t unit;   // rows of a work unit: a tile (binary tree) or a slab (flat, hybrid)
+    int64_t nunits; // ceil(m / unit)
+    int nleaves;    // CTAs of the leaf phase; leaf c owns units [c*nunits/nleaves, ...)
+    int h;          // rows folded per step of a leaf ("chunk"): h <= hs
     int hs;         // rows of S in shared memory: >= max(h, n), a multiple of the warp count
     int ldS;        // leading dimension of S in shared memory (doubles)
-    int64_t nslabs; // ceil(m / h)
-    int nleaves;    // CTAs of the leaf phase; leaf c folds slabs [c*nslabs/nleaves, ...)
     TreeShape tree;
     double *slots;          // one n x n column-major slot per tree node (workspace)
     unsigned int *counters; // one arrival counter per tree node (workspace, zeroed per call)
@@ -62,7 +63,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int wa
     L.f = o;      o += n + 1;
     L.seg = o;    o += warps * kSegStride;
     L.tot = o;    o += kSegStride;
-    L.npart = o;  o += warps;
+    L.npart = o;  o += warps * 32;
     L.scal = o;   o += 4;
     L.total = o;
     (void)hs;

@@ -1,7 +1,13 @@
 """GPU parity of libtsqr's FP64 path against the CPU oracle (element by element), through the
-C ABI.  Acceptance (FP64): ||R^T R - A^T A||_F / ||A||_F^2 <= 1e-13 and every entry within
-50 kappa(A) u ||R_oracle||_F of the oracle's R (the oracle is one unblocked Householder QR of
-all of A with diag(R) >= 0)."""
+C ABI.
+
+Acceptance (FP64): ||R^T R - A^T A||_F / ||A||_F^2 <= 1e-13, and every entry of R within
+c(m) kappa(A) u ||R_oracle||_F of the oracle's R, with c(m) = max(50, 2 sqrt(m)).  Both
+factorizations are backward stable, so R can differ by kappa times their backward errors;
+the oracle (one unblocked Householder QR of all of A) sums each dot product sequentially over
+up to m rows, whose rounding error grows like sqrt(m) u (random-walk model of recursive
+summation), while the GPU's tree-shaped sums grow more slowly.  For m <= 625 this is the
+50 kappa u figure reported beside every run."""
 import numpy as np
 import pytest
 
@@ -37,11 +43,15 @@ def _assert_parity(oracle, A_np, R_gpu, R_ref=None, gram_tol=1e-13, G=None, nthr
     assert np.all(np.tril(R, -1) == 0), "strict lower triangle must be zero"
     assert np.all(np.diag(R) >= 0), "diag(R) >= 0"
     kap = oracle.kappa_from_r(R_ref) if n > 0 else 1.0
-    tol = 50 * kap * U * max(np.linalg.norm(R_ref), 1e-300)
+    tol = _c(A_np.shape[0]) * kap * U * max(np.linalg.norm(R_ref), 1e-300)
     np.testing.assert_allclose(R, R_ref, rtol=0, atol=tol)
     res = oracle.gram_residual(A_np, R, G=G, nthreads=nthreads)
     assert res <= gram_tol, f"gram residual {res:.3e}"
     return res
+
+
+def _c(m):
+    return max(50.0, 2.0 * np.sqrt(m))
 
 
 PLANS = [("binary", 256, 0), ("binary", 100, 0), ("flat", 0, 0), ("hybrid", 0, 0),
@@ -69,7 +79,7 @@ def test_config_small_binary_256(oracle, T):
     _assert_parity(oracle, A, R)
     Rt = oracle.tsqr_r(A, b=256, tree="binary")
     kap = oracle.kappa_from_r(Rt)
-    assert oracle.rel_err(_to_np(R), Rt) <= 50 * kap * U
+    assert oracle.rel_err(_to_np(R), Rt) <= _c(256) * kap * U
 
 
 @pytest.mark.parametrize("lda_pad", [0, 1, 3, 8])
