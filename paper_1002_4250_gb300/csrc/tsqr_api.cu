@@ -56,6 +56,7 @@ struct F64Plan {
     int warps = 4;
     int64_t unit = 0, nunits = 0;  // rows per work unit (tile or slab) and their count
     int h = 0, hs = 0, ldS = 0;    // chunk rows, shared-memory rows, leading dimension
+    int blk = 1;                   // inner-loop block of the leaf fold
     int nleaves = 0;
     size_t smem = 0;
     TreeShape shape{};
@@ -82,23 +83,23 @@ tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
 
 int ld_for(int hs) { return (hs % 2 == 0) ? hs + 1 : hs; }
 
-// Shared-memory rows for a chunk of `rows` rows: a multiple of the warp count, and of
-// 32 x warps once that large (every lane then owns the same number of a warp's rows).
-int slab_rows_for(int64_t rows, int n, int warps) {
-    int64_t r = std::max<int64_t>(rows, n);
-    const int64_t g = (r >= 32 * warps) ? 32 * warps : warps;
-    return (int)round_up(r, g);
+
+// Rows per lane whose inner loop blocks well: a multiple of 4 or 3 when r >= 3.
+int good_r(int r) {
+    if (r < 3) return r;
+    while (r % 4 && r % 3) --r;
+    return r;
 }
 
-// Largest shared-memory row count (multiple of 32 x warps when >= that, else of warps,
-// and >= n) whose shared memory fits `budget` bytes; 0 if none.
-int max_slab_rows(int n, int warps, size_t budget) {
+int block_for(int r) { return (r % 4 == 0) ? 4 : (r % 3 == 0) ? 3 : (r % 2 == 0) ? 2 : 1; }
+
+// Largest r (rows per lane) whose shared memory, with hs = 32 r warps rows, fits `budget`.
+int max_rows_per_lane(int n, int warps, size_t budget) {
     int best = 0;
-    for (int hs = slab_rows_for(n, n, warps); hs <= (1 << 16);) {
+    for (int r = 1; r <= 256; ++r) {
+        const int hs = 32 * warps * r;
         if (f64_smem_bytes(n, hs, ld_for(hs), warps) > budget) break;
-        best = hs;
-        hs += (hs >= 32 * warps) ? 32 * warps : warps;
-        if (hs > 32 * warps && hs % (32 * warps)) hs = (int)round_up(hs, 32 * warps);
+        best = r;
     }
     return best;
 }
@@ -110,7 +111,7 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
-    p->warps = (n <= 64) ? 4 : 8;
+    p->warps = 4;
     if (over && over->warps) {
         if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
@@ -120,22 +121,31 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     const size_t reserve = 1024;
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
-    int hs_fit = max_slab_rows(n, W, two_per_sm);
-    if (hs_fit < n) hs_fit = max_slab_rows(n, W, one_per_sm);
-    if (hs_fit < n) return TSQR_ERR_UNSUPPORTED;
+    // two CTAs per SM hide each other's per-column serial work; take one per SM only when two
+    // would leave fewer than 2 rows per lane
+    int r_fit = max_rows_per_lane(n, W, two_per_sm);
+    if (r_fit < 2) r_fit = std::max(r_fit, max_rows_per_lane(n, W, one_per_sm));
+    if (r_fit < 1 || 32 * W * r_fit < n) return TSQR_ERR_UNSUPPORTED;
+    r_fit = good_r(r_fit);
     const int64_t mm = std::max<int64_t>(m, 1);
     const bool tiled = (p->tree == TSQR_TREE_BINARY) || (over && over->tile_rows > 0);
+    int r;
     if (tiled) {
         // work unit = one tile of b rows; a tile taller than fits on chip is folded in chunks
         p->unit = (over && over->tile_rows > 0) ? over->tile_rows : 256;
-        p->hs = std::min(slab_rows_for(std::min<int64_t>(p->unit, mm), n, W), hs_fit);
+        r = (int)std::min<int64_t>(r_fit, (std::max<int64_t>(std::min<int64_t>(p->unit, mm), n) +
+                                           32 * W - 1) / (32 * W));
+        p->hs = 32 * W * r;
         p->h = (int)std::min<int64_t>(p->unit, p->hs);
     } else {
         // work unit = one slab as tall as fits (a slab taller than A only multiplies zeros)
-        p->hs = std::min(hs_fit, slab_rows_for(mm, n, W));
+        r = (int)std::min<int64_t>(r_fit, (std::max<int64_t>(mm, n) + 32 * W - 1) / (32 * W));
+        p->hs = 32 * W * r;
         p->h = p->hs;
         p->unit = p->h;
     }
+    if (p->hs < n) return TSQR_ERR_UNSUPPORTED;
+    p->blk = block_for(r);
     p->ldS = ld_for(p->hs);
     p->smem = f64_smem_bytes(n, p->hs, p->ldS, W);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
@@ -211,6 +221,7 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     a.nleaves = p.nleaves;
     a.h = p.h;
     a.hs = p.hs;
+    a.blk = p.blk;
     a.ldS = p.ldS;
     a.tree = p.shape;
     a.counters = (unsigned int *)ws->base;

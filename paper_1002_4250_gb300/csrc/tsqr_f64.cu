@@ -41,8 +41,9 @@ __device__ __forceinline__ void prefetch_column(double *S, int ldS, int hs, cons
 //
 // Rp: the top block R, packed upper triangle (row J at rowoff(n, J)).
 // S : the bottom block, column-major with leading dimension ldS.
-//   kTri == false (leaf): S is a dense chunk of hs rows; warp w owns rows [w*hs/W, (w+1)*hs/W).
-//   kTri == true  (tree operator, Table 3): S is the upper triangle R2, so the support of
+//   leaf (fold_leaf): S is a dense chunk of hs rows; warp w owns rows [w*Hw, (w+1)*Hw),
+//     Hw = hs / W = 32 r.
+//   tree operator (fold_tri, Table 3): S is the upper triangle R2, so the support of
 //     reflector J in S is rows 0..J (the j+2-entry reflector of the paper's operator);
 //     the warps split the trailing columns instead of the rows.
 //
@@ -61,176 +62,267 @@ __device__ __forceinline__ void prefetch_column(double *S, int ldS, int hs, cons
 //   B  (per warp)   every other trailing column k > J gets reflector J-1 and, in the same
 //                   sweep, its partial dot product with column J.  The warp's (column, row)
 //                   items are cut into 32 equal contiguous runs in column-major order, one
-//                   per lane; a lane writes one partial per column its run touches into slot
-//                   (lane + column) -- slot ids are distinct and ordered along the items;
+//                   per lane, processed in lockstep; a lane writes one partial per column its
+//                   run touches into slot (lane + column) -- slot ids are distinct and
+//                   ordered along the items;
 //   barrier; warp 0 sums the partials in a fixed order, forms reflector J, updates row J of
 //   R and publishes f[k] for k > J; barrier.
-// In leaf mode, columns that are no longer read (J-2 at step J) receive the next chunk of
-// rows by cp.async while the fold goes on.
 // ------------------------------------------------------------------------------------------
-template <bool kTri>
-__device__ __forceinline__ void fold(double *__restrict__ S, const int ldS, const int hs,
-                                     double *__restrict__ Rp, double *__restrict__ f,
-                                     double *__restrict__ seg_all, double *__restrict__ tot,
-                                     double *__restrict__ npart, const int n,
-                                     const Prefetch pf) {
+
+// Warp 0's part of step J.  npart holds W x 32 per-lane partial squared norms; dk[kk] the
+// summed dot product of column J+1+kk with column J (written by the same warp).
+__device__ __forceinline__ void reflect(const int lane, const int W, const int n, const int J,
+                                        double *__restrict__ Rp, double *__restrict__ f,
+                                        const double *__restrict__ npart,
+                                        const double *__restrict__ dk) {
+    const int U = n - J - 1;
+    double v = npart[lane];
+    for (int w = 1; w < W; ++w) v += npart[w * 32 + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const double sig2 = __shfl_sync(0xffffffffu, v, 0);
+    const int ro = rowoff(n, J);
+    const double alpha = Rp[ro];
+    // identity reflector only for an exactly zero tail; NaN/Inf propagate into R
+    const bool ident = (sig2 == 0.0);
+    double beta = alpha, tau = 0.0, c = 0.0, ib = 0.0;
+    if (!ident) {
+        const double t = fma(alpha, alpha, sig2);
+        const double y = rsqrt(t);
+        const double r = t * y;
+        beta = (alpha >= 0.0) ? -r : r;
+        ib = (alpha >= 0.0) ? -y : y;
+        tau = fma(-alpha, ib, 1.0);
+        c = __drcp_rn(alpha - beta);
+    }
+    for (int kk = lane; kk < U; kk += 32) {
+        const int k = J + 1 + kk;
+        const double d = dk[kk];
+        const int idx = ro + 1 + kk;
+        if (ident) {
+            f[k] = 0.0;
+        } else {
+            const double rjk = Rp[idx];
+            const double wk = fma(c, d, rjk);
+            Rp[idx] = fma(-tau, wk, rjk);
+            f[k] = -wk * ib;
+        }
+    }
+    if (lane == 0) Rp[ro] = beta;
+}
+
+// Leaf fold.  Every lane owns r rows of its warp's block (Hw = 32 r) and a phase-B run of
+// U r items starting at item lane * U r; runs and column boundaries are multiples of r, so
+// blocks of B items (B divides r) never straddle a column: the inner loop has no per-item
+// bookkeeping and all lanes stay in lockstep.  The next chunk of rows streams into columns
+// no longer read (J-2 at step J) by cp.async.
+template <int B>
+__device__ __forceinline__ void fold_leaf(double *__restrict__ S, const int ldS, const int hs,
+                                          double *__restrict__ Rp, double *__restrict__ f,
+                                          double *__restrict__ seg_all, double *__restrict__ tot,
+                                          double *__restrict__ npart, const int n,
+                                          const Prefetch pf) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
     const int Hw = hs / W;
+    const int r = Hw >> 5;
+    const int r0 = warp * Hw;
     double *seg = seg_all + warp * kSegStride;
 
     for (int J = 0; J < n; ++J) {
-        if (!kTri && pf.src && J >= 2) prefetch_column(S, ldS, hs, pf, J - 2);
+        if (pf.src && J >= 2) prefetch_column(S, ldS, hs, pf, J - 2);
         const int U = n - J - 1;
-        double *SJ = S + (size_t)J * ldS;
-        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS;
-        int r0, cw, kc0, kc1;
-        if (kTri) {
-            r0 = 0;
-            cw = J + 1;
-            kc0 = (warp * U) / W;
-            kc1 = ((warp + 1) * U) / W;
-        } else {
-            r0 = warp * Hw;
-            cw = Hw;
-            kc0 = 0;
-            kc1 = U;
-        }
+        double *SJ = S + (size_t)J * ldS + r0;
+        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS + r0;
 
         // ---- A: column J gets reflector J-1; per-lane partial squared norm of column J
         double nacc = 0.0;
-        if (!kTri || warp == 0) {
-            if (J > 0) {
-                const double fJ = f[J];
-                for (int i = lane; i < cw; i += 32) {
-                    const double s = fma(-fJ, Sj[r0 + i], SJ[r0 + i]);
-                    SJ[r0 + i] = s;
-                    nacc = fma(s, s, nacc);
-                }
-            } else {
-                for (int i = lane; i < cw; i += 32) {
-                    const double s = SJ[r0 + i];
-                    nacc = fma(s, s, nacc);
-                }
+        if (J > 0) {
+            const double fJ = f[J];
+            for (int t = 0; t < r; ++t) {
+                const int i = lane + 32 * t;
+                const double s = fma(-fJ, Sj[i], SJ[i]);
+                SJ[i] = s;
+                nacc = fma(s, s, nacc);
+            }
+        } else {
+            for (int t = 0; t < r; ++t) {
+                const double s = SJ[lane + 32 * t];
+                nacc = fma(s, s, nacc);
             }
         }
         npart[warp * 32 + lane] = nacc;
         for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
-        if (kTri)
-            __syncthreads();
-        else
-            __syncwarp();
+        __syncwarp();
 
-        // ---- B: fused update by reflector J-1 and dots with column J, one column segment
-        //      of the lane's run at a time
+        // ---- B: fused update by reflector J-1 and dots with column J
+        if (U > 0) {
+            const int run = U * r;
+            const int p = lane * run;
+            int kk = p / Hw;
+            int i = p - kk * Hw;
+            double *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
+            double acc = 0.0;
+            if (J > 0) {
+                double fk = f[J + 1 + kk];
+                for (int blk = 0; blk < run; blk += B) {
+                    double x[B];
+#pragma unroll
+                    for (int q = 0; q < B; ++q) x[q] = fma(-fk, Sj[i + q], Sk[i + q]);
+#pragma unroll
+                    for (int q = 0; q < B; ++q) Sk[i + q] = x[q];
+#pragma unroll
+                    for (int q = 0; q < B; ++q) acc = fma(SJ[i + q], x[q], acc);
+                    i += B;
+                    if (i == Hw) {
+                        seg[lane + kk] = acc;
+                        acc = 0.0;
+                        i = 0;
+                        ++kk;
+                        Sk += ldS;
+                        fk = f[min(J + 1 + kk, n - 1)];
+                    }
+                }
+            } else {
+                for (int blk = 0; blk < run; blk += B) {
+#pragma unroll
+                    for (int q = 0; q < B; ++q) acc = fma(SJ[i + q], Sk[i + q], acc);
+                    i += B;
+                    if (i == Hw) {
+                        seg[lane + kk] = acc;
+                        acc = 0.0;
+                        i = 0;
+                        ++kk;
+                        Sk += ldS;
+                    }
+                }
+            }
+            if (i != 0) seg[lane + kk] = acc;
+        }
+        __syncthreads();
+
+        // ---- reducer
+        if (warp == 0) {
+            for (int id = lane; id < 32 + U; id += 32) {
+                double t = seg_all[id];
+                for (int w = 1; w < W; ++w) t += seg_all[w * kSegStride + id];
+                tot[id] = t;
+            }
+            __syncwarp();
+            const int Nw = U * Hw;
+            double *dk = tot + kSegStride;
+            for (int kk = lane; kk < U; kk += 32) {
+                const int la = (32 * (kk * Hw + 1) - 1) / Nw;
+                const int lb = (32 * (kk + 1) * Hw - 1) / Nw;
+                double d = tot[kk + la];
+                for (int l = la + 1; l <= lb; ++l) d += tot[kk + l];
+                dk[kk] = d;
+            }
+            __syncwarp();
+            reflect(lane, W, n, J, Rp, f, npart, dk);
+        }
+        __syncthreads();
+    }
+    if (pf.src) {
+        for (int col = n - 2; col < n; ++col)
+            if (col >= 0) prefetch_column(S, ldS, hs, pf, col);
+    }
+}
+
+// Tree-operator fold (Table 3): S = R2, reflector J's support in S is rows 0..J.  Warp 0
+// updates column J; the warps split the trailing columns, each lane taking an equal
+// contiguous run of the warp's (column, row) items in lockstep.
+__device__ __forceinline__ void fold_tri(double *__restrict__ S, const int ldS,
+                                         double *__restrict__ Rp, double *__restrict__ f,
+                                         double *__restrict__ seg_all,
+                                         double *__restrict__ npart, const int n) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    double *seg = seg_all + warp * kSegStride;
+
+    for (int J = 0; J < n; ++J) {
+        const int U = n - J - 1;
+        const int cw = J + 1;
+        double *SJ = S + (size_t)J * ldS;
+        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS;
+        const int kc0 = (warp * U) / W, kc1 = ((warp + 1) * U) / W;
+
+        double nacc = 0.0;
+        if (warp == 0) {
+            const double fJ = (J > 0) ? f[J] : 0.0;
+            for (int i = lane; i < cw; i += 32) {
+                double s = SJ[i];
+                if (J > 0) {
+                    s = fma(-fJ, Sj[i], s);
+                    SJ[i] = s;
+                }
+                nacc = fma(s, s, nacc);
+            }
+        }
+        npart[warp * 32 + lane] = nacc;
+        for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
+        __syncthreads();
+
         const int N = (kc1 - kc0) * cw;
         if (N > 0) {
             int p = (int)(((long long)lane * N) >> 5);
             const int pend = (int)(((long long)(lane + 1) * N) >> 5);
-            int kk = p / cw;
-            int i = p - kk * cw;
-            while (p < pend) {
-                const int len = min(cw - i, pend - p);
-                const int k = J + 1 + kc0 + kk;
-                // distinct columns of S: the three never overlap
-                double *__restrict__ Sk = S + (size_t)k * ldS + r0 + i;
-                const double *__restrict__ a = Sj + r0 + i;
-                const double *__restrict__ b = SJ + r0 + i;
+            if (p < pend) {
+                int kk = p / cw;
+                int i = p - kk * cw;
+                int k = J + 1 + kc0 + kk;
+                double *Sk = S + (size_t)k * ldS;
+                double fk = (J > 0) ? f[k] : 0.0;
                 double acc = 0.0;
-                if (J > 0) {
-                    const double fk = f[k];
-#pragma unroll 4
-                    for (int t = 0; t < len; ++t) {
-                        const double s = fma(-fk, a[t], Sk[t]);
-                        Sk[t] = s;
-                        acc = fma(b[t], s, acc);
+                for (;;) {
+                    double s = Sk[i];
+                    if (J > 0) {
+                        s = fma(-fk, Sj[i], s);
+                        Sk[i] = s;
                     }
-                } else {
-#pragma unroll 4
-                    for (int t = 0; t < len; ++t) acc = fma(b[t], Sk[t], acc);
+                    acc = fma(SJ[i], s, acc);
+                    if (++p == pend) break;
+                    if (++i == cw) {
+                        seg[lane + kk] = acc;
+                        acc = 0.0;
+                        i = 0;
+                        ++kk;
+                        ++k;
+                        Sk += ldS;
+                        fk = (J > 0) ? f[k] : 0.0;
+                    }
                 }
                 seg[lane + kk] = acc;
-                p += len;
-                i = 0;
-                ++kk;
             }
         }
         __syncthreads();
 
-        // ---- reducer: reflector J, row J of R, factors f[k] for k > J
         if (warp == 0) {
-            double v = npart[lane];
-            for (int w = 1; w < W; ++w) v += npart[w * 32 + lane];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            const double sig2 = __shfl_sync(0xffffffffu, v, 0);
-            if (!kTri && W > 1) {
-                for (int id = lane; id < 32 + U; id += 32) {
-                    double t = seg_all[id];
-                    for (int w = 1; w < W; ++w) t += seg_all[w * kSegStride + id];
-                    tot[id] = t;
-                }
-                __syncwarp();
-            }
-            const double *totp = (!kTri && W > 1) ? tot : seg_all;
-            const int ro = rowoff(n, J);
-            const double alpha = Rp[ro];
-            // identity reflector only for an exactly zero tail; NaN/Inf propagate into R
-            const bool ident = (sig2 == 0.0);
-            double beta = alpha, tau = 0.0, c = 0.0, ib = 0.0;
-            if (!ident) {
-                const double t = fma(alpha, alpha, sig2);
-                const double y = rsqrt(t);
-                const double r = t * y;
-                beta = (alpha >= 0.0) ? -r : r;
-                ib = (alpha >= 0.0) ? -y : y;
-                tau = fma(-alpha, ib, 1.0);
-                c = __drcp_rn(alpha - beta);
-            }
+            double *dk = seg_all + W * kSegStride + kSegStride;
             for (int kk = lane; kk < U; kk += 32) {
-                const int k = J + 1 + kk;
-                double d;
-                if (!kTri) {
-                    const int Nw = U * Hw;
-                    const int la = (32 * (kk * Hw + 1) - 1) / Nw;
-                    const int lb = (32 * (kk + 1) * Hw - 1) / Nw;
-                    d = totp[kk + la];
-                    for (int l = la + 1; l <= lb; ++l) d += totp[kk + l];
-                } else {
-                    d = 0.0;
-                    bool first = true;
-                    for (int w = 0; w < W; ++w) {
-                        const int a0 = (w * U) / W, a1 = ((w + 1) * U) / W;
-                        if (kk < a0 || kk >= a1) continue;
-                        const int rel = kk - a0;
-                        const int Nw = (a1 - a0) * (J + 1);
-                        const int la = (32 * (rel * (J + 1) + 1) - 1) / Nw;
-                        const int lb = (32 * (rel + 1) * (J + 1) - 1) / Nw;
-                        for (int l = la; l <= lb; ++l) {
-                            const double x = seg_all[w * kSegStride + rel + l];
-                            d = first ? x : d + x;
-                            first = false;
-                        }
+                double d = 0.0;
+                bool first = true;
+                for (int w = 0; w < W; ++w) {
+                    const int a0 = (w * U) / W, a1 = ((w + 1) * U) / W;
+                    if (kk < a0 || kk >= a1) continue;
+                    const int rel = kk - a0;
+                    const int Nw = (a1 - a0) * cw;
+                    const int la = (32 * (rel * cw + 1) - 1) / Nw;
+                    const int lb = (32 * (rel + 1) * cw - 1) / Nw;
+                    for (int l = la; l <= lb; ++l) {
+                        const double x = seg_all[w * kSegStride + rel + l];
+                        d = first ? x : d + x;
+                        first = false;
                     }
                 }
-                const int idx = ro + 1 + kk;
-                if (ident) {
-                    f[k] = 0.0;
-                } else {
-                    const double rjk = Rp[idx];
-                    const double wk = fma(c, d, rjk);
-                    Rp[idx] = fma(-tau, wk, rjk);
-                    f[k] = -wk * ib;
-                }
+                dk[kk] = d;
             }
-            if (lane == 0) Rp[ro] = beta;
+            __syncwarp();
+            reflect(lane, W, n, J, Rp, f, npart, dk);
         }
         __syncthreads();
-    }
-    if (!kTri && pf.src) {
-        for (int col = n - 2; col < n; ++col)
-            if (col >= 0) prefetch_column(S, ldS, hs, pf, col);
     }
 }
 
@@ -288,7 +380,7 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // combines [R_left; R_right] (left = lower index, always on top) and climbs on; the first
 // returns.  No CTA ever waits for another, and the operand order depends only on the indices.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) tsqr_f64_kernel(const F64Args a) {
+__global__ void __launch_bounds__(256, 1) tsqr_f64_kernel(const F64Args a) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n;
     const SmemLayout L = smem_layout(n, a.hs, a.ldS, blockDim.x >> 5);
@@ -328,7 +420,12 @@ __global__ void __launch_bounds__(256) tsqr_f64_kernel(const F64Args a) {
             next.src = a.A + r1;
             next.rows = (int)((rend - r1 < a.h) ? rend - r1 : a.h);
         }
-        fold<false>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next);
+        switch (a.blk) {
+            case 4: fold_leaf<4>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            case 3: fold_leaf<3>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            case 2: fold_leaf<2>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            default: fold_leaf<1>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+        }
         if (next.src) {
             cp_async_wait_all();
             __syncthreads();
@@ -370,14 +467,14 @@ __global__ void __launch_bounds__(256) tsqr_f64_kernel(const F64Args a) {
             load_tri_cg(other, n, n, S, a.ldS);
         }
         __syncthreads();
-        fold<true>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, Prefetch{nullptr, 0, 0});
+        fold_tri(S, a.ldS, Rp, f, seg, npart, n);
         ++level;
         t >>= 1;
     }
 }
 
 // One tree node: R = qr(R1, R2) (Table 3), optionally sign-normalized.
-__global__ void __launch_bounds__(256) tsqr_f64_combine_kernel(int n, const double *R1, int64_t ld1,
+__global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const double *R1, int64_t ld1,
                                                                const double *R2, int64_t ld2,
                                                                double *R, int64_t ldr,
                                                                int normalize, int ldS, int hs,
@@ -389,8 +486,7 @@ __global__ void __launch_bounds__(256) tsqr_f64_combine_kernel(int n, const doub
     load_packed_cg(R1, ld1, n, Rp);
     load_tri_cg(R2, ld2, n, S, ldS);
     __syncthreads();
-    fold<true>(S, ldS, hs, Rp, smem + L.f, smem + L.seg, smem + L.tot, smem + L.npart, n,
-               Prefetch{nullptr, 0, 0});
+    fold_tri(S, ldS, Rp, smem + L.f, smem + L.seg, smem + L.npart, n);
     if (normalize)
         store_normalized(Rp, n, R, ldr, status);
     else

@@ -40,7 +40,8 @@ struct F64Args {
     int64_t nunits; // ceil(m / unit)
     int nleaves;    // CTAs of the leaf phase; leaf c owns units [c*nunits/nleaves, ...)
     int h;          // rows folded per step of a leaf ("chunk"): h <= hs
-    int hs;         // rows of S in shared memory: >= max(h, n), a multiple of the warp count
+    int hs;         // rows of S in shared memory: >= max(h, n), a multiple of 32 x warps
+    int blk;        // rows per inner-loop block: divides hs / (32 x warps)
     int ldS;        // leading dimension of S in shared memory (doubles)
     TreeShape tree;
     double *slots;          // one n x n column-major slot per tree node (workspace)
@@ -62,7 +63,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int wa
     L.Rp = o;     o += n * (n + 1) / 2 + 1;
     L.f = o;      o += n + 1;
     L.seg = o;    o += warps * kSegStride;
-    L.tot = o;    o += kSegStride;
+    L.tot = o;    o += 2 * kSegStride;  // summed slots, then the per-column dot products
     L.npart = o;  o += warps * 32;
     L.scal = o;   o += 4;
     L.total = o;
