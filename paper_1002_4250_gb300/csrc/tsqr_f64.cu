@@ -65,11 +65,11 @@ __device__ __forceinline__ void prefetch_column(double *S, int ldS, int hs, cons
 //                   per lane, processed in lockstep; a lane writes one partial per column its
 //                   run touches into slot (lane + column) -- slot ids are distinct and
 //                   ordered along the items;
-//   barrier; warp 0 sums the partials in a fixed order, forms reflector J, updates row J of
-//   R and publishes f[k] for k > J; barrier.
+//   barrier; warp J mod W sums the partials in a fixed order, forms reflector J, updates row
+//   J of R and publishes f[k] for k > J; barrier.
 // ------------------------------------------------------------------------------------------
 
-// Warp 0's part of step J.  npart holds W x 32 per-lane partial squared norms; dk[kk] the
+// The reducer warp's part of step J.  npart holds W x 32 per-lane partial squared norms; dk[kk] the
 // summed dot product of column J+1+kk with column J (written by the same warp).
 __device__ __forceinline__ void reflect(const int lane, const int W, const int n, const int J,
                                         double *__restrict__ Rp, double *__restrict__ f,
@@ -202,8 +202,8 @@ __device__ __forceinline__ void fold_leaf(double *__restrict__ S, const int ldS,
         }
         __syncthreads();
 
-        // ---- reducer
-        if (warp == 0) {
+        // ---- reducer (warp J mod W: the serial FP64 work visits every sub-partition in turn)
+        if (warp == J % W) {
             for (int id = lane; id < 32 + U; id += 32) {
                 double t = seg_all[id];
                 for (int w = 1; w < W; ++w) t += seg_all[w * kSegStride + id];
@@ -299,7 +299,7 @@ __device__ __forceinline__ void fold_tri(double *__restrict__ S, const int ldS,
         }
         __syncthreads();
 
-        if (warp == 0) {
+        if (warp == J % W) {
             double *dk = seg_all + W * kSegStride + kSegStride;
             for (int kk = lane; kk < U; kk += 32) {
                 double d = 0.0;
