@@ -116,6 +116,30 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream);
 
+/* Size of the fixed device array tsqr_r_noalloc works in (16 MiB). */
+#define TSQR_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* tsqr_r for callers that cannot allocate device memory when they call: for example a serving
+ * loop that must not allocate after start-up, or a process whose framework has already
+ * reserved the device's memory for its own caching allocator.  The paper has no counterpart;
+ * this is a deployment variant of tsqr_r.
+ *   Same arguments, plan, kernel and result as tsqr_r (FP64, AUTO plan).  Instead of the
+ *   per-stream workspace it uses one static device array of TSQR_NOALLOC_SCRATCH_BYTES that
+ *   every GPU loading the library holds until the process exits.  It calls no cudaMalloc,
+ *   cudaFree or other allocating routine.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture on that device.
+ *   - All calls share the array and it keeps the last call's contents (each call clears the
+ *     part that must start at zero): calls that overlap on the GPU, on any streams, race and
+ *     must be serialized by the caller.
+ *   - A problem whose reduction tree needs more than the array (one n x n FP64 slot and one
+ *     counter per tree node; with the AUTO plan every n <= 80 fits, n = 128 does not)
+ *     returns TSQR_ERR_UNSUPPORTED before enqueuing anything.
+ *   - No device status is recorded: NaN/Inf still propagate into R, but
+ *     tsqr_get_device_status() does not report them for these calls.                       */
+tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                             int64_t ldr, tsqr_stream_t stream);
+
 /* Synchronizes `stream`, returns the device-side status recorded by the calls made on it since
  * the last query (TSQR_SUCCESS or TSQR_STATUS_NONFINITE) and clears it.  TSQR_ERR_CUDA if the
  * stream reports an error. */

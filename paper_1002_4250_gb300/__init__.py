@@ -68,6 +68,8 @@ def _load():
     capi.tsqr_status_string.restype = ctypes.c_char_p
     capi.tsqr_resolve_plan.argtypes = [_i64, _i64, _i32, _i32, ctypes.POINTER(Plan), ctypes.POINTER(Plan)]
     capi.tsqr_resolve_plan.restype = _i32
+    capi.tsqr_r_noalloc.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
+    capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
 
@@ -84,7 +86,7 @@ def __getattr__(name):
 #: every symbol include/tsqr.h declares
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
-               "tsqr_last_launch_count")
+               "tsqr_last_launch_count", "tsqr_r_noalloc")
 
 
 class TsqrError(RuntimeError):

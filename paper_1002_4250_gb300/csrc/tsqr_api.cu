@@ -242,6 +242,34 @@ bool bad_dims(int64_t m, int64_t n, int64_t lda, int64_t ldr) {
 
 }  // namespace
 
+namespace tsqr {
+
+// The AUTO plan of tsqr_r expressed as kernel arguments (A, R, workspace and status left for
+// the caller to fill), for entry points that bring their own workspace.
+tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,
+                            int64_t *nodes) {
+    F64Plan p;
+    const tsqr_status_t st = plan_f64(m, n, nullptr, &p);
+    if (st != TSQR_SUCCESS) return st;
+    std::memset(a, 0, sizeof(*a));
+    a->m = m;
+    a->n = n;
+    a->unit = p.unit;
+    a->nunits = p.nunits;
+    a->nleaves = p.nleaves;
+    a->h = p.h;
+    a->hs = p.hs;
+    a->blk = p.blk;
+    a->ldS = p.ldS;
+    a->tree = p.shape;
+    *warps = p.warps;
+    *smem = p.smem;
+    *nodes = p.nodes;
+    return TSQR_SUCCESS;
+}
+
+}  // namespace tsqr
+
 extern "C" {
 
 const char *tsqr_status_string(int32_t s) {

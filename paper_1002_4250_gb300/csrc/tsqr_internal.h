@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "tsqr.h"
 #include "tsqr_f64.cuh"
 
 namespace tsqr {
@@ -20,5 +21,10 @@ cudaError_t f64_combine_launch(int n, const double *R1, int64_t ld1, const doubl
                                int64_t ld2, double *R, int64_t ldr, int normalize, int warps,
                                int ldS, int hs, size_t smem_bytes, int *status,
                                cudaStream_t stream);
+
+// The AUTO plan of tsqr_r as kernel arguments (tsqr_api.cu); A, R, workspace and status
+// pointers are left for the caller.
+tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,
+                            int64_t *nodes);
 
 }  // namespace tsqr
