@@ -274,6 +274,10 @@ def bench_ours(args, world, rank, local):
         if tr.get("kernel_sha") == kernel_sha():
             roof["traffic"] = tr.get("bytes_per_launch")
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = bench_extras(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(At_cpu, os.cpu_count() or 1, R.cpu().numpy())
@@ -290,10 +294,52 @@ def bench_ours(args, world, rank, local):
                            "l2": "input 1 GiB per GPU > 129 MB L2; no flush"},
                 "a_read_gbs": world * bytes_a * args.steps / (ms / 1e3) / 1e9,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "cpu_baseline": cpu, "clocks": clk.summary(), "extras": extras,
                 "device_status": int(status)}
         print(json.dumps(line))
     return 0
+
+
+def time_call(fn, reps, warmup=2):
+    """Mean device time (ms) of fn() over reps calls, CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_extras(dev):
+    """The mixed-precision path against the FP64 path on the mixed workload's shape
+    (16,777,216 x 64, N(0,1)): GFLOP/s, A-read GB/s and the speedup factor."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    m, n = 1 << 24, 64
+    fl = flops(m, n)
+    out = {"workload": f"{m:,} x {n} N(0,1) seed 0 (generated on the GPU)"}
+    A64 = workloads.gaussian(m, n, seed=0, device=dev).T
+    R = T.empty_r(n, dev)
+    ms64 = time_call(lambda: T.tsqr_r(A64, R=R), reps=2, warmup=1)
+    out["fp64"] = {"ms": ms64, "gflops": fl / ms64 / 1e6, "frac_of_fp64_peak": fl / ms64 / 1e9 / peaks()["fp64_tflops"]}
+    for name, dt in (("mixed_fp32", torch.float32), ("mixed_bf16", torch.bfloat16)):
+        A = A64.T.to(dt).T
+        ms = time_call(lambda: T.tsqr_r_ex(A, R=R), reps=5)
+        bytes_a = A.element_size() * m * n
+        out[name] = {"ms": ms, "gflops": fl / ms / 1e6, "a_read_gbs": bytes_a / ms / 1e6,
+                     "a_read_frac_of_hbm": bytes_a / ms / 1e6 / peaks()["hbm_gbs"],
+                     "speedup_vs_fp64": ms64 / ms}
+        del A
+    del A64
+    torch.cuda.empty_cache()
+    return out
 
 
 def kernel_sha():
@@ -312,6 +358,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision vs FP64 comparison at 16,777,216 x 64")
     args = ap.parse_args()
     world, rank, local = dist_init() if args.impl == "ours" else (
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)

@@ -93,18 +93,29 @@ int good_r(int r) {
 
 int block_for(int r) { return (r % 4 == 0) ? 4 : (r % 3 == 0) ? 3 : (r % 2 == 0) ? 2 : 1; }
 
+// Plan for the FP64 path (mixed == false) or the mixed path (FP32 chunk in shared memory).
+tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p);
+
+tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    return plan_leaf(m, n, over, false, p);
+}
+
+size_t leaf_smem_bytes(int n, int hs, int warps, bool mixed) {
+    return mixed ? mixed_smem_bytes(n, ld_for(hs), warps)
+                 : f64_smem_bytes(n, hs, ld_for(hs), warps);
+}
+
 // Largest r (rows per lane) whose shared memory, with hs = 32 r warps rows, fits `budget`.
-int max_rows_per_lane(int n, int warps, size_t budget) {
+int max_rows_per_lane_p(int n, int warps, size_t budget, bool mixed) {
     int best = 0;
     for (int r = 1; r <= 256; ++r) {
-        const int hs = 32 * warps * r;
-        if (f64_smem_bytes(n, hs, ld_for(hs), warps) > budget) break;
+        if (leaf_smem_bytes(n, 32 * warps * r, warps, mixed) > budget) break;
         best = r;
     }
     return best;
 }
 
-tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
@@ -121,10 +132,18 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     const size_t reserve = 1024;
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
-    // two CTAs per SM hide each other's per-column serial work; take one per SM only when two
-    // would leave fewer than 2 rows per lane
-    int r_fit = max_rows_per_lane(n, W, two_per_sm);
-    if (r_fit < 2) r_fit = std::max(r_fit, max_rows_per_lane(n, W, one_per_sm));
+    int r_fit;
+    const int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
+    const int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
+    if (!mixed) {
+        // two CTAs per SM hide each other's per-column serial work; take one per SM only when
+        // two would leave fewer than 2 rows per lane
+        r_fit = (r2 >= 2) ? r2 : std::max(r2, r1);
+    } else {
+        // the FP32 bulk is cheap: what counts is the number of rows sharing each reflector's
+        // serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs)
+        r_fit = (2 * good_r(r2) >= good_r(r1)) ? r2 : r1;
+    }
     if (r_fit < 1 || 32 * W * r_fit < n) return TSQR_ERR_UNSUPPORTED;
     r_fit = good_r(r_fit);
     const int64_t mm = std::max<int64_t>(m, 1);
@@ -147,7 +166,7 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     if (p->hs < n) return TSQR_ERR_UNSUPPORTED;
     p->blk = block_for(r);
     p->ldS = ld_for(p->hs);
-    p->smem = f64_smem_bytes(n, p->hs, p->ldS, W);
+    p->smem = leaf_smem_bytes(n, p->hs, W, mixed);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
     p->nunits = (mm + p->unit - 1) / p->unit;
     int64_t leaves;
@@ -158,8 +177,10 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     } else if (over && over->ctas > 0) {
         leaves = over->ctas;
     } else {
-        if (f64_prepare(p->smem) != cudaSuccess) return TSQR_ERR_CUDA;
-        const int per_sm = std::max(1, f64_blocks_per_sm(W, p->smem));
+        if ((mixed ? mixed_prepare(p->smem) : f64_prepare(p->smem)) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        const int per_sm = std::max(1, mixed ? mixed_blocks_per_sm(W, p->smem)
+                                             : f64_blocks_per_sm(W, p->smem));
         leaves = (int64_t)di.sms * per_sm;
     }
     leaves = std::min<int64_t>(leaves, p->nunits);
@@ -236,6 +257,50 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     return TSQR_SUCCESS;
 }
 
+tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
+                        int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
+    g_last_launches = 0;
+    if (n == 0) return TSQR_SUCCESS;
+    if (m == 0) return zero_r(R, n, ldr, stream);
+    F64Plan p;
+    tsqr_status_t st = plan_leaf(m, (int)n, over, true, &p);
+    if (st != TSQR_SUCCESS) return st;
+    if (mixed_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = (size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, cnt_bytes + slot_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    MixedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.base.A = nullptr;
+    a.base.m = m;
+    a.base.lda = lda;
+    a.base.n = (int)n;
+    a.base.unit = p.unit;
+    a.base.nunits = p.nunits;
+    a.base.nleaves = p.nleaves;
+    a.base.h = p.h;
+    a.base.hs = p.hs;
+    a.base.blk = p.blk;
+    a.base.ldS = p.ldS;
+    a.base.tree = p.shape;
+    a.base.counters = (unsigned int *)ws->base;
+    a.base.slots = (double *)((char *)ws->base + cnt_bytes);
+    a.base.R = R;
+    a.base.ldr = ldr;
+    a.base.status = ws->status;
+    a.A = A;
+    a.ldSd = mixed_ldsd((int)n);
+    a.s_doubles = mixed_s_doubles((int)n, p.ldS);
+    if (cudaMemsetAsync(a.base.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (mixed_launch(a, bf16, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    g_last_launches = 1;
+    return TSQR_SUCCESS;
+}
+
 bool bad_dims(int64_t m, int64_t n, int64_t lda, int64_t ldr) {
     return m < 0 || n < 0 || lda < std::max<int64_t>(1, m) || ldr < std::max<int64_t>(1, n);
 }
@@ -308,7 +373,7 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
     if (dtype == TSQR_F64 && prec == TSQR_PREC_F64)
         return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
     if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
-    return TSQR_ERR_UNSUPPORTED;
+    return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
 }
 
 tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const double *R2,
@@ -382,9 +447,11 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
                                 const tsqr_plan_t *plan, tsqr_plan_t *out) {
     if (!out || m < 0 || n < 1) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
-    if (dtype != TSQR_F64 || prec != TSQR_PREC_F64) return TSQR_ERR_UNSUPPORTED;
+    const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
+    const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
+    if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
     F64Plan p;
-    tsqr_status_t st = plan_f64(m, (int)n, plan, &p);
+    tsqr_status_t st = plan_leaf(m, (int)n, plan, mixed, &p);
     if (st != TSQR_SUCCESS) return st;
     out->tree = p.tree;
     out->tile_rows = (int32_t)p.unit;

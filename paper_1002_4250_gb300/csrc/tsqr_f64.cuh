@@ -51,15 +51,25 @@ struct F64Args {
     int *status;            // device status word (TSQR_STATUS_NONFINITE is or-ed in)
 };
 
-// Shared-memory carve-up (offsets in doubles), identical on host and device.
+// Mixed-precision kernel arguments: the FP64 arguments (base.A unused) plus A of another
+// type, and the FP64 view of the S region used by the tree operator.
+struct MixedArgs {
+    F64Args base;
+    const void *A;  // FP32 or BF16, column-major, leading dimension base.lda
+    int ldSd;       // leading dimension of the FP64 view of S (tree operator)
+    int s_doubles;  // size of the S region in doubles
+};
+
+// Shared-memory carve-up (offsets in doubles), identical on host and device.  The S region
+// holds s_doubles doubles.
 struct SmemLayout {
     int S, Rp, f, seg, tot, npart, scal, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int warps) {
+__host__ __device__ inline SmemLayout smem_layout_s(int n, int s_doubles, int warps) {
     SmemLayout L;
     int o = 0;
-    L.S = o;      o += ldS * n;
+    L.S = o;      o += s_doubles;
     L.Rp = o;     o += n * (n + 1) / 2 + 1;
     L.f = o;      o += n + 1;
     L.seg = o;    o += warps * kSegStride;
@@ -67,8 +77,13 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int wa
     L.npart = o;  o += warps * 32;
     L.scal = o;   o += 4;
     L.total = o;
-    (void)hs;
     return L;
+}
+
+// The FP64 layout: S is an ldS x n FP64 chunk.
+__host__ __device__ inline SmemLayout smem_layout(int n, int hs, int ldS, int warps) {
+    (void)hs;
+    return smem_layout_s(n, ldS * n, warps);
 }
 
 // Packed upper triangle, row-major: row j holds R(j, j..n-1) at rowoff(j).

@@ -1,0 +1,599 @@
+// Device code shared by libtsqr's kernels: the shared-memory fold R <- R([R; S]) that serves
+// both as the leaf (S = a chunk of rows of A, Section 2 step 1 fused with a flat tree,
+// Section 1) and as the tree operator qr(R1, R2) (S = R2, an upper triangle; Section 2,
+// Table 3), and the body of the leaf + binary-tree kernel (Fig. 1) with the "last child to
+// arrive combines" rule.
+//
+// Cost model this is written for (measured on GB300): one warp-wide FP64 instruction occupies a
+// sub-partition's FP64 unit for ~64 cycles whether 1 or 32 lanes are active, FP64 latency is
+// ~65 cycles, sqrt ~620 and divide ~375 cycles; shared-memory traffic, integer work, shuffles
+// and barriers are nearly free by comparison.  Hence the bulk pass spreads its (row, column)
+// items evenly over all 32 lanes in lockstep, fuses the update by reflector j with the dot
+// products for reflector j+1, sums partials along fixed index orders (bit-reproducible), and
+// does the per-column scalar work once per CTA on one warp.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tsqr_f64.cuh"
+#include "tsqr_internal.h"
+
+namespace tsqr {
+
+// ------------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async of 8 or 4 bytes; src_bytes = 0 zero-fills).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// A chunk of rows of A (src == nullptr: none).
+template <typename Tin>
+struct Chunk {
+    const Tin *src;  // row 0, column 0 of the chunk in A
+    int64_t lda;
+    int rows;        // rows of A in the chunk; the rest of the hs rows of S are zero-filled
+};
+
+// Element types: T is the leaf's storage and arithmetic type in shared memory, Tin the type
+// of A in global memory.  Same type: copied by cp.async.  BF16 -> FP32: widened (exactly)
+// through registers.
+template <typename T, typename Tin>
+struct Copy {
+    static constexpr bool kAsync = sizeof(T) == sizeof(Tin);
+};
+
+__device__ __forceinline__ float widen(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Copy column `col` of the chunk into column `col` of S (asynchronously when the types agree).
+template <typename T, typename Tin>
+__device__ __forceinline__ void load_column(T *S, int ldS, int hs, const Chunk<Tin> c, int col) {
+    const Tin *src = c.src + (int64_t)col * c.lda;
+    T *dst = S + (size_t)col * ldS;
+    if constexpr (Copy<T, Tin>::kAsync) {
+        for (int i = threadIdx.x; i < hs; i += blockDim.x) {
+            const bool ok = i < c.rows;
+            if constexpr (sizeof(T) == 8)
+                cp_async8(dst + i, ok ? (const void *)(src + i) : (const void *)c.src, ok ? 8 : 0);
+            else
+                cp_async4(dst + i, ok ? (const void *)(src + i) : (const void *)c.src, ok ? 4 : 0);
+        }
+        cp_async_commit();
+    } else {
+        for (int i = threadIdx.x; i < hs; i += blockDim.x)
+            dst[i] = (i < c.rows) ? (T)widen(src[i]) : (T)0;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// R <- R([R; S]) in shared memory, one Householder reflector per column J = 0..n-1.
+//
+// Rp: the top block R, packed upper triangle (row J at rowoff(n, J)).
+// S : the bottom block, column-major with leading dimension ldS.
+//   leaf (fold_leaf): S is a dense chunk of hs rows; warp w owns rows [w*Hw, (w+1)*Hw),
+//     Hw = hs / W = 32 r.
+//   tree operator (fold_tri, Table 3): S is the upper triangle R2, so the support of
+//     reflector J in S is rows 0..J (the j+2-entry reflector of the paper's operator);
+//     the warps split the trailing columns instead of the rows.
+//
+// Reflector J (the LAPACK dlarfg rule the paper's operator uses): alpha = R(J,J), x = the
+// support of column J in S, sigma^2 = ||x||^2.  If sigma^2 == 0 it is the identity (the
+// paper's tau == 0 skip).  Otherwise beta = -sign(alpha) sqrt(alpha^2 + sigma^2) with
+// sign(0) = +1, tau = (beta - alpha) / beta and v = x / (alpha - beta).  S keeps x unscaled;
+// for each trailing column k, with d_k = x . S(:,k):
+//   w_k = R(J,k) + d_k / (alpha - beta),   R(J,k) -= tau w_k,   S(:,k) -= f_k x,
+//   f_k = tau w_k / (alpha - beta) = -w_k / beta.
+// 1/sqrt(alpha^2 + sigma^2) gives both |beta| and 1/beta; 1/(alpha - beta) is the one
+// reciprocal (alpha - beta has the sign of alpha and magnitude >= |beta|: no cancellation).
+//
+// Each step J does:
+//   A  (per warp)   column J gets reflector J-1 (f[J]); per-lane partial ||column J||^2;
+//   B  (per warp)   every other trailing column k > J gets reflector J-1 and, in the same
+//                   sweep, its partial dot product with column J.  The warp's (column, row)
+//                   items are cut into 32 equal contiguous runs in column-major order, one
+//                   per lane, processed in lockstep; a lane writes one partial per column its
+//                   run touches into slot (lane + column) -- slot ids are distinct and
+//                   ordered along the items;
+//   then one warp sums the partials in a fixed order, forms reflector J, updates row J of R
+//   and publishes f[k] for k > J (in the leaf a dedicated reducer warp, whose scalar work
+//   overlaps phase B; in the tree operator warp J mod W).
+// ------------------------------------------------------------------------------------------
+
+// 1/sqrt(t) for finite t > 0 by Newton's iteration for the reciprocal square root,
+// y <- y + y (1 - t y^2) / 2, started from the FP32 hardware estimate.  t is first scaled by an
+// even power of two into [1, 4) (exact, on the exponent bits) so that the FP32 estimate cannot
+// overflow or underflow; two steps take its ~2^-22 relative error below FP64 rounding.  Zero,
+// subnormal, infinite and NaN arguments take the library's rsqrt.
+__device__ __forceinline__ double recip_sqrt(double t) {
+    const long long b = __double_as_longlong(t);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0 || e == 0x7ff) return rsqrt(t);
+    const int k = (e - 1023) >> 1;  // t = tm 4^k, tm in [1, 4)
+    const double tm = __longlong_as_double(b - ((long long)(2 * k) << 52));
+    double y = (double)rsqrtf((float)tm);
+    double h = fma(-tm * y, y, 1.0);
+    y = fma(__longlong_as_double(__double_as_longlong(y) - (1LL << 52)), h, y);  // y/2 exactly
+    h = fma(-tm * y, y, 1.0);
+    y = fma(__longlong_as_double(__double_as_longlong(y) - (1LL << 52)), h, y);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));  // y 2^-k
+}
+
+// 1/x for finite nonzero x by Newton's iteration for the reciprocal, y <- y + y (1 - x y),
+// started from the FP32 estimate of 1/xm with x = xm 2^k, |xm| in [1, 2) (exact rescaling);
+// two steps reach FP64 rounding.  Zero, subnormal, infinite and NaN arguments, and |x| >= 2^1022
+// (whose reciprocal is subnormal), divide.
+__device__ __forceinline__ double recip(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0 || e >= 0x7fd) return 1.0 / x;
+    const int k = e - 1023;
+    const double xm = __longlong_as_double(b - ((long long)k << 52));
+    double y = (double)__fdividef(1.0f, (float)xm);
+    double h = fma(-xm, y, 1.0);
+    y = fma(y, h, y);
+    h = fma(-xm, y, 1.0);
+    y = fma(y, h, y);
+    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+}
+
+// Reflector J's scalars from alpha = R(J,J) and sigma^2 (see the comment above).
+struct Reflector {
+    double beta, tau, c, ib;
+    bool ident;
+};
+
+__device__ __forceinline__ Reflector make_reflector(const double alpha, const double sig2) {
+    Reflector h;
+    // identity reflector only for an exactly zero tail; NaN/Inf propagate into R
+    h.ident = (sig2 == 0.0);
+    h.beta = alpha;
+    h.tau = 0.0;
+    h.c = 0.0;
+    h.ib = 0.0;
+    if (!h.ident) {
+        const double t = fma(alpha, alpha, sig2);
+        const double y = recip_sqrt(t);
+        const double r = t * y;
+        const bool pos = alpha >= 0.0;
+        h.beta = pos ? -r : r;
+        h.ib = pos ? -y : y;
+        h.tau = fma(-alpha, h.ib, 1.0);
+        h.c = recip(alpha - h.beta);
+    }
+    return h;
+}
+
+// sigma^2 from W x 32 per-lane partials, summed in a fixed order (same value in every lane).
+__device__ __forceinline__ double sum_norm_partials(const int lane, const int W,
+                                                    const double *__restrict__ npart) {
+    double v = npart[lane];
+    for (int w = 1; w < W; ++w) v += npart[w * 32 + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Row J of R and the factors f[k], k > J, from the reflector and the dot products dk[kk] of
+// column J+1+kk with column J.
+__device__ __forceinline__ void apply_reflector(const int lane, const int n, const int J,
+                                                const Reflector &h, double *__restrict__ Rp,
+                                                double *__restrict__ f,
+                                                const double *__restrict__ dk) {
+    const int U = n - J - 1;
+    const int ro = rowoff(n, J);
+    for (int kk = lane; kk < U; kk += 32) {
+        const int k = J + 1 + kk;
+        const int idx = ro + 1 + kk;
+        if (h.ident) {
+            f[k] = 0.0;
+        } else {
+            const double rjk = Rp[idx];
+            const double wk = fma(h.c, dk[kk], rjk);
+            Rp[idx] = fma(-h.tau, wk, rjk);
+            f[k] = -wk * h.ib;
+        }
+    }
+    if (lane == 0) Rp[ro] = h.beta;
+}
+
+// Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warp Wb is the reducer.
+// Every bulk lane owns r rows of its warp's block (Hw = 32 r) and a phase-B run of U r items
+// starting at item lane * U r; runs and column boundaries are multiples of r, so blocks of B
+// items (B divides r) never straddle a column: the inner loop has no per-item bookkeeping and
+// all lanes stay in lockstep.  The reducer forms reflector J's scalars (its long FP64 chain)
+// while the bulk warps run phase B, then sums the dot products and updates R and f:
+//   A (bulk) | barrier | B (bulk) || scalars (reducer) | barrier | dots, R, f (reducer) | barrier.
+// The next chunk of rows streams into columns no longer read (J-2 at step J) by cp.async when
+// A's type is T; a BF16 A is widened after the fold instead.  T = double is the FP64 path;
+// T = float the mixed path, where only the bulk arithmetic is FP32 and the reflector scalars,
+// partial-sum reductions, R and f stay FP64.
+template <typename T, typename Tin, int B>
+__device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, const int hs,
+                                          double *__restrict__ Rp, double *__restrict__ f,
+                                          double *__restrict__ seg_all, double *__restrict__ tot,
+                                          double *__restrict__ npart, const int n,
+                                          const Chunk<Tin> pf) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int Wb = (blockDim.x >> 5) - 1;
+    const bool reducer = (warp == Wb);
+    const int Hw = hs / Wb;
+    const int r = Hw >> 5;
+    const int r0 = warp * Hw;
+    double *seg = seg_all + warp * kSegStride;
+
+    for (int J = 0; J < n; ++J) {
+        if (Copy<T, Tin>::kAsync && pf.src && J >= 2) load_column(S, ldS, hs, pf, J - 2);
+        const int U = n - J - 1;
+        T *SJ = S + (size_t)J * ldS + r0;
+        const T *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS + r0;
+
+        // ---- A: column J gets reflector J-1; per-lane partial squared norm of column J
+        if (!reducer) {
+            T nacc = (T)0;
+            if (J > 0) {
+                const T fJ = (T)f[J];
+                for (int t = 0; t < r; ++t) {
+                    const int i = lane + 32 * t;
+                    const T s = fmat(-fJ, Sj[i], SJ[i]);
+                    SJ[i] = s;
+                    nacc = fmat(s, s, nacc);
+                }
+            } else {
+                for (int t = 0; t < r; ++t) {
+                    const T s = SJ[lane + 32 * t];
+                    nacc = fmat(s, s, nacc);
+                }
+            }
+            npart[warp * 32 + lane] = (double)nacc;
+            for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
+        }
+        __syncthreads();
+
+        Reflector h;
+        if (reducer) {
+            // ---- reflector J's scalars, overlapping phase B
+            h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, Wb, npart));
+        } else if (U > 0) {
+            // ---- B: fused update by reflector J-1 and dots with column J
+            const int run = U * r;
+            const int p = lane * run;
+            int kk = p / Hw;
+            int i = p - kk * Hw;
+            T *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
+            T acc = (T)0;
+            if (J > 0) {
+                T fk = (T)f[J + 1 + kk];
+                for (int blk = 0; blk < run; blk += B) {
+                    T x[B];
+#pragma unroll
+                    for (int q = 0; q < B; ++q) x[q] = fmat(-fk, Sj[i + q], Sk[i + q]);
+#pragma unroll
+                    for (int q = 0; q < B; ++q) Sk[i + q] = x[q];
+#pragma unroll
+                    for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], x[q], acc);
+                    i += B;
+                    if (i == Hw) {
+                        seg[lane + kk] = (double)acc;
+                        acc = (T)0;
+                        i = 0;
+                        ++kk;
+                        Sk += ldS;
+                        fk = (T)f[min(J + 1 + kk, n - 1)];
+                    }
+                }
+            } else {
+                for (int blk = 0; blk < run; blk += B) {
+#pragma unroll
+                    for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], Sk[i + q], acc);
+                    i += B;
+                    if (i == Hw) {
+                        seg[lane + kk] = (double)acc;
+                        acc = (T)0;
+                        i = 0;
+                        ++kk;
+                        Sk += ldS;
+                    }
+                }
+            }
+            if (i != 0) seg[lane + kk] = (double)acc;
+        }
+        __syncthreads();
+
+        // ---- reducer: dot products in a fixed order, row J of R, factors f[k] for k > J
+        if (reducer) {
+            for (int id = lane; id < 32 + U; id += 32) {
+                double t = seg_all[id];
+                for (int w = 1; w < Wb; ++w) t += seg_all[w * kSegStride + id];
+                tot[id] = t;
+            }
+            __syncwarp();
+            const int Nw = U * Hw;
+            double *dk = tot + kSegStride;
+            for (int kk = lane; kk < U; kk += 32) {
+                const int la = (32 * (kk * Hw + 1) - 1) / Nw;
+                const int lb = (32 * (kk + 1) * Hw - 1) / Nw;
+                double d = tot[kk + la];
+                for (int l = la + 1; l <= lb; ++l) d += tot[kk + l];
+                dk[kk] = d;
+            }
+            __syncwarp();
+            apply_reflector(lane, n, J, h, Rp, f, dk);
+        }
+        __syncthreads();
+    }
+    if (Copy<T, Tin>::kAsync && pf.src) {
+        for (int col = n - 2; col < n; ++col)
+            if (col >= 0) load_column(S, ldS, hs, pf, col);
+    }
+}
+
+// Tree-operator fold (Table 3): S = R2, reflector J's support in S is rows 0..J.  Warp 0
+// updates column J; the warps split the trailing columns, each lane taking an equal
+// contiguous run of the warp's (column, row) items in lockstep.
+__device__ __forceinline__ void fold_tri(double *__restrict__ S, const int ldS,
+                                         double *__restrict__ Rp, double *__restrict__ f,
+                                         double *__restrict__ seg_all,
+                                         double *__restrict__ npart, const int n) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    double *seg = seg_all + warp * kSegStride;
+
+    for (int J = 0; J < n; ++J) {
+        const int U = n - J - 1;
+        const int cw = J + 1;
+        double *SJ = S + (size_t)J * ldS;
+        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS;
+        const int kc0 = (warp * U) / W, kc1 = ((warp + 1) * U) / W;
+
+        double nacc = 0.0;
+        if (warp == 0) {
+            const double fJ = (J > 0) ? f[J] : 0.0;
+            for (int i = lane; i < cw; i += 32) {
+                double s = SJ[i];
+                if (J > 0) {
+                    s = fma(-fJ, Sj[i], s);
+                    SJ[i] = s;
+                }
+                nacc = fma(s, s, nacc);
+            }
+        }
+        npart[warp * 32 + lane] = nacc;
+        for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
+        __syncthreads();
+
+        const int N = (kc1 - kc0) * cw;
+        if (N > 0) {
+            int p = (int)(((long long)lane * N) >> 5);
+            const int pend = (int)(((long long)(lane + 1) * N) >> 5);
+            if (p < pend) {
+                int kk = p / cw;
+                int i = p - kk * cw;
+                int k = J + 1 + kc0 + kk;
+                double *Sk = S + (size_t)k * ldS;
+                double fk = (J > 0) ? f[k] : 0.0;
+                double acc = 0.0;
+                for (;;) {
+                    double s = Sk[i];
+                    if (J > 0) {
+                        s = fma(-fk, Sj[i], s);
+                        Sk[i] = s;
+                    }
+                    acc = fma(SJ[i], s, acc);
+                    if (++p == pend) break;
+                    if (++i == cw) {
+                        seg[lane + kk] = acc;
+                        acc = 0.0;
+                        i = 0;
+                        ++kk;
+                        ++k;
+                        Sk += ldS;
+                        fk = (J > 0) ? f[k] : 0.0;
+                    }
+                }
+                seg[lane + kk] = acc;
+            }
+        }
+        __syncthreads();
+
+        if (warp == J % W) {
+            double *dk = seg_all + W * kSegStride + kSegStride;
+            for (int kk = lane; kk < U; kk += 32) {
+                double d = 0.0;
+                bool first = true;
+                for (int w = 0; w < W; ++w) {
+                    const int a0 = (w * U) / W, a1 = ((w + 1) * U) / W;
+                    if (kk < a0 || kk >= a1) continue;
+                    const int rel = kk - a0;
+                    const int Nw = (a1 - a0) * cw;
+                    const int la = (32 * (rel * cw + 1) - 1) / Nw;
+                    const int lb = (32 * (rel + 1) * cw - 1) / Nw;
+                    for (int l = la; l <= lb; ++l) {
+                        const double x = seg_all[w * kSegStride + rel + l];
+                        d = first ? x : d + x;
+                        first = false;
+                    }
+                }
+                dk[kk] = d;
+            }
+            __syncwarp();
+            const Reflector h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, W, npart));
+            apply_reflector(lane, n, J, h, Rp, f, dk);
+        }
+        __syncthreads();
+    }
+}
+
+// Packed upper triangle (smem) -> column-major n x n (global), zeros below the diagonal.
+__device__ __forceinline__ void store_packed(const double *__restrict__ Rp, int n,
+                                             double *__restrict__ dst, int64_t ld) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        dst[row + (int64_t)col * ld] = (row <= col) ? Rp[rowoff(n, row) + col - row] : 0.0;
+    }
+}
+
+// Column-major global (L2, bypassing L1) -> packed upper triangle in smem.
+__device__ __forceinline__ void load_packed_cg(const double *src, int64_t ld, int n,
+                                               double *__restrict__ Rp) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        if (row <= col) Rp[rowoff(n, row) + col - row] = __ldcg(src + row + (int64_t)col * ld);
+    }
+}
+
+// Column-major global -> S (upper triangle kept, strict lower part stored as zero).
+__device__ __forceinline__ void load_tri_cg(const double *src, int64_t ld, int n,
+                                            double *__restrict__ S, int ldS) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        S[row + col * ldS] = (row <= col) ? __ldcg(src + row + (int64_t)col * ld) : 0.0;
+    }
+}
+
+// Root: rows flipped so that diag(R) >= 0 (Section 2), strict lower part zero, NaN/Inf noted.
+__device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, int n,
+                                                 double *__restrict__ R, int64_t ldr,
+                                                 int *status) {
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        double v = 0.0;
+        if (row <= col) {
+            v = Rp[rowoff(n, row) + col - row];
+            if (Rp[rowoff(n, row)] < 0.0) v = -v;
+            bad |= !isfinite(v);
+        }
+        R[row + (int64_t)col * ldr] = v;
+    }
+    if (bad && status) atomicOr(status, kStatusNonfiniteBit);
+}
+
+// ------------------------------------------------------------------------------------------
+// Leaf + tree kernel.  CTA c owns the work units [c*nunits/nleaves, (c+1)*nunits/nleaves) of A
+// (one tile for the binary tree, a run of slabs for the flat and hybrid trees) and folds their
+// rows, h at a time, into its R (a flat tree over its chunks, Section 1, with the next chunk
+// streamed in during the current fold), then climbs the binary tree (Fig. 1): it
+// publishes R in its node's slot and bumps the parent's counter; the second child to arrive
+// combines [R_left; R_right] (left = lower index, always on top) and climbs on; the first
+// returns.  No CTA ever waits for another, and the operand order depends only on the indices.
+// ------------------------------------------------------------------------------------------
+// T: leaf storage/arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading
+// dimension a.ldS); the tree operator works in the same memory viewed as FP64 with leading
+// dimension ldSd.
+template <typename T, typename Tin>
+__device__ __forceinline__ void leaf_tree_body(const F64Args &a, const Tin *A, const int ldSd,
+                                               const int s_doubles) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n;
+    const SmemLayout L = smem_layout_s(n, s_doubles, blockDim.x >> 5);
+    T *S = reinterpret_cast<T *>(smem + L.S);
+    double *Sd = smem + L.S;
+    double *Rp = smem + L.Rp;
+    double *f = smem + L.f;
+    double *seg = smem + L.seg;
+    double *tot = smem + L.tot;
+    double *npart = smem + L.npart;
+    unsigned int *flag = reinterpret_cast<unsigned int *>(smem + L.scal);
+
+    const int leaf = blockIdx.x;
+    for (int i = threadIdx.x; i < n * (n + 1) / 2; i += blockDim.x) Rp[i] = 0.0;
+
+    // rows of this leaf, folded in chunks of h rows
+    const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
+    const int64_t rbeg = u0 * a.unit;
+    const int64_t rend = (u1 * a.unit < a.m) ? u1 * a.unit : a.m;
+    const int64_t nchunks = (rend - rbeg + a.h - 1) / a.h;
+    if (nchunks > 0) {
+        Chunk<Tin> first;
+        first.src = A + rbeg;
+        first.lda = a.lda;
+        first.rows = (int)((rend - rbeg < a.h) ? rend - rbeg : a.h);
+        for (int col = 0; col < n; ++col) load_column(S, a.ldS, a.hs, first, col);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int64_t c = 0; c < nchunks; ++c) {
+        Chunk<Tin> next;
+        next.src = nullptr;
+        next.lda = a.lda;
+        next.rows = 0;
+        if (c + 1 < nchunks) {
+            const int64_t r1 = rbeg + (c + 1) * a.h;
+            next.src = A + r1;
+            next.rows = (int)((rend - r1 < a.h) ? rend - r1 : a.h);
+        }
+        switch (a.blk) {
+            case 4: fold_leaf<T, Tin, 4>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            case 3: fold_leaf<T, Tin, 3>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            case 2: fold_leaf<T, Tin, 2>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+            default: fold_leaf<T, Tin, 1>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
+        }
+        if (next.src) {
+            if constexpr (!Copy<T, Tin>::kAsync) {
+                __syncthreads();
+                for (int col = 0; col < n; ++col) load_column(S, a.ldS, a.hs, next, col);
+            }
+            cp_async_wait_all();
+            __syncthreads();
+        }
+    }
+
+    int level = 0, t = leaf;
+    for (;;) {
+        const int cnt = a.tree.count[level];
+        if (cnt == 1) {
+            store_normalized(Rp, n, a.R, a.ldr, a.status);
+            return;
+        }
+        const int sib = t ^ 1;
+        if (sib >= cnt) {  // odd last node: promoted unchanged
+            ++level;
+            t >>= 1;
+            continue;
+        }
+        double *mine = a.slots + (size_t)(a.tree.offset[level] + t) * n * n;
+        store_packed(Rp, n, mine, n);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0)
+            flag[0] = atomicAdd(&a.counters[a.tree.offset[level + 1] + (t >> 1)], 1u);
+        __syncthreads();
+        if (flag[0] == 0) return;  // the sibling combines
+        __threadfence();
+        const double *other = a.slots + (size_t)(a.tree.offset[level] + sib) * n * n;
+        if (t & 1) {
+            // this CTA holds the right (lower) operand: it becomes S, the left one comes to Rp
+            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+                const int col = idx / n, row = idx - col * n;
+                Sd[row + col * ldSd] = (row <= col) ? Rp[rowoff(n, row) + col - row] : 0.0;
+            }
+            __syncthreads();
+            load_packed_cg(other, n, n, Rp);
+        } else {
+            load_tri_cg(other, n, n, Sd, ldSd);
+        }
+        __syncthreads();
+        fold_tri(Sd, ldSd, Rp, f, seg, npart, n);
+        ++level;
+        t >>= 1;
+    }
+}
+
+
+}  // namespace tsqr

@@ -22,6 +22,15 @@ cudaError_t f64_combine_launch(int n, const double *R1, int64_t ld1, const doubl
                                int ldS, int hs, size_t smem_bytes, int *status,
                                cudaStream_t stream);
 
+// Mixed path (tsqr_mixed.cu); `warps` counts bulk warps as for the FP64 path.
+int mixed_ldsd(int n);
+int mixed_s_doubles(int n, int ldS);
+size_t mixed_smem_bytes(int n, int ldS, int warps);
+cudaError_t mixed_prepare(size_t smem_bytes);
+int mixed_blocks_per_sm(int warps, size_t smem_bytes);
+cudaError_t mixed_launch(const MixedArgs &a, bool bf16, int warps, size_t smem_bytes,
+                         cudaStream_t stream);
+
 // The AUTO plan of tsqr_r as kernel arguments (tsqr_api.cu); A, R, workspace and status
 // pointers are left for the caller.
 tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,
