@@ -339,7 +339,36 @@ def bench_extras(dev):
         del A
     del A64
     torch.cuda.empty_cache()
+    out["varlen_batch"] = bench_batched(dev)
     return out
+
+
+def bench_batched(dev):
+    """The varlen batch: 4096 problems, m log-uniform in [512, 262144], n uniform in
+    {8, 16, 32, 64}, packed in one buffer, one persistent launch per call; FP64 and mixed FP32."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    buf, ms, ns, offs = workloads.varlen_batch(4096, 512, 262144, seed=0, device=dev)
+    fl = sum(flops(m, n) for m, n in zip(ms, ns))
+    roff = [0]
+    for n in ns:
+        roff.append(roff[-1] + n * n)
+    Rp = torch.empty(roff[-1], dtype=torch.float64, device=dev)
+    res = {"problems": len(ms), "elements": int(offs[-1]), "gflop_per_call": fl / 1e9}
+    for name, dt, code, prec in (("fp64", torch.float64, T.F64, T.PREC_F64),
+                                 ("mixed_fp32", torch.float32, T.F32, T.PREC_MIXED)):
+        b = buf if dt == torch.float64 else buf.to(dt)
+        ptrs = [b.data_ptr() + b.element_size() * o for o in offs[:-1]]
+        ms_ = time_call(lambda: T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec),
+                        reps=2 if name == "fp64" else 5, warmup=1)
+        res[name] = {"ms": ms_, "gflops": fl / ms_ / 1e6,
+                     "a_read_gbs": b.element_size() * offs[-1] / ms_ / 1e6}
+        del b
+    res["mixed_speedup_vs_fp64"] = res["fp64"]["ms"] / res["mixed_fp32"]["ms"]
+    del buf
+    torch.cuda.empty_cache()
+    return res
 
 
 def kernel_sha():

@@ -5,7 +5,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <utility>
+#include <vector>
 
 #include "tsqr.h"
 #include "tsqr_internal.h"
@@ -20,6 +22,9 @@ struct Workspace {
     void *base = nullptr;   // counters + slots (grown on demand)
     size_t bytes = 0;
     int *status = nullptr;  // device status word (lives as long as the workspace entry)
+    // batched calls: the problem table and work items last copied to base + table_off
+    std::vector<char> table;
+    size_t table_off = 0;
 };
 
 std::mutex g_mu;
@@ -203,6 +208,7 @@ tsqr_status_t get_workspace(cudaStream_t stream, size_t bytes, Workspace **out) 
         if (w.base) cudaFreeAsync(w.base, stream);
         w.base = nullptr;
         w.bytes = 0;
+        w.table.clear();
         const size_t nb = align_up(bytes, 1 << 20);
         if (cudaMallocAsync(&w.base, nb, stream) != cudaSuccess) return TSQR_ERR_ALLOC;
         w.bytes = nb;
@@ -244,7 +250,6 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     a.hs = p.hs;
     a.blk = p.blk;
     a.ldS = p.ldS;
-    a.tree = p.shape;
     a.counters = (unsigned int *)ws->base;
     a.slots = (double *)((char *)ws->base + cnt_bytes);
     a.R = R;
@@ -284,7 +289,6 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     a.base.hs = p.hs;
     a.base.blk = p.blk;
     a.base.ldS = p.ldS;
-    a.base.tree = p.shape;
     a.base.counters = (unsigned int *)ws->base;
     a.base.slots = (double *)((char *)ws->base + cnt_bytes);
     a.base.R = R;
@@ -297,6 +301,124 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
         cudaSuccess)
         return TSQR_ERR_CUDA;
     if (mixed_launch(a, bf16, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    g_last_launches = 1;
+    return TSQR_SUCCESS;
+}
+
+// ------------------------------------------------------------------------------------------
+// Varlen batch.  One CTA size and shared-memory budget for the whole batch (set by its widest
+// problem); per width n the tallest chunk that fits; per problem leaves of a few chunks sized
+// so that the batch has several leaves per CTA; work items (problem, leaf) ordered by work,
+// largest first, for the persistent kernel's queue.
+// ------------------------------------------------------------------------------------------
+tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                          const int64_t *offsets, int32_t count, double *R_packed, int dt,
+                          cudaStream_t stream) {
+    g_last_launches = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    if (di.sms <= 0) return TSQR_ERR_CUDA;
+    const bool mixed = dt != 0;
+    const int W = 4;
+    const size_t reserve = 1024 + 256;  // per-CTA reserve plus the kernel's static shared memory
+    const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
+    const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
+    int nmax = 1;
+    for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
+    size_t budget = two_per_sm;
+    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2) budget = one_per_sm;
+    // per width: chunk rows
+    std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1);
+    size_t smem = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const int n = ns[i];
+        if (hs_of[n]) continue;
+        const int r = good_r(max_rows_per_lane_p(n, W, budget, mixed));
+        if (r < 1 || 32 * W * r < n) return TSQR_ERR_UNSUPPORTED;
+        hs_of[n] = 32 * W * r;
+        blk_of[n] = block_for(r);
+        smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], W, mixed));
+    }
+    if (batched_prepare(dt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int per_sm = std::max(1, batched_blocks_per_sm(dt, W, smem));
+    const int64_t ctas = (int64_t)di.sms * per_sm;
+    // leaf size: about 6 leaves per CTA over the whole batch
+    double work = 0.0;
+    for (int32_t i = 0; i < count; ++i) work += (double)std::max<int64_t>(ms[i], 1) * ns[i] * ns[i];
+    const double target = work / (double)(ctas * 6);
+
+    std::vector<BatchProblem> probs(count);
+    std::vector<std::pair<double, int2>> items;
+    int64_t slot_doubles = 0, nodes_total = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const int n = ns[i];
+        const int64_t m = std::max<int64_t>(ms[i], 1);
+        BatchProblem &P = probs[i];
+        P.A = ptrs[i];
+        P.m = ms[i];
+        P.lda = std::max<int64_t>(ms[i], 1);
+        P.R = R_packed + offsets[i];
+        P.n = n;
+        P.hs = hs_of[n];
+        P.blk = blk_of[n];
+        P.ldS = ld_for(P.hs);
+        const int64_t chunks = std::max<int64_t>(1, (int64_t)(target / ((double)n * n * P.hs)));
+        P.unit = chunks * P.hs;
+        P.h = P.hs;
+        P.nunits = (m + P.unit - 1) / P.unit;
+        if (P.nunits > (1 << 24)) return TSQR_ERR_UNSUPPORTED;
+        P.nleaves = (int)P.nunits;
+        TreeShape shape;
+        int64_t nodes = 0;
+        if (build_tree(P.nleaves, &shape, &nodes) != TSQR_SUCCESS) return TSQR_ERR_UNSUPPORTED;
+        P.slot_off = slot_doubles;
+        P.cnt_off = nodes_total;
+        slot_doubles += nodes * (int64_t)n * n;
+        nodes_total += nodes;
+        for (int l = 0; l < P.nleaves; ++l) {
+            const int64_t rows = std::min<int64_t>(P.unit, m - (int64_t)l * P.unit);
+            items.push_back({(double)rows * n * n, make_int2(i, l)});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2> &a, const std::pair<double, int2> &b) {
+                         return a.first > b.first;
+                     });
+    if (items.size() > (size_t)0x7fffffff) return TSQR_ERR_UNSUPPORTED;
+    // table: problems then items, copied once and reused while the batch is unchanged
+    std::vector<char> table(sizeof(BatchProblem) * probs.size() + sizeof(int2) * items.size());
+    std::memcpy(table.data(), probs.data(), sizeof(BatchProblem) * probs.size());
+    int2 *it_host = reinterpret_cast<int2 *>(table.data() + sizeof(BatchProblem) * probs.size());
+    for (size_t k = 0; k < items.size(); ++k) it_host[k] = items[k].second;
+
+    const size_t head_bytes = align_up((size_t)(1 + nodes_total) * sizeof(unsigned int), 256);
+    const size_t slots_bytes = align_up((size_t)slot_doubles * sizeof(double), 256);
+    Workspace *ws = nullptr;
+    tsqr_status_t st = get_workspace(stream, head_bytes + slots_bytes + table.size(), &ws);
+    if (st != TSQR_SUCCESS) return st;
+    const size_t table_off = head_bytes + slots_bytes;
+    char *base = (char *)ws->base;
+    if (ws->table != table || ws->table_off != table_off) {
+        if (cudaMemcpyAsync(base + table_off, table.data(), table.size(), cudaMemcpyHostToDevice,
+                            stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        ws->table = table;
+        ws->table_off = table_off;
+    }
+    BatchArgs b;
+    b.probs = reinterpret_cast<const BatchProblem *>(base + table_off);
+    b.items = reinterpret_cast<const int2 *>(base + table_off + sizeof(BatchProblem) * probs.size());
+    b.nitems = (int)items.size();
+    b.queue = reinterpret_cast<unsigned int *>(base);
+    b.counters = b.queue + 1;
+    b.slots = reinterpret_cast<double *>(base + head_bytes);
+    b.status = ws->status;
+    if (cudaMemsetAsync(base, 0, (size_t)(1 + nodes_total) * sizeof(unsigned int), stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    const int grid = (int)std::min<int64_t>(ctas, (int64_t)items.size());
+    if (batched_launch(dt, b, grid, W, smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     g_last_launches = 1;
     return TSQR_SUCCESS;
 }
@@ -326,7 +448,6 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
     a->hs = p.hs;
     a->blk = p.blk;
     a->ldS = p.ldS;
-    a->tree = p.shape;
     *warps = p.warps;
     *smem = p.smem;
     *nodes = p.nodes;
@@ -405,11 +526,20 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream) {
     g_last_launches = 0;
-    (void)ptrs; (void)ms; (void)ns; (void)offsets; (void)R_packed; (void)dtype; (void)prec;
-    (void)stream;
     if (count < 0) return TSQR_ERR_INVALID_ARG;
     if (count == 0) return TSQR_SUCCESS;
-    return TSQR_ERR_UNSUPPORTED;
+    if (!ptrs || !ms || !ns || !offsets || !R_packed) return TSQR_ERR_INVALID_ARG;
+    const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
+    const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
+    if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i) {
+        if (ms[i] < 0 || ns[i] < 1 || offsets[i] < 0) return TSQR_ERR_INVALID_ARG;
+        if (ns[i] > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+        if (offsets[i + 1] - offsets[i] < (int64_t)ns[i] * ns[i]) return TSQR_ERR_INVALID_ARG;
+        if (ms[i] > 0 && !ptrs[i]) return TSQR_ERR_INVALID_ARG;
+    }
+    return run_batched(ptrs, ms, ns, offsets, count, R_packed, f64 ? 0 : (dtype == TSQR_F32 ? 1 : 2),
+                       (cudaStream_t)stream);
 }
 
 tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream) {

@@ -1,0 +1,90 @@
+// Varlen batched TSQR in one persistent launch: every CTA takes (problem, leaf) work items from
+// a global queue, folds the leaf and climbs that problem's binary tree (Fig. 1) with the same
+// "last child to arrive combines" rule as the single-matrix kernel, then takes the next item.
+// Items are ordered largest first, so the queue balances uneven problems.  No CTA ever waits
+// for another.
+#include "tsqr_fold.cuh"
+
+namespace tsqr {
+
+template <typename T, typename Tin>
+__device__ __forceinline__ void batched_body(const BatchArgs &b) {
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= b.nitems) return;
+        const int2 w = b.items[it];
+        const BatchProblem P = b.probs[w.x];
+        F64Args a;
+        a.A = static_cast<const double *>(P.A);
+        a.m = P.m;
+        a.lda = P.lda;
+        a.n = P.n;
+        a.unit = P.unit;
+        a.nunits = P.nunits;
+        a.nleaves = P.nleaves;
+        a.h = P.h;
+        a.hs = P.hs;
+        a.blk = P.blk;
+        a.ldS = P.ldS;
+        a.slots = b.slots + P.slot_off;
+        a.counters = b.counters + P.cnt_off;
+        a.R = P.R;
+        a.ldr = P.n;
+        a.status = b.status;
+        if constexpr (sizeof(T) == 8)
+            leaf_tree_job<T, Tin>(a, static_cast<const Tin *>(P.A), P.ldS, P.ldS * P.n, w.y);
+        else
+            leaf_tree_job<T, Tin>(a, static_cast<const Tin *>(P.A), mixed_ldsd_of(P.n),
+                                  mixed_s_doubles_of(P.n, P.ldS), w.y);
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
+    batched_body<double, double>(b);
+}
+__global__ void __launch_bounds__(256, 1) tsqr_batched_f32_kernel(const BatchArgs b) {
+    batched_body<float, float>(b);
+}
+__global__ void __launch_bounds__(256, 1) tsqr_batched_bf16_kernel(const BatchArgs b) {
+    batched_body<float, __nv_bfloat16>(b);
+}
+
+namespace {
+const void *batched_fn(int dtype) {
+    return dtype == 0 ? (const void *)tsqr_batched_f64_kernel
+                      : dtype == 1 ? (const void *)tsqr_batched_f32_kernel
+                                   : (const void *)tsqr_batched_bf16_kernel;
+}
+}  // namespace
+
+// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); `warps` counts bulk warps (+1 reducer).
+cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
+    return cudaFuncSetAttribute(batched_fn(dtype), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes);
+}
+
+int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_fn(dtype), (warps + 1) * 32,
+                                                      smem_bytes) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, size_t smem_bytes,
+                           cudaStream_t stream) {
+    const int threads = (warps + 1) * 32;
+    if (dtype == 0)
+        tsqr_batched_f64_kernel<<<grid, threads, smem_bytes, stream>>>(b);
+    else if (dtype == 1)
+        tsqr_batched_f32_kernel<<<grid, threads, smem_bytes, stream>>>(b);
+    else
+        tsqr_batched_bf16_kernel<<<grid, threads, smem_bytes, stream>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace tsqr

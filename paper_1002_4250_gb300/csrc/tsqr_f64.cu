@@ -5,7 +5,7 @@
 namespace tsqr {
 
 __global__ void __launch_bounds__(256, 1) tsqr_f64_kernel(const F64Args a) {
-    leaf_tree_body<double, double>(a, a.A, a.ldS, a.ldS * a.n);
+    leaf_tree_job<double, double>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
 }
 
 // One tree node: R = qr(R1, R2) (Table 3), optionally sign-normalized.

@@ -23,9 +23,9 @@ constexpr int kMaxN = 128;
 constexpr int kMaxLevels = 48;
 constexpr int kSegStride = 32 + kMaxN;  // segment slots per warp (lanes + column boundaries)
 
-// Binary reduction tree over `count[0]` leaves: level l has count[l] nodes; node t of level
-// l+1 has children 2t and 2t+1 of level l (an odd last child is promoted unchanged).  Node
-// (l, t) has the global id offset[l] + t.
+// Binary reduction tree over `count[0]` leaves (host side): level l has count[l] nodes; node t
+// of level l+1 has children 2t and 2t+1 of level l (an odd last child is promoted unchanged).
+// Node (l, t) has the global id offset[l] + t; the kernels walk the same levels incrementally.
 struct TreeShape {
     int levels;
     int count[kMaxLevels];
@@ -42,8 +42,7 @@ struct F64Args {
     int h;          // rows folded per step of a leaf ("chunk"): h <= hs
     int hs;         // rows of S in shared memory: >= max(h, n), a multiple of 32 x warps
     int blk;        // rows per inner-loop block: divides hs / (32 x warps)
-    int ldS;        // leading dimension of S in shared memory (doubles)
-    TreeShape tree;
+    int ldS;        // leading dimension of S in shared memory (elements)
     double *slots;          // one n x n column-major slot per tree node (workspace)
     unsigned int *counters; // one arrival counter per tree node (workspace, zeroed per call)
     double *R;              // output, column-major n x n, ld ldr
@@ -59,6 +58,37 @@ struct MixedArgs {
     int ldSd;       // leading dimension of the FP64 view of S (tree operator)
     int s_doubles;  // size of the S region in doubles
 };
+
+// One problem of a varlen batch, as the batched kernel sees it (device memory).
+struct BatchProblem {
+    const void *A;           // column-major m x n, leading dimension lda (FP64, FP32 or BF16)
+    int64_t m, lda;
+    double *R;               // column-major n x n, leading dimension n
+    int64_t unit, nunits;    // rows per leaf, number of leaves
+    int n, h, hs, blk, ldS;  // as in F64Args
+    int nleaves;
+    int64_t slot_off;        // first tree slot of this problem (doubles into the slots buffer)
+    int64_t cnt_off;         // first tree counter of this problem
+};
+
+struct BatchArgs {
+    const BatchProblem *probs;
+    const int2 *items;       // (problem, leaf) work items, in the order CTAs take them
+    int nitems;
+    unsigned int *queue;     // work-queue head, zeroed per call
+    double *slots;
+    unsigned int *counters;  // zeroed per call
+    int *status;
+};
+
+// FP64 view of the mixed kernels' S region (tree operator): odd leading dimension >= n.
+__host__ __device__ inline int mixed_ldsd_of(int n) { return (n % 2 == 0) ? n + 1 : n; }
+// Size in doubles of the mixed kernels' S region: the FP32 chunk or the FP64 triangle.
+__host__ __device__ inline int mixed_s_doubles_of(int n, int ldS) {
+    const int leaf = (ldS * n + 1) / 2;
+    const int tree = mixed_ldsd_of(n) * n;
+    return leaf > tree ? leaf : tree;
+}
 
 // Shared-memory carve-up (offsets in doubles), identical on host and device.  The S region
 // holds s_doubles doubles.

@@ -492,12 +492,14 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // combines [R_left; R_right] (left = lower index, always on top) and climbs on; the first
 // returns.  No CTA ever waits for another, and the operand order depends only on the indices.
 // ------------------------------------------------------------------------------------------
-// T: leaf storage/arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading
-// dimension a.ldS); the tree operator works in the same memory viewed as FP64 with leading
-// dimension ldSd.
+// One leaf of one problem: fold the leaf's rows into R, then climb the problem's binary tree
+// (level l has ceil(nleaves / 2^l) nodes, stored level after level).  T: leaf storage and
+// arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading dimension a.ldS); the
+// tree operator works in the same memory viewed as FP64 with leading dimension ldSd.  Returns
+// when the CTA is the first of two children to arrive at a node, or after writing the root.
 template <typename T, typename Tin>
-__device__ __forceinline__ void leaf_tree_body(const F64Args &a, const Tin *A, const int ldSd,
-                                               const int s_doubles) {
+__device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, const int ldSd,
+                                              const int s_doubles, const int leaf) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n;
     const SmemLayout L = smem_layout_s(n, s_doubles, blockDim.x >> 5);
@@ -510,7 +512,6 @@ __device__ __forceinline__ void leaf_tree_body(const F64Args &a, const Tin *A, c
     double *npart = smem + L.npart;
     unsigned int *flag = reinterpret_cast<unsigned int *>(smem + L.scal);
 
-    const int leaf = blockIdx.x;
     for (int i = threadIdx.x; i < n * (n + 1) / 2; i += blockDim.x) Rp[i] = 0.0;
 
     // rows of this leaf, folded in chunks of h rows
@@ -554,29 +555,29 @@ __device__ __forceinline__ void leaf_tree_body(const F64Args &a, const Tin *A, c
         }
     }
 
-    int level = 0, t = leaf;
+    int cnt = a.nleaves, off = 0, t = leaf;  // nodes and first node id of the current level
     for (;;) {
-        const int cnt = a.tree.count[level];
         if (cnt == 1) {
             store_normalized(Rp, n, a.R, a.ldr, a.status);
             return;
         }
+        const int next_off = off + cnt, next_cnt = (cnt + 1) >> 1;
         const int sib = t ^ 1;
         if (sib >= cnt) {  // odd last node: promoted unchanged
-            ++level;
+            off = next_off;
+            cnt = next_cnt;
             t >>= 1;
             continue;
         }
-        double *mine = a.slots + (size_t)(a.tree.offset[level] + t) * n * n;
+        double *mine = a.slots + (size_t)(off + t) * n * n;
         store_packed(Rp, n, mine, n);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0)
-            flag[0] = atomicAdd(&a.counters[a.tree.offset[level + 1] + (t >> 1)], 1u);
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + (t >> 1)], 1u);
         __syncthreads();
         if (flag[0] == 0) return;  // the sibling combines
         __threadfence();
-        const double *other = a.slots + (size_t)(a.tree.offset[level] + sib) * n * n;
+        const double *other = a.slots + (size_t)(off + sib) * n * n;
         if (t & 1) {
             // this CTA holds the right (lower) operand: it becomes S, the left one comes to Rp
             for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -590,7 +591,8 @@ __device__ __forceinline__ void leaf_tree_body(const F64Args &a, const Tin *A, c
         }
         __syncthreads();
         fold_tri(Sd, ldSd, Rp, f, seg, npart, n);
-        ++level;
+        off = next_off;
+        cnt = next_cnt;
         t >>= 1;
     }
 }

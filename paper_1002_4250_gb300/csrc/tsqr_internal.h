@@ -31,6 +31,12 @@ int mixed_blocks_per_sm(int warps, size_t smem_bytes);
 cudaError_t mixed_launch(const MixedArgs &a, bool bf16, int warps, size_t smem_bytes,
                          cudaStream_t stream);
 
+// Batched path (tsqr_batched.cu); dtype 0 FP64, 1 FP32, 2 BF16; `warps` counts bulk warps.
+cudaError_t batched_prepare(int dtype, size_t smem_bytes);
+int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes);
+cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, size_t smem_bytes,
+                           cudaStream_t stream);
+
 // The AUTO plan of tsqr_r as kernel arguments (tsqr_api.cu); A, R, workspace and status
 // pointers are left for the caller.
 tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,

@@ -7,22 +7,18 @@
 namespace tsqr {
 
 __global__ void __launch_bounds__(256, 1) tsqr_mixed_f32_kernel(const MixedArgs a) {
-    leaf_tree_body<float, float>(a.base, static_cast<const float *>(a.A), a.ldSd, a.s_doubles);
+    leaf_tree_job<float, float>(a.base, static_cast<const float *>(a.A), a.ldSd, a.s_doubles,
+                                blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256, 1) tsqr_mixed_bf16_kernel(const MixedArgs a) {
-    leaf_tree_body<float, __nv_bfloat16>(a.base, static_cast<const __nv_bfloat16 *>(a.A), a.ldSd,
-                                         a.s_doubles);
+    leaf_tree_job<float, __nv_bfloat16>(a.base, static_cast<const __nv_bfloat16 *>(a.A), a.ldSd,
+                                        a.s_doubles, blockIdx.x);
 }
 
-// FP64 view of the S region for the tree operator: an n x n triangle, odd leading dimension.
-int mixed_ldsd(int n) { return (n % 2 == 0) ? n + 1 : n; }
+int mixed_ldsd(int n) { return mixed_ldsd_of(n); }
 
-int mixed_s_doubles(int n, int ldS) {
-    const int leaf = (ldS * n + 1) / 2;  // FP32 chunk, in doubles
-    const int tree = mixed_ldsd(n) * n;
-    return leaf > tree ? leaf : tree;
-}
+int mixed_s_doubles(int n, int ldS) { return mixed_s_doubles_of(n, ldS); }
 
 // `warps` counts bulk warps; the kernels launch one more, the reducer warp.
 size_t mixed_smem_bytes(int n, int ldS, int warps) {

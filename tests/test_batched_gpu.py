@@ -1,0 +1,162 @@
+"""GPU parity of tsqr_r_batched (varlen batch, one persistent launch) against the CPU oracle,
+problem by problem, through the C ABI.  FP64: every R_i within c(m_i) kappa u ||R_i||_F of the
+oracle's and a Gram residual <= 1e-13; mixed FP32: Gram residual <= 2e-6 (tolerances of the
+single-matrix tests)."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_4250_gb300 as T
+    return T
+
+
+def _c(m):
+    return max(50.0, 2.0 * np.sqrt(max(m, 1)))
+
+
+def _run(T, buf_dev, ms, ns, offs, dtype, prec):
+    import torch
+    es = buf_dev.element_size()
+    base = buf_dev.data_ptr()
+    ptrs = [base + es * offs[i] for i in range(len(ms))]
+    roff = [0]
+    for n in ns:
+        roff.append(roff[-1] + n * n)
+    Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=dtype, prec=prec)
+    torch.cuda.synchronize()
+    return Rp.cpu().numpy(), roff
+
+
+def _problem(buf_cpu, offs, ms, ns, i):
+    m, n = ms[i], ns[i]
+    return np.asarray(buf_cpu[offs[i]:offs[i] + m * n], dtype=np.float64).reshape(n, m).T
+
+
+def _edge_batch():
+    import torch
+    g = torch.Generator().manual_seed(7)
+    ms = [0, 1, 2, 5, 7, 63, 64, 65, 300, 1000, 4097, 12345, 3, 129, 50000, 256]
+    ns = [4, 1, 3, 8, 7, 16, 64, 64, 32, 128, 5, 24, 12, 128, 64, 16]
+    offs = [0]
+    for m, n in zip(ms, ns):
+        offs.append(offs[-1] + m * n)
+    buf = torch.randn(offs[-1], generator=g, dtype=torch.float64)
+    return buf, ms, ns, offs
+
+
+def test_batched_fp64_edge_cases(oracle, T):
+    buf, ms, ns, offs = _edge_batch()
+    R, roff = _run(T, buf.cuda(), ms, ns, offs, T.F64, T.PREC_F64)
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Ri = R[roff[i]:roff[i + 1]].reshape(n, n).T
+        A = _problem(buf.numpy(), offs, ms, ns, i)
+        Ro = oracle.householder_r(A)
+        assert np.all(np.isfinite(Ri)) and np.all(np.tril(Ri, -1) == 0), i
+        if m == 0:
+            assert np.all(Ri == 0)
+            continue
+        assert oracle.gram_residual(A, Ri) <= 1e-13, i
+        if m >= n:
+            kap = oracle.kappa_from_r(Ro)
+            np.testing.assert_allclose(Ri, Ro, rtol=0, atol=_c(m) * kap * U * np.linalg.norm(Ro))
+
+
+def test_batched_matches_single_calls(T):
+    import torch
+    buf, ms, ns, offs = _edge_batch()
+    bd = buf.cuda()
+    R, roff = _run(T, bd, ms, ns, offs, T.F64, T.PREC_F64)
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        if m == 0:
+            continue
+        A = bd[offs[i]:offs[i] + m * n].view(n, m).T
+        Rs = T.tsqr_r(A).cpu().numpy()
+        Ri = R[roff[i]:roff[i + 1]].reshape(n, n).T
+        s = np.linalg.svd(Rs, compute_uv=False)
+        kap = s[0] / s[-1] if s[-1] > 0 else 1e16
+        if m >= n and kap < 1e12:
+            np.testing.assert_allclose(Ri, Rs, rtol=0, atol=_c(m) * kap * U * np.linalg.norm(Rs))
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+def test_batched_mixed(oracle, T, dtype):
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(48, 512, 40000, seed=1)
+    low = buf.to(getattr(torch, dtype))
+    code = T.F32 if dtype == "float32" else T.BF16
+    R, roff = _run(T, low.cuda(), ms, ns, offs, code, T.PREC_MIXED)
+    wide = low.to(torch.float64).numpy()
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Ri = R[roff[i]:roff[i + 1]].reshape(n, n).T
+        A = _problem(wide, offs, ms, ns, i)
+        assert oracle.gram_residual(A, Ri) <= 2e-6, i
+
+
+def test_batched_varlen_distribution(oracle, T):
+    """The varlen workload's distribution (m log-uniform in [512, 262144], n in {8,16,32,64})
+    with 256 problems; every problem's Gram residual, and the oracle's R on a sample."""
+    buf, ms, ns, offs = workloads.varlen_batch(256, 512, 262144, seed=0)
+    R, roff = _run(T, buf.cuda(), ms, ns, offs, T.F64, T.PREC_F64)
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(len(ms), size=12, replace=False).tolist())
+    bn = buf.numpy()
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Ri = R[roff[i]:roff[i + 1]].reshape(n, n).T
+        A = _problem(bn, offs, ms, ns, i)
+        assert oracle.gram_residual(A, Ri, nthreads=16) <= 1e-13, i
+        if i in sample:
+            Ro = oracle.householder_r(A, nthreads=16)
+            kap = oracle.kappa_from_r(Ro)
+            np.testing.assert_allclose(Ri, Ro, rtol=0, atol=_c(m) * kap * U * np.linalg.norm(Ro))
+
+
+def test_batched_bit_reproducible_and_graph_capture(T):
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(64, 512, 20000, seed=2)
+    bd = buf.cuda()
+    R1, roff = _run(T, bd, ms, ns, offs, T.F64, T.PREC_F64)
+    R2, _ = _run(T, bd, ms, ns, offs, T.F64, T.PREC_F64)
+    assert np.array_equal(R1, R2)
+    # capture the same call (descriptors already resident) in a CUDA graph and replay it
+    es = bd.element_size()
+    ptrs = [bd.data_ptr() + es * o for o in offs[:-1]]
+    Rg = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        T.tsqr_r_batched(ptrs, ms, ns, roff, Rg)   # warm-up on the capture stream
+    torch.cuda.synchronize()
+    Rg.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        T.tsqr_r_batched(ptrs, ms, ns, roff, Rg)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(Rg.cpu().numpy(), R1)
+
+
+def test_batched_argument_errors(T):
+    import ctypes
+    import torch
+    Rp = torch.zeros(100, dtype=torch.float64, device="cuda")
+    A = torch.zeros(1000, dtype=torch.float64, device="cuda")
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_r_batched([A.data_ptr()], [100], [8], [0, 10], Rp)   # room for 10 < 64 entries
+    assert e.value.status == T.ERR_INVALID_ARG
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_r_batched([A.data_ptr()], [5], [129], [0, 129 * 129], Rp)
+    assert e.value.status == T.ERR_UNSUPPORTED
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_r_batched([A.data_ptr()], [5], [4], [0, 16], Rp, dtype=T.F32, prec=T.PREC_F64)
+    assert e.value.status == T.ERR_INVALID_ARG

@@ -65,11 +65,13 @@ def conditioned(m: int, n: int, kappa: float, seed: int = 0, dtype=torch.float64
 
 
 def varlen_batch(count: int, m_lo: int, m_hi: int, n_choices=(8, 16, 32, 64), seed: int = 0,
-                 dtype=torch.float64):
+                 dtype=torch.float64, device="cpu"):
     """Packed varlen batch.
 
     Returns (buf, ms, ns, offs): ``buf`` a flat tensor holding every A_i column-major with
-    lda_i = m_i back to back, ``offs[i]`` the element offset of A_i in ``buf``."""
+    lda_i = m_i back to back, ``offs[i]`` the element offset of A_i in ``buf``.  With a CUDA
+    ``device`` the sizes are drawn as on the CPU but the entries come from one device-side
+    N(0,1) draw (for large batches)."""
     g = torch.Generator().manual_seed(seed)
     u = torch.rand(count, generator=g, dtype=torch.float64)
     ms = torch.round(torch.exp(math.log(m_lo) + u * (math.log(m_hi) - math.log(m_lo))))
@@ -79,6 +81,11 @@ def varlen_batch(count: int, m_lo: int, m_hi: int, n_choices=(8, 16, 32, 64), se
     sizes = ms * ns
     offs = torch.zeros(count + 1, dtype=torch.int64)
     offs[1:] = torch.cumsum(sizes, 0)
+    if device != "cpu":
+        gd = torch.Generator(device=device).manual_seed(seed)
+        buf = torch.randn(int(offs[-1]), generator=gd, dtype=torch.float64, device=device)
+        return (buf if dtype == torch.float64 else buf.to(dtype)), ms.tolist(), ns.tolist(), \
+            offs.tolist()
     buf = torch.empty(int(offs[-1]), dtype=torch.float64)
     for i in range(count):
         buf[int(offs[i]):int(offs[i + 1])] = torch.randn(int(sizes[i]), generator=g,
