@@ -124,13 +124,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over the ranks (the job's time is its slowest replica's)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(local_ms, steps, world, flops_per_step):
+    """Whole-job GFLOP/s: every replica's flops over the slowest replica's time, and that time."""
+    ms = max_over_ranks(local_ms, world)
+    return world * flops_per_step * steps / (ms / 1e3) / 1e9, ms
 
 
 def run_cpu_baseline(At_cpu, threads, R_gpu, target_s=10.0, max_reps=40):
@@ -229,10 +237,9 @@ def bench_ours(args, world, rank, local):
         barrier(world)
     ms_local = start.elapsed_time(end)
     per_launch = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(ms_local, world)
+    value, ms = job_value(ms_local, args.steps, world, fl)
     status = T.tsqr_get_device_status()
     ms_step = ms / args.steps
-    value = world * fl * args.steps / (ms / 1e3) / 1e9
 
     # end to end through the public call with HOST buffers: pinned H2D of A, the call, D2H of R
     A_host = At_cpu.pin_memory()
