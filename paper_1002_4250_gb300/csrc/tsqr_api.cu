@@ -127,9 +127,7 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
-    // FP64: 4 bulk warps, the FP64 pipe being the limit; mixed: 8, the FP32 bulk being
-    // latency-bound and wanting more warps in flight
-    p->warps = mixed ? 8 : 4;
+    p->warps = 4;
     if (over && over->warps) {
         if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
@@ -144,9 +142,8 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     const int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
     if (!mixed) {
         // two CTAs per SM hide each other's per-column serial work; take one per SM only when
-        // two would leave fewer than 2 rows per lane, except for wide panels (n >= 48), whose
-        // per-column work is large enough for r = 1
-        r_fit = (r2 >= 2 || (r2 >= 1 && n >= 48)) ? r2 : std::max(r2, r1);
+        // two would leave fewer than 2 rows per lane
+        r_fit = (r2 >= 2) ? r2 : std::max(r2, r1);
     } else {
         // the FP32 bulk is cheap: what counts is the number of rows sharing each reflector's
         // serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs)

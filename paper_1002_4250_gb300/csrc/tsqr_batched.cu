@@ -43,13 +43,13 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
     }
 }
 
-__global__ void __launch_bounds__(256, 2) tsqr_batched_f64_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(256, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
     batched_body<double, double>(b);
 }
-__global__ void __launch_bounds__(256, 2) tsqr_batched_f32_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(256, 1) tsqr_batched_f32_kernel(const BatchArgs b) {
     batched_body<float, float>(b);
 }
-__global__ void __launch_bounds__(256, 2) tsqr_batched_bf16_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(256, 1) tsqr_batched_bf16_kernel(const BatchArgs b) {
     batched_body<float, __nv_bfloat16>(b);
 }
 
@@ -61,7 +61,7 @@ const void *batched_fn(int dtype) {
 }
 }  // namespace
 
-// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); `warps` counts bulk warps (+kReducers).
+// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); `warps` counts bulk warps (+1 reducer).
 cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
     return cudaFuncSetAttribute(batched_fn(dtype), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes);
@@ -69,7 +69,7 @@ cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
 
 int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_fn(dtype), (warps + kReducers) * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_fn(dtype), (warps + 1) * 32,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
@@ -77,7 +77,7 @@ int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes) {
 
 cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, size_t smem_bytes,
                            cudaStream_t stream) {
-    const int threads = (warps + kReducers) * 32;
+    const int threads = (warps + 1) * 32;
     if (dtype == 0)
         tsqr_batched_f64_kernel<<<grid, threads, smem_bytes, stream>>>(b);
     else if (dtype == 1)

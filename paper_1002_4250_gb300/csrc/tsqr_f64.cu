@@ -4,7 +4,7 @@
 
 namespace tsqr {
 
-__global__ void __launch_bounds__(384, 1) tsqr_f64_kernel(const F64Args a) {
+__global__ void __launch_bounds__(256, 1) tsqr_f64_kernel(const F64Args a) {
     leaf_tree_job<double, double>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
 }
 
@@ -31,9 +31,9 @@ __global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const d
 // ------------------------------------------------------------------------------------------
 // host-side launchers
 // ------------------------------------------------------------------------------------------
-// `warps` counts the leaf kernel's bulk warps; it launches kReducers more, the reducers.
+// `warps` counts the leaf kernel's bulk warps; it launches one more, the reducer warp.
 size_t f64_smem_bytes(int n, int hs, int ldS, int warps) {
-    return sizeof(double) * (size_t)smem_layout(n, hs, ldS, warps + kReducers).total;
+    return sizeof(double) * (size_t)smem_layout(n, hs, ldS, warps + 1).total;
 }
 
 cudaError_t f64_prepare(size_t smem_bytes) {
@@ -47,14 +47,14 @@ cudaError_t f64_prepare(size_t smem_bytes) {
 
 int f64_blocks_per_sm(int warps, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tsqr_f64_kernel, (warps + kReducers) * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tsqr_f64_kernel, (warps + 1) * 32,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
 }
 
 cudaError_t f64_launch(const F64Args &a, int warps, size_t smem_bytes, cudaStream_t stream) {
-    tsqr_f64_kernel<<<a.nleaves, (warps + kReducers) * 32, smem_bytes, stream>>>(a);
+    tsqr_f64_kernel<<<a.nleaves, (warps + 1) * 32, smem_bytes, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -20,10 +20,6 @@
 
 namespace tsqr {
 
-// Reducer warps of a leaf CTA (one per SM sub-partition); step J's duty falls to warp
-// Wb + J mod kReducers, so the per-column FP64 work visits every sub-partition in turn.
-constexpr int kReducers = 4;
-
 // ------------------------------------------------------------------------------------------
 // Asynchronous global -> shared copies (cp.async of 8 or 4 bytes; src_bytes = 0 zero-fills).
 // ------------------------------------------------------------------------------------------
@@ -213,18 +209,17 @@ __device__ __forceinline__ void apply_reflector(const int lane, const int n, con
     if (lane == 0) Rp[ro] = h.beta;
 }
 
-// Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warps Wb..Wb+kReducers-1 are
-// reducers, step J's duty falling to warp Wb + J mod kReducers.
+// Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warp Wb is the reducer.
 // Every bulk lane owns r rows of its warp's block (Hw = 32 r) and a phase-B run of U r items
 // starting at item lane * U r; runs and column boundaries are multiples of r, so blocks of B
 // items (B divides r) never straddle a column: the inner loop has no per-item bookkeeping and
 // all lanes stay in lockstep.  The reducer forms reflector J's scalars (its long FP64 chain)
 // while the bulk warps run phase B, then sums the dot products and updates R and f:
-//   A (bulk) | barrier | B (bulk) || scalars (duty reducer) | barrier | dots, R, f | barrier.
+//   A (bulk) | barrier | B (bulk) || scalars (reducer) | barrier | dots, R, f (reducer) | barrier.
 // The next chunk of rows streams into columns no longer read (J-2 at step J) by cp.async when
 // A's type is T; a BF16 A is widened after the fold instead.  T = double is the FP64 path;
-// T = float the mixed path, where the bulk arithmetic and the sums of the dot-product partials
-// are FP32 and the reflector norms and scalars, R and f stay FP64.
+// T = float the mixed path, where only the bulk arithmetic is FP32 and the reflector scalars,
+// partial-sum reductions, R and f stay FP64.
 template <typename T, typename Tin, int B>
 __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, const int hs,
                                           double *__restrict__ Rp, double *__restrict__ f,
@@ -233,7 +228,8 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
                                           const Chunk<Tin> pf) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int Wb = (blockDim.x >> 5) - kReducers;
+    const int Wb = (blockDim.x >> 5) - 1;
+    const bool reducer = (warp == Wb);
     const int Hw = hs / Wb;
     const int r = Hw >> 5;
     const int r0 = warp * Hw;
@@ -242,13 +238,11 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
     for (int J = 0; J < n; ++J) {
         if (Copy<T, Tin>::kAsync && pf.src && J >= 2) load_column(S, ldS, hs, pf, J - 2);
         const int U = n - J - 1;
-        const bool bulk = warp < Wb;
-        const bool reducer = (warp == Wb + J % kReducers);
         T *SJ = S + (size_t)J * ldS + r0;
         const T *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS + r0;
 
         // ---- A: column J gets reflector J-1; per-lane partial squared norm of column J
-        if (bulk) {
+        if (!reducer) {
             T nacc = (T)0;
             if (J > 0) {
                 const T fJ = (T)f[J];
@@ -273,7 +267,7 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
         if (reducer) {
             // ---- reflector J's scalars, overlapping phase B
             h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, Wb, npart));
-        } else if (bulk && U > 0) {
+        } else if (U > 0) {
             // ---- B: fused update by reflector J-1 and dots with column J
             const int run = U * r;
             const int p = lane * run;
@@ -321,12 +315,10 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
 
         // ---- reducer: dot products in a fixed order, row J of R, factors f[k] for k > J
         if (reducer) {
-            // partial dot products are summed in the leaf's type T: FP64 on the FP64 path, FP32
-            // (trailing-update arithmetic) on the mixed path
             for (int id = lane; id < 32 + U; id += 32) {
-                T t = (T)seg_all[id];
-                for (int w = 1; w < Wb; ++w) t += (T)seg_all[w * kSegStride + id];
-                tot[id] = (double)t;
+                double t = seg_all[id];
+                for (int w = 1; w < Wb; ++w) t += seg_all[w * kSegStride + id];
+                tot[id] = t;
             }
             __syncwarp();
             const int Nw = U * Hw;
@@ -334,9 +326,9 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
             for (int kk = lane; kk < U; kk += 32) {
                 const int la = (32 * (kk * Hw + 1) - 1) / Nw;
                 const int lb = (32 * (kk + 1) * Hw - 1) / Nw;
-                T d = (T)tot[kk + la];
-                for (int l = la + 1; l <= lb; ++l) d += (T)tot[kk + l];
-                dk[kk] = (double)d;
+                double d = tot[kk + la];
+                for (int l = la + 1; l <= lb; ++l) d += tot[kk + l];
+                dk[kk] = d;
             }
             __syncwarp();
             apply_reflector(lane, n, J, h, Rp, f, dk);
