@@ -61,7 +61,7 @@ struct F64Plan {
     int warps = 4;
     int64_t unit = 0, nunits = 0;  // rows per work unit (tile or slab) and their count
     int h = 0, hs = 0, ldS = 0;    // chunk rows, shared-memory rows, leading dimension
-    int blk = 1;                   // inner-loop block of the leaf fold
+    int blk = 1, vec = 1;          // inner-loop block and vector width of the leaf fold
     int nleaves = 0;
     size_t smem = 0;
     TreeShape shape{};
@@ -86,7 +86,16 @@ tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
     return TSQR_SUCCESS;
 }
 
-int ld_for(int hs) { return (hs % 2 == 0) ? hs + 1 : hs; }
+// Leading dimension of the chunk in shared memory for accesses of `vec` elements: a multiple of
+// vec whose quotient by vec is odd, so that the lanes' accesses into different columns at the
+// same row fall into different banks.
+int ld_for(int hs, int vec = 1) {
+    const int q = (hs + vec - 1) / vec;
+    return vec * ((q % 2 == 0) ? q + 1 : q);
+}
+
+// Upper bound of ld_for over the vector widths, for shared-memory budgets.
+int ld_bound(int hs) { return hs + 8; }
 
 
 // Rows per lane whose inner loop blocks well: a multiple of 4 or 3 when r >= 3.
@@ -96,7 +105,21 @@ int good_r(int r) {
     return r;
 }
 
-int block_for(int r) { return (r % 4 == 0) ? 4 : (r % 3 == 0) ? 3 : (r % 2 == 0) ? 2 : 1; }
+// Inner-loop block (rows, a divisor of the rows per lane r) and vector width (elements per
+// shared-memory access) of the leaf fold; the pairs are those the kernels are instantiated for.
+void block_for(int r, bool fp32, int *blk, int *vec) {
+    if (fp32) {
+        if (r % 8 == 0) { *blk = 8; *vec = 4; }
+        else if (r % 4 == 0) { *blk = 4; *vec = 4; }
+        else if (r % 6 == 0) { *blk = 6; *vec = 2; }
+        else if (r % 3 == 0) { *blk = 3; *vec = 1; }
+        else if (r % 2 == 0) { *blk = 2; *vec = 2; }
+        else { *blk = 1; *vec = 1; }
+    } else {
+        *blk = (r % 4 == 0) ? 4 : (r % 3 == 0) ? 3 : (r % 2 == 0) ? 2 : 1;
+        *vec = 1;
+    }
+}
 
 // Plan for the FP64 path (mixed == false) or the mixed path (FP32 chunk in shared memory).
 tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p);
@@ -106,8 +129,8 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
 }
 
 size_t leaf_smem_bytes(int n, int hs, int warps, bool mixed) {
-    return mixed ? mixed_smem_bytes(n, ld_for(hs), warps)
-                 : f64_smem_bytes(n, hs, ld_for(hs), warps);
+    return mixed ? mixed_smem_bytes(n, ld_bound(hs), warps)
+                 : f64_smem_bytes(n, hs, ld_bound(hs), warps);
 }
 
 // Largest r (rows per lane) whose shared memory, with hs = 32 r warps rows, fits `budget`.
@@ -169,8 +192,8 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
         p->unit = p->h;
     }
     if (p->hs < n) return TSQR_ERR_UNSUPPORTED;
-    p->blk = block_for(r);
-    p->ldS = ld_for(p->hs);
+    block_for(r, mixed, &p->blk, &p->vec);
+    p->ldS = ld_for(p->hs, p->vec);
     p->smem = leaf_smem_bytes(n, p->hs, W, mixed);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
     p->nunits = (mm + p->unit - 1) / p->unit;
@@ -249,6 +272,7 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     a.h = p.h;
     a.hs = p.hs;
     a.blk = p.blk;
+    a.vec = p.vec;
     a.ldS = p.ldS;
     a.counters = (unsigned int *)ws->base;
     a.slots = (double *)((char *)ws->base + cnt_bytes);
@@ -288,6 +312,7 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     a.base.h = p.h;
     a.base.hs = p.hs;
     a.base.blk = p.blk;
+    a.base.vec = p.vec;
     a.base.ldS = p.ldS;
     a.base.counters = (unsigned int *)ws->base;
     a.base.slots = (double *)((char *)ws->base + cnt_bytes);
@@ -329,15 +354,17 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     size_t budget = two_per_sm;
     if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2) budget = one_per_sm;
     // per width: chunk rows
-    std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1);
+    std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1), vec_of(TSQR_MAX_N + 1, 1);
     size_t smem = 0;
     for (int32_t i = 0; i < count; ++i) {
         const int n = ns[i];
         if (hs_of[n]) continue;
-        const int r = good_r(max_rows_per_lane_p(n, W, budget, mixed));
+        int r = good_r(max_rows_per_lane_p(n, W, budget, mixed));
+        // the batched mixed kernels are instantiated for blocks (4,4), (2,2) and (1,1)
+        if (mixed && r >= 4) r -= r % 4;
         if (r < 1 || 32 * W * r < n) return TSQR_ERR_UNSUPPORTED;
         hs_of[n] = 32 * W * r;
-        blk_of[n] = block_for(r);
+        block_for(r, mixed, &blk_of[n], &vec_of[n]);
         smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], W, mixed));
     }
     if (batched_prepare(dt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -362,7 +389,8 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         P.n = n;
         P.hs = hs_of[n];
         P.blk = blk_of[n];
-        P.ldS = ld_for(P.hs);
+        P.vec = vec_of[n];
+        P.ldS = ld_for(P.hs, P.vec);
         const int64_t chunks = std::max<int64_t>(1, (int64_t)(target / ((double)n * n * P.hs)));
         P.unit = chunks * P.hs;
         P.h = P.hs;
@@ -447,6 +475,7 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
     a->h = p.h;
     a->hs = p.hs;
     a->blk = p.blk;
+    a->vec = p.vec;
     a->ldS = p.ldS;
     *warps = p.warps;
     *smem = p.smem;

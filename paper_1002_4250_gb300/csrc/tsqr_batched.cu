@@ -29,17 +29,29 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
         a.h = P.h;
         a.hs = P.hs;
         a.blk = P.blk;
+        a.vec = P.vec;
         a.ldS = P.ldS;
         a.slots = b.slots + P.slot_off;
         a.counters = b.counters + P.cnt_off;
         a.R = P.R;
         a.ldr = P.n;
         a.status = b.status;
-        if constexpr (sizeof(T) == 8)
-            leaf_tree_job<T, Tin>(a, static_cast<const Tin *>(P.A), P.ldS, P.ldS * P.n, w.y);
-        else
-            leaf_tree_job<T, Tin>(a, static_cast<const Tin *>(P.A), mixed_ldsd_of(P.n),
-                                  mixed_s_doubles_of(P.n, P.ldS), w.y);
+        const Tin *A = static_cast<const Tin *>(P.A);
+        if constexpr (sizeof(T) == 8) {
+            switch (P.blk) {
+                case 4: leaf_tree_job<T, Tin, 4, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
+                case 3: leaf_tree_job<T, Tin, 3, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
+                case 2: leaf_tree_job<T, Tin, 2, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
+                default: leaf_tree_job<T, Tin, 1, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
+            }
+        } else {
+            const int ldSd = mixed_ldsd_of(P.n), sd = mixed_s_doubles_of(P.n, P.ldS);
+            switch (P.blk * 10 + P.vec) {
+                case 44: leaf_tree_job<T, Tin, 4, 4, true>(a, A, ldSd, sd, w.y); break;
+                case 22: leaf_tree_job<T, Tin, 2, 2, true>(a, A, ldSd, sd, w.y); break;
+                default: leaf_tree_job<T, Tin, 1, 1, true>(a, A, ldSd, sd, w.y); break;
+            }
+        }
     }
 }
 

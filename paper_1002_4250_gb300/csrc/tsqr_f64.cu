@@ -4,9 +4,22 @@
 
 namespace tsqr {
 
+template <int B>
 __global__ void __launch_bounds__(256, 1) tsqr_f64_kernel(const F64Args a) {
-    leaf_tree_job<double, double>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
+    leaf_tree_job<double, double, B, 1, false>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
 }
+
+// The FP64 leaf is instantiated for blocks of 1, 2, 3 and 4 rows (scalar accesses).
+namespace {
+const void *f64_fn(int blk) {
+    switch (blk) {
+        case 4: return (const void *)tsqr_f64_kernel<4>;
+        case 3: return (const void *)tsqr_f64_kernel<3>;
+        case 2: return (const void *)tsqr_f64_kernel<2>;
+        default: return (const void *)tsqr_f64_kernel<1>;
+    }
+}
+}  // namespace
 
 // One tree node: R = qr(R1, R2) (Table 3), optionally sign-normalized.
 __global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const double *R1, int64_t ld1,
@@ -37,24 +50,31 @@ size_t f64_smem_bytes(int n, int hs, int ldS, int warps) {
 }
 
 cudaError_t f64_prepare(size_t smem_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(tsqr_f64_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
+    for (int b = 1; b <= 4; ++b) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            f64_fn(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(tsqr_f64_combine_kernel,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 int f64_blocks_per_sm(int warps, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tsqr_f64_kernel, (warps + 1) * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f64_fn(3), (warps + 1) * 32,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
 }
 
 cudaError_t f64_launch(const F64Args &a, int warps, size_t smem_bytes, cudaStream_t stream) {
-    tsqr_f64_kernel<<<a.nleaves, (warps + 1) * 32, smem_bytes, stream>>>(a);
+    const dim3 grid(a.nleaves), block((warps + 1) * 32);
+    switch (a.blk) {
+        case 4: tsqr_f64_kernel<4><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 3: tsqr_f64_kernel<3><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 2: tsqr_f64_kernel<2><<<grid, block, smem_bytes, stream>>>(a); break;
+        default: tsqr_f64_kernel<1><<<grid, block, smem_bytes, stream>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

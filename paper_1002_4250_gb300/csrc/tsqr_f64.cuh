@@ -42,6 +42,7 @@ struct F64Args {
     int h;          // rows folded per step of a leaf ("chunk"): h <= hs
     int hs;         // rows of S in shared memory: >= max(h, n), a multiple of 32 x warps
     int blk;        // rows per inner-loop block: divides hs / (32 x warps)
+    int vec;        // elements per shared-memory access in that loop (divides blk and ldS)
     int ldS;        // leading dimension of S in shared memory (elements)
     double *slots;          // one n x n column-major slot per tree node (workspace)
     unsigned int *counters; // one arrival counter per tree node (workspace, zeroed per call)
@@ -65,7 +66,7 @@ struct BatchProblem {
     int64_t m, lda;
     double *R;               // column-major n x n, leading dimension n
     int64_t unit, nunits;    // rows per leaf, number of leaves
-    int n, h, hs, blk, ldS;  // as in F64Args
+    int n, h, hs, blk, vec, ldS;  // as in F64Args
     int nleaves;
     int64_t slot_off;        // first tree slot of this problem (doubles into the slots buffer)
     int64_t cnt_off;         // first tree counter of this problem

@@ -209,6 +209,199 @@ __device__ __forceinline__ void apply_reflector(const int lane, const int n, con
     if (lane == 0) Rp[ro] = h.beta;
 }
 
+// V consecutive elements of T in one shared-memory access (V*sizeof(T) <= 16 bytes; the
+// address must be V*sizeof(T)-aligned).
+template <int V, typename T>
+__device__ __forceinline__ void ld_vec(const T *p, T *out) {
+    if constexpr (V == 1) {
+        out[0] = p[0];
+    } else if constexpr (sizeof(T) == 8) {
+        static_assert(V == 2, "FP64 vectors are double2");
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+    } else if constexpr (V == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+    } else {
+        static_assert(V == 4, "FP32 vectors are float2 or float4");
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    }
+}
+
+template <int V, typename T>
+__device__ __forceinline__ void st_vec(T *p, const T *in) {
+    if constexpr (V == 1) {
+        p[0] = in[0];
+    } else if constexpr (sizeof(T) == 8) {
+        *reinterpret_cast<double2 *>(p) = make_double2(in[0], in[1]);
+    } else if constexpr (V == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(in[0], in[1]);
+    } else {
+        *reinterpret_cast<float4 *>(p) = make_float4(in[0], in[1], in[2], in[3]);
+    }
+}
+
+template <int B, int V, typename T>
+__device__ __forceinline__ void ld_block(const T *p, T *out) {
+#pragma unroll
+    for (int q = 0; q < B; q += V) ld_vec<V>(p + q, out + q);
+}
+
+// Phase B of step J for one bulk lane, plain form (the FP64 path, whose limit is the FP64
+// pipe): blocks of B rows, loaded, updated, stored and dotted in program order.
+template <typename T, int B>
+__device__ __forceinline__ void phase_b_plain(const int lane, const int J, const int U,
+                                              const int r, const int Hw, const int n,
+                                              T *__restrict__ S, const int ldS, const int r0,
+                                              const T *__restrict__ Sj,
+                                              const T *__restrict__ SJ,
+                                              const double *__restrict__ f,
+                                              double *__restrict__ seg) {
+    const int run = U * r;
+    const int p = lane * run;
+    int kk = p / Hw;
+    int i = p - kk * Hw;
+    T *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
+    T acc = (T)0;
+    if (J > 0) {
+        T fk = (T)f[J + 1 + kk];
+        for (int blk = 0; blk < run; blk += B) {
+            T x[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) x[q] = fmat(-fk, Sj[i + q], Sk[i + q]);
+#pragma unroll
+            for (int q = 0; q < B; ++q) Sk[i + q] = x[q];
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], x[q], acc);
+            i += B;
+            if (i == Hw) {
+                seg[lane + kk] = (double)acc;
+                acc = (T)0;
+                i = 0;
+                ++kk;
+                Sk += ldS;
+                fk = (T)f[min(J + 1 + kk, n - 1)];
+            }
+        }
+    } else {
+        for (int blk = 0; blk < run; blk += B) {
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], Sk[i + q], acc);
+            i += B;
+            if (i == Hw) {
+                seg[lane + kk] = (double)acc;
+                acc = (T)0;
+                i = 0;
+                ++kk;
+                Sk += ldS;
+            }
+        }
+    }
+    if (i != 0) seg[lane + kk] = (double)acc;
+}
+
+// Phase B of step J for one bulk lane, pipelined form (the mixed path, whose FP32 bulk is
+// latency-bound): its run of U r items (column-major over the U trailing
+// columns x its warp's Hw rows), in blocks of B rows that never straddle a column.  Software
+// pipelined: the next block's three operands are loaded before the current block is updated
+// and stored (the two blocks never overlap: different rows, or the next column).
+template <typename T, int B, int V>
+__device__ __forceinline__ void phase_b(const int lane, const int J, const int U, const int r,
+                                        const int Hw, const int n, T *__restrict__ S,
+                                        const int ldS, const int r0, const T *__restrict__ Sj,
+                                        const T *__restrict__ SJ, const double *__restrict__ f,
+                                        double *__restrict__ seg) {
+    const int run = U * r;
+    const int nblk = run / B;
+    const int p = lane * run;
+    int kk = p / Hw;
+    int i = p - kk * Hw;
+    T *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
+    T acc = (T)0;
+    T s[B], b[B];
+    ld_block<B, V>(Sk + i, s);
+    ld_block<B, V>(SJ + i, b);
+    if (J > 0) {
+        T fk = (T)f[J + 1 + kk];
+        T a[B];
+        ld_block<B, V>(Sj + i, a);
+        for (int blk = 0; blk < nblk; ++blk) {
+            int i2 = i + B, kk2 = kk;
+            T *Sk2 = Sk;
+            const bool cross = (i2 == Hw);
+            if (cross) {
+                i2 = 0;
+                ++kk2;
+                Sk2 += ldS;
+            }
+            T a2[B], s2[B], b2[B];
+            if (blk + 1 < nblk) {
+                ld_block<B, V>(Sk2 + i2, s2);
+                ld_block<B, V>(Sj + i2, a2);
+                ld_block<B, V>(SJ + i2, b2);
+            }
+            T x[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) x[q] = fmat(-fk, a[q], s[q]);
+#pragma unroll
+            for (int q = 0; q < B; q += V) st_vec<V>(Sk + i + q, x + q);
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fmat(b[q], x[q], acc);
+            if (cross) {
+                seg[lane + kk] = (double)acc;
+                acc = (T)0;
+                fk = (T)f[min(J + 1 + kk2, n - 1)];
+            }
+            i = i2;
+            kk = kk2;
+            Sk = Sk2;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                a[q] = a2[q];
+                s[q] = s2[q];
+                b[q] = b2[q];
+            }
+        }
+    } else {
+        for (int blk = 0; blk < nblk; ++blk) {
+            int i2 = i + B, kk2 = kk;
+            T *Sk2 = Sk;
+            const bool cross = (i2 == Hw);
+            if (cross) {
+                i2 = 0;
+                ++kk2;
+                Sk2 += ldS;
+            }
+            T s2[B], b2[B];
+            if (blk + 1 < nblk) {
+                ld_block<B, V>(Sk2 + i2, s2);
+                ld_block<B, V>(SJ + i2, b2);
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fmat(b[q], s[q], acc);
+            if (cross) {
+                seg[lane + kk] = (double)acc;
+                acc = (T)0;
+            }
+            i = i2;
+            kk = kk2;
+            Sk = Sk2;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                s[q] = s2[q];
+                b[q] = b2[q];
+            }
+        }
+    }
+    if (i != 0) seg[lane + kk] = (double)acc;
+}
+
 // Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warp Wb is the reducer.
 // Every bulk lane owns r rows of its warp's block (Hw = 32 r) and a phase-B run of U r items
 // starting at item lane * U r; runs and column boundaries are multiples of r, so blocks of B
@@ -220,7 +413,7 @@ __device__ __forceinline__ void apply_reflector(const int lane, const int n, con
 // A's type is T; a BF16 A is widened after the fold instead.  T = double is the FP64 path;
 // T = float the mixed path, where only the bulk arithmetic is FP32 and the reflector scalars,
 // partial-sum reductions, R and f stay FP64.
-template <typename T, typename Tin, int B>
+template <typename T, typename Tin, int B, int V, bool kPipe>
 __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, const int hs,
                                           double *__restrict__ Rp, double *__restrict__ f,
                                           double *__restrict__ seg_all, double *__restrict__ tot,
@@ -269,47 +462,10 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
             h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, Wb, npart));
         } else if (U > 0) {
             // ---- B: fused update by reflector J-1 and dots with column J
-            const int run = U * r;
-            const int p = lane * run;
-            int kk = p / Hw;
-            int i = p - kk * Hw;
-            T *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
-            T acc = (T)0;
-            if (J > 0) {
-                T fk = (T)f[J + 1 + kk];
-                for (int blk = 0; blk < run; blk += B) {
-                    T x[B];
-#pragma unroll
-                    for (int q = 0; q < B; ++q) x[q] = fmat(-fk, Sj[i + q], Sk[i + q]);
-#pragma unroll
-                    for (int q = 0; q < B; ++q) Sk[i + q] = x[q];
-#pragma unroll
-                    for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], x[q], acc);
-                    i += B;
-                    if (i == Hw) {
-                        seg[lane + kk] = (double)acc;
-                        acc = (T)0;
-                        i = 0;
-                        ++kk;
-                        Sk += ldS;
-                        fk = (T)f[min(J + 1 + kk, n - 1)];
-                    }
-                }
-            } else {
-                for (int blk = 0; blk < run; blk += B) {
-#pragma unroll
-                    for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], Sk[i + q], acc);
-                    i += B;
-                    if (i == Hw) {
-                        seg[lane + kk] = (double)acc;
-                        acc = (T)0;
-                        i = 0;
-                        ++kk;
-                        Sk += ldS;
-                    }
-                }
-            }
-            if (i != 0) seg[lane + kk] = (double)acc;
+            if constexpr (kPipe)
+                phase_b<T, B, V>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, f, seg);
+            else
+                phase_b_plain<T, B>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, f, seg);
         }
         __syncthreads();
 
@@ -497,7 +653,7 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading dimension a.ldS); the
 // tree operator works in the same memory viewed as FP64 with leading dimension ldSd.  Returns
 // when the CTA is the first of two children to arrive at a node, or after writing the root.
-template <typename T, typename Tin>
+template <typename T, typename Tin, int B, int V, bool kPipe>
 __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, const int ldSd,
                                               const int s_doubles, const int leaf) {
     extern __shared__ __align__(16) double smem[];
@@ -539,12 +695,7 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
             next.src = A + r1;
             next.rows = (int)((rend - r1 < a.h) ? rend - r1 : a.h);
         }
-        switch (a.blk) {
-            case 4: fold_leaf<T, Tin, 4>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
-            case 3: fold_leaf<T, Tin, 3>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
-            case 2: fold_leaf<T, Tin, 2>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
-            default: fold_leaf<T, Tin, 1>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next); break;
-        }
+        fold_leaf<T, Tin, B, V, kPipe>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next);
         if (next.src) {
             if constexpr (!Copy<T, Tin>::kAsync) {
                 __syncthreads();

@@ -6,15 +6,43 @@
 
 namespace tsqr {
 
-__global__ void __launch_bounds__(256, 1) tsqr_mixed_f32_kernel(const MixedArgs a) {
-    leaf_tree_job<float, float>(a.base, static_cast<const float *>(a.A), a.ldSd, a.s_doubles,
-                                blockIdx.x);
+template <typename Tin, int B, int V>
+__global__ void __launch_bounds__(256, 1) tsqr_mixed_kernel(const MixedArgs a) {
+    leaf_tree_job<float, Tin, B, V, true>(a.base, static_cast<const Tin *>(a.A), a.ldSd,
+                                          a.s_doubles, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256, 1) tsqr_mixed_bf16_kernel(const MixedArgs a) {
-    leaf_tree_job<float, __nv_bfloat16>(a.base, static_cast<const __nv_bfloat16 *>(a.A), a.ldSd,
-                                        a.s_doubles, blockIdx.x);
+// Instances: FP32 or BF16 input x (block, vector) in {(8,4), (6,2), (4,4), (3,1), (2,2), (1,1)}.
+namespace {
+template <typename Tin>
+const void *mixed_fn_t(int blk, int vec) {
+    switch (blk * 10 + vec) {
+        case 84: return (const void *)tsqr_mixed_kernel<Tin, 8, 4>;
+        case 62: return (const void *)tsqr_mixed_kernel<Tin, 6, 2>;
+        case 44: return (const void *)tsqr_mixed_kernel<Tin, 4, 4>;
+        case 31: return (const void *)tsqr_mixed_kernel<Tin, 3, 1>;
+        case 22: return (const void *)tsqr_mixed_kernel<Tin, 2, 2>;
+        default: return (const void *)tsqr_mixed_kernel<Tin, 1, 1>;
+    }
 }
+const void *mixed_fn(bool bf16, int blk, int vec) {
+    return bf16 ? mixed_fn_t<__nv_bfloat16>(blk, vec) : mixed_fn_t<float>(blk, vec);
+}
+constexpr int kVariants[6][2] = {{8, 4}, {6, 2}, {4, 4}, {3, 1}, {2, 2}, {1, 1}};
+
+template <typename Tin>
+void launch_t(const MixedArgs &a, int threads, size_t smem, cudaStream_t stream) {
+    const dim3 grid(a.base.nleaves);
+    switch (a.base.blk * 10 + a.base.vec) {
+        case 84: tsqr_mixed_kernel<Tin, 8, 4><<<grid, threads, smem, stream>>>(a); break;
+        case 62: tsqr_mixed_kernel<Tin, 6, 2><<<grid, threads, smem, stream>>>(a); break;
+        case 44: tsqr_mixed_kernel<Tin, 4, 4><<<grid, threads, smem, stream>>>(a); break;
+        case 31: tsqr_mixed_kernel<Tin, 3, 1><<<grid, threads, smem, stream>>>(a); break;
+        case 22: tsqr_mixed_kernel<Tin, 2, 2><<<grid, threads, smem, stream>>>(a); break;
+        default: tsqr_mixed_kernel<Tin, 1, 1><<<grid, threads, smem, stream>>>(a); break;
+    }
+}
+}  // namespace
 
 int mixed_ldsd(int n) { return mixed_ldsd_of(n); }
 
@@ -26,17 +54,19 @@ size_t mixed_smem_bytes(int n, int ldS, int warps) {
 }
 
 cudaError_t mixed_prepare(size_t smem_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(tsqr_mixed_f32_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tsqr_mixed_bf16_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    for (const auto &v : kVariants)
+        for (int bf = 0; bf < 2; ++bf) {
+            const cudaError_t e = cudaFuncSetAttribute(
+                mixed_fn(bf != 0, v[0], v[1]), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                (int)smem_bytes);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 int mixed_blocks_per_sm(int warps, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tsqr_mixed_f32_kernel, (warps + 1) * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mixed_fn(false, 6, 2), (warps + 1) * 32,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
@@ -44,10 +74,11 @@ int mixed_blocks_per_sm(int warps, size_t smem_bytes) {
 
 cudaError_t mixed_launch(const MixedArgs &a, bool bf16, int warps, size_t smem_bytes,
                          cudaStream_t stream) {
+    const int threads = (warps + 1) * 32;
     if (bf16)
-        tsqr_mixed_bf16_kernel<<<a.base.nleaves, (warps + 1) * 32, smem_bytes, stream>>>(a);
+        launch_t<__nv_bfloat16>(a, threads, smem_bytes, stream);
     else
-        tsqr_mixed_f32_kernel<<<a.base.nleaves, (warps + 1) * 32, smem_bytes, stream>>>(a);
+        launch_t<float>(a, threads, smem_bytes, stream);
     return cudaGetLastError();
 }
 
