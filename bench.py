@@ -8,8 +8,10 @@ Metric: GFLOP/s counted as (2 m n^2 - 2 n^3 / 3) per step; A-read GB/s reported 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (one unblocked Householder QR, FP64) on the host cores,
-each step a bounded row sample of the same workload.  Under torchrun every rank factorizes its
-own replica (the method needs no exchange between GPUs); rank 0 prints one JSON line.
+each step one factorization of the whole workload (about 0.7 s on 16 cores).  Under torchrun
+every rank factorizes its own replica (the method needs no exchange between GPUs); rank 0
+prints one JSON line.  Unless --no-extras, the line also carries the mixed-precision and
+varlen-batched paths measured against the FP64 path ("extras").
 """
 from __future__ import annotations
 

@@ -61,7 +61,8 @@ typedef enum { TSQR_PREC_F64 = 0, TSQR_PREC_MIXED = 1 } tsqr_prec_t;
  *         lower index on top, an odd last node promoted unchanged (Fig. 1 for four leaves).
  * FLAT:   one CTA folds every tile in row order, R <- R([R; A_t]) (the tile algorithms' tree).
  * HYBRID: `ctas` CTAs each fold a contiguous run of tiles flat, their R factors then reduced
- *         by the BINARY rule.  AUTO picks HYBRID.                                            */
+ *         by a fixed tree of `arity` children per node (children in index order, the lowest on
+ *         top; a lone last child promoted unchanged).  AUTO picks HYBRID.                    */
 typedef enum {
     TSQR_TREE_AUTO = 0, TSQR_TREE_BINARY = 1, TSQR_TREE_FLAT = 2, TSQR_TREE_HYBRID = 3
 } tsqr_tree_t;
@@ -72,7 +73,12 @@ typedef struct {
     int32_t tree;       /* tsqr_tree_t                                                     */
     int32_t tile_rows;  /* rows per tile (slab) b; must fit the kernel's shared memory      */
     int32_t ctas;       /* HYBRID: number of leaf CTAs                                      */
-    int32_t warps;      /* warps per CTA (2, 4 or 8)                                         */
+    int32_t warps;      /* bulk warps per CTA (2, 4 or 8)                                    */
+    int32_t arity;      /* children per tree node, 2..8.  BINARY uses 2, the operator of
+                           Table 3; a node with c > 2 children folds their c stacked triangles
+                           in one sweep (the R factor of [R_1; ...; R_c], equal to a sequence of
+                           binary operators by associativity, Section 2).  0 = as many as the
+                           kernel's shared memory holds.                                     */
 } tsqr_plan_t;
 
 typedef void *tsqr_stream_t; /* a cudaStream_t */

@@ -31,9 +31,9 @@ _TREES = {"auto": TREE_AUTO, "binary": TREE_BINARY, "flat": TREE_FLAT, "hybrid":
 
 
 class Plan(ctypes.Structure):
-    """tsqr_plan_t: tree, tile_rows, ctas, warps (zeros mean "choose")."""
+    """tsqr_plan_t: tree, tile_rows, ctas, warps, arity (zeros mean "choose")."""
     _fields_ = [("tree", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("ctas", ctypes.c_int32), ("warps", ctypes.c_int32)]
+                ("ctas", ctypes.c_int32), ("warps", ctypes.c_int32), ("arity", ctypes.c_int32)]
 
 
 _capi = None
@@ -130,9 +130,9 @@ def empty_r(n: int, device=None):
     return torch.empty((n, n), dtype=torch.float64, device=device).T
 
 
-def make_plan(tree="auto", tile_rows=0, ctas=0, warps=0) -> Plan:
+def make_plan(tree="auto", tile_rows=0, ctas=0, warps=0, arity=0) -> Plan:
     return Plan(_TREES[tree] if isinstance(tree, str) else int(tree), int(tile_rows), int(ctas),
-                int(warps))
+                int(warps), int(arity))
 
 
 def tsqr_r(A, R=None, stream=None):

@@ -62,13 +62,15 @@ struct F64Plan {
     int64_t unit = 0, nunits = 0;  // rows per work unit (tile or slab) and their count
     int h = 0, hs = 0, ldS = 0;    // chunk rows, shared-memory rows, leading dimension
     int blk = 1, vec = 1;          // inner-loop block and vector width of the leaf fold
+    int arity = 2;                 // children per tree node
+    int ldSd = 0, s_doubles = 0;   // FP64 view of the S region for the tree operator
     int nleaves = 0;
     size_t smem = 0;
     TreeShape shape{};
     int64_t nodes = 0;
 };
 
-tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
+tsqr_status_t build_tree(int64_t leaves, int arity, TreeShape *t, int64_t *nodes) {
     std::memset(t, 0, sizeof(*t));
     int64_t c = leaves, off = 0;
     int l = 0;
@@ -79,7 +81,7 @@ tsqr_status_t build_tree(int64_t leaves, TreeShape *t, int64_t *nodes) {
         off += c;
         ++l;
         if (c == 1) break;
-        c = (c + 1) / 2;
+        c = (c + arity - 1) / arity;
     }
     t->levels = l;
     *nodes = off;
@@ -214,7 +216,23 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     leaves = std::min<int64_t>(leaves, p->nunits);
     if (leaves < 1 || leaves > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
     p->nleaves = (int)leaves;
-    return build_tree(leaves, &p->shape, &p->nodes);
+    // tree arity: 2 (the paper's binary operator) for the BINARY tree, else as many stacked
+    // triangles as the S region holds (at most 8), unless the plan says otherwise
+    const int s_avail = mixed ? mixed_s_doubles(n, p->ldS) : p->ldS * n;
+    if (over && over->arity < 0) return TSQR_ERR_INVALID_ARG;
+    if (p->tree == TSQR_TREE_BINARY) {
+        p->arity = 2;
+    } else if (over && over->arity > 0) {
+        if (over->arity < 2 || over->arity > 8) return TSQR_ERR_INVALID_ARG;
+        p->arity = over->arity;
+        if (tree_ldsd(n, p->arity) * n > s_avail) return TSQR_ERR_UNSUPPORTED;
+    } else {
+        p->arity = arity_for(n, s_avail);
+    }
+    p->ldSd = mixed ? tree_ldsd(n, p->arity) : p->ldS;
+    p->s_doubles = mixed ? mixed_s_doubles_of(n, p->ldS, p->arity) : p->ldS * n;
+    if (!mixed && tree_ldsd(n, p->arity) > p->ldS) return TSQR_ERR_UNSUPPORTED;
+    return build_tree(leaves, p->arity, &p->shape, &p->nodes);
 }
 
 // Workspace for (current device, stream): at least `bytes` bytes plus a status word.
@@ -269,6 +287,7 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     a.unit = p.unit;
     a.nunits = p.nunits;
     a.nleaves = p.nleaves;
+    a.arity = p.arity;
     a.h = p.h;
     a.hs = p.hs;
     a.blk = p.blk;
@@ -309,6 +328,7 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     a.base.unit = p.unit;
     a.base.nunits = p.nunits;
     a.base.nleaves = p.nleaves;
+    a.base.arity = p.arity;
     a.base.h = p.h;
     a.base.hs = p.hs;
     a.base.blk = p.blk;
@@ -320,8 +340,8 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     a.base.ldr = ldr;
     a.base.status = ws->status;
     a.A = A;
-    a.ldSd = mixed_ldsd((int)n);
-    a.s_doubles = mixed_s_doubles((int)n, p.ldS);
+    a.ldSd = p.ldSd;
+    a.s_doubles = p.s_doubles;
     if (cudaMemsetAsync(a.base.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
         cudaSuccess)
         return TSQR_ERR_CUDA;
@@ -397,9 +417,11 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         P.nunits = (m + P.unit - 1) / P.unit;
         if (P.nunits > (1 << 24)) return TSQR_ERR_UNSUPPORTED;
         P.nleaves = (int)P.nunits;
+        P.arity = arity_for(n, mixed ? mixed_s_doubles(n, P.ldS) : P.ldS * n);
+        if (!mixed && tree_ldsd(n, P.arity) > P.ldS) P.arity = 2;
         TreeShape shape;
         int64_t nodes = 0;
-        if (build_tree(P.nleaves, &shape, &nodes) != TSQR_SUCCESS) return TSQR_ERR_UNSUPPORTED;
+        if (build_tree(P.nleaves, P.arity, &shape, &nodes) != TSQR_SUCCESS) return TSQR_ERR_UNSUPPORTED;
         P.slot_off = slot_doubles;
         P.cnt_off = nodes_total;
         slot_doubles += nodes * (int64_t)n * n;
@@ -472,6 +494,7 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
     a->unit = p.unit;
     a->nunits = p.nunits;
     a->nleaves = p.nleaves;
+    a->arity = p.arity;
     a->h = p.h;
     a->hs = p.hs;
     a->blk = p.blk;
@@ -616,6 +639,7 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
     out->tile_rows = (int32_t)p.unit;
     out->ctas = p.nleaves;
     out->warps = p.warps;
+    out->arity = p.arity;
     return TSQR_SUCCESS;
 }
 

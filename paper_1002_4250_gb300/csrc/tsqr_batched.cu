@@ -26,6 +26,7 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
         a.unit = P.unit;
         a.nunits = P.nunits;
         a.nleaves = P.nleaves;
+        a.arity = P.arity;
         a.h = P.h;
         a.hs = P.hs;
         a.blk = P.blk;
@@ -45,7 +46,7 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
                 default: leaf_tree_job<T, Tin, 1, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
             }
         } else {
-            const int ldSd = mixed_ldsd_of(P.n), sd = mixed_s_doubles_of(P.n, P.ldS);
+            const int ldSd = tree_ldsd(P.n, P.arity), sd = mixed_s_doubles_of(P.n, P.ldS, P.arity);
             switch (P.blk * 10 + P.vec) {
                 case 44: leaf_tree_job<T, Tin, 4, 4, true>(a, A, ldSd, sd, w.y); break;
                 case 22: leaf_tree_job<T, Tin, 2, 2, true>(a, A, ldSd, sd, w.y); break;

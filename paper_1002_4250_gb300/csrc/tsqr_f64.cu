@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const d
     load_packed_cg(R1, ld1, n, Rp);
     load_tri_cg(R2, ld2, n, S, ldS);
     __syncthreads();
-    fold_tri(S, ldS, Rp, smem + L.f, smem + L.seg, smem + L.npart, n);
+    fold_stack(S, ldS, 1, Rp, smem + L.f, smem + L.seg, smem + L.tot + kSegStride, n);
     if (normalize)
         store_normalized(Rp, n, R, ldr, status);
     else

@@ -39,6 +39,7 @@ struct F64Args {
     int64_t unit;   // rows of a work unit: a tile (binary tree) or a slab (flat, hybrid)
     int64_t nunits; // ceil(m / unit)
     int nleaves;    // CTAs of the leaf phase; leaf c owns units [c*nunits/nleaves, ...)
+    int arity;      // children per tree node (2 = the paper's binary operator)
     int h;          // rows folded per step of a leaf ("chunk"): h <= hs
     int hs;         // rows of S in shared memory: >= max(h, n), a multiple of 32 x warps
     int blk;        // rows per inner-loop block: divides hs / (32 x warps)
@@ -67,7 +68,7 @@ struct BatchProblem {
     double *R;               // column-major n x n, leading dimension n
     int64_t unit, nunits;    // rows per leaf, number of leaves
     int n, h, hs, blk, vec, ldS;  // as in F64Args
-    int nleaves;
+    int nleaves, arity;
     int64_t slot_off;        // first tree slot of this problem (doubles into the slots buffer)
     int64_t cnt_off;         // first tree counter of this problem
 };
@@ -82,13 +83,23 @@ struct BatchArgs {
     int *status;
 };
 
-// FP64 view of the mixed kernels' S region (tree operator): odd leading dimension >= n.
-__host__ __device__ inline int mixed_ldsd_of(int n) { return (n % 2 == 0) ? n + 1 : n; }
-// Size in doubles of the mixed kernels' S region: the FP32 chunk or the FP64 triangle.
-__host__ __device__ inline int mixed_s_doubles_of(int n, int ldS) {
+// Leading dimension of the tree operator's FP64 view of the S region: odd, and room for
+// arity-1 stacked n x n triangles.
+__host__ __device__ inline int tree_ldsd(int n, int arity) {
+    const int v = (arity > 2 ? arity - 1 : 1) * n;
+    return (v % 2 == 0) ? v + 1 : v;
+}
+// Size in doubles of the mixed kernels' S region: the FP32 chunk or the FP64 triangles.
+__host__ __device__ inline int mixed_s_doubles_of(int n, int ldS, int arity) {
     const int leaf = (ldS * n + 1) / 2;
-    const int tree = mixed_ldsd_of(n) * n;
+    const int tree = tree_ldsd(n, arity) * n;
     return leaf > tree ? leaf : tree;
+}
+// Largest arity (<= 8) whose stacked triangles fit in `s_doubles` doubles of the S region.
+__host__ __device__ inline int arity_for(int n, int s_doubles) {
+    int k = 2;
+    while (k < 8 && tree_ldsd(n, k + 1) * n <= s_doubles) ++k;
+    return k;
 }
 
 // Shared-memory carve-up (offsets in doubles), identical on host and device.  The S region

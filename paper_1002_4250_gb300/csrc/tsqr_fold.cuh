@@ -497,98 +497,125 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
     }
 }
 
-// Tree-operator fold (Table 3): S = R2, reflector J's support in S is rows 0..J.  Warp 0
-// updates column J; the warps split the trailing columns, each lane taking an equal
-// contiguous run of the warp's (column, row) items in lockstep.
-__device__ __forceinline__ void fold_tri(double *__restrict__ S, const int ldS,
-                                         double *__restrict__ Rp, double *__restrict__ f,
-                                         double *__restrict__ seg_all,
-                                         double *__restrict__ npart, const int n) {
+// Tree-operator fold: R <- R([R; T_1; ...; T_c]) for c upper triangles stacked in S (FP64,
+// column-major, leading dimension ldSd; triangle t in rows t n .. t n + n-1).  For c = 1 this
+// is the operator qr(R1, R2) of Table 3; c > 1 reduces c+1 tree nodes in one sweep (the stacked
+// triangles' QR, which associativity allows, Section 2).  At step J the reflector's support in
+// S is rows 0..J of every triangle (the paper's j+2-entry reflector for c = 1).
+// Warp 0 updates column J, forms its squared norm and then reflector J's scalars while the
+// other warps (which split the trailing columns) run the fused update + dot sweep; warp 0 then
+// sums their partials in a fixed order and updates R and f.  Needs at least two warps.
+__device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldSd, const int c,
+                                           double *__restrict__ Rp, double *__restrict__ f,
+                                           double *__restrict__ seg_all,
+                                           double *__restrict__ dk, const int n) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int W = blockDim.x >> 5;
-    double *seg = seg_all + warp * kSegStride;
+    const int Wp = (blockDim.x >> 5) - 1;  // worker warps 1..Wp
+    double *seg = seg_all + (warp > 0 ? warp - 1 : 0) * kSegStride;
 
     for (int J = 0; J < n; ++J) {
         const int U = n - J - 1;
-        const int cw = J + 1;
-        double *SJ = S + (size_t)J * ldS;
-        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS;
-        const int kc0 = (warp * U) / W, kc1 = ((warp + 1) * U) / W;
+        const int h1 = J + 1;    // active rows per triangle
+        const int cw = c * h1;   // active rows per column
+        double *SJ = S + (size_t)J * ldSd;
+        const double *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldSd;
 
-        double nacc = 0.0;
+        double sig2 = 0.0;
         if (warp == 0) {
+            // ---- A: column J gets reflector J-1; its squared norm
             const double fJ = (J > 0) ? f[J] : 0.0;
-            for (int i = lane; i < cw; i += 32) {
-                double s = SJ[i];
+            double nacc = 0.0;
+            for (int q = lane; q < cw; q += 32) {
+                const int t = q / h1;
+                const int row = q + t * (n - h1);  // t n + (q - t h1)
+                double x = SJ[row];
                 if (J > 0) {
-                    s = fma(-fJ, Sj[i], s);
-                    SJ[i] = s;
+                    x = fma(-fJ, Sj[row], x);
+                    SJ[row] = x;
                 }
-                nacc = fma(s, s, nacc);
+                nacc = fma(x, x, nacc);
             }
-        }
-        npart[warp * 32 + lane] = nacc;
-        for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
-        __syncthreads();
-
-        const int N = (kc1 - kc0) * cw;
-        if (N > 0) {
-            int p = (int)(((long long)lane * N) >> 5);
-            const int pend = (int)(((long long)(lane + 1) * N) >> 5);
-            if (p < pend) {
-                int kk = p / cw;
-                int i = p - kk * cw;
-                int k = J + 1 + kc0 + kk;
-                double *Sk = S + (size_t)k * ldS;
-                double fk = (J > 0) ? f[k] : 0.0;
-                double acc = 0.0;
-                for (;;) {
-                    double s = Sk[i];
-                    if (J > 0) {
-                        s = fma(-fk, Sj[i], s);
-                        Sk[i] = s;
-                    }
-                    acc = fma(SJ[i], s, acc);
-                    if (++p == pend) break;
-                    if (++i == cw) {
-                        seg[lane + kk] = acc;
-                        acc = 0.0;
-                        i = 0;
-                        ++kk;
-                        ++k;
-                        Sk += ldS;
-                        fk = (J > 0) ? f[k] : 0.0;
-                    }
-                }
-                seg[lane + kk] = acc;
-            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+            sig2 = __shfl_sync(0xffffffffu, nacc, 0);
+        } else {
+            for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
         }
         __syncthreads();
 
-        if (warp == J % W) {
-            double *dk = seg_all + W * kSegStride + kSegStride;
+        Reflector hr;
+        if (warp == 0) {
+            hr = make_reflector(Rp[rowoff(n, J)], sig2);
+        } else {
+            // ---- B: worker warp w owns trailing columns [kc0, kc1); its (column, row) items
+            //      are cut into 32 equal contiguous runs in lockstep
+            const int w = warp - 1;
+            const int kc0 = (w * U) / Wp, kc1 = ((w + 1) * U) / Wp;
+            const int N = (kc1 - kc0) * cw;
+            if (N > 0) {
+                int p = (int)(((long long)lane * N) >> 5);
+                const int pend = (int)(((long long)(lane + 1) * N) >> 5);
+                if (p < pend) {
+                    int kk = p / cw;
+                    int q = p - kk * cw;
+                    int t = q / h1;
+                    int i = q - t * h1;
+                    int row = t * n + i;
+                    int k = J + 1 + kc0 + kk;
+                    double *Sk = S + (size_t)k * ldSd;
+                    double fk = (J > 0) ? f[k] : 0.0;
+                    double acc = 0.0;
+                    for (;;) {
+                        double x = Sk[row];
+                        if (J > 0) {
+                            x = fma(-fk, Sj[row], x);
+                            Sk[row] = x;
+                        }
+                        acc = fma(SJ[row], x, acc);
+                        if (++p == pend) break;
+                        ++row;
+                        if (++i == h1) {
+                            i = 0;
+                            row += n - h1;
+                            if (++t == c) {
+                                seg[lane + kk] = acc;
+                                acc = 0.0;
+                                t = 0;
+                                row = 0;
+                                ++kk;
+                                ++k;
+                                Sk += ldSd;
+                                fk = (J > 0) ? f[k] : 0.0;
+                            }
+                        }
+                    }
+                    seg[lane + kk] = acc;
+                }
+            }
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            // ---- column kk's partials: those of its owner warp's lanes la..lb
             for (int kk = lane; kk < U; kk += 32) {
-                double d = 0.0;
-                bool first = true;
-                for (int w = 0; w < W; ++w) {
-                    const int a0 = (w * U) / W, a1 = ((w + 1) * U) / W;
-                    if (kk < a0 || kk >= a1) continue;
-                    const int rel = kk - a0;
-                    const int Nw = (a1 - a0) * cw;
-                    const int la = (32 * (rel * cw + 1) - 1) / Nw;
-                    const int lb = (32 * (rel + 1) * cw - 1) / Nw;
-                    for (int l = la; l <= lb; ++l) {
-                        const double x = seg_all[w * kSegStride + rel + l];
-                        d = first ? x : d + x;
-                        first = false;
-                    }
+                const int w = ((kk + 1) * Wp - 1) / U;
+                const int kc0 = (w * U) / Wp, kc1 = ((w + 1) * U) / Wp;
+                const int rel = kk - kc0;
+                const int Nw = (kc1 - kc0) * cw;
+                const int la = (32 * (rel * cw + 1) - 1) / Nw;
+                const int lb = (32 * (rel + 1) * cw - 1) / Nw;
+                const double *sg = seg_all + w * kSegStride + rel;
+                double d0 = sg[la], d1 = 0.0;
+                for (int l = la + 1; l + 1 <= lb; l += 2) {
+                    d0 += sg[l];
+                    d1 += sg[l + 1];
                 }
-                dk[kk] = d;
+                if (((lb - la) & 1) == 1) d0 += sg[lb];
+                dk[kk] = d0 + d1;
             }
             __syncwarp();
-            const Reflector h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, W, npart));
-            apply_reflector(lane, n, J, h, Rp, f, dk);
+            apply_reflector(lane, n, J, hr, Rp, f, dk);
         }
         __syncthreads();
     }
@@ -648,11 +675,13 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // combines [R_left; R_right] (left = lower index, always on top) and climbs on; the first
 // returns.  No CTA ever waits for another, and the operand order depends only on the indices.
 // ------------------------------------------------------------------------------------------
-// One leaf of one problem: fold the leaf's rows into R, then climb the problem's binary tree
-// (level l has ceil(nleaves / 2^l) nodes, stored level after level).  T: leaf storage and
+// One leaf of one problem: fold the leaf's rows into R, then climb the problem's k-ary tree
+// (k = a.arity; level l has ceil(nleaves / k^l) nodes, stored level after level).  T: leaf storage and
 // arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading dimension a.ldS); the
 // tree operator works in the same memory viewed as FP64 with leading dimension ldSd.  Returns
-// when the CTA is the first of two children to arrive at a node, or after writing the root.
+// when the CTA is not the last of a node's children to arrive, or after writing the root.
+// The tree operator's FP64 view of S (leading dimension ldSd) must hold arity-1 stacked n x n
+// triangles.
 template <typename T, typename Tin, int B, int V, bool kPipe>
 __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, const int ldSd,
                                               const int s_doubles, const int leaf) {
@@ -706,45 +735,40 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
         }
     }
 
+    // k-ary tree: node t of level l+1 has children k t .. k t + k-1 of level l
+    const int k = a.arity;
     int cnt = a.nleaves, off = 0, t = leaf;  // nodes and first node id of the current level
     for (;;) {
         if (cnt == 1) {
             store_normalized(Rp, n, a.R, a.ldr, a.status);
             return;
         }
-        const int next_off = off + cnt, next_cnt = (cnt + 1) >> 1;
-        const int sib = t ^ 1;
-        if (sib >= cnt) {  // odd last node: promoted unchanged
+        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
+        const int parent = t / k, first = parent * k;
+        const int nchild = min(k, cnt - first);
+        if (nchild == 1) {  // a lone last child: promoted unchanged
             off = next_off;
             cnt = next_cnt;
-            t >>= 1;
+            t = parent;
             continue;
         }
-        double *mine = a.slots + (size_t)(off + t) * n * n;
-        store_packed(Rp, n, mine, n);
+        store_packed(Rp, n, a.slots + (size_t)(off + t) * n * n, n);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + (t >> 1)], 1u);
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + parent], 1u);
         __syncthreads();
-        if (flag[0] == 0) return;  // the sibling combines
+        if (flag[0] + 1 < (unsigned)nchild) return;  // a later sibling combines
         __threadfence();
-        const double *other = a.slots + (size_t)(off + sib) * n * n;
-        if (t & 1) {
-            // this CTA holds the right (lower) operand: it becomes S, the left one comes to Rp
-            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-                const int col = idx / n, row = idx - col * n;
-                Sd[row + col * ldSd] = (row <= col) ? Rp[rowoff(n, row) + col - row] : 0.0;
-            }
-            __syncthreads();
-            load_packed_cg(other, n, n, Rp);
-        } else {
-            load_tri_cg(other, n, n, Sd, ldSd);
-        }
+        // the last child to arrive stacks the children in index order: the first on top
+        load_packed_cg(a.slots + (size_t)(off + first) * n * n, n, n, Rp);
+        for (int ch = 1; ch < nchild; ++ch)
+            load_tri_cg(a.slots + (size_t)(off + first + ch) * n * n, n, n,
+                        Sd + (size_t)(ch - 1) * n, ldSd);
         __syncthreads();
-        fold_tri(Sd, ldSd, Rp, f, seg, npart, n);
+        fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + kSegStride, n);
         off = next_off;
         cnt = next_cnt;
-        t >>= 1;
+        t = parent;
     }
 }
 

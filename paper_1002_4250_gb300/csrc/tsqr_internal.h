@@ -23,7 +23,6 @@ cudaError_t f64_combine_launch(int n, const double *R1, int64_t ld1, const doubl
                                cudaStream_t stream);
 
 // Mixed path (tsqr_mixed.cu); `warps` counts bulk warps as for the FP64 path.
-int mixed_ldsd(int n);
 int mixed_s_doubles(int n, int ldS);
 size_t mixed_smem_bytes(int n, int ldS, int warps);
 cudaError_t mixed_prepare(size_t smem_bytes);

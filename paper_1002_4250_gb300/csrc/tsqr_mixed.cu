@@ -44,13 +44,11 @@ void launch_t(const MixedArgs &a, int threads, size_t smem, cudaStream_t stream)
 }
 }  // namespace
 
-int mixed_ldsd(int n) { return mixed_ldsd_of(n); }
-
-int mixed_s_doubles(int n, int ldS) { return mixed_s_doubles_of(n, ldS); }
+int mixed_s_doubles(int n, int ldS) { return (ldS * n + 1) / 2; }
 
 // `warps` counts bulk warps; the kernels launch one more, the reducer warp.
 size_t mixed_smem_bytes(int n, int ldS, int warps) {
-    return sizeof(double) * (size_t)smem_layout_s(n, mixed_s_doubles(n, ldS), warps + 1).total;
+    return sizeof(double) * (size_t)smem_layout_s(n, mixed_s_doubles_of(n, ldS, 2), warps + 1).total;
 }
 
 cudaError_t mixed_prepare(size_t smem_bytes) {

@@ -212,3 +212,21 @@ def test_full_size_4m_x_32(oracle, T, kappa):
     A = oracle.from_torch_colmajor(At)
     R = T.tsqr_r(_gpu(At))
     _assert_parity(oracle, A, R, nthreads=16)
+
+
+@pytest.mark.parametrize("arity", [2, 3, 5, 8])
+@pytest.mark.parametrize("m,n,ctas", [(300001, 8, 37), (200003, 32, 61), (100003, 48, 9)])
+def test_tree_arity(oracle, T, arity, m, n, ctas):
+    """Stacked-triangle tree nodes (arity > 2) give the same R as the binary operator's tree."""
+    At = workloads.gaussian(m, n, seed=arity + n)
+    A = oracle.from_torch_colmajor(At)
+    plan = T.make_plan("hybrid", ctas=ctas, arity=arity)
+    assert T.tsqr_resolve_plan(m, n, plan=plan).arity == arity
+    R = T.tsqr_r_ex(_gpu(At), plan=plan)
+    _assert_parity(oracle, A, R, nthreads=16)
+
+
+def test_auto_plan_uses_wide_tree_nodes(T):
+    p = T.tsqr_resolve_plan(4194304, 32)
+    assert p.arity >= 4
+    assert T.tsqr_resolve_plan(10000, 16, plan=T.make_plan("binary", tile_rows=256)).arity == 2
