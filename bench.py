@@ -348,8 +348,37 @@ def bench_extras(dev):
         del A
     del A64
     torch.cuda.empty_cache()
+    out["widths_2e24"] = bench_widths(dev, ms64)
     out["varlen_batch"] = bench_batched(dev)
     return out
+
+
+def bench_widths(dev, ms64=None):
+    """FP64 at 16,777,216 x n for n in {4, 8, 16, 32, 64, 128}, N(0,1): GFLOP/s, A-read GB/s and
+    the fraction of the roofline time max(bytes(A) / HBM, flops / FP64 peak)."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    m = 1 << 24
+    pk = peaks()
+    res = {}
+    for n in (4, 8, 16, 32, 64, 128):
+        fl = flops(m, n)
+        bytes_a = 8.0 * m * n
+        t_roof = max(bytes_a / (pk["hbm_gbs"] * 1e9), fl / (pk["fp64_tflops"] * 1e12)) * 1e3
+        if n == 64 and ms64 is not None:
+            ms = ms64
+        else:
+            A = workloads.gaussian(m, n, seed=0, device=dev).T
+            R = T.empty_r(n, dev)
+            ms = time_call(lambda: T.tsqr_r(A, R=R), reps=2 if n >= 64 else 5, warmup=1)
+            del A
+            torch.cuda.empty_cache()
+        res[str(n)] = {"ms": ms, "gflops": fl / ms / 1e6, "a_read_gbs": bytes_a / ms / 1e6,
+                       "roofline_ms": t_roof, "frac_of_roofline": t_roof / ms,
+                       "bound": "hbm" if bytes_a / (pk["hbm_gbs"] * 1e9) > fl / (pk["fp64_tflops"] * 1e12)
+                       else "alu"}
+    return res
 
 
 def bench_batched(dev):

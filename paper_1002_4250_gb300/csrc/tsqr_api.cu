@@ -96,9 +96,6 @@ int ld_for(int hs, int vec = 1) {
     return vec * ((q % 2 == 0) ? q + 1 : q);
 }
 
-// Upper bound of ld_for over the vector widths, for shared-memory budgets.
-int ld_bound(int hs) { return hs + 8; }
-
 
 // Rows per lane whose inner loop blocks well: a multiple of 4 or 3 when r >= 3.
 int good_r(int r) {
@@ -130,50 +127,29 @@ tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     return plan_leaf(m, n, over, false, p);
 }
 
-size_t leaf_smem_bytes(int n, int hs, int warps, bool mixed) {
-    return mixed ? mixed_smem_bytes(n, ld_bound(hs), warps)
-                 : f64_smem_bytes(n, hs, ld_bound(hs), warps);
+// Shared memory of a leaf CTA holding an hs-row chunk with leading dimension ld.
+size_t leaf_smem_bytes(int n, int hs, int ld, int warps, bool mixed) {
+    return mixed ? mixed_smem_bytes(n, ld, warps) : f64_smem_bytes(n, hs, ld, warps);
 }
 
-// Largest r (rows per lane) whose shared memory, with hs = 32 r warps rows, fits `budget`.
+// Largest r (rows per lane) whose shared memory, with hs = 32 r warps rows and the leading
+// dimension its inner-loop vector width implies, fits `budget`.
 int max_rows_per_lane_p(int n, int warps, size_t budget, bool mixed) {
     int best = 0;
     for (int r = 1; r <= 256; ++r) {
-        if (leaf_smem_bytes(n, 32 * warps * r, warps, mixed) > budget) break;
+        int blk = 1, vec = 1;
+        block_for(r, mixed, &blk, &vec);
+        const int hs = 32 * warps * r;
+        if (leaf_smem_bytes(n, hs, ld_for(hs, vec), warps, mixed) > budget) break;
         best = r;
     }
     return best;
 }
 
-tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
-    const DeviceInfo di = device_info(dev);
-    if (di.sms <= 0) return TSQR_ERR_CUDA;
-    p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
-    if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
-    p->warps = 4;
-    if (over && over->warps) {
-        if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
-        p->warps = over->warps;
-    }
-    if (over && (over->tile_rows < 0 || over->ctas < 0)) return TSQR_ERR_INVALID_ARG;
+// The rest of plan_leaf once the rows per lane that fit (r_fit) are chosen.
+tsqr_status_t plan_with_r(int64_t m, int n, const tsqr_plan_t *over, bool mixed, int r_fit,
+                          const DeviceInfo &di, F64Plan *p) {
     const int W = p->warps;
-    const size_t reserve = 1024;
-    const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
-    const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
-    int r_fit;
-    const int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
-    const int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
-    if (!mixed) {
-        // two CTAs per SM hide each other's per-column serial work; take one per SM only when
-        // two would leave fewer than 2 rows per lane
-        r_fit = (r2 >= 2) ? r2 : std::max(r2, r1);
-    } else {
-        // the FP32 bulk is cheap: what counts is the number of rows sharing each reflector's
-        // serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs)
-        r_fit = (2 * good_r(r2) >= good_r(r1)) ? r2 : r1;
-    }
     if (r_fit < 1 || 32 * W * r_fit < n) return TSQR_ERR_UNSUPPORTED;
     r_fit = good_r(r_fit);
     const int64_t mm = std::max<int64_t>(m, 1);
@@ -196,7 +172,7 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     if (p->hs < n) return TSQR_ERR_UNSUPPORTED;
     block_for(r, mixed, &p->blk, &p->vec);
     p->ldS = ld_for(p->hs, p->vec);
-    p->smem = leaf_smem_bytes(n, p->hs, W, mixed);
+    p->smem = leaf_smem_bytes(n, p->hs, p->ldS, W, mixed);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
     p->nunits = (mm + p->unit - 1) / p->unit;
     int64_t leaves;
@@ -219,7 +195,6 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     // tree arity: 2 (the paper's binary operator) for the BINARY tree, else as many stacked
     // triangles as the S region holds (at most 8), unless the plan says otherwise
     const int s_avail = mixed ? mixed_s_doubles(n, p->ldS) : p->ldS * n;
-    if (over && over->arity < 0) return TSQR_ERR_INVALID_ARG;
     if (p->tree == TSQR_TREE_BINARY) {
         p->arity = 2;
     } else if (over && over->arity > 0) {
@@ -233,6 +208,39 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     p->s_doubles = mixed ? mixed_s_doubles_of(n, p->ldS, p->arity) : p->ldS * n;
     if (!mixed && tree_ldsd(n, p->arity) > p->ldS) return TSQR_ERR_UNSUPPORTED;
     return build_tree(leaves, p->arity, &p->shape, &p->nodes);
+}
+
+tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    if (di.sms <= 0) return TSQR_ERR_CUDA;
+    p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
+    if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
+    p->warps = 4;
+    if (over && over->warps) {
+        if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
+        p->warps = over->warps;
+    }
+    if (over && (over->tile_rows < 0 || over->ctas < 0 || over->arity < 0))
+        return TSQR_ERR_INVALID_ARG;
+    const int W = p->warps;
+    const size_t reserve = 1024;
+    const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
+    const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
+    const int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
+    const int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
+    // FP64: two CTAs per SM hide each other's per-column serial work (the reflector chain,
+    // the barriers), which pays even at one row per lane (measured at n = 16, 32, 64).
+    // Mixed: the FP32 bulk is cheap, so what counts is the number of rows sharing each
+    // reflector's serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs).
+    const bool two = mixed ? (r2 >= 1 && 2 * good_r(r2) >= good_r(r1)) : (r2 >= 1);
+    tsqr_status_t st = plan_with_r(m, n, over, mixed, two ? r2 : r1, di, p);
+    // an explicit arity whose stacked triangles need a taller S region than two CTAs per SM
+    // leave room for: one CTA per SM
+    if (st == TSQR_ERR_UNSUPPORTED && two && over && over->arity > 0)
+        st = plan_with_r(m, n, over, mixed, r1, di, p);
+    return st;
 }
 
 // Workspace for (current device, stream): at least `bytes` bytes plus a status word.
@@ -371,8 +379,11 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
     int nmax = 1;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
+    // two CTAs per SM as for single problems: FP64 whenever the widest problem's chunk fits
+    // at one row per lane, mixed when it fits at two
     size_t budget = two_per_sm;
-    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2) budget = one_per_sm;
+    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < (mixed ? 2 : 1))
+        budget = one_per_sm;
     // per width: chunk rows
     std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1), vec_of(TSQR_MAX_N + 1, 1);
     size_t smem = 0;
@@ -385,7 +396,12 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         if (r < 1 || 32 * W * r < n) return TSQR_ERR_UNSUPPORTED;
         hs_of[n] = 32 * W * r;
         block_for(r, mixed, &blk_of[n], &vec_of[n]);
-        smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], W, mixed));
+        if (mixed && blk_of[n] * 10 + vec_of[n] != 44 && blk_of[n] * 10 + vec_of[n] != 22) {
+            blk_of[n] = (r % 4 == 0) ? 4 : (r % 2 == 0) ? 2 : 1;
+            vec_of[n] = blk_of[n];
+        }
+        smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], ld_for(hs_of[n], vec_of[n]), W,
+                                              mixed));
     }
     if (batched_prepare(dt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int per_sm = std::max(1, batched_blocks_per_sm(dt, W, smem));

@@ -76,8 +76,7 @@ const void *batched_fn(int dtype) {
 
 // dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); `warps` counts bulk warps (+1 reducer).
 cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
-    return cudaFuncSetAttribute(batched_fn(dtype), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
+    return set_smem_attrs(batched_fn(dtype), smem_bytes);
 }
 
 int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes) {

@@ -5,7 +5,7 @@
 namespace tsqr {
 
 template <int B>
-__global__ void __launch_bounds__(256, 1) tsqr_f64_kernel(const F64Args a) {
+__global__ void __launch_bounds__(288, 1) tsqr_f64_kernel(const F64Args a) {
     leaf_tree_job<double, double, B, 1, false>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
 }
 
@@ -22,7 +22,7 @@ const void *f64_fn(int blk) {
 }  // namespace
 
 // One tree node: R = qr(R1, R2) (Table 3), optionally sign-normalized.
-__global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const double *R1, int64_t ld1,
+__global__ void __launch_bounds__(288, 1) tsqr_f64_combine_kernel(int n, const double *R1, int64_t ld1,
                                                                const double *R2, int64_t ld2,
                                                                double *R, int64_t ldr,
                                                                int normalize, int ldS, int hs,
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_f64_combine_kernel(int n, const d
     load_packed_cg(R1, ld1, n, Rp);
     load_tri_cg(R2, ld2, n, S, ldS);
     __syncthreads();
-    fold_stack(S, ldS, 1, Rp, smem + L.f, smem + L.seg, smem + L.tot + kSegStride, n);
+    fold_stack(S, ldS, 1, Rp, smem + L.f, smem + L.seg, smem + L.tot + seg_stride(n), n);
     if (normalize)
         store_normalized(Rp, n, R, ldr, status);
     else
@@ -51,12 +51,10 @@ size_t f64_smem_bytes(int n, int hs, int ldS, int warps) {
 
 cudaError_t f64_prepare(size_t smem_bytes) {
     for (int b = 1; b <= 4; ++b) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            f64_fn(b), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+        const cudaError_t e = set_smem_attrs(f64_fn(b), smem_bytes);
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute(tsqr_f64_combine_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return set_smem_attrs(tsqr_f64_combine_kernel, smem_bytes);
 }
 
 int f64_blocks_per_sm(int warps, size_t smem_bytes) {

@@ -21,7 +21,9 @@ namespace tsqr {
 
 constexpr int kMaxN = 128;
 constexpr int kMaxLevels = 48;
-constexpr int kSegStride = 32 + kMaxN;  // segment slots per warp (lanes + column boundaries)
+// Partial-sum slots per warp for width n: one per lane plus one per column boundary a lane's
+// run can cross (a slot index is lane + column offset < 32 + n).
+__host__ __device__ inline int seg_stride(int n) { return 32 + n; }
 
 // Binary reduction tree over `count[0]` leaves (host side): level l has count[l] nodes; node t
 // of level l+1 has children 2t and 2t+1 of level l (an odd last child is promoted unchanged).
@@ -105,7 +107,7 @@ __host__ __device__ inline int arity_for(int n, int s_doubles) {
 // Shared-memory carve-up (offsets in doubles), identical on host and device.  The S region
 // holds s_doubles doubles.
 struct SmemLayout {
-    int S, Rp, f, seg, tot, npart, scal, total;
+    int S, Rp, f, fs, seg, tot, npart, scal, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout_s(int n, int s_doubles, int warps) {
@@ -114,8 +116,9 @@ __host__ __device__ inline SmemLayout smem_layout_s(int n, int s_doubles, int wa
     L.S = o;      o += s_doubles;
     L.Rp = o;     o += n * (n + 1) / 2 + 1;
     L.f = o;      o += n + 1;
-    L.seg = o;    o += warps * kSegStride;
-    L.tot = o;    o += 2 * kSegStride;  // summed slots, then the per-column dot products
+    L.fs = o;     o += n / 2 + 1;  // FP32 copy of f (mixed leaf)
+    L.seg = o;    o += warps * seg_stride(n);
+    L.tot = o;    o += 2 * seg_stride(n);  // summed slots, then the per-column dot products
     L.npart = o;  o += warps * 32;
     L.scal = o;   o += 4;
     L.total = o;

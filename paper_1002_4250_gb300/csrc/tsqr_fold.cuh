@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 
 #include "tsqr_f64.cuh"
 #include "tsqr_internal.h"
@@ -85,9 +86,10 @@ __device__ __forceinline__ void load_column(T *S, int ldS, int hs, const Chunk<T
 // S : the bottom block, column-major with leading dimension ldS.
 //   leaf (fold_leaf): S is a dense chunk of hs rows; warp w owns rows [w*Hw, (w+1)*Hw),
 //     Hw = hs / W = 32 r.
-//   tree operator (fold_tri, Table 3): S is the upper triangle R2, so the support of
-//     reflector J in S is rows 0..J (the j+2-entry reflector of the paper's operator);
-//     the warps split the trailing columns instead of the rows.
+//   tree operator (fold_stack, Table 3): S holds c stacked upper triangles (c = 1 is the
+//     paper's R2), so the support of reflector J in S is rows 0..J of each triangle (the
+//     j+2-entry reflector of the paper's operator for c = 1); the warps split the trailing
+//     columns instead of the rows.
 //
 // Reflector J (the LAPACK dlarfg rule the paper's operator uses): alpha = R(J,J), x = the
 // support of column J in S, sigma^2 = ||x||^2.  If sigma^2 == 0 it is the identity (the
@@ -187,24 +189,28 @@ __device__ __forceinline__ double sum_norm_partials(const int lane, const int W,
 }
 
 // Row J of R and the factors f[k], k > J, from the reflector and the dot products dk[kk] of
-// column J+1+kk with column J.
+// column J+1+kk with column J.  With T = float the bulk's FP32 copy fT of f is written too
+// (one conversion per factor here instead of one per column crossing in every bulk lane).
+template <typename T = double>
 __device__ __forceinline__ void apply_reflector(const int lane, const int n, const int J,
                                                 const Reflector &h, double *__restrict__ Rp,
                                                 double *__restrict__ f,
-                                                const double *__restrict__ dk) {
+                                                const double *__restrict__ dk,
+                                                T *fT = nullptr) {
     const int U = n - J - 1;
     const int ro = rowoff(n, J);
     for (int kk = lane; kk < U; kk += 32) {
         const int k = J + 1 + kk;
         const int idx = ro + 1 + kk;
-        if (h.ident) {
-            f[k] = 0.0;
-        } else {
+        double fk = 0.0;
+        if (!h.ident) {
             const double rjk = Rp[idx];
             const double wk = fma(h.c, dk[kk], rjk);
             Rp[idx] = fma(-h.tau, wk, rjk);
-            f[k] = -wk * h.ib;
+            fk = -wk * h.ib;
         }
+        f[k] = fk;
+        if constexpr (!std::is_same<T, double>::value) fT[k] = (T)fk;
     }
     if (lane == 0) Rp[ro] = h.beta;
 }
@@ -261,8 +267,8 @@ __device__ __forceinline__ void phase_b_plain(const int lane, const int J, const
                                               T *__restrict__ S, const int ldS, const int r0,
                                               const T *__restrict__ Sj,
                                               const T *__restrict__ SJ,
-                                              const double *__restrict__ f,
-                                              double *__restrict__ seg) {
+                                              const T *fT,
+                                              T *__restrict__ seg) {
     const int run = U * r;
     const int p = lane * run;
     int kk = p / Hw;
@@ -270,7 +276,7 @@ __device__ __forceinline__ void phase_b_plain(const int lane, const int J, const
     T *Sk = S + (size_t)(J + 1 + kk) * ldS + r0;
     T acc = (T)0;
     if (J > 0) {
-        T fk = (T)f[J + 1 + kk];
+        T fk = fT[J + 1 + kk];
         for (int blk = 0; blk < run; blk += B) {
             T x[B];
 #pragma unroll
@@ -281,12 +287,12 @@ __device__ __forceinline__ void phase_b_plain(const int lane, const int J, const
             for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], x[q], acc);
             i += B;
             if (i == Hw) {
-                seg[lane + kk] = (double)acc;
+                seg[lane + kk] = acc;
                 acc = (T)0;
                 i = 0;
                 ++kk;
                 Sk += ldS;
-                fk = (T)f[min(J + 1 + kk, n - 1)];
+                fk = fT[min(J + 1 + kk, n - 1)];
             }
         }
     } else {
@@ -295,7 +301,7 @@ __device__ __forceinline__ void phase_b_plain(const int lane, const int J, const
             for (int q = 0; q < B; ++q) acc = fmat(SJ[i + q], Sk[i + q], acc);
             i += B;
             if (i == Hw) {
-                seg[lane + kk] = (double)acc;
+                seg[lane + kk] = acc;
                 acc = (T)0;
                 i = 0;
                 ++kk;
@@ -303,7 +309,7 @@ __device__ __forceinline__ void phase_b_plain(const int lane, const int J, const
             }
         }
     }
-    if (i != 0) seg[lane + kk] = (double)acc;
+    if (i != 0) seg[lane + kk] = acc;
 }
 
 // Phase B of step J for one bulk lane, pipelined form (the mixed path, whose FP32 bulk is
@@ -315,8 +321,8 @@ template <typename T, int B, int V>
 __device__ __forceinline__ void phase_b(const int lane, const int J, const int U, const int r,
                                         const int Hw, const int n, T *__restrict__ S,
                                         const int ldS, const int r0, const T *__restrict__ Sj,
-                                        const T *__restrict__ SJ, const double *__restrict__ f,
-                                        double *__restrict__ seg) {
+                                        const T *__restrict__ SJ, const T *fT,
+                                        T *__restrict__ seg) {
     const int run = U * r;
     const int nblk = run / B;
     const int p = lane * run;
@@ -328,7 +334,7 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
     ld_block<B, V>(Sk + i, s);
     ld_block<B, V>(SJ + i, b);
     if (J > 0) {
-        T fk = (T)f[J + 1 + kk];
+        T fk = fT[J + 1 + kk];
         T a[B];
         ld_block<B, V>(Sj + i, a);
         for (int blk = 0; blk < nblk; ++blk) {
@@ -354,9 +360,9 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
 #pragma unroll
             for (int q = 0; q < B; ++q) acc = fmat(b[q], x[q], acc);
             if (cross) {
-                seg[lane + kk] = (double)acc;
+                seg[lane + kk] = acc;
                 acc = (T)0;
-                fk = (T)f[min(J + 1 + kk2, n - 1)];
+                fk = fT[min(J + 1 + kk2, n - 1)];
             }
             i = i2;
             kk = kk2;
@@ -386,7 +392,7 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
 #pragma unroll
             for (int q = 0; q < B; ++q) acc = fmat(b[q], s[q], acc);
             if (cross) {
-                seg[lane + kk] = (double)acc;
+                seg[lane + kk] = acc;
                 acc = (T)0;
             }
             i = i2;
@@ -399,7 +405,7 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
             }
         }
     }
-    if (i != 0) seg[lane + kk] = (double)acc;
+    if (i != 0) seg[lane + kk] = acc;
 }
 
 // Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warp Wb is the reducer.
@@ -411,14 +417,18 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
 //   A (bulk) | barrier | B (bulk) || scalars (reducer) | barrier | dots, R, f (reducer) | barrier.
 // The next chunk of rows streams into columns no longer read (J-2 at step J) by cp.async when
 // A's type is T; a BF16 A is widened after the fold instead.  T = double is the FP64 path;
-// T = float the mixed path, where only the bulk arithmetic is FP32 and the reflector scalars,
-// partial-sum reductions, R and f stay FP64.
+// T = float the mixed path, where the bulk arithmetic and its dot-product partials are FP32
+// and the reflector norms, scalars, R and f are FP64.  On the mixed path the bulk lanes do no
+// FP64 work beyond one conversion of their norm partial per column: they read an FP32 copy
+// fT of f and write FP32 partials, which the reducer sums across warps in FP32 and converts
+// once per slot (an FP64-unit instruction costs the same whatever the active lanes, and lanes
+// cross column boundaries at different blocks).  With T = double, fT is f itself.
 template <typename T, typename Tin, int B, int V, bool kPipe>
 __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, const int hs,
                                           double *__restrict__ Rp, double *__restrict__ f,
-                                          double *__restrict__ seg_all, double *__restrict__ tot,
-                                          double *__restrict__ npart, const int n,
-                                          const Chunk<Tin> pf) {
+                                          T *fT, double *__restrict__ seg_dbl,
+                                          double *__restrict__ tot, double *__restrict__ npart,
+                                          const int n, const Chunk<Tin> pf) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int Wb = (blockDim.x >> 5) - 1;
@@ -426,7 +436,9 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
     const int Hw = hs / Wb;
     const int r = Hw >> 5;
     const int r0 = warp * Hw;
-    double *seg = seg_all + warp * kSegStride;
+    const int ss = seg_stride(n);
+    T *seg_all = reinterpret_cast<T *>(seg_dbl);
+    T *seg = seg_all + warp * ss;
 
     for (int J = 0; J < n; ++J) {
         if (Copy<T, Tin>::kAsync && pf.src && J >= 2) load_column(S, ldS, hs, pf, J - 2);
@@ -438,7 +450,7 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
         if (!reducer) {
             T nacc = (T)0;
             if (J > 0) {
-                const T fJ = (T)f[J];
+                const T fJ = fT[J];
                 for (int t = 0; t < r; ++t) {
                     const int i = lane + 32 * t;
                     const T s = fmat(-fJ, Sj[i], SJ[i]);
@@ -452,7 +464,7 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
                 }
             }
             npart[warp * 32 + lane] = (double)nacc;
-            for (int id = lane; id < 32 + U; id += 32) seg[id] = 0.0;
+            for (int id = lane; id < 32 + U; id += 32) seg[id] = (T)0;
         }
         __syncthreads();
 
@@ -463,31 +475,35 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
         } else if (U > 0) {
             // ---- B: fused update by reflector J-1 and dots with column J
             if constexpr (kPipe)
-                phase_b<T, B, V>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, f, seg);
+                phase_b<T, B, V>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, fT, seg);
             else
-                phase_b_plain<T, B>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, f, seg);
+                phase_b_plain<T, B>(lane, J, U, r, Hw, n, S, ldS, r0, Sj, SJ, fT, seg);
         }
         __syncthreads();
 
         // ---- reducer: dot products in a fixed order, row J of R, factors f[k] for k > J
         if (reducer) {
             for (int id = lane; id < 32 + U; id += 32) {
-                double t = seg_all[id];
-                for (int w = 1; w < Wb; ++w) t += seg_all[w * kSegStride + id];
-                tot[id] = t;
+                T t = seg_all[id];
+                for (int w = 1; w < Wb; ++w) t += seg_all[w * ss + id];
+                tot[id] = (double)t;
             }
             __syncwarp();
             const int Nw = U * Hw;
-            double *dk = tot + kSegStride;
+            double *dk = tot + ss;
             for (int kk = lane; kk < U; kk += 32) {
                 const int la = (32 * (kk * Hw + 1) - 1) / Nw;
                 const int lb = (32 * (kk + 1) * Hw - 1) / Nw;
-                double d = tot[kk + la];
-                for (int l = la + 1; l <= lb; ++l) d += tot[kk + l];
-                dk[kk] = d;
+                double d0 = tot[kk + la], d1 = 0.0;  // two chains: half the latency
+                for (int l = la + 1; l + 1 <= lb; l += 2) {
+                    d0 += tot[kk + l];
+                    d1 += tot[kk + l + 1];
+                }
+                if (((lb - la) & 1) == 1) d0 += tot[kk + lb];
+                dk[kk] = d0 + d1;
             }
             __syncwarp();
-            apply_reflector(lane, n, J, h, Rp, f, dk);
+            apply_reflector<T>(lane, n, J, h, Rp, f, dk, fT);
         }
         __syncthreads();
     }
@@ -512,7 +528,8 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int Wp = (blockDim.x >> 5) - 1;  // worker warps 1..Wp
-    double *seg = seg_all + (warp > 0 ? warp - 1 : 0) * kSegStride;
+    const int ss = seg_stride(n);
+    double *seg = seg_all + (warp > 0 ? warp - 1 : 0) * ss;
 
     for (int J = 0; J < n; ++J) {
         const int U = n - J - 1;
@@ -605,7 +622,7 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
                 const int Nw = (kc1 - kc0) * cw;
                 const int la = (32 * (rel * cw + 1) - 1) / Nw;
                 const int lb = (32 * (rel + 1) * cw - 1) / Nw;
-                const double *sg = seg_all + w * kSegStride + rel;
+                const double *sg = seg_all + w * ss + rel;
                 double d0 = sg[la], d1 = 0.0;
                 for (int l = la + 1; l + 1 <= lb; l += 2) {
                     d0 += sg[l];
@@ -692,6 +709,11 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
     double *Sd = smem + L.S;
     double *Rp = smem + L.Rp;
     double *f = smem + L.f;
+    T *fT;
+    if constexpr (std::is_same<T, double>::value)
+        fT = f;
+    else
+        fT = reinterpret_cast<T *>(smem + L.fs);
     double *seg = smem + L.seg;
     double *tot = smem + L.tot;
     double *npart = smem + L.npart;
@@ -724,7 +746,7 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
             next.src = A + r1;
             next.rows = (int)((rend - r1 < a.h) ? rend - r1 : a.h);
         }
-        fold_leaf<T, Tin, B, V, kPipe>(S, a.ldS, a.hs, Rp, f, seg, tot, npart, n, next);
+        fold_leaf<T, Tin, B, V, kPipe>(S, a.ldS, a.hs, Rp, f, fT, seg, tot, npart, n, next);
         if (next.src) {
             if constexpr (!Copy<T, Tin>::kAsync) {
                 __syncthreads();
@@ -765,7 +787,7 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
             load_tri_cg(a.slots + (size_t)(off + first + ch) * n * n, n, n,
                         Sd + (size_t)(ch - 1) * n, ldSd);
         __syncthreads();
-        fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + kSegStride, n);
+        fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
         off = next_off;
         cnt = next_cnt;
         t = parent;

@@ -12,6 +12,17 @@ namespace tsqr {
 
 constexpr int kStatusNonfiniteBit = 1;
 
+// Dynamic shared-memory size of a kernel, with the whole unified L1/shared array given to
+// shared memory (the kernels keep their working set there and read A past L1).
+template <typename F>
+inline cudaError_t set_smem_attrs(F *fn, size_t smem_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // FP64 path (tsqr_f64.cu)
 size_t f64_smem_bytes(int n, int hs, int ldS, int warps);
 cudaError_t f64_prepare(size_t smem_bytes);

@@ -7,7 +7,7 @@
 namespace tsqr {
 
 template <typename Tin, int B, int V>
-__global__ void __launch_bounds__(256, 1) tsqr_mixed_kernel(const MixedArgs a) {
+__global__ void __launch_bounds__(288, 1) tsqr_mixed_kernel(const MixedArgs a) {
     leaf_tree_job<float, Tin, B, V, true>(a.base, static_cast<const Tin *>(a.A), a.ldSd,
                                           a.s_doubles, blockIdx.x);
 }
@@ -54,9 +54,7 @@ size_t mixed_smem_bytes(int n, int ldS, int warps) {
 cudaError_t mixed_prepare(size_t smem_bytes) {
     for (const auto &v : kVariants)
         for (int bf = 0; bf < 2; ++bf) {
-            const cudaError_t e = cudaFuncSetAttribute(
-                mixed_fn(bf != 0, v[0], v[1]), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                (int)smem_bytes);
+            const cudaError_t e = set_smem_attrs(mixed_fn(bf != 0, v[0], v[1]), smem_bytes);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
