@@ -1,4 +1,4 @@
-"""TEST INFRASTRUCTURE ONLY -- the plain FP64 CPU oracle for the R factor of A = QR.
+"""TEST INFRASTRUCTURE ONLY -- the plain FP64 CPU oracle for the R (and thin Q) factor of A = QR.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package.  The GPU library (``paper_1002_4250_gb300``) never imports it, and it
@@ -13,6 +13,8 @@ skinny matrices using MPI_Reduce" (arXiv:1002.4250) they follow:
 
 * ``householder_r``  -- Section 3 / Table 1 (the local Householder QR) applied to all of A,
   then the diag(R) >= 0 sign convention of Section 2;
+* ``householder_qr`` -- the same factorization plus the thin Q factor, formed by applying the
+  reflectors to the identity (Section 3, the remark on computing Q);
 * ``qr_uppers``      -- Section 2 / Table 3, the reduction operator qr(R1, R2);
 * ``tsqr_r``         -- Section 2 (local QR per tile, then the reduction) with the binary,
   flat and hybrid trees of Section 1 and Fig. 1;
@@ -62,6 +64,8 @@ def _bind(lib):
     d, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.oracle_householder_r.argtypes = [d, i64, i64, i64, d, i64, i32]
     lib.oracle_householder_r.restype = i32
+    lib.oracle_householder_qr.argtypes = [d, i64, i64, i64, d, i64, d, i64, i32]
+    lib.oracle_householder_qr.restype = i32
     lib.oracle_qr_uppers.argtypes = [i64, d, i64, d, i64, d, d]
     lib.oracle_qr_uppers.restype = None
     lib.oracle_tsqr_r.argtypes = [d, i64, i64, i64, i64, i32, i64, d, i64]
@@ -129,6 +133,19 @@ def householder_r(A, nthreads: int = 1, lib=None) -> np.ndarray:
     _check((lib or _load()).oracle_householder_r(_ptr(A), m, n, max(m, 1), _ptr(R), max(n, 1),
                                         int(nthreads)), "householder_r")
     return R
+
+
+def householder_qr(A, nthreads: int = 1, lib=None):
+    """(Q, R) of one unblocked Householder QR of all of A (m >= n), in FP64: Q m x n with
+    orthonormal columns, R n x n with diag(R) >= 0, A = Q R."""
+    A = as_colmajor(A)
+    m, n = A.shape
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    _check((lib or _load()).oracle_householder_qr(_ptr(A), m, n, max(m, 1), _ptr(Q), max(m, 1),
+                                                  _ptr(R), max(n, 1), int(nthreads)),
+           "householder_qr")
+    return Q, R
 
 
 def qr_uppers(R1, R2, count_flops: bool = False, lib=None):

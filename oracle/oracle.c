@@ -1,8 +1,8 @@
 /*
  * oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, obviously correct FP64 CPU oracle for the R factor of A = QR of a
- * tall-and-skinny matrix, written from J. Langou, "Computing the R of the QR factorization
+ * A plain, slow, obviously correct FP64 CPU oracle for the R factor (and the thin Q factor)
+ * of A = QR of a tall-and-skinny matrix, written from J. Langou, "Computing the R of the QR factorization
  * of tall and skinny matrices using MPI_Reduce" (arXiv:1002.4250).
  *
  * Only the test suite, the smoke check and the CPU-baseline leg of the benchmark may load
@@ -168,6 +168,102 @@ int oracle_householder_r(const double *A, int64_t m, int64_t n, int64_t lda, dou
         for (int64_t i = 0; i <= k && i < rows; ++i) AT(R, ldr, i, k) = AT(W, m, i, k);
     oracle_sign_fix(n, R, ldr);
     free(team);
+    free(th);
+    free(W);
+    free(tau);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Thin QR of all of A (m >= n): Q (m x n, orthonormal columns) and R (n x n, diag >= 0)    */
+/* with A = Q R.  The factorization is the one of oracle_householder_r; Q is then formed by */
+/* applying its reflectors to the first n columns of the identity, Q = H_0 H_1 ... H_{n-1}   */
+/* [I_n; 0] (Section 3: the Q factor is obtained by applying the stored Householder        */
+/* transformations to the identity).  Column k of [I_n; 0] is e_k, which H_j leaves alone   */
+/* for j > k (it is zero on rows j..m-1), so column k receives H_k, H_{k-1}, ..., H_0 in    */
+/* that order.  Columns are independent: with nthreads > 1 they are split cyclically and    */
+/* the result is bitwise independent of nthreads.  The sign convention diag(R) >= 0 negates */
+/* row k of R and column k of Q together, which leaves Q R unchanged.                       */
+/* ------------------------------------------------------------------------------------- */
+typedef struct {
+    const double *W;
+    double *Q;
+    int64_t m, n, ldw, ldq;
+    const double *tau;
+    int nthreads, tid;
+} q_team_t;
+
+static void *q_worker(void *p) {
+    q_team_t *a = (q_team_t *)p;
+    for (int64_t k = a->tid; k < a->n; k += a->nthreads) {
+        double *q = &AT(a->Q, a->ldq, 0, k);
+        for (int64_t i = 0; i < a->m; ++i) q[i] = (i == k) ? 1.0 : 0.0;
+        for (int64_t j = k; j >= 0; --j) {
+            const double t = a->tau[j];
+            if (t == 0.0) continue;
+            const double *u = &AT(a->W, a->ldw, 0, j);
+            double s = q[j];
+            for (int64_t i = j + 1; i < a->m; ++i) s = fma(u[i], q[i], s);
+            const double ts = t * s;
+            q[j] -= ts;
+            for (int64_t i = j + 1; i < a->m; ++i) q[i] = fma(-ts, u[i], q[i]);
+        }
+    }
+    return NULL;
+}
+
+int oracle_householder_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q,
+                          int64_t ldq, double *R, int64_t ldr, int nthreads) {
+    if (n < 0 || m < n || ldr < n || (m > 0 && (lda < m || ldq < m))) return 1;
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t i = 0; i < n; ++i) AT(R, ldr, i, k) = 0.0;
+    if (n == 0) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = (int)n;
+    double *W = (double *)malloc(sizeof(double) * (size_t)m * (size_t)n);
+    double *tau = (double *)calloc((size_t)n, sizeof(double));
+    hh_team_t *team = (hh_team_t *)malloc(sizeof(hh_team_t) * nthreads);
+    q_team_t *qteam = (q_team_t *)malloc(sizeof(q_team_t) * nthreads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    if (!W || !tau || !team || !qteam || !th) {
+        free(W);
+        free(tau);
+        free(team);
+        free(qteam);
+        free(th);
+        return 2;
+    }
+    for (int64_t k = 0; k < n; ++k) memcpy(&AT(W, m, 0, k), &AT(A, lda, 0, k), sizeof(double) * m);
+
+    /* the factorization: reflector j's tail is W(j+1:m-1, j), its scalar tau[j] */
+    pthread_barrier_t bar;
+    if (nthreads > 1) pthread_barrier_init(&bar, NULL, (unsigned)nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        team[t] = (hh_team_t){W, m, n, m, nthreads, t, tau, &bar};
+        if (t > 0) pthread_create(&th[t], NULL, hh_worker, &team[t]);
+    }
+    hh_worker(&team[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    if (nthreads > 1) pthread_barrier_destroy(&bar);
+
+    /* Q = H_0 ... H_{n-1} [I_n; 0], column by column */
+    for (int t = 0; t < nthreads; ++t) {
+        qteam[t] = (q_team_t){W, Q, m, n, m, ldq, tau, nthreads, t};
+        if (t > 0) pthread_create(&th[t], NULL, q_worker, &qteam[t]);
+    }
+    q_worker(&qteam[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t i = 0; i <= k; ++i) AT(R, ldr, i, k) = AT(W, m, i, k);
+    for (int64_t k = 0; k < n; ++k) {
+        const double dkk = AT(R, ldr, k, k);  /* before the sign fix below negates row k */
+        if (dkk < 0.0)
+            for (int64_t i = 0; i < m; ++i) AT(Q, ldq, i, k) = -AT(Q, ldq, i, k);
+    }
+    oracle_sign_fix(n, R, ldr);
+    free(team);
+    free(qteam);
     free(th);
     free(W);
     free(tau);

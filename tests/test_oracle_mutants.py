@@ -43,6 +43,14 @@ MUTANTS = {
                               "for (int64_t i = 0; i < k; ++i) d -= G[i + k * n];"),
     "residual_drops_last_row": ("int64_t len = (k < l ? k : l) + 1;",
                                 "int64_t len = (k < l ? k : l);"),
+    "q_reflectors_in_forward_order": ("for (int64_t j = k; j >= 0; --j) {",
+                                      "for (int64_t j = 0; j <= k; ++j) {"),
+    "q_skips_first_reflector": ("for (int64_t j = k; j >= 0; --j) {",
+                                "for (int64_t j = k; j > 0; --j) {"),
+    "q_column_not_flipped": ("AT(Q, ldq, i, k) = -AT(Q, ldq, i, k);",
+                             "AT(Q, ldq, i, k) = AT(Q, ldq, i, k);"),
+    "q_wrong_identity_column": ("q[i] = (i == k) ? 1.0 : 0.0;", "q[i] = (i == 0) ? 1.0 : 0.0;"),
+    "q_dot_drops_pivot_entry": ("double s = q[j];", "double s = 0.0;"),
 }
 
 
@@ -58,11 +66,21 @@ def _pins_pass(lib) -> bool:
                     return False
         rng = np.random.default_rng(5)
         R0 = _rand_upper(rng, 8, 100.0)
-        A = _planted_q0(rng, 120, 8) @ R0
+        Q0 = _planted_q0(rng, 120, 8)
+        A = Q0 @ R0
         kap = np.linalg.cond(R0)
         for R in (O.householder_r(A, lib=lib), O.tsqr_r(A, b=16, tree="binary", lib=lib)):
             if not O.rel_err(R, R0) <= 50 * kap * U:
                 return False
+        # the thin Q factor: planted, and A = Q R with orthonormal columns
+        Q, Rq = O.householder_qr(A, lib=lib)
+        if not (O.rel_err(Rq, R0) <= 50 * kap * U and O.rel_err(Q, Q0) <= 50 * kap * U):
+            return False
+        G = rng.standard_normal((60, 5))
+        Qg, Rg = O.householder_qr(G, lib=lib)
+        if not (np.abs(Qg.T @ Qg - np.eye(5)).max() <= 300 * U
+                and np.linalg.norm(G - Qg @ Rg) <= 300 * U * np.linalg.norm(G)):
+            return False
         A = np.array([[1.0, 2.0], [1e-9, 3.0], [0.0, 4.0], [1e-12, -1.0]])
         if not O.rel_err(O.householder_r(A, lib=lib), _mp_cholesky_r(A)) <= 50 * np.linalg.cond(A) * U:
             return False
