@@ -379,11 +379,11 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
     int nmax = 1;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
-    // two CTAs per SM as for single problems: FP64 whenever the widest problem's chunk fits
-    // at one row per lane, mixed when it fits at two
+    // two CTAs per SM when the widest problem's chunk fits at two rows per lane (one CTA per
+    // SM with taller chunks measured faster on the varlen batch otherwise: 717 against
+    // 1010 ms for FP64 with widths up to 64)
     size_t budget = two_per_sm;
-    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < (mixed ? 2 : 1))
-        budget = one_per_sm;
+    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2) budget = one_per_sm;
     // per width: chunk rows
     std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1), vec_of(TSQR_MAX_N + 1, 1);
     size_t smem = 0;

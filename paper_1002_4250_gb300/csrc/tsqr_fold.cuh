@@ -448,22 +448,39 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
 
         // ---- A: column J gets reflector J-1; per-lane partial squared norm of column J
         if (!reducer) {
-            T nacc = (T)0;
+            T nacc = (T)0, nacc2 = (T)0;  // two chains: half the latency for tall lanes
             if (J > 0) {
                 const T fJ = fT[J];
-                for (int t = 0; t < r; ++t) {
+                int t = 0;
+                for (; t + 1 < r; t += 2) {
+                    const int i = lane + 32 * t;
+                    const T s = fmat(-fJ, Sj[i], SJ[i]);
+                    const T s2 = fmat(-fJ, Sj[i + 32], SJ[i + 32]);
+                    SJ[i] = s;
+                    SJ[i + 32] = s2;
+                    nacc = fmat(s, s, nacc);
+                    nacc2 = fmat(s2, s2, nacc2);
+                }
+                if (t < r) {
                     const int i = lane + 32 * t;
                     const T s = fmat(-fJ, Sj[i], SJ[i]);
                     SJ[i] = s;
                     nacc = fmat(s, s, nacc);
                 }
             } else {
-                for (int t = 0; t < r; ++t) {
+                int t = 0;
+                for (; t + 1 < r; t += 2) {
+                    const T s = SJ[lane + 32 * t];
+                    const T s2 = SJ[lane + 32 * t + 32];
+                    nacc = fmat(s, s, nacc);
+                    nacc2 = fmat(s2, s2, nacc2);
+                }
+                if (t < r) {
                     const T s = SJ[lane + 32 * t];
                     nacc = fmat(s, s, nacc);
                 }
             }
-            npart[warp * 32 + lane] = (double)nacc;
+            npart[warp * 32 + lane] = (double)(nacc + nacc2);
             for (int id = lane; id < 32 + U; id += 32) seg[id] = (T)0;
         }
         __syncthreads();
