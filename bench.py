@@ -350,7 +350,33 @@ def bench_extras(dev):
     torch.cuda.empty_cache()
     out["widths_2e24"] = bench_widths(dev, ms64)
     out["varlen_batch"] = bench_batched(dev)
+    out["thin_qr"] = bench_qr(dev)
     return out
+
+
+def bench_qr(dev):
+    """tsqr_qr (thin Q and R, FP64) on 4,194,304 x 32 and 16,777,216 x 64: time, GFLOP/s with
+    LAPACK's counts (geqrf 2mn^2 - 2n^3/3 plus orgqr 2mn^2 - 2n^3/3), the Q passes' share
+    (tsqr_qr minus tsqr_r with the same plan), and the Q passes' FP64 rate on the flops they
+    execute (4mn^2: every leaf reflector meets all n columns of the carried block)."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    res = {}
+    for m, n in ((4194304, 32), (1 << 24, 64)):
+        A = workloads.gaussian(m, n, seed=0, device=dev).T
+        Q = torch.empty(n, m, dtype=torch.float64, device=dev).T
+        R = T.empty_r(n, dev)
+        reps = 5 if n <= 32 else 2
+        ms_qr = time_call(lambda: T.tsqr_qr(A, Q=Q, R=R), reps=reps, warmup=1)
+        ms_r = time_call(lambda: T.tsqr_r(A, R=R), reps=reps, warmup=1)
+        fl = 4.0 * m * n * n - 4.0 * n ** 3 / 3
+        res[f"{m}x{n}"] = {"ms": ms_qr, "gflops_lapack_count": fl / ms_qr / 1e6,
+                           "r_only_ms": ms_r, "q_passes_ms": ms_qr - ms_r,
+                           "q_passes_gflops_executed": 4.0 * m * n * n / (ms_qr - ms_r) / 1e6}
+        del A, Q
+        torch.cuda.empty_cache()
+    return res
 
 
 def bench_widths(dev, ms64=None):

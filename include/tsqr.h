@@ -109,6 +109,33 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
                              int64_t ld2, double *R, int64_t ldr, int32_t normalize,
                              tsqr_stream_t stream);
 
+/* Thin QR: Q (m x n, orthonormal columns) and R (n x n, diag(R) >= 0) with A = Q R, FP64.
+ * Section 3 notes that the Q factor is obtained by applying the Householder transformations
+ * of the reduction to the identity, which requires keeping every node's Householder vectors
+ * and the shape of the tree.  This call does that: the factorization is tsqr_r's (same plan,
+ * same kernels, the same R bit for bit) with the reflectors of every leaf chunk and tree node
+ * kept, then Q = H [I_n; 0] (with the sign convention applied to Q's columns) is formed top-down
+ * through the tree and backwards through each leaf's chunks.  Q is unique for A of full rank
+ * (as R is); with Householder reflectors it is then orthonormal to working accuracy however
+ * ill-conditioned A is.  For rank-deficient A (a zero on R's diagonal) A = Q R still holds,
+ * but the columns of Q beyond the rank are not guaranteed orthonormal: each leaf's first chunk
+ * is folded under a zero triangle, and the part of Q that an identity reflector leaves in
+ * those rows is dropped (the zero matrix gives Q = 0).
+ *   A    : device, column-major m x n, lda >= m; read only.  m >= n >= 1.
+ *   Q    : device, column-major m x n, ldq >= m; must not overlap A.  It also serves as the
+ *          store of the leaf reflectors between the two passes.
+ *   R    : device, column-major n x n, ldr >= n.
+ *   plan : NULL = AUTO, or as for tsqr_r_ex.  The plan's chunking must put every chunk
+ *          boundary at a multiple of its chunk height (AUTO and HYBRID/FLAT plans do; a BINARY
+ *          tile taller than one chunk that is not a multiple of it does not).
+ * Returns TSQR_ERR_UNSUPPORTED when the Q pass's chunk buffers (two chunks and an n x n block
+ * in shared memory) do not fit: with the AUTO plan every n <= 64 fits.  Workspace: about
+ * (2 + arity) n^2 doubles per tree node plus 2n per chunk, from the per-stream pool.
+ * Launches: the factorization, one per tree level below the root, and the leaf pass. */
+tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q,
+                      int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
+                      tsqr_stream_t stream);
+
 /* Varlen batch of independent problems: R_i = R factor of A_i for i < count.
  *   ptrs    : host array of `count` device pointers; A_i is column-major m_i x n_i with
  *             lda_i = m_i (e.g. all pointing into one packed buffer).

@@ -69,6 +69,8 @@ def _load():
     capi.tsqr_resolve_plan.argtypes = [_i64, _i64, _i32, _i32, ctypes.POINTER(Plan), ctypes.POINTER(Plan)]
     capi.tsqr_resolve_plan.restype = _i32
     capi.tsqr_r_noalloc.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
+    capi.tsqr_qr.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p, _i64, ctypes.POINTER(Plan), _p]
+    capi.tsqr_qr.restype = _i32
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -86,7 +88,7 @@ def __getattr__(name):
 #: every symbol include/tsqr.h declares
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
-               "tsqr_last_launch_count", "tsqr_r_noalloc")
+               "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr")
 
 
 class TsqrError(RuntimeError):
@@ -172,6 +174,22 @@ def tsqr_r_ex(A, prec=None, plan: Plan | None = None, R=None, stream=None):
     check(_load().tsqr_r_ex(A.data_ptr(), dt, int(prec), m, n, lda, R.data_ptr(),
                          max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_r_ex")
     return R
+
+
+def tsqr_qr(A, Q=None, R=None, plan: Plan | None = None, stream=None):
+    """Thin QR of a logical (m, n) column-major FP64 tensor: returns (Q, R) with Q (m, n)
+    column-major (orthonormal columns) and R (n, n), diag(R) >= 0, A = Q R."""
+    m, n, lda = _colmajor_dims(A)
+    if Q is None:
+        import torch
+        Q = torch.empty(n, m, dtype=torch.float64, device=A.device).T
+    _, _, ldq = _colmajor_dims(Q, "Q")
+    if R is None:
+        R = empty_r(n, A.device)
+    pp = ctypes.byref(plan) if plan is not None else None
+    check(_load().tsqr_qr(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(),
+                          max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_qr")
+    return Q, R
 
 
 def tsqr_qr_uppers(R1, R2, normalize=False, R=None, stream=None):

@@ -11,6 +11,7 @@
 
 #include "tsqr.h"
 #include "tsqr_internal.h"
+#include "tsqr_qr.cuh"
 
 using namespace tsqr;
 
@@ -313,6 +314,112 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     return TSQR_SUCCESS;
 }
 
+// Thin QR: the FP64 factorization with its reflectors kept, then the Q passes (tsqr_qr.cu).
+// Workspace: counters | tree slots | chunk scalars | node tails | node scalars | node blocks |
+// signs.
+tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q, int64_t ldq,
+                     double *R, int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
+    g_last_launches = 0;
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, over, &p);
+    if (st != TSQR_SUCCESS) return st;
+    if (p.unit % p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    const size_t leaf_smem = q_leaf_smem_bytes((int)n, p.ldS, p.warps);
+    const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity);
+    if (leaf_smem > di.smem_block_optin || tree_smem > di.smem_block_optin)
+        return TSQR_ERR_UNSUPPORTED;
+    if (qr_prepare(p.smem, leaf_smem, tree_smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int64_t nchunks = (m + p.h - 1) / p.h;
+    const size_t nn = (size_t)n * (size_t)n;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
+    const size_t csc_bytes = align_up((size_t)nchunks * 2 * n * sizeof(double), 256);
+    const size_t nv_bytes = align_up((size_t)p.nodes * (p.arity - 1) * nn * sizeof(double), 256);
+    const size_t nsc_bytes = align_up((size_t)p.nodes * 2 * n * sizeof(double), 256);
+    const size_t blk_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
+    const size_t sgn_bytes = align_up((size_t)n * sizeof(double), 256);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, cnt_bytes + slot_bytes + csc_bytes + nv_bytes + nsc_bytes +
+                                   blk_bytes + sgn_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *base = (char *)ws->base;
+    F64Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = A;
+    a.m = m;
+    a.lda = lda;
+    a.n = (int)n;
+    a.unit = p.unit;
+    a.nunits = p.nunits;
+    a.nleaves = p.nleaves;
+    a.arity = p.arity;
+    a.h = p.h;
+    a.hs = p.hs;
+    a.blk = p.blk;
+    a.vec = p.vec;
+    a.ldS = p.ldS;
+    a.counters = (unsigned int *)base;
+    a.slots = (double *)(base + cnt_bytes);
+    a.R = R;
+    a.ldr = ldr;
+    a.status = ws->status;
+    size_t o = cnt_bytes + slot_bytes;
+    a.q.V = Q;
+    a.q.ldv = ldq;
+    a.q.chunk_sc = (double *)(base + o);
+    o += csc_bytes;
+    a.q.node_V = (double *)(base + o);
+    o += nv_bytes;
+    a.q.node_sc = (double *)(base + o);
+    o += nsc_bytes;
+    double *blocks = (double *)(base + o);
+    o += blk_bytes;
+    a.q.signs = (double *)(base + o);
+    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    int launches = 1;
+    // tree pass, from the root's level down to level 1 (whose children are the leaves)
+    const TreeShape &sh = p.shape;
+    for (int L = sh.levels - 1; L >= 1; --L) {
+        QTreeArgs t;
+        t.n = (int)n;
+        t.arity = p.arity;
+        t.level_off = sh.offset[L];
+        t.child_cnt = sh.count[L - 1];
+        t.child_off = sh.offset[L - 1];
+        t.is_root = (L == sh.levels - 1) ? 1 : 0;
+        t.node_V = a.q.node_V;
+        t.node_sc = a.q.node_sc;
+        t.signs = a.q.signs;
+        t.B = blocks;
+        if (q_tree_launch(t, sh.count[L], tree_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+        ++launches;
+    }
+    QLeafArgs l;
+    l.Q = Q;
+    l.m = m;
+    l.ldq = ldq;
+    l.n = (int)n;
+    l.unit = p.unit;
+    l.nunits = p.nunits;
+    l.nleaves = p.nleaves;
+    l.h = p.h;
+    l.hs = p.hs;
+    l.ldS = p.ldS;
+    l.chunk_sc = a.q.chunk_sc;
+    l.B = blocks;
+    l.signs = a.q.signs;
+    l.single = (sh.levels == 1) ? 1 : 0;
+    if (q_leaf_launch(l, p.blk, p.warps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    g_last_launches = launches + 1;
+    return TSQR_SUCCESS;
+}
+
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
@@ -563,6 +670,16 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
         return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
     if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
     return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
+}
+
+tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q,
+                      int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
+                      tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr) || n < 1 || m < n || ldq < m) return TSQR_ERR_INVALID_ARG;
+    if (!A || !Q || !R) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    return run_qr(A, m, n, lda, Q, ldq, R, ldr, plan, (cudaStream_t)stream);
 }
 
 tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const double *R2,

@@ -34,6 +34,19 @@ struct TreeShape {
     int offset[kMaxLevels];
 };
 
+// Where the factorization behind tsqr_qr keeps its reflectors for forming Q (all null for the
+// R-only kernels).  Reflector J of a chunk or node is H = I - tau v v^T with v = [e_J; c x],
+// x its stored tail; (tau, c) = (0, 0) for an identity reflector.
+struct QStore {
+    double *V;         // m x n, leading dimension ldv: each chunk's tails, in the chunk's rows
+    int64_t ldv;
+    double *chunk_sc;  // per chunk (id = first row / h): tau_J, c_J for J = 0..n-1
+    double *node_V;    // per tree node id: arity-1 stacked n x n tails, leading dim (arity-1) n
+    double *node_sc;   // per tree node id: tau_J, c_J
+    double *signs;     // n entries: -1 where the root's R(k,k) < 0 (rows the sign convention
+                       // negates), else +1
+};
+
 struct F64Args {
     const double *A;
     int64_t m, lda;
@@ -52,6 +65,7 @@ struct F64Args {
     double *R;              // output, column-major n x n, ld ldr
     int64_t ldr;
     int *status;            // device status word (TSQR_STATUS_NONFINITE is or-ed in)
+    QStore q;               // reflector storage (tsqr_qr's factorization only)
 };
 
 // Mixed-precision kernel arguments: the FP64 arguments (base.A unused) plus A of another

@@ -114,6 +114,25 @@ __device__ __forceinline__ void load_column(T *S, int ldS, int hs, const Chunk<T
 //   overlaps phase B; in the tree operator warp J mod W).
 // ------------------------------------------------------------------------------------------
 
+// Conversions between a double x with 1 <= |x| < 4 and float, on the IEEE-754 bit fields with
+// integer instructions: double <-> float conversions issue to the FP64 unit, whose every
+// instruction the reducer pays for.  Toward zero to float (the top 23 fraction bits; the seeds
+// below need ~2^-20 only); exact back to double.
+__device__ __forceinline__ float seed_f32(const double x) {
+    const long long b = __double_as_longlong(x);
+    const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    const unsigned frac = (unsigned)((b >> 29) & 0x7fffff);
+    return __uint_as_float(sign | ((unsigned)e << 23) | frac);
+}
+// y a normal float
+__device__ __forceinline__ double widen_f32(const float y) {
+    const unsigned u = __float_as_uint(y);
+    const long long sign = (long long)(u >> 31) << 63;
+    const long long e = (long long)((u >> 23) & 0xff) - 127 + 1023;
+    return __longlong_as_double(sign | (e << 52) | ((long long)(u & 0x7fffff) << 29));
+}
+
 // 1/sqrt(t) for finite t > 0 by Newton's iteration for the reciprocal square root,
 // y <- y + y (1 - t y^2) / 2, started from the FP32 hardware estimate.  t is first scaled by an
 // even power of two into [1, 4) (exact, on the exponent bits) so that the FP32 estimate cannot
@@ -125,7 +144,7 @@ __device__ __forceinline__ double recip_sqrt(double t) {
     if (e == 0 || e == 0x7ff) return rsqrt(t);
     const int k = (e - 1023) >> 1;  // t = tm 4^k, tm in [1, 4)
     const double tm = __longlong_as_double(b - ((long long)(2 * k) << 52));
-    double y = (double)rsqrtf((float)tm);
+    double y = widen_f32(rsqrtf(seed_f32(tm)));
     double h = fma(-tm * y, y, 1.0);
     y = fma(__longlong_as_double(__double_as_longlong(y) - (1LL << 52)), h, y);  // y/2 exactly
     h = fma(-tm * y, y, 1.0);
@@ -143,7 +162,7 @@ __device__ __forceinline__ double recip(double x) {
     if (e == 0 || e >= 0x7fd) return 1.0 / x;
     const int k = e - 1023;
     const double xm = __longlong_as_double(b - ((long long)k << 52));
-    double y = (double)__fdividef(1.0f, (float)xm);
+    double y = widen_f32(__fdividef(1.0f, seed_f32(xm)));
     double h = fma(-xm, y, 1.0);
     y = fma(y, h, y);
     h = fma(-xm, y, 1.0);
@@ -408,6 +427,29 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
     if (i != 0) seg[lane + kk] = acc;
 }
 
+// Where one chunk's reflectors go when the fold keeps them (tsqr_qr): the tails of column J
+// into V(0:rows-1, J) (leading dimension ldv), (tau_J, c_J) into sc[2J], sc[2J+1].
+struct QChunk {
+    double *V;
+    int64_t ldv;
+    int rows;
+    double *sc;
+};
+
+// A bulk lane's rows (r0 + lane + 32 t, t < r) of column `col` of the chunk to qc.V, rows
+// past the chunk's last row of A skipped.
+template <typename T>
+__device__ __forceinline__ void store_tail_rows(const T *S, const int ldS, const int r0,
+                                                const int r, const int lane, const int col,
+                                                const QChunk &qc) {
+    const T *src = S + (size_t)col * ldS;
+    double *dst = qc.V + (int64_t)col * qc.ldv;
+    for (int t = 0; t < r; ++t) {
+        const int i = r0 + lane + 32 * t;
+        if (i < qc.rows) dst[i] = (double)src[i];
+    }
+}
+
 // Leaf fold.  Warps 0..Wb-1 ("bulk" warps) own the chunk's rows; warp Wb is the reducer.
 // Every bulk lane owns r rows of its warp's block (Hw = 32 r) and a phase-B run of U r items
 // starting at item lane * U r; runs and column boundaries are multiples of r, so blocks of B
@@ -423,12 +465,16 @@ __device__ __forceinline__ void phase_b(const int lane, const int J, const int U
 // fT of f and write FP32 partials, which the reducer sums across warps in FP32 and converts
 // once per slot (an FP64-unit instruction costs the same whatever the active lanes, and lanes
 // cross column boundaries at different blocks).  With T = double, fT is f itself.
-template <typename T, typename Tin, int B, int V, bool kPipe>
+// With kStore (FP64 only) the fold also keeps its reflectors (qc): column J's tail is final
+// once phase A of step J has run, and is written out during step J+1, before the prefetch of
+// step J+2 reuses the column.
+template <typename T, typename Tin, int B, int V, bool kPipe, bool kStore = false>
 __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, const int hs,
                                           double *__restrict__ Rp, double *__restrict__ f,
                                           T *fT, double *__restrict__ seg_dbl,
                                           double *__restrict__ tot, double *__restrict__ npart,
-                                          const int n, const Chunk<Tin> pf) {
+                                          const int n, const Chunk<Tin> pf,
+                                          const QChunk qc = QChunk{}) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int Wb = (blockDim.x >> 5) - 1;
@@ -442,6 +488,9 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
 
     for (int J = 0; J < n; ++J) {
         if (Copy<T, Tin>::kAsync && pf.src && J >= 2) load_column(S, ldS, hs, pf, J - 2);
+        if constexpr (kStore) {
+            if (!reducer && J >= 1) store_tail_rows(S, ldS, r0, r, lane, J - 1, qc);
+        }
         const int U = n - J - 1;
         T *SJ = S + (size_t)J * ldS + r0;
         const T *Sj = S + (size_t)(J > 0 ? J - 1 : 0) * ldS + r0;
@@ -489,6 +538,12 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
         if (reducer) {
             // ---- reflector J's scalars, overlapping phase B
             h = make_reflector(Rp[rowoff(n, J)], sum_norm_partials(lane, Wb, npart));
+            if constexpr (kStore) {
+                if (lane == 0) {
+                    qc.sc[2 * J] = h.ident ? 0.0 : h.tau;
+                    qc.sc[2 * J + 1] = h.ident ? 0.0 : h.c;
+                }
+            }
         } else if (U > 0) {
             // ---- B: fused update by reflector J-1 and dots with column J
             if constexpr (kPipe)
@@ -524,6 +579,10 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
         }
         __syncthreads();
     }
+    if constexpr (kStore) {
+        if (!reducer) store_tail_rows(S, ldS, r0, r, lane, n - 1, qc);
+        __syncthreads();  // the prefetch below reuses column n-1
+    }
     if (Copy<T, Tin>::kAsync && pf.src) {
         for (int col = n - 2; col < n; ++col)
             if (col >= 0) load_column(S, ldS, hs, pf, col);
@@ -538,10 +597,13 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
 // Warp 0 updates column J, forms its squared norm and then reflector J's scalars while the
 // other warps (which split the trailing columns) run the fused update + dot sweep; warp 0 then
 // sums their partials in a fixed order and updates R and f.  Needs at least two warps.
+// With nsc non-null the reflectors' (tau_J, c_J) go to nsc[2J], nsc[2J+1] (their tails stay
+// in S: rows 0..J of each triangle's column J).
 __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldSd, const int c,
                                            double *__restrict__ Rp, double *__restrict__ f,
                                            double *__restrict__ seg_all,
-                                           double *__restrict__ dk, const int n) {
+                                           double *__restrict__ dk, const int n,
+                                           double *nsc = nullptr) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int Wp = (blockDim.x >> 5) - 1;  // worker warps 1..Wp
@@ -581,6 +643,10 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
         Reflector hr;
         if (warp == 0) {
             hr = make_reflector(Rp[rowoff(n, J)], sig2);
+            if (nsc && lane == 0) {
+                nsc[2 * J] = hr.ident ? 0.0 : hr.tau;
+                nsc[2 * J + 1] = hr.ident ? 0.0 : hr.c;
+            }
         } else {
             // ---- B: worker warp w owns trailing columns [kc0, kc1); its (column, row) items
             //      are cut into 32 equal contiguous runs in lockstep
@@ -704,10 +770,11 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // Leaf + tree kernel.  CTA c owns the work units [c*nunits/nleaves, (c+1)*nunits/nleaves) of A
 // (one tile for the binary tree, a run of slabs for the flat and hybrid trees) and folds their
 // rows, h at a time, into its R (a flat tree over its chunks, Section 1, with the next chunk
-// streamed in during the current fold), then climbs the binary tree (Fig. 1): it
-// publishes R in its node's slot and bumps the parent's counter; the second child to arrive
-// combines [R_left; R_right] (left = lower index, always on top) and climbs on; the first
-// returns.  No CTA ever waits for another, and the operand order depends only on the indices.
+// streamed in during the current fold), then climbs the k-ary tree (k = 2: Fig. 1): it
+// publishes R in its node's slot and bumps the parent's counter; the last child to arrive
+// stacks the children in index order (the lowest on top), folds them and climbs on; the
+// others return.  No CTA ever waits for another, and the operand order depends only on the
+// indices.
 // ------------------------------------------------------------------------------------------
 // One leaf of one problem: fold the leaf's rows into R, then climb the problem's k-ary tree
 // (k = a.arity; level l has ceil(nleaves / k^l) nodes, stored level after level).  T: leaf storage and
@@ -716,7 +783,9 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // when the CTA is not the last of a node's children to arrive, or after writing the root.
 // The tree operator's FP64 view of S (leading dimension ldSd) must hold arity-1 stacked n x n
 // triangles.
-template <typename T, typename Tin, int B, int V, bool kPipe>
+// With kStore (FP64 only) every chunk's and every tree node's reflectors, and the root's row
+// signs, are kept in a.q for forming Q (tsqr_qr); chunk boundaries are then multiples of a.h.
+template <typename T, typename Tin, int B, int V, bool kPipe, bool kStore = false>
 __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, const int ldSd,
                                               const int s_doubles, const int leaf) {
     extern __shared__ __align__(16) double smem[];
@@ -763,7 +832,16 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
             next.src = A + r1;
             next.rows = (int)((rend - r1 < a.h) ? rend - r1 : a.h);
         }
-        fold_leaf<T, Tin, B, V, kPipe>(S, a.ldS, a.hs, Rp, f, fT, seg, tot, npart, n, next);
+        QChunk qc{};
+        if constexpr (kStore) {
+            const int64_t row0 = rbeg + c * a.h;
+            qc.V = a.q.V + row0;
+            qc.ldv = a.q.ldv;
+            qc.rows = (int)((rend - row0 < a.h) ? rend - row0 : a.h);
+            qc.sc = a.q.chunk_sc + (row0 / a.h) * 2 * n;
+        }
+        fold_leaf<T, Tin, B, V, kPipe, kStore>(S, a.ldS, a.hs, Rp, f, fT, seg, tot, npart, n,
+                                               next, qc);
         if (next.src) {
             if constexpr (!Copy<T, Tin>::kAsync) {
                 __syncthreads();
@@ -779,6 +857,10 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
     int cnt = a.nleaves, off = 0, t = leaf;  // nodes and first node id of the current level
     for (;;) {
         if (cnt == 1) {
+            if constexpr (kStore) {
+                for (int k2 = threadIdx.x; k2 < n; k2 += blockDim.x)
+                    a.q.signs[k2] = (Rp[rowoff(n, k2)] < 0.0) ? -1.0 : 1.0;
+            }
             store_normalized(Rp, n, a.R, a.ldr, a.status);
             return;
         }
@@ -804,7 +886,21 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
             load_tri_cg(a.slots + (size_t)(off + first + ch) * n * n, n, n,
                         Sd + (size_t)(ch - 1) * n, ldSd);
         __syncthreads();
-        fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
+        if constexpr (kStore) {
+            const size_t id = (size_t)next_off + parent;
+            const int ldv = (k - 1) * n;
+            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n,
+                       a.q.node_sc + id * 2 * n);
+            // the node's tails: rows 0..(nchild-1) n - 1 of S (zero below each diagonal)
+            double *dst = a.q.node_V + id * (size_t)ldv * n;
+            const int rows = (nchild - 1) * n;
+            for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+                const int col = idx / rows, row = idx - col * rows;
+                dst[row + (size_t)col * ldv] = Sd[row + (size_t)col * ldSd];
+            }
+        } else {
+            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
+        }
         off = next_off;
         cnt = next_cnt;
         t = parent;

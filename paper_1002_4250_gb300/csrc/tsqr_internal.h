@@ -47,6 +47,17 @@ int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes);
 cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, size_t smem_bytes,
                            cudaStream_t stream);
 
+// Thin QR (tsqr_qr.cu)
+struct QTreeArgs;
+struct QLeafArgs;
+size_t q_leaf_smem_bytes(int n, int ldS, int warps);
+size_t q_tree_smem_bytes(int n, int arity);
+cudaError_t qr_prepare(size_t factor_smem, size_t leaf_smem, size_t tree_smem);
+cudaError_t qr_factor_launch(const F64Args &a, int warps, size_t smem_bytes, cudaStream_t stream);
+cudaError_t q_tree_launch(const QTreeArgs &a, int grid, size_t smem_bytes, cudaStream_t stream);
+cudaError_t q_leaf_launch(const QLeafArgs &a, int blk, int warps, size_t smem_bytes,
+                          cudaStream_t stream);
+
 // The AUTO plan of tsqr_r as kernel arguments (tsqr_api.cu); A, R, workspace and status
 // pointers are left for the caller.
 tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,

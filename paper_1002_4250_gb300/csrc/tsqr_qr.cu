@@ -1,0 +1,370 @@
+// Thin QR (tsqr_qr): the R factorization of tsqr_r with its reflectors kept, then Q formed by
+// applying them to the first n columns of the identity, top-down through the tree and then
+// backwards through each leaf's chunks.  Section 3: computing Q means applying the stored
+// Householder transformations to the identity, which needs every node's Householder vectors
+// and the shape of the reduction tree.
+//
+// Q = H_tree [D; 0] spread over the leaves, D = diag(row signs of the sign convention), where a
+// tree node with children c_0 .. c_{k-1} (stacked in index order, c_0 on top) maps its block
+// B (n x n) to its children's blocks [B_0; ...; B_{k-1}] = H_node [B; 0]; a leaf maps its block
+// to its rows of Q chunk by chunk, last chunk first: [B'; Q_c] = H_chunk [B; 0], B' going on
+// to the previous chunk (the leaf folded its chunks in order, R_c = R([R_{c-1}; S_c])).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tsqr_fold.cuh"
+#include "tsqr_internal.h"
+#include "tsqr_qr.cuh"
+
+namespace tsqr {
+
+// ------------------------------------------------------------------------------------------
+// Factorization with storage: tsqr_r's leaf + tree kernel keeping its reflectors in a.q.
+// ------------------------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(288, 1) tsqr_qr_factor_kernel(const F64Args a) {
+    leaf_tree_job<double, double, B, 1, B == 1, true>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
+}
+
+namespace {
+const void *qr_factor_fn(int blk) {
+    switch (blk) {
+        case 4: return (const void *)tsqr_qr_factor_kernel<4>;
+        case 3: return (const void *)tsqr_qr_factor_kernel<3>;
+        case 2: return (const void *)tsqr_qr_factor_kernel<2>;
+        default: return (const void *)tsqr_qr_factor_kernel<1>;
+    }
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Tree pass, one launch per level from the root down: CTA t applies node (L, t)'s reflectors
+// to [B; 0] and writes its children's blocks.  Reflector J (reverse order) touches row J of the
+// top block and rows 0..J of each stacked block; its columns are independent, so each column
+// is handled by tpc lanes of one warp (no block barrier inside the loop).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tsqr_q_tree_kernel(const QTreeArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n, k = a.arity, t = blockIdx.x;
+    const int first = t * k;
+    const int nchild = min(k, a.child_cnt - first);
+    const size_t id = (size_t)a.level_off + t;
+    double *top = smem;          // n x n, leading dimension n
+    double *T = smem + n * n;    // (nchild-1) n x n, leading dimension (nchild-1) n
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        top[idx] = a.is_root ? ((row == col) ? a.signs[row] : 0.0) : a.B[id * n * n + idx];
+    }
+    if (nchild == 1) {  // a promoted lone child: its block is the node's
+        __syncthreads();
+        double *dst = a.B + ((size_t)a.child_off + first) * n * n;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) dst[idx] = top[idx];
+        return;
+    }
+    const int c = nchild - 1, ldT = c * n, ldX = (k - 1) * n;
+    for (int idx = threadIdx.x; idx < ldT * n; idx += blockDim.x) T[idx] = 0.0;
+    __syncthreads();
+    const double *X = a.node_V + id * (size_t)ldX * n;
+    const double *sc = a.node_sc + id * 2 * n;
+    int tpc = 1;  // lanes per column: a power of two <= 32 with tpc n <= blockDim
+    while (tpc < 32 && 2 * tpc * n <= (int)blockDim.x) tpc *= 2;
+    const int q0 = threadIdx.x / tpc, sub = threadIdx.x - q0 * tpc;
+    const bool active = q0 < n;
+    const int q = active ? q0 : n - 1;  // idle lanes shadow the last column, writing nothing
+    for (int J = n - 1; J >= 0; --J) {
+        const double tau = sc[2 * J], cj = sc[2 * J + 1];
+        if (tau == 0.0) continue;
+        const int h1 = J + 1, E = c * h1;
+        double d = 0.0;
+        for (int e = sub; e < E; e += tpc) {
+            const int tt = e / h1, i = e - tt * h1;
+            d = fma(X[tt * n + i + (size_t)J * ldX], T[tt * n + i + q * ldT], d);
+        }
+        for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
+        const double w = fma(cj, d, top[J + q * n]);
+        __syncwarp();
+        if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
+        const double gq = tau * cj * w;
+        if (active) {
+            for (int e = sub; e < E; e += tpc) {
+                const int tt = e / h1, i = e - tt * h1;
+                T[tt * n + i + q * ldT] = fma(-gq, X[tt * n + i + (size_t)J * ldX],
+                                              T[tt * n + i + q * ldT]);
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int ch = 0; ch < nchild; ++ch) {
+        double *dst = a.B + ((size_t)a.child_off + first + ch) * n * n;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+            const int col = idx / n, row = idx - col * n;
+            dst[idx] = (ch == 0) ? top[idx] : T[(ch - 1) * n + row + col * ldT];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Leaf pass.  One CTA per leaf, with the leaf fold's warps (W bulk + 1 reducer) and its
+// lockstep item split.  Per chunk, last first: X = the chunk's tails (read from Q), Z = 0 and
+// the carried block B ("top"); for J = n-1 .. 0, the bulk sweep applies reflector J+1's update
+// Z(:,q) -= g_q x_{J+1} and forms x_J . Z(:,q) for every column q; the reducer sums the
+// partials, w_q = B(J,q) + c_J d_q, B(J,q) -= tau_J w_q, g_q = tau_J c_J w_q.  After J = 0,
+// Z(:,q) -= g_q x_0 and Z is the chunk's rows of Q.
+// ------------------------------------------------------------------------------------------
+// Software pipelined: the next block's operands are loaded before the current block is
+// updated and stored (the two blocks never overlap: different rows, or the next column).
+template <int B>
+__device__ __forceinline__ void q_sweep(const int lane, const int n, const int r, const int Hw,
+                                        double *__restrict__ Z, const int ldS, const int r0,
+                                        const double *__restrict__ xu,
+                                        const double *__restrict__ xd,
+                                        const double *__restrict__ g, double *__restrict__ seg) {
+    const int run = n * r;
+    const int nblk = run / B;
+    const int p = lane * run;
+    int kk = p / Hw;
+    int i = p - kk * Hw;
+    double *Zk = Z + (size_t)kk * ldS + r0;
+    double acc = 0.0;
+    double z[B], d[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        z[q] = Zk[i + q];
+        d[q] = xd[i + q];
+    }
+    if (xu) {
+        double gk = g[kk];
+        double u[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) u[q] = xu[i + q];
+        for (int blk = 0; blk < nblk; ++blk) {
+            int i2 = i + B, kk2 = kk;
+            double *Zk2 = Zk;
+            const bool cross = (i2 == Hw);
+            if (cross) {
+                i2 = 0;
+                ++kk2;
+                Zk2 += ldS;
+            }
+            double z2[B], d2[B], u2[B];
+            if (blk + 1 < nblk) {
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    z2[q] = Zk2[i2 + q];
+                    d2[q] = xd[i2 + q];
+                    u2[q] = xu[i2 + q];
+                }
+            }
+            double x[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) x[q] = fma(-gk, u[q], z[q]);
+#pragma unroll
+            for (int q = 0; q < B; ++q) Zk[i + q] = x[q];
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fma(d[q], x[q], acc);
+            if (cross) {
+                seg[lane + kk] = acc;
+                acc = 0.0;
+                gk = g[min(kk2, n - 1)];
+            }
+            i = i2;
+            kk = kk2;
+            Zk = Zk2;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                z[q] = z2[q];
+                d[q] = d2[q];
+                u[q] = u2[q];
+            }
+        }
+    } else {
+        for (int blk = 0; blk < nblk; ++blk) {
+            int i2 = i + B, kk2 = kk;
+            double *Zk2 = Zk;
+            const bool cross = (i2 == Hw);
+            if (cross) {
+                i2 = 0;
+                ++kk2;
+                Zk2 += ldS;
+            }
+            double z2[B], d2[B];
+            if (blk + 1 < nblk) {
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    z2[q] = Zk2[i2 + q];
+                    d2[q] = xd[i2 + q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fma(d[q], z[q], acc);
+            if (cross) {
+                seg[lane + kk] = acc;
+                acc = 0.0;
+            }
+            i = i2;
+            kk = kk2;
+            Zk = Zk2;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                z[q] = z2[q];
+                d[q] = d2[q];
+            }
+        }
+    }
+    if (i != 0) seg[lane + kk] = acc;
+}
+
+template <int B>
+__global__ void __launch_bounds__(288, 1) tsqr_q_leaf_kernel(const QLeafArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Wb = (blockDim.x >> 5) - 1;
+    const bool reducer = (warp == Wb);
+    const int Hw = a.hs / Wb, r = Hw >> 5, r0 = warp * Hw;
+    const QLeafLayout L = q_leaf_layout(n, a.ldS, Wb + 1);
+    double *X = smem + L.X;
+    double *Z = smem + L.Z;
+    double *top = smem + L.top;
+    double *g = smem + L.g;
+    double *sc = smem + L.sc;
+    const int ss = seg_stride(n);
+    double *seg_all = smem + L.seg;
+    double *seg = seg_all + warp * ss;
+    double *tot = smem + L.tot;
+    const int leaf = blockIdx.x;
+
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        top[idx] = a.single ? ((row == col) ? a.signs[row] : 0.0)
+                            : a.B[(size_t)leaf * n * n + idx];
+    }
+    const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
+    const int64_t rbeg = u0 * a.unit;
+    const int64_t rend = (u1 * a.unit < a.m) ? u1 * a.unit : a.m;
+    const int64_t nchunks = (rend - rbeg + a.h - 1) / a.h;
+    for (int64_t c = nchunks - 1; c >= 0; --c) {
+        const int64_t row0 = rbeg + c * a.h;
+        const int rows = (int)((rend - row0 < a.h) ? rend - row0 : a.h);
+        __syncthreads();  // the previous chunk's X and Z are no longer read
+        for (int idx = threadIdx.x; idx < a.hs * n; idx += blockDim.x) {
+            const int col = idx / a.hs, i = idx - col * a.hs;
+            X[i + (size_t)col * a.ldS] = (i < rows) ? a.Q[row0 + i + (int64_t)col * a.ldq] : 0.0;
+            Z[i + (size_t)col * a.ldS] = 0.0;
+        }
+        const double *csc = a.chunk_sc + (row0 / a.h) * 2 * n;
+        for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) sc[j] = csc[j];
+        __syncthreads();
+        for (int J = n - 1; J >= 0; --J) {
+            if (!reducer) {
+                for (int id = lane; id < 32 + n; id += 32) seg[id] = 0.0;
+                __syncwarp();
+                q_sweep<B>(lane, n, r, Hw, Z, a.ldS, r0,
+                           (J + 1 < n) ? X + (size_t)(J + 1) * a.ldS + r0 : nullptr,
+                           X + (size_t)J * a.ldS + r0, g, seg);
+            }
+            __syncthreads();
+            if (reducer) {
+                for (int id = lane; id < 32 + n; id += 32) {
+                    double t = seg_all[id];
+                    for (int w = 1; w < Wb; ++w) t += seg_all[w * ss + id];
+                    tot[id] = t;
+                }
+                __syncwarp();
+                const double tau = sc[2 * J], cj = sc[2 * J + 1];
+                const int Nw = n * Hw;
+                for (int q = lane; q < n; q += 32) {
+                    // column q's partials: slots q + la .. q + lb (as in the leaf fold)
+                    const int la = (32 * (q * Hw + 1) - 1) / Nw;
+                    const int lb = (32 * (q + 1) * Hw - 1) / Nw;
+                    double d0 = tot[q + la], d1 = 0.0;
+                    for (int l = la + 1; l + 1 <= lb; l += 2) {
+                        d0 += tot[q + l];
+                        d1 += tot[q + l + 1];
+                    }
+                    if (((lb - la) & 1) == 1) d0 += tot[q + lb];
+                    const double w = fma(cj, d0 + d1, top[J + q * n]);
+                    top[J + q * n] = fma(-tau, w, top[J + q * n]);
+                    g[q] = tau * cj * w;
+                }
+            }
+            __syncthreads();
+        }
+        if (!reducer) {  // reflector 0's update
+            for (int q = 0; q < n; ++q) {
+                const double gq = g[q];
+                for (int t = 0; t < r; ++t) {
+                    const int i = r0 + lane + 32 * t;
+                    Z[i + (size_t)q * a.ldS] = fma(-gq, X[i], Z[i + (size_t)q * a.ldS]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+            const int col = idx / rows, i = idx - col * rows;
+            a.Q[row0 + i + (int64_t)col * a.ldq] = Z[i + (size_t)col * a.ldS];
+        }
+    }
+}
+
+namespace {
+const void *q_leaf_fn(int blk) {
+    switch (blk) {
+        case 4: return (const void *)tsqr_q_leaf_kernel<4>;
+        case 3: return (const void *)tsqr_q_leaf_kernel<3>;
+        case 2: return (const void *)tsqr_q_leaf_kernel<2>;
+        default: return (const void *)tsqr_q_leaf_kernel<1>;
+    }
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers
+// ------------------------------------------------------------------------------------------
+size_t q_leaf_smem_bytes(int n, int ldS, int warps) {
+    return sizeof(double) * (size_t)q_leaf_layout(n, ldS, warps + 1).total;
+}
+
+size_t q_tree_smem_bytes(int n, int arity) { return sizeof(double) * (size_t)arity * n * n; }
+
+cudaError_t qr_prepare(size_t factor_smem, size_t leaf_smem, size_t tree_smem) {
+    for (int b = 1; b <= 4; ++b) {
+        cudaError_t e = set_smem_attrs(qr_factor_fn(b), factor_smem);
+        if (e != cudaSuccess) return e;
+        e = set_smem_attrs(q_leaf_fn(b), leaf_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return set_smem_attrs(tsqr_q_tree_kernel, tree_smem);
+}
+
+cudaError_t qr_factor_launch(const F64Args &a, int warps, size_t smem_bytes,
+                             cudaStream_t stream) {
+    const dim3 grid(a.nleaves), block((warps + 1) * 32);
+    switch (a.blk) {
+        case 4: tsqr_qr_factor_kernel<4><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 3: tsqr_qr_factor_kernel<3><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 2: tsqr_qr_factor_kernel<2><<<grid, block, smem_bytes, stream>>>(a); break;
+        default: tsqr_qr_factor_kernel<1><<<grid, block, smem_bytes, stream>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t q_tree_launch(const QTreeArgs &a, int grid, size_t smem_bytes, cudaStream_t stream) {
+    tsqr_q_tree_kernel<<<grid, 256, smem_bytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t q_leaf_launch(const QLeafArgs &a, int blk, int warps, size_t smem_bytes,
+                          cudaStream_t stream) {
+    const dim3 grid(a.nleaves), block((warps + 1) * 32);
+    switch (blk) {
+        case 4: tsqr_q_leaf_kernel<4><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 3: tsqr_q_leaf_kernel<3><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 2: tsqr_q_leaf_kernel<2><<<grid, block, smem_bytes, stream>>>(a); break;
+        default: tsqr_q_leaf_kernel<1><<<grid, block, smem_bytes, stream>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,0 +1,137 @@
+"""GPU parity of tsqr_qr (thin Q and R) against the CPU oracle's Householder QR, through the C
+ABI.  Q is unique for A of full rank under diag(R) >= 0, so the GPU's Q is compared entry by
+entry with the oracle's: every entry within c(m) kappa u ||Q_oracle||_F, c(m) = max(50, 2 sqrt(m))
+as for R.  R must be bit-identical to tsqr_r's under the same plan (same kernels, same order).
+Orthogonality ||Q^T Q - I||_max and the backward error ||A - Q R||_F / ||A||_F are bounded by
+c(m) n u."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_4250_gb300 as T
+    return T
+
+
+def _c(m):
+    return max(50.0, 2.0 * np.sqrt(max(m, 1)))
+
+
+def _check(oracle, T, At, plan=None, nthreads=16):
+    """At: (n, m) CPU FP64 tensor holding the column-major input."""
+    A = oracle.from_torch_colmajor(At)
+    m, n = A.shape
+    Ad = At.cuda().T
+    Q, R = T.tsqr_qr(Ad, plan=plan)
+    Rr = T.tsqr_r_ex(Ad, plan=plan)
+    Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.array_equal(Rh, Rr.cpu().numpy()), "R differs from tsqr_r's under the same plan"
+    Qo, Ro = oracle.householder_qr(A, nthreads=nthreads)
+    kap = oracle.kappa_from_r(Ro)
+    tol = _c(m) * kap * U * np.linalg.norm(Qo)
+    np.testing.assert_allclose(Qh, Qo, rtol=0, atol=tol)
+    assert np.abs(Qh.T @ Qh - np.eye(n)).max() <= _c(m) * n * U
+    assert np.linalg.norm(A - Qh @ Rh) / np.linalg.norm(A) <= _c(m) * n * U
+    return Qh, Rh
+
+
+@pytest.mark.parametrize("m,n", [(10000, 16), (100003, 32), (65537, 8), (50001, 64), (3000, 1),
+                                 (777, 3), (200003, 48), (4097, 5)])
+def test_qr_gaussian(oracle, T, m, n):
+    _check(oracle, T, workloads.gaussian(m, n, seed=m % 101))
+
+
+@pytest.mark.parametrize("tree,b,ctas,arity", [("binary", 256, 0, 0), ("flat", 0, 0, 0),
+                                               ("hybrid", 0, 37, 2), ("hybrid", 0, 61, 5),
+                                               ("hybrid", 0, 100, 8)])
+def test_qr_trees(oracle, T, tree, b, ctas, arity):
+    At = workloads.gaussian(120001, 24, seed=11)
+    _check(oracle, T, At, plan=T.make_plan(tree, tile_rows=b, ctas=ctas, arity=arity))
+
+
+def test_qr_conditioned(oracle, T):
+    _check(oracle, T, workloads.conditioned(200000, 32, 1e8, seed=0))
+
+
+@pytest.mark.parametrize("m,n", [(32, 32), (300, 32), (129, 64), (1, 1), (5, 5)])
+def test_qr_single_leaf_and_square(oracle, T, m, n):
+    _check(oracle, T, workloads.gaussian(m, n, seed=3))
+
+
+def test_qr_leading_dimensions(oracle, T):
+    import torch
+    m, n = 33333, 20
+    At = workloads.gaussian(m, n, seed=5)
+    big = torch.zeros(n, m + 7, dtype=torch.float64)
+    big[:, :m] = At
+    Ad = big.cuda().T[:m, :]
+    Qbig = torch.full((n, m + 3), float("nan"), dtype=torch.float64, device="cuda")
+    Q, R = T.tsqr_qr(Ad, Q=Qbig.T[:m, :])
+    A = oracle.from_torch_colmajor(At)
+    Qo, Ro = oracle.householder_qr(A, nthreads=16)
+    tol = _c(m) * oracle.kappa_from_r(Ro) * U * np.linalg.norm(Qo)
+    np.testing.assert_allclose(Q.cpu().numpy(), Qo, rtol=0, atol=tol)
+    assert torch.isnan(Qbig[:, m:]).all()  # the padding rows of Q are not written
+
+
+def test_qr_bit_reproducible_and_launches(T):
+    import torch
+    Ad = workloads.gaussian(300000, 32, seed=4).cuda().T
+    Q1, R1 = T.tsqr_qr(Ad)
+    Q1 = Q1.clone()
+    n_launch = T.capi.tsqr_last_launch_count()
+    Q2, R2 = T.tsqr_qr(Ad)
+    torch.cuda.synchronize()
+    assert torch.equal(Q1, Q2) and torch.equal(R1, R2)
+    levels = 1
+    p = T.tsqr_resolve_plan(300000, 32)
+    c = p.ctas
+    while c > 1:
+        c = (c + p.arity - 1) // p.arity
+        levels += 1
+    assert n_launch == 1 + (levels - 1) + 1
+
+
+def test_qr_full_size_4m_x_32(oracle, T):
+    """The benchmark's workload at full size."""
+    _check(oracle, T, workloads.gaussian(4194304, 32, seed=0))
+
+
+def test_qr_argument_errors(T):
+    import torch
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_qr(torch.zeros(8, 4, dtype=torch.float64, device="cuda").T)  # m = 4 < n = 8
+    assert e.value.status == T.ERR_INVALID_ARG
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_qr(torch.zeros(128, 1000, dtype=torch.float64, device="cuda").T)
+    assert e.value.status == T.ERR_UNSUPPORTED
+    with pytest.raises(T.TsqrError) as e:  # a binary tile of 600 rows is folded in chunks of 384
+        T.tsqr_qr(workloads.gaussian(5000, 32, seed=1).cuda().T,
+                  plan=T.make_plan("binary", tile_rows=600))
+    assert e.value.status == T.ERR_UNSUPPORTED
+
+
+def test_qr_rank_deficient(oracle, T):
+    """Rank-deficient A has no unique Q; what holds is A = Q R with R the (valid) R factor.
+    The zero matrix gives R = 0; two equal columns give a zero (to rounding) R(1,1)."""
+    import torch
+    Z = torch.zeros(8, 100, dtype=torch.float64, device="cuda").T
+    Q, R = T.tsqr_qr(Z)
+    torch.cuda.synchronize()
+    assert np.all(R.cpu().numpy() == 0) and np.all(np.isfinite(Q.cpu().numpy()))
+    At = workloads.gaussian(50000, 6, seed=9)
+    At[3] = At[1]
+    A = oracle.from_torch_colmajor(At)
+    Q, R = T.tsqr_qr(At.cuda().T)
+    Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
+    assert oracle.gram_residual(A, Rh) <= 1e-13
+    assert np.linalg.norm(A - Qh @ Rh) / np.linalg.norm(A) <= _c(50000) * 6 * U
