@@ -280,7 +280,9 @@ def bench_ours(args, world, rank, local):
     if os.path.exists(traffic_path):
         with open(traffic_path) as f:
             tr = json.load(f)
-        if tr.get("kernel_sha") == kernel_sha():
+        launch = {"tile_rows": plan.tile_rows, "ctas": plan.ctas, "warps": plan.warps,
+                  "arity": plan.arity}
+        if tr.get("kernel_sha") == kernel_sha() and tr.get("launch") == launch:
             roof["traffic"] = tr.get("bytes_per_launch")
 
     extras = None
@@ -435,11 +437,20 @@ def bench_batched(dev):
     return res
 
 
+# The sources the FP64 leaf + tree kernel's code comes from: its translation unit and the
+# device headers (the C-ABI header it also includes holds declarations only).
+KERNEL_SOURCES = ("paper_1002_4250_gb300/csrc/tsqr_f64.cu",
+                  "paper_1002_4250_gb300/csrc/tsqr_f64.cuh",
+                  "paper_1002_4250_gb300/csrc/tsqr_fold.cuh",
+                  "paper_1002_4250_gb300/csrc/tsqr_internal.h")
+
+
 def kernel_sha():
+    """First 16 hex digits of SHA-256 over the FP64 kernel's sources, in KERNEL_SOURCES order."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1002_4250_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_1002_4250_gb300", "csrc", f), "rb") as fh:
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -173,6 +173,26 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
 tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                              int64_t ldr, tsqr_stream_t stream);
 
+/* Plan autotuning: times candidate plans for an (m, n, dtype, prec) problem on the caller's A
+ * and caches the fastest.  From then on every AUTO call (plan NULL or all fields zero: tsqr_r,
+ * tsqr_r_ex, tsqr_qr, tsqr_r_noalloc, tsqr_resolve_plan) on the same device with the same n,
+ * the same leaf precision and the same floor(log2 m) uses the tuned plan, and returns the
+ * bytes that plan gives.  The paper has no counterpart: its trees are picked by hand or by the
+ * MPI library (Section 1).
+ *   A, m, n, lda, dtype, prec, R, ldr as for tsqr_r_ex; R is overwritten (the last candidate's
+ *   result).  best: optional, receives the chosen plan.
+ *   Candidates: HYBRID slabs as tall as fit 1, 2 or 3 CTAs per SM, and half as tall, with that
+ *   many CTAs per SM on every SM; 4 bulk warps for FP64, 4 and 8 for the mixed path.  Each is
+ *   timed over three calls with CUDA events on `stream`.
+ *   Synchronizes `stream`; not for use under stream capture.  Returns TSQR_ERR_UNSUPPORTED if
+ *   no candidate runs. */
+tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
+                            int64_t lda, double *R, int64_t ldr, tsqr_plan_t *best,
+                            tsqr_stream_t stream);
+
+/* Forgets every tuned plan: AUTO calls go back to the built-in rules. */
+void tsqr_autotune_reset(void);
+
 /* Synchronizes `stream`, returns the device-side status recorded by the calls made on it since
  * the last query (TSQR_SUCCESS or TSQR_STATUS_NONFINITE) and clears it.  TSQR_ERR_CUDA if the
  * stream reports an error. */

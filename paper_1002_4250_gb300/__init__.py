@@ -71,6 +71,11 @@ def _load():
     capi.tsqr_r_noalloc.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
     capi.tsqr_qr.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p, _i64, ctypes.POINTER(Plan), _p]
     capi.tsqr_qr.restype = _i32
+    capi.tsqr_autotune.argtypes = [_p, _i32, _i32, _i64, _i64, _i64, _p, _i64,
+                                   ctypes.POINTER(Plan), _p]
+    capi.tsqr_autotune.restype = _i32
+    capi.tsqr_autotune_reset.argtypes = []
+    capi.tsqr_autotune_reset.restype = None
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -88,7 +93,8 @@ def __getattr__(name):
 #: every symbol include/tsqr.h declares
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
-               "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr")
+               "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
+               "tsqr_autotune_reset")
 
 
 class TsqrError(RuntimeError):
@@ -190,6 +196,26 @@ def tsqr_qr(A, Q=None, R=None, plan: Plan | None = None, stream=None):
     check(_load().tsqr_qr(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(),
                           max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_qr")
     return Q, R
+
+
+def tsqr_autotune(A, prec=None, R=None, stream=None) -> Plan:
+    """Time candidate plans on A (FP64 / FP32 / BF16, logical (m, n) column-major), cache the
+    fastest for AUTO calls of the same (n, leaf precision, floor(log2 m)), and return it."""
+    m, n, lda = _colmajor_dims(A)
+    dt = _dtype_code(A.dtype)
+    if prec is None:
+        prec = PREC_F64 if dt == F64 else PREC_MIXED
+    if R is None:
+        R = empty_r(n, A.device)
+    best = Plan()
+    check(_load().tsqr_autotune(A.data_ptr(), dt, int(prec), m, n, lda, R.data_ptr(),
+                                max(R.stride(1), n, 1), ctypes.byref(best), _stream_ptr(stream)),
+          "tsqr_autotune")
+    return best
+
+
+def tsqr_autotune_reset() -> None:
+    _load().tsqr_autotune_reset()
 
 
 def tsqr_qr_uppers(R1, R2, normalize=False, R=None, stream=None):

@@ -147,6 +147,39 @@ int max_rows_per_lane_p(int n, int warps, size_t budget, bool mixed) {
     return best;
 }
 
+// Plans chosen by tsqr_autotune, per (device, n, leaf precision, floor(log2 m)); the AUTO plan
+// of a problem in a tuned bucket is the tuned plan.
+struct TuneKey {
+    int dev, n, mixed, mlog;
+    bool operator<(const TuneKey &o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (n != o.n) return n < o.n;
+        if (mixed != o.mixed) return mixed < o.mixed;
+        return mlog < o.mlog;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, tsqr_plan_t> g_tuned;
+
+int floor_log2(int64_t m) {
+    int l = 0;
+    while (l < 62 && ((int64_t)1 << (l + 1)) <= m) ++l;
+    return l;
+}
+
+bool plan_is_auto(const tsqr_plan_t *p) {
+    return !p || (p->tree == 0 && p->tile_rows == 0 && p->ctas == 0 && p->warps == 0 &&
+                  p->arity == 0);
+}
+
+bool tuned_plan(int dev, int64_t m, int n, bool mixed, tsqr_plan_t *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{dev, n, mixed ? 1 : 0, floor_log2(std::max<int64_t>(m, 1))});
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 // The rest of plan_leaf once the rows per lane that fit (r_fit) are chosen.
 tsqr_status_t plan_with_r(int64_t m, int n, const tsqr_plan_t *over, bool mixed, int r_fit,
                           const DeviceInfo &di, F64Plan *p) {
@@ -216,6 +249,8 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
     if (di.sms <= 0) return TSQR_ERR_CUDA;
+    tsqr_plan_t tuned;
+    if (plan_is_auto(over) && tuned_plan(dev, m, n, mixed, &tuned)) over = &tuned;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
     p->warps = 4;
@@ -236,7 +271,9 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     // Mixed: the FP32 bulk is cheap, so what counts is the number of rows sharing each
     // reflector's serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs).
     const bool two = mixed ? (r2 >= 1 && 2 * good_r(r2) >= good_r(r1)) : (r2 >= 1);
-    tsqr_status_t st = plan_with_r(m, n, over, mixed, two ? r2 : r1, di, p);
+    // explicit tile rows are honoured up to what one CTA per SM holds
+    const bool tile_given = over && over->tile_rows > 0;
+    tsqr_status_t st = plan_with_r(m, n, over, mixed, (two && !tile_given) ? r2 : r1, di, p);
     // an explicit arity whose stacked triangles need a taller S region than two CTAs per SM
     // leave room for: one CTA per SM
     if (st == TSQR_ERR_UNSUPPORTED && two && over && over->arity > 0)
@@ -327,7 +364,22 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
-    const size_t leaf_smem = q_leaf_smem_bytes((int)n, p.ldS, p.warps);
+    // the leaf pass has no serial reflector chain, so more, shorter warps hide its latency:
+    // 12 or 8 bulk warps (three or two per sub-partition) where they divide the chunk
+    int qwarps = p.warps;
+    for (int c : {12, 8})
+        if (c > qwarps && p.hs % (32 * c) == 0) {
+            qwarps = c;
+            break;
+        }
+    const int qr_rows = p.hs / (32 * qwarps);
+    int qblk = 1;
+    for (int c = 4; c >= 1; --c)
+        if (qr_rows % c == 0) {
+            qblk = c;
+            break;
+        }
+    const size_t leaf_smem = q_leaf_smem_bytes((int)n, p.ldS, qwarps);
     const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity);
     if (leaf_smem > di.smem_block_optin || tree_smem > di.smem_block_optin)
         return TSQR_ERR_UNSUPPORTED;
@@ -415,7 +467,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     l.B = blocks;
     l.signs = a.q.signs;
     l.single = (sh.levels == 1) ? 1 : 0;
-    if (q_leaf_launch(l, p.blk, p.warps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (q_leaf_launch(l, qblk, qwarps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     g_last_launches = launches + 1;
     return TSQR_SUCCESS;
 }
@@ -774,6 +826,92 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
     out->warps = p.warps;
     out->arity = p.arity;
     return TSQR_SUCCESS;
+}
+
+tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
+                            int64_t lda, double *R, int64_t ldr, tsqr_plan_t *best,
+                            tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr) || n < 1 || m < 1 || !A || !R) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
+    const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
+    if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    if (di.sms <= 0) return TSQR_ERR_CUDA;
+    const cudaStream_t s = (cudaStream_t)stream;
+    // candidates: HYBRID slabs as tall as fit k CTAs per SM (k = 1, 2, 3), and half as tall,
+    // with 4 bulk warps (FP64) or 4 and 8 (mixed); k CTAs per SM on every SM
+    std::vector<tsqr_plan_t> cands;
+    const int warps_opts[2] = {4, 8};
+    for (int wi = 0; wi < (mixed ? 2 : 1); ++wi) {
+        const int W = warps_opts[wi];
+        for (int k = 1; k <= 3; ++k) {
+            const size_t reserve = 1024;
+            if (di.smem_sm <= k * reserve) continue;
+            const size_t budget = std::min(di.smem_block_optin, (di.smem_sm - k * reserve) / k);
+            const int rmax = good_r(max_rows_per_lane_p((int)n, W, budget, mixed));
+            if (rmax < 1) continue;
+            for (int r : {rmax, good_r(std::max(1, rmax / 2))}) {
+                const int64_t tile = 32LL * W * r;
+                if (tile < n) continue;
+                const int64_t units = (m + tile - 1) / tile;
+                tsqr_plan_t c{TSQR_TREE_HYBRID, (int32_t)tile,
+                              (int32_t)std::min<int64_t>((int64_t)di.sms * k, units), W, 0};
+                bool dup = false;
+                for (const auto &o : cands)
+                    dup |= (o.tile_rows == c.tile_rows && o.ctas == c.ctas && o.warps == c.warps);
+                if (!dup) cands.push_back(c);
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TSQR_ERR_CUDA;
+    }
+    float best_ms = -1.0f;
+    tsqr_plan_t best_plan{};
+    tsqr_status_t st = TSQR_SUCCESS;
+    for (const auto &c : cands) {
+        auto call = [&]() {
+            return f64 ? run_f64((const double *)A, m, n, lda, R, ldr, &c, s)
+                       : run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, &c, s);
+        };
+        if (call() != TSQR_SUCCESS) continue;  // a candidate the planner rejects is skipped
+        float ms = 0.0f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = TSQR_ERR_CUDA; break; }
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) ok = (call() == TSQR_SUCCESS);
+        if (!ok || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = TSQR_ERR_CUDA;
+            break;
+        }
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best_plan = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_last_launches = 0;
+    if (st != TSQR_SUCCESS) return st;
+    if (best_ms < 0.0f) return TSQR_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[TuneKey{dev, (int)n, mixed ? 1 : 0, floor_log2(m)}] = best_plan;
+    }
+    if (best) *best = best_plan;
+    return TSQR_SUCCESS;
+}
+
+void tsqr_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
 }
 
 }  // extern "C"

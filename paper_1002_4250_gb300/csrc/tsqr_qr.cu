@@ -215,8 +215,9 @@ __device__ __forceinline__ void q_sweep(const int lane, const int n, const int r
     if (i != 0) seg[lane + kk] = acc;
 }
 
+// Block: W bulk warps (a multiple of 4 up to 12, hs a multiple of 32 W) and the reducer.
 template <int B>
-__global__ void __launch_bounds__(288, 1) tsqr_q_leaf_kernel(const QLeafArgs a) {
+__global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Wb = (blockDim.x >> 5) - 1;
@@ -232,6 +233,8 @@ __global__ void __launch_bounds__(288, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
     double *seg_all = smem + L.seg;
     double *seg = seg_all + warp * ss;
     double *tot = smem + L.tot;
+    const int nslot = 32 + n;
+    constexpr int kGroups = 4;
     const int leaf = blockIdx.x;
 
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -265,13 +268,38 @@ __global__ void __launch_bounds__(288, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
                            X + (size_t)J * a.ldS + r0, g, seg);
             }
             __syncthreads();
-            if (reducer) {
-                for (int id = lane; id < 32 + n; id += 32) {
-                    double t = seg_all[id];
-                    for (int w = 1; w < Wb; ++w) t += seg_all[w * ss + id];
-                    tot[id] = t;
+            // slot sums over the bulk warps.  With more than 4 bulk warps they are spread over
+            // the whole CTA: slot id's partials in kGroups runs of consecutive warps, each run
+            // summed by one lane of a kGroups-lane team, the runs then combined by shuffles (a
+            // fixed order); with 4 or fewer the reducer sums them in order
+            if (Wb <= 4) {
+                if (reducer) {
+                    for (int id = lane; id < nslot; id += 32) {
+                        double v = seg_all[id];
+                        for (int w = 1; w < Wb; ++w) v += seg_all[w * ss + id];
+                        tot[id] = v;
+                    }
                 }
+            } else {
+                for (int base = 0; base < nslot * kGroups; base += blockDim.x) {
+                    const int t = base + threadIdx.x;
+                    const int id = t / kGroups, gi = t - id * kGroups;
+                    double v = 0.0;
+                    if (id < nslot) {
+                        const int w0 = (gi * Wb) / kGroups, w1 = ((gi + 1) * Wb) / kGroups;
+                        for (int w = w0; w < w1; ++w) v += seg_all[w * ss + id];
+                    }
+#pragma unroll
+                    for (int o = kGroups >> 1; o > 0; o >>= 1)
+                        v += __shfl_xor_sync(0xffffffffu, v, o, kGroups);
+                    if (id < nslot && gi == 0) tot[id] = v;
+                }
+            }
+            if (Wb <= 4)
                 __syncwarp();
+            else
+                __syncthreads();
+            if (reducer) {
                 const double tau = sc[2 * J], cj = sc[2 * J + 1];
                 const int Nw = n * Hw;
                 for (int q = lane; q < n; q += 32) {
