@@ -73,7 +73,7 @@ typedef struct {
     int32_t tree;       /* tsqr_tree_t                                                     */
     int32_t tile_rows;  /* rows per tile (slab) b; must fit the kernel's shared memory      */
     int32_t ctas;       /* HYBRID: number of leaf CTAs                                      */
-    int32_t warps;      /* bulk warps per CTA (2, 4 or 8)                                    */
+    int32_t warps;      /* bulk warps per CTA (2, 4, 8 or 12)                                */
     int32_t arity;      /* children per tree node, 2..8.  BINARY uses 2, the operator of
                            Table 3; a node with c > 2 children folds their c stacked triangles
                            in one sweep (the R factor of [R_1; ...; R_c], equal to a sequence of
@@ -182,8 +182,8 @@ tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda,
  *   A, m, n, lda, dtype, prec, R, ldr as for tsqr_r_ex; R is overwritten (the last candidate's
  *   result).  best: optional, receives the chosen plan.
  *   Candidates: HYBRID slabs as tall as fit 1, 2 or 3 CTAs per SM, and half as tall, with that
- *   many CTAs per SM on every SM; 4 bulk warps for FP64, 4 and 8 for the mixed path.  Each is
- *   timed over three calls with CUDA events on `stream`.
+ *   many CTAs per SM on every SM; 4 or 12 bulk warps for FP64, 4, 8 or 12 for the mixed path.
+ *   Each is timed over three calls with CUDA events on `stream`.
  *   Synchronizes `stream`; not for use under stream capture.  Returns TSQR_ERR_UNSUPPORTED if
  *   no candidate runs. */
 tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,

@@ -253,9 +253,12 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     if (plan_is_auto(over) && tuned_plan(dev, m, n, mixed, &tuned)) over = &tuned;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
-    p->warps = 4;
+    // bulk warps: 4; 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep
+    // gains from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms)
+    p->warps = (mixed && n >= 48) ? 8 : 4;
     if (over && over->warps) {
-        if (over->warps != 2 && over->warps != 4 && over->warps != 8) return TSQR_ERR_INVALID_ARG;
+        if (over->warps != 2 && over->warps != 4 && over->warps != 8 && over->warps != 12)
+            return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
     }
     if (over && (over->tile_rows < 0 || over->ctas < 0 || over->arity < 0))
@@ -843,10 +846,10 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     const cudaStream_t s = (cudaStream_t)stream;
     // candidates: HYBRID slabs as tall as fit k CTAs per SM (k = 1, 2, 3), and half as tall,
-    // with 4 bulk warps (FP64) or 4 and 8 (mixed); k CTAs per SM on every SM
+    // with 4 or 12 bulk warps (FP64) or 4, 12 and 8 (mixed); k CTAs per SM on every SM
     std::vector<tsqr_plan_t> cands;
-    const int warps_opts[2] = {4, 8};
-    for (int wi = 0; wi < (mixed ? 2 : 1); ++wi) {
+    const int warps_opts[3] = {4, 12, 8};
+    for (int wi = 0; wi < (mixed ? 3 : 2); ++wi) {
         const int W = warps_opts[wi];
         for (int k = 1; k <= 3; ++k) {
             const size_t reserve = 1024;

@@ -5,7 +5,7 @@
 namespace tsqr {
 
 template <int B>
-__global__ void __launch_bounds__(288, 1) tsqr_f64_kernel(const F64Args a) {
+__global__ void __launch_bounds__(416, 1) tsqr_f64_kernel(const F64Args a) {
     // one row per lane (B = 1): the software-pipelined sweep hides the shared-memory latency
     // a single block per item exposes (measured +3% at n = 64); taller lanes keep the plain
     // loop, which measured faster there

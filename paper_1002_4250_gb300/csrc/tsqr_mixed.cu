@@ -7,7 +7,7 @@
 namespace tsqr {
 
 template <typename Tin, int B, int V>
-__global__ void __launch_bounds__(288, 1) tsqr_mixed_kernel(const MixedArgs a) {
+__global__ void __launch_bounds__(416, 1) tsqr_mixed_kernel(const MixedArgs a) {
     leaf_tree_job<float, Tin, B, V, true>(a.base, static_cast<const Tin *>(a.A), a.ldSd,
                                           a.s_doubles, blockIdx.x);
 }

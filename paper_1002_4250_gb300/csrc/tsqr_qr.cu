@@ -22,7 +22,7 @@ namespace tsqr {
 // Factorization with storage: tsqr_r's leaf + tree kernel keeping its reflectors in a.q.
 // ------------------------------------------------------------------------------------------
 template <int B>
-__global__ void __launch_bounds__(288, 1) tsqr_qr_factor_kernel(const F64Args a) {
+__global__ void __launch_bounds__(416, 1) tsqr_qr_factor_kernel(const F64Args a) {
     leaf_tree_job<double, double, B, 1, B == 1, true>(a, a.A, a.ldS, a.ldS * a.n, blockIdx.x);
 }
 
@@ -268,37 +268,23 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
                            X + (size_t)J * a.ldS + r0, g, seg);
             }
             __syncthreads();
-            // slot sums over the bulk warps.  With more than 4 bulk warps they are spread over
-            // the whole CTA: slot id's partials in kGroups runs of consecutive warps, each run
-            // summed by one lane of a kGroups-lane team, the runs then combined by shuffles (a
-            // fixed order); with 4 or fewer the reducer sums them in order
-            if (Wb <= 4) {
-                if (reducer) {
-                    for (int id = lane; id < nslot; id += 32) {
-                        double v = seg_all[id];
-                        for (int w = 1; w < Wb; ++w) v += seg_all[w * ss + id];
-                        tot[id] = v;
-                    }
+            // slot sums over the bulk warps, spread over the whole CTA: slot id's partials in
+            // kGroups runs of consecutive warps, each run summed by one lane of a kGroups-lane
+            // team, the runs then combined by shuffles (a fixed order)
+            for (int base = 0; base < nslot * kGroups; base += blockDim.x) {
+                const int t = base + threadIdx.x;
+                const int id = t / kGroups, gi = t - id * kGroups;
+                double v = 0.0;
+                if (id < nslot) {
+                    const int w0 = (gi * Wb) / kGroups, w1 = ((gi + 1) * Wb) / kGroups;
+                    for (int w = w0; w < w1; ++w) v += seg_all[w * ss + id];
                 }
-            } else {
-                for (int base = 0; base < nslot * kGroups; base += blockDim.x) {
-                    const int t = base + threadIdx.x;
-                    const int id = t / kGroups, gi = t - id * kGroups;
-                    double v = 0.0;
-                    if (id < nslot) {
-                        const int w0 = (gi * Wb) / kGroups, w1 = ((gi + 1) * Wb) / kGroups;
-                        for (int w = w0; w < w1; ++w) v += seg_all[w * ss + id];
-                    }
 #pragma unroll
-                    for (int o = kGroups >> 1; o > 0; o >>= 1)
-                        v += __shfl_xor_sync(0xffffffffu, v, o, kGroups);
-                    if (id < nslot && gi == 0) tot[id] = v;
-                }
+                for (int o = kGroups >> 1; o > 0; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o, kGroups);
+                if (id < nslot && gi == 0) tot[id] = v;
             }
-            if (Wb <= 4)
-                __syncwarp();
-            else
-                __syncthreads();
+            __syncthreads();
             if (reducer) {
                 const double tau = sc[2 * J], cj = sc[2 * J + 1];
                 const int Nw = n * Hw;
