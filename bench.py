@@ -243,27 +243,25 @@ def bench_ours(args, world, rank, local):
     status = T.tsqr_get_device_status()
     ms_step = ms / args.steps
 
-    # end to end through the public call with HOST buffers: pinned H2D of A, the call, D2H of R
+    # end to end through the public host-buffer call (tsqr_r_host): A from pinned host memory,
+    # its copy to the device overlapped with the leaves, R back to pinned host memory
     A_host = At_cpu.pin_memory()
-    A_dev = torch.empty_like(A_host, device=dev)
-    R_host = torch.empty((N, N), dtype=torch.float64).pin_memory()
+    R_host = torch.empty((N, N), dtype=torch.float64).pin_memory().T
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
-        A_dev.copy_(A_host, non_blocking=True)
-        T.tsqr_r(A_dev.T, R=R)
-        R_host.copy_(R.T, non_blocking=True)
+        T.tsqr_r_host(A_host.T, R=R_host)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        A_dev.copy_(A_host, non_blocking=True)
-        T.tsqr_r(A_dev.T, R=R)
-        R_host.copy_(R.T, non_blocking=True)
+        T.tsqr_r_host(A_host.T, R=R_host)
         torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e = {"value": world * fl / e2e_s / 1e9, "unit": "GFLOP/s",
            "h2d_bytes_per_step": int(A_host.numel() * 8), "d2h_bytes_per_step": int(N * N * 8),
-           "ms_per_step": e2e_s * 1e3}
+           "ms_per_step": e2e_s * 1e3,
+           "call": "tsqr_r_host: pinned host A and R, the H2D copy in row pieces overlapped "
+                   "with the leaves"}
 
     pk = peaks()
     kern_ms = statistics.mean(per_launch)

@@ -92,6 +92,21 @@ typedef void *tsqr_stream_t; /* a cudaStream_t */
 tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
                      tsqr_stream_t stream);
 
+/* tsqr_r for A and R in HOST memory, FP64: the copy of A to the device overlaps the leaf
+ * factorizations.  TSQR streams naturally (Section 2: each row block is factorized on its own
+ * and only the n x n factors meet in the tree), so A is copied in up to 8 row pieces on a
+ * second stream while the leaves of the pieces already on the device run; the leaves of all
+ * pieces share one reduction tree, and R is copied back at the end.  The plan is the AUTO
+ * rule with as many times more leaves as there are pieces (tuned plans do not apply).
+ *   A : host, column-major m x n, lda >= m (page-locked memory lets the copies overlap;
+ *       pageable memory works but its copies are staged by the driver).
+ *   R : host, column-major n x n, ldr >= n, written as by tsqr_r.
+ * Asynchronous on `stream` like tsqr_r: A must not be modified, nor R read, until the stream
+ * has been synchronized (for m = 0, R is zeroed before the call returns).  Workspace: A's size
+ * on the device plus the tree's slots, from the per-stream pool. */
+tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                          int64_t ldr, tsqr_stream_t stream);
+
 /* tsqr_r with the storage type of A, the leaf arithmetic and an optional plan (NULL = AUTO).
  * (dtype, prec) must be (F64, F64), (F32, MIXED) or (BF16, MIXED).  lda counts elements. */
 tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,

@@ -76,6 +76,8 @@ def _load():
     capi.tsqr_autotune.restype = _i32
     capi.tsqr_autotune_reset.argtypes = []
     capi.tsqr_autotune_reset.restype = None
+    capi.tsqr_r_host.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
+    capi.tsqr_r_host.restype = _i32
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -94,7 +96,7 @@ def __getattr__(name):
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
                "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
-               "tsqr_autotune_reset")
+               "tsqr_autotune_reset", "tsqr_r_host")
 
 
 class TsqrError(RuntimeError):
@@ -196,6 +198,25 @@ def tsqr_qr(A, Q=None, R=None, plan: Plan | None = None, stream=None):
     check(_load().tsqr_qr(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(),
                           max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_qr")
     return Q, R
+
+
+def tsqr_r_host(A, R=None, stream=None):
+    """tsqr_r for a CPU FP64 tensor A (logical (m, n), column-major, ideally pinned): the copy to
+    the device overlaps the leaf factorizations.  Returns R as a CPU (n, n) column-major tensor;
+    synchronize the stream before reading it."""
+    import torch
+    if A.dim() != 2 or A.is_cuda or A.dtype != torch.float64:
+        raise ValueError("A must be a 2-D CPU float64 tensor")
+    m, n = A.shape
+    if n > 1 and m > 1 and A.stride(0) != 1:
+        raise ValueError(f"A must be column-major (strides (1, lda)); got strides {A.stride()}")
+    lda = max(A.stride(1) if n > 1 else m, m, 1)
+    if R is None:
+        R = torch.empty(n, n, dtype=torch.float64).T
+    ldr = max(R.stride(1) if n > 1 else n, n, 1)
+    check(_load().tsqr_r_host(A.data_ptr(), m, n, lda, R.data_ptr(), ldr, _stream_ptr(stream)),
+          "tsqr_r_host")
+    return R
 
 
 def tsqr_autotune(A, prec=None, R=None, stream=None) -> Plan:

@@ -13,6 +13,13 @@
 #include "tsqr_internal.h"
 #include "tsqr_qr.cuh"
 
+namespace tsqr {
+// Leaves of one row piece (tsqr_host.cu)
+cudaError_t f64_piece_prepare(size_t smem_bytes);
+cudaError_t f64_piece_launch(const F64Args &a, int leaf0, int leaves, int warps,
+                             size_t smem_bytes, cudaStream_t stream);
+}  // namespace tsqr
+
 using namespace tsqr;
 
 namespace {
@@ -26,6 +33,9 @@ struct Workspace {
     // batched calls: the problem table and work items last copied to base + table_off
     std::vector<char> table;
     size_t table_off = 0;
+    // host-input calls: the copy stream and the events ordering it with the call's stream
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> events;
 };
 
 std::mutex g_mu;
@@ -475,6 +485,113 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     return TSQR_SUCCESS;
 }
 
+// Host-input FP64 call: A and R in host memory.  A is copied in P row pieces on a copy stream
+// while the leaves of the pieces already copied run on `stream`; all pieces' leaves share one
+// tree (one launch per piece over its leaves, see tsqr_host.cu).  The AUTO rules with P times
+// as many leaves, P in {8, 4, 2, 1}: as many as leave every leaf at least two work units.
+// Workspace: counters | tree slots | A (ld m) | R (ld n).
+tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                           int64_t ldr, cudaStream_t stream) {
+    g_last_launches = 0;
+    if (n == 0) return TSQR_SUCCESS;
+    if (m == 0) {
+        for (int64_t c = 0; c < n; ++c)
+            for (int64_t i = 0; i < n; ++i) R[i + c * ldr] = 0.0;
+        return TSQR_SUCCESS;
+    }
+    F64Plan p0;
+    tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p0);
+    if (st != TSQR_SUCCESS) return st;
+    const int wave = p0.nleaves;
+    int P = 1;
+    for (int c : {8, 4, 2})
+        if (p0.tree == TSQR_TREE_HYBRID && p0.nunits >= 2LL * c * wave) {
+            P = c;
+            break;
+        }
+    F64Plan p = p0;
+    if (P > 1) {
+        const tsqr_plan_t over{TSQR_TREE_HYBRID, 0, P * wave, p0.warps, 0};
+        st = plan_f64(m, (int)n, &over, &p);
+        if (st != TSQR_SUCCESS) return st;
+        if (p.nleaves != P * wave) return TSQR_ERR_UNSUPPORTED;
+    }
+    if (f64_piece_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
+    const size_t a_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
+    const size_t r_bytes = (size_t)n * (size_t)n * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, cnt_bytes + slot_bytes + a_bytes + r_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!ws->copy_stream &&
+            cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        while (ws->events.size() < (size_t)P + 1) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return TSQR_ERR_CUDA;
+            ws->events.push_back(e);
+        }
+    }
+    char *base = (char *)ws->base;
+    double *Ad = (double *)(base + cnt_bytes + slot_bytes);
+    double *Rd = (double *)(base + cnt_bytes + slot_bytes + a_bytes);
+    F64Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = Ad;
+    a.m = m;
+    a.lda = m;
+    a.n = (int)n;
+    a.unit = p.unit;
+    a.nunits = p.nunits;
+    a.nleaves = p.nleaves;
+    a.arity = p.arity;
+    a.h = p.h;
+    a.hs = p.hs;
+    a.blk = p.blk;
+    a.vec = p.vec;
+    a.ldS = p.ldS;
+    a.counters = (unsigned int *)base;
+    a.slots = (double *)(base + cnt_bytes);
+    a.R = Rd;
+    a.ldr = n;
+    a.status = ws->status;
+    cudaStream_t cs = ws->copy_stream;
+    // the copies must not overwrite A while earlier work on `stream` may still read it
+    if (cudaEventRecord(ws->events[P], stream) != cudaSuccess ||
+        cudaStreamWaitEvent(cs, ws->events[P], 0) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    const int L = p.nleaves / P;
+    for (int q = 0; q < P; ++q) {
+        const int64_t u0 = ((int64_t)q * L * p.nunits) / p.nleaves;
+        const int64_t u1 = ((int64_t)(q + 1) * L * p.nunits) / p.nleaves;
+        const int64_t r0 = std::min<int64_t>(u0 * p.unit, m);
+        const int64_t r1 = std::min<int64_t>(u1 * p.unit, m);
+        if (r1 > r0 &&
+            cudaMemcpy2DAsync(Ad + r0, (size_t)m * sizeof(double), A + r0,
+                              (size_t)lda * sizeof(double), (size_t)(r1 - r0) * sizeof(double),
+                              (size_t)n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        if (cudaEventRecord(ws->events[q], cs) != cudaSuccess ||
+            cudaStreamWaitEvent(stream, ws->events[q], 0) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        if (f64_piece_launch(a, q * L, L, p.warps, p.smem, stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+    }
+    if (cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Rd, (size_t)n * sizeof(double),
+                          (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost,
+                          stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    g_last_launches = P;
+    return TSQR_SUCCESS;
+}
+
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
@@ -727,6 +844,15 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
     return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
 }
 
+tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                          int64_t ldr, tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
+    return run_f64_host(A, m, n, lda, R, ldr, (cudaStream_t)stream);
+}
+
 tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q,
                       int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
                       tsqr_stream_t stream) {
@@ -808,6 +934,8 @@ void tsqr_release_workspace(void) {
         cudaDeviceSynchronize();
         if (kv.second.base) cudaFree(kv.second.base);
         if (kv.second.status) cudaFree(kv.second.status);
+        for (cudaEvent_t e : kv.second.events) cudaEventDestroy(e);
+        if (kv.second.copy_stream) cudaStreamDestroy(kv.second.copy_stream);
     }
     g_ws.clear();
     cudaSetDevice(cur);

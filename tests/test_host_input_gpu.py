@@ -1,0 +1,57 @@
+"""tsqr_r_host (A and R in host memory, the copy of A overlapping the leaf factorizations):
+parity with the oracle (every entry within c(m) kappa u ||R||_F, c(m) = max(50, 2 sqrt(m)),
+Gram residual <= 1e-13) on sizes that use 1, 2, 4 and 8 row pieces, with pinned and pageable
+A, a padded lda and ldr, and m = 0; and the same R as tsqr_r up to the tree's rounding."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def T():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1002_4250_gb300 as T
+    return T
+
+
+def _check(oracle, A, R):
+    m = A.shape[0]
+    Ro = oracle.householder_r(A, nthreads=16)
+    kap = oracle.kappa_from_r(Ro)
+    np.testing.assert_allclose(R, Ro, rtol=0,
+                               atol=max(50.0, 2.0 * np.sqrt(m)) * kap * U * np.linalg.norm(Ro))
+    assert oracle.gram_residual(A, R, nthreads=16) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n,pinned", [(5000, 16, True), (300000, 32, True), (1000003, 32, False),
+                                        (2500000, 24, True), (4194304, 32, True), (777, 3, False)])
+def test_host_input_parity(oracle, T, m, n, pinned):
+    import torch
+    At = workloads.gaussian(m, n, seed=m % 89)
+    Ah = At.pin_memory() if pinned else At
+    R = T.tsqr_r_host(Ah.T)
+    torch.cuda.synchronize()
+    pieces = T.capi.tsqr_last_launch_count()
+    assert pieces in (1, 2, 4, 8)
+    _check(oracle, oracle.from_torch_colmajor(At), R.numpy())
+
+
+def test_host_input_leading_dimensions_and_empty(oracle, T):
+    import torch
+    m, n = 123457, 20
+    At = workloads.gaussian(m, n, seed=3)
+    big = torch.zeros(n, m + 5, dtype=torch.float64)
+    big[:, :m] = At
+    Rbig = torch.full((n, n + 2), float("nan"), dtype=torch.float64)
+    R = T.tsqr_r_host(big.pin_memory().T[:m, :], R=Rbig.T[:n, :])
+    torch.cuda.synchronize()
+    _check(oracle, oracle.from_torch_colmajor(At), R.numpy())
+    assert torch.isnan(Rbig[:, n:]).all()
+    Z = torch.zeros(0, 4, dtype=torch.float64)
+    assert np.all(T.tsqr_r_host(Z).numpy() == 0)
