@@ -43,7 +43,9 @@ typedef enum {
     TSQR_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. n > TSQR_MAX_N)              */
     TSQR_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, allocation, copy)      */
     TSQR_ERR_ALLOC = 4,         /* workspace could not be allocated                           */
-    TSQR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (reserved)              */
+    TSQR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (tsqr_r_host's wait for
+                                   a piece of A that never arrived; read by
+                                   tsqr_get_device_status)                                    */
     TSQR_STATUS_NONFINITE = 6   /* R holds NaN or Inf (the input held NaN/Inf or overflowed)  */
 } tsqr_status_t;
 
@@ -94,12 +96,14 @@ tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double 
 
 /* tsqr_r for A and R in HOST memory, FP64: the copy of A to the device overlaps the leaf
  * factorizations.  TSQR streams naturally (Section 2: each row block is factorized on its own
- * and only the n x n factors meet in the tree), so A is copied in up to 8 row pieces on a
- * second stream while the leaves of the pieces already on the device run; the leaves of all
- * pieces share one reduction tree, and R is copied back at the end.  The plan is the AUTO
- * rule with as many times more leaves as there are pieces (tuned plans do not apply).
- *   A : host, column-major m x n, lda >= m (page-locked memory lets the copies overlap;
- *       pageable memory works but its copies are staged by the driver).
+ * and only the n x n factors meet in the tree).  With page-locked A, A is copied in up to 8 row
+ * pieces on a second stream while ONE launch already folds the pieces that have arrived: its
+ * leaves take the work units round-robin (leaf l: units l, l + L, l + 2L, ...), wait for a
+ * piece's arrival flag before loading from it (a bounded wait; on timeout the device status
+ * becomes TSQR_ERR_TIMEOUT and R is not written), and then climb the usual tree.  With pageable
+ * A, A is copied whole and the ordinary kernel runs.  The plan is the AUTO plan; the
+ * round-robin rows give an R equal to tsqr_r's up to rounding (not bit for bit).
+ *   A : host, column-major m x n, lda >= m.
  *   R : host, column-major n x n, ldr >= n, written as by tsqr_r.
  * Asynchronous on `stream` like tsqr_r: A must not be modified, nor R read, until the stream
  * has been synchronized (for m = 0, R is zeroed before the call returns).  Workspace: A's size

@@ -14,10 +14,10 @@
 #include "tsqr_qr.cuh"
 
 namespace tsqr {
-// Leaves of one row piece (tsqr_host.cu)
-cudaError_t f64_piece_prepare(size_t smem_bytes);
-cudaError_t f64_piece_launch(const F64Args &a, int leaf0, int leaves, int warps,
-                             size_t smem_bytes, cudaStream_t stream);
+// Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
+cudaError_t f64_stream_prepare(size_t smem_bytes);
+cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
+                              size_t smem_bytes, cudaStream_t stream);
 }  // namespace tsqr
 
 using namespace tsqr;
@@ -485,11 +485,24 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     return TSQR_SUCCESS;
 }
 
-// Host-input FP64 call: A and R in host memory.  A is copied in P row pieces on a copy stream
-// while the leaves of the pieces already copied run on `stream`; all pieces' leaves share one
-// tree (one launch per piece over its leaves, see tsqr_host.cu).  The AUTO rules with P times
-// as many leaves, P in {8, 4, 2, 1}: as many as leave every leaf at least two work units.
-// Workspace: counters | tree slots | A (ld m) | R (ld n).
+// A page-locked host word holding 1 (the value of an arrived piece's flag), allocated once.
+const unsigned int *host_ones() {
+    static unsigned int *ones = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        if (cudaHostAlloc((void **)&ones, sizeof(unsigned int), cudaHostAllocPortable) ==
+            cudaSuccess)
+            *ones = 1u;
+        else
+            ones = nullptr;
+    });
+    return ones;
+}
+
+// Host-input FP64 call: A and R in host memory.  With page-locked A, A is copied in P row
+// pieces on a copy stream while one streaming launch (tsqr_host.cu) already folds the pieces
+// that have arrived; otherwise A is copied whole and the ordinary kernel runs.  The plan is the
+// AUTO plan.  Workspace: counters | tree slots | piece flags | A (ld m) | R (ld n).
 tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                            int64_t ldr, cudaStream_t stream) {
     g_last_launches = 0;
@@ -499,37 +512,28 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
             for (int64_t i = 0; i < n; ++i) R[i + c * ldr] = 0.0;
         return TSQR_SUCCESS;
     }
-    F64Plan p0;
-    tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p0);
+    cudaPointerAttributes attr;
+    const bool pinned = cudaPointerGetAttributes(&attr, A) == cudaSuccess &&
+                        attr.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
-    const int wave = p0.nleaves;
-    int P = 1;
-    for (int c : {8, 4, 2})
-        if (p0.tree == TSQR_TREE_HYBRID && p0.nunits >= 2LL * c * wave) {
-            P = c;
-            break;
-        }
-    F64Plan p = p0;
-    if (P > 1) {
-        const tsqr_plan_t over{TSQR_TREE_HYBRID, 0, P * wave, p0.warps, 0};
-        st = plan_f64(m, (int)n, &over, &p);
-        if (st != TSQR_SUCCESS) return st;
-        if (p.nleaves != P * wave) return TSQR_ERR_UNSUPPORTED;
-    }
-    if (f64_piece_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int P = (int)std::min<int64_t>(8, p.nunits);
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
+    const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
     const size_t a_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
     const size_t r_bytes = (size_t)n * (size_t)n * sizeof(double);
     Workspace *ws = nullptr;
-    st = get_workspace(stream, cnt_bytes + slot_bytes + a_bytes + r_bytes, &ws);
+    st = get_workspace(stream, cnt_bytes + slot_bytes + flag_bytes + a_bytes + r_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (!ws->copy_stream &&
             cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
             return TSQR_ERR_CUDA;
-        while (ws->events.size() < (size_t)P + 1) {
+        while (ws->events.size() < 2) {
             cudaEvent_t e;
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
                 return TSQR_ERR_CUDA;
@@ -537,8 +541,9 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
         }
     }
     char *base = (char *)ws->base;
-    double *Ad = (double *)(base + cnt_bytes + slot_bytes);
-    double *Rd = (double *)(base + cnt_bytes + slot_bytes + a_bytes);
+    unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
+    double *Ad = (double *)(base + cnt_bytes + slot_bytes + flag_bytes);
+    double *Rd = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
     F64Args a;
     std::memset(&a, 0, sizeof(a));
     a.A = Ad;
@@ -559,36 +564,53 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     a.R = Rd;
     a.ldr = n;
     a.status = ws->status;
-    cudaStream_t cs = ws->copy_stream;
-    // the copies must not overwrite A while earlier work on `stream` may still read it
-    if (cudaEventRecord(ws->events[P], stream) != cudaSuccess ||
-        cudaStreamWaitEvent(cs, ws->events[P], 0) != cudaSuccess)
-        return TSQR_ERR_CUDA;
-    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
-        cudaSuccess)
-        return TSQR_ERR_CUDA;
-    const int L = p.nleaves / P;
-    for (int q = 0; q < P; ++q) {
-        const int64_t u0 = ((int64_t)q * L * p.nunits) / p.nleaves;
-        const int64_t u1 = ((int64_t)(q + 1) * L * p.nunits) / p.nleaves;
-        const int64_t r0 = std::min<int64_t>(u0 * p.unit, m);
-        const int64_t r1 = std::min<int64_t>(u1 * p.unit, m);
-        if (r1 > r0 &&
-            cudaMemcpy2DAsync(Ad + r0, (size_t)m * sizeof(double), A + r0,
-                              (size_t)lda * sizeof(double), (size_t)(r1 - r0) * sizeof(double),
-                              (size_t)n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+    if (!pinned || p.unit != p.h || !host_ones()) {
+        // staged copy of the whole of A, then the ordinary kernel
+        if (cudaMemcpy2DAsync(Ad, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                              (size_t)m * sizeof(double), (size_t)n, cudaMemcpyHostToDevice,
+                              stream) != cudaSuccess ||
+            cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+                cudaSuccess)
             return TSQR_ERR_CUDA;
-        if (cudaEventRecord(ws->events[q], cs) != cudaSuccess ||
-            cudaStreamWaitEvent(stream, ws->events[q], 0) != cudaSuccess)
+        if (f64_prepare(p.smem) != cudaSuccess ||
+            f64_launch(a, p.warps, p.smem, stream) != cudaSuccess)
             return TSQR_ERR_CUDA;
-        if (f64_piece_launch(a, q * L, L, p.warps, p.smem, stream) != cudaSuccess)
+    } else {
+        cudaStream_t cs = ws->copy_stream;
+        // the copy stream starts after earlier work on `stream` (which may still read A) and
+        // zeroes the piece flags before the kernel, launched after that, can poll them
+        if (cudaEventRecord(ws->events[0], stream) != cudaSuccess ||
+            cudaStreamWaitEvent(cs, ws->events[0], 0) != cudaSuccess ||
+            cudaMemsetAsync(flags, 0, (size_t)P * sizeof(unsigned int), cs) != cudaSuccess ||
+            cudaEventRecord(ws->events[1], cs) != cudaSuccess ||
+            cudaStreamWaitEvent(stream, ws->events[1], 0) != cudaSuccess ||
+            cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+                cudaSuccess)
             return TSQR_ERR_CUDA;
+        if (f64_stream_prepare(p.smem) != cudaSuccess ||
+            f64_stream_launch(a, flags, P, p.warps, p.smem, stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        for (int q = 0; q < P; ++q) {
+            const int64_t r0 = std::min<int64_t>(((int64_t)q * p.nunits / P) * p.unit, m);
+            const int64_t r1 = std::min<int64_t>(((int64_t)(q + 1) * p.nunits / P) * p.unit, m);
+            // one contiguous copy per column segment (copy engines), then the piece's flag
+            for (int64_t c = 0; c < n && r1 > r0; ++c)
+                if (cudaMemcpyAsync(Ad + r0 + c * m, A + r0 + c * lda,
+                                    (size_t)(r1 - r0) * sizeof(double), cudaMemcpyHostToDevice,
+                                    cs) != cudaSuccess)
+                    return TSQR_ERR_CUDA;
+            // the flag is copied from page-locked host memory: a copy-engine transfer, which
+            // needs no SM while the streaming kernel occupies them all
+            if (cudaMemcpyAsync(flags + q, host_ones(), sizeof(unsigned int),
+                                cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                return TSQR_ERR_CUDA;
+        }
     }
     if (cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Rd, (size_t)n * sizeof(double),
                           (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost,
                           stream) != cudaSuccess)
         return TSQR_ERR_CUDA;
-    g_last_launches = P;
+    g_last_launches = 1;
     return TSQR_SUCCESS;
 }
 
@@ -922,6 +944,7 @@ tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream) {
             return TSQR_ERR_CUDA;
         if (cudaMemset(it->second.status, 0, sizeof(int)) != cudaSuccess) return TSQR_ERR_CUDA;
     }
+    if (flags & kStatusTimeoutBit) return TSQR_ERR_TIMEOUT;
     return (flags & kStatusNonfiniteBit) ? TSQR_STATUS_NONFINITE : TSQR_SUCCESS;
 }
 

@@ -776,6 +776,71 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // others return.  No CTA ever waits for another, and the operand order depends only on the
 // indices.
 // ------------------------------------------------------------------------------------------
+// The k-ary tree above leaf `leaf` (k = a.arity; level l has ceil(nleaves / k^l) nodes,
+// stored level after level): publish R in the node's slot and bump the parent's counter; the
+// last child to arrive stacks the children in index order (the lowest on top), folds them and
+// climbs on; the others return.  The root writes the sign-normalized R.  Rp holds the leaf's
+// R; Sd (leading dimension ldSd) must hold arity-1 stacked n x n triangles.
+template <bool kStore>
+__device__ __forceinline__ void climb_tree(const F64Args &a, double *Sd, const int ldSd,
+                                           double *Rp, double *f, double *seg, double *tot,
+                                           unsigned int *flag, const int leaf) {
+    const int n = a.n;
+    // k-ary tree: node t of level l+1 has children k t .. k t + k-1 of level l
+    const int k = a.arity;
+    int cnt = a.nleaves, off = 0, t = leaf;  // nodes and first node id of the current level
+    for (;;) {
+        if (cnt == 1) {
+            if constexpr (kStore) {
+                for (int k2 = threadIdx.x; k2 < n; k2 += blockDim.x)
+                    a.q.signs[k2] = (Rp[rowoff(n, k2)] < 0.0) ? -1.0 : 1.0;
+            }
+            store_normalized(Rp, n, a.R, a.ldr, a.status);
+            return;
+        }
+        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
+        const int parent = t / k, first = parent * k;
+        const int nchild = min(k, cnt - first);
+        if (nchild == 1) {  // a lone last child: promoted unchanged
+            off = next_off;
+            cnt = next_cnt;
+            t = parent;
+            continue;
+        }
+        store_packed(Rp, n, a.slots + (size_t)(off + t) * n * n, n);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + parent], 1u);
+        __syncthreads();
+        if (flag[0] + 1 < (unsigned)nchild) return;  // a later sibling combines
+        __threadfence();
+        // the last child to arrive stacks the children in index order: the first on top
+        load_packed_cg(a.slots + (size_t)(off + first) * n * n, n, n, Rp);
+        for (int ch = 1; ch < nchild; ++ch)
+            load_tri_cg(a.slots + (size_t)(off + first + ch) * n * n, n, n,
+                        Sd + (size_t)(ch - 1) * n, ldSd);
+        __syncthreads();
+        if constexpr (kStore) {
+            const size_t id = (size_t)next_off + parent;
+            const int ldv = (k - 1) * n;
+            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n,
+                       a.q.node_sc + id * 2 * n);
+            // the node's tails: rows 0..(nchild-1) n - 1 of S (zero below each diagonal)
+            double *dst = a.q.node_V + id * (size_t)ldv * n;
+            const int rows = (nchild - 1) * n;
+            for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+                const int col = idx / rows, row = idx - col * rows;
+                dst[row + (size_t)col * ldv] = Sd[row + (size_t)col * ldSd];
+            }
+        } else {
+            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
+        }
+        off = next_off;
+        cnt = next_cnt;
+        t = parent;
+    }
+}
+
 // One leaf of one problem: fold the leaf's rows into R, then climb the problem's k-ary tree
 // (k = a.arity; level l has ceil(nleaves / k^l) nodes, stored level after level).  T: leaf storage and
 // arithmetic type; Tin: type of A.  S is the leaf's chunk (T, leading dimension a.ldS); the
@@ -852,59 +917,7 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
         }
     }
 
-    // k-ary tree: node t of level l+1 has children k t .. k t + k-1 of level l
-    const int k = a.arity;
-    int cnt = a.nleaves, off = 0, t = leaf;  // nodes and first node id of the current level
-    for (;;) {
-        if (cnt == 1) {
-            if constexpr (kStore) {
-                for (int k2 = threadIdx.x; k2 < n; k2 += blockDim.x)
-                    a.q.signs[k2] = (Rp[rowoff(n, k2)] < 0.0) ? -1.0 : 1.0;
-            }
-            store_normalized(Rp, n, a.R, a.ldr, a.status);
-            return;
-        }
-        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
-        const int parent = t / k, first = parent * k;
-        const int nchild = min(k, cnt - first);
-        if (nchild == 1) {  // a lone last child: promoted unchanged
-            off = next_off;
-            cnt = next_cnt;
-            t = parent;
-            continue;
-        }
-        store_packed(Rp, n, a.slots + (size_t)(off + t) * n * n, n);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + parent], 1u);
-        __syncthreads();
-        if (flag[0] + 1 < (unsigned)nchild) return;  // a later sibling combines
-        __threadfence();
-        // the last child to arrive stacks the children in index order: the first on top
-        load_packed_cg(a.slots + (size_t)(off + first) * n * n, n, n, Rp);
-        for (int ch = 1; ch < nchild; ++ch)
-            load_tri_cg(a.slots + (size_t)(off + first + ch) * n * n, n, n,
-                        Sd + (size_t)(ch - 1) * n, ldSd);
-        __syncthreads();
-        if constexpr (kStore) {
-            const size_t id = (size_t)next_off + parent;
-            const int ldv = (k - 1) * n;
-            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n,
-                       a.q.node_sc + id * 2 * n);
-            // the node's tails: rows 0..(nchild-1) n - 1 of S (zero below each diagonal)
-            double *dst = a.q.node_V + id * (size_t)ldv * n;
-            const int rows = (nchild - 1) * n;
-            for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
-                const int col = idx / rows, row = idx - col * rows;
-                dst[row + (size_t)col * ldv] = Sd[row + (size_t)col * ldSd];
-            }
-        } else {
-            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
-        }
-        off = next_off;
-        cnt = next_cnt;
-        t = parent;
-    }
+    climb_tree<kStore>(a, Sd, ldSd, Rp, f, seg, tot, flag, leaf);
 }
 
 

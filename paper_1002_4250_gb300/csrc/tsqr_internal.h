@@ -11,6 +11,7 @@
 namespace tsqr {
 
 constexpr int kStatusNonfiniteBit = 1;
+constexpr int kStatusTimeoutBit = 2;  // a bounded device-side wait gave up (tsqr_r_host)
 
 // Dynamic shared-memory size of a kernel, with the whole unified L1/shared array given to
 // shared memory (the kernels keep their working set there and read A past L1).
