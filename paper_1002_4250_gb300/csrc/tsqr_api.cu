@@ -17,7 +17,7 @@ namespace tsqr {
 // Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
 cudaError_t f64_stream_prepare(size_t smem_bytes);
 cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
-                              size_t smem_bytes, cudaStream_t stream);
+                              size_t smem_bytes, long long wait_iters, cudaStream_t stream);
 }  // namespace tsqr
 
 using namespace tsqr;
@@ -588,7 +588,7 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
                 cudaSuccess)
             return TSQR_ERR_CUDA;
         if (f64_stream_prepare(p.smem) != cudaSuccess ||
-            f64_stream_launch(a, flags, P, p.warps, p.smem, stream) != cudaSuccess)
+            f64_stream_launch(a, flags, P, p.warps, p.smem, 1LL << 23, stream) != cudaSuccess)
             return TSQR_ERR_CUDA;
         for (int q = 0; q < P; ++q) {
             const int64_t r0 = std::min<int64_t>(((int64_t)q * p.nunits / P) * p.unit, m);
@@ -864,6 +864,56 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
         return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
     if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
     return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
+}
+
+// Test hook (not part of the C ABI's documented calls): one streaming launch over a device
+// buffer of m x n zeros whose pieces never arrive (their flags stay zero), each wait limited to
+// wait_iters polls; the CTAs give up, record the timeout in the status word and return, and
+// tsqr_get_device_status(stream) then reports TSQR_ERR_TIMEOUT.  Exercises the failure path of
+// tsqr_r_host's bounded waits without a fault or a hang.
+int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_iters,
+                                          tsqr_stream_t stream) {
+    if (m < 1 || n < 1 || n > TSQR_MAX_N || wait_iters < 1) return TSQR_ERR_INVALID_ARG;
+    const cudaStream_t s = (cudaStream_t)stream;
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
+    if (st != TSQR_SUCCESS) return st;
+    const int P = (int)std::min<int64_t>(8, p.nunits);
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
+    const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
+    const size_t a_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
+    const size_t r_bytes = (size_t)n * (size_t)n * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(s, cnt_bytes + slot_bytes + flag_bytes + a_bytes + r_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *base = (char *)ws->base;
+    F64Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = (double *)(base + cnt_bytes + slot_bytes + flag_bytes);
+    a.m = m;
+    a.lda = m;
+    a.n = (int)n;
+    a.unit = p.unit;
+    a.nunits = p.nunits;
+    a.nleaves = p.nleaves;
+    a.arity = p.arity;
+    a.h = p.h;
+    a.hs = p.hs;
+    a.blk = p.blk;
+    a.vec = p.vec;
+    a.ldS = p.ldS;
+    a.counters = (unsigned int *)base;
+    a.slots = (double *)(base + cnt_bytes);
+    a.R = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
+    a.ldr = n;
+    a.status = ws->status;
+    unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
+    if (cudaMemsetAsync(base, 0, cnt_bytes + slot_bytes + flag_bytes + a_bytes, s) != cudaSuccess ||
+        f64_stream_prepare(p.smem) != cudaSuccess ||
+        f64_stream_launch(a, flags, P, p.warps, p.smem, (long long)wait_iters, s) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    return TSQR_SUCCESS;
 }
 
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,

@@ -17,7 +17,6 @@ namespace tsqr {
 
 namespace {
 
-constexpr long long kWaitIters = 1LL << 23;  // x >= 256 ns each: several seconds
 
 // Piece q holds work units [q nunits / P, (q+1) nunits / P).
 __device__ __forceinline__ int piece_of(const int64_t u, const int64_t nunits, const int P) {
@@ -31,14 +30,15 @@ __device__ __forceinline__ unsigned int load_flag(const unsigned int *p) {
     return *reinterpret_cast<const volatile unsigned int *>(p);
 }
 
-// Whether piece q has arrived, as the whole CTA sees it; with `wait`, thread 0 polls (bounded)
-// until it has.  The copy's writes precede the flag's in stream order, and A is read through
+// Whether piece q has arrived, as the whole CTA sees it; with `wait`, thread 0 polls until it
+// has, at most wait_iters times with a 256 ns sleep between polls.  The copy's writes precede the flag's in stream order, and A is read through
 // L2 (cp.async.cg), so the data is there once the flag is.
 __device__ __forceinline__ bool piece_arrived(const unsigned int *flags, const int q,
-                                              const bool wait, unsigned int *sflag) {
+                                              const bool wait, const long long wait_iters,
+                                              unsigned int *sflag) {
     if (threadIdx.x == 0) {
         unsigned int ok = load_flag(flags + q) != 0u;
-        for (long long it = 0; wait && !ok && it < kWaitIters; ++it) {
+        for (long long it = 0; wait && !ok && it < wait_iters; ++it) {
             __nanosleep(256);
             ok = load_flag(flags + q) != 0u;
         }
@@ -64,7 +64,8 @@ __device__ __forceinline__ Chunk<double> unit_chunk(const F64Args &a, const int6
 
 template <int B>
 __global__ void __launch_bounds__(416, 1)
-    tsqr_f64_stream_kernel(const F64Args a, const unsigned int *flags, const int pieces) {
+    tsqr_f64_stream_kernel(const F64Args a, const unsigned int *flags, const int pieces,
+                           const long long wait_iters) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n;
     const SmemLayout L = smem_layout(n, a.hs, a.ldS, blockDim.x >> 5);
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(416, 1)
     const int64_t stride = a.nleaves;
     int64_t u = leaf;
     if (u < a.nunits) {
-        if (!piece_arrived(flags, piece_of(u, a.nunits, pieces), true, pflag)) {
+        if (!piece_arrived(flags, piece_of(u, a.nunits, pieces), true, wait_iters, pflag)) {
             if (threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusTimeoutBit);
             return;
         }
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(416, 1)
         for (;;) {
             const int64_t nx = u + stride;
             const bool have = nx < a.nunits;
-            const bool pre = have && piece_arrived(flags, piece_of(nx, a.nunits, pieces), false, pflag);
+            const bool pre = have && piece_arrived(flags, piece_of(nx, a.nunits, pieces), false, 0,
+                                                  pflag);
             Chunk<double> next;
             next.src = nullptr;
             next.lda = a.lda;
@@ -102,7 +104,8 @@ __global__ void __launch_bounds__(416, 1)
                                                    next);
             if (!have) break;
             if (!pre) {
-                if (!piece_arrived(flags, piece_of(nx, a.nunits, pieces), true, pflag)) {
+                if (!piece_arrived(flags, piece_of(nx, a.nunits, pieces), true, wait_iters,
+                                   pflag)) {
                     if (threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusTimeoutBit);
                     return;
                 }
@@ -125,14 +128,23 @@ cudaError_t f64_stream_prepare(size_t smem_bytes) {
     return e;
 }
 
+// wait_iters: polls per wait (1 << 23 in tsqr_r_host: seconds before a timeout)
 cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
-                              size_t smem_bytes, cudaStream_t stream) {
+                              size_t smem_bytes, long long wait_iters, cudaStream_t stream) {
     const dim3 grid(a.nleaves), block((warps + 1) * 32);
     switch (a.blk) {
-        case 4: tsqr_f64_stream_kernel<4><<<grid, block, smem_bytes, stream>>>(a, flags, pieces); break;
-        case 3: tsqr_f64_stream_kernel<3><<<grid, block, smem_bytes, stream>>>(a, flags, pieces); break;
-        case 2: tsqr_f64_stream_kernel<2><<<grid, block, smem_bytes, stream>>>(a, flags, pieces); break;
-        default: tsqr_f64_stream_kernel<1><<<grid, block, smem_bytes, stream>>>(a, flags, pieces); break;
+        case 4:
+            tsqr_f64_stream_kernel<4><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            break;
+        case 3:
+            tsqr_f64_stream_kernel<3><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            break;
+        case 2:
+            tsqr_f64_stream_kernel<2><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            break;
+        default:
+            tsqr_f64_stream_kernel<1><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            break;
     }
     return cudaGetLastError();
 }

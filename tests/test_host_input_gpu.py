@@ -55,3 +55,22 @@ def test_host_input_leading_dimensions_and_empty(oracle, T):
     assert torch.isnan(Rbig[:, n:]).all()
     Z = torch.zeros(0, 4, dtype=torch.float64)
     assert np.all(T.tsqr_r_host(Z).numpy() == 0)
+
+
+def test_stream_wait_times_out_and_reports(oracle, T):
+    """The failure path of the streaming launch's bounded waits: pieces that never arrive (flags
+    nothing sets) with a ~1 ms wait limit.  Every CTA gives up and returns, the status word says
+    TSQR_ERR_TIMEOUT, and the context stays usable for the next call."""
+    import ctypes
+    import torch
+    fn = T.capi.tsqr_internal_stream_timeout_selftest
+    fn.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    T.tsqr_get_device_status()  # clear
+    assert fn(200000, 16, 4096, T._stream_ptr(None)) == T.SUCCESS
+    assert T.tsqr_get_device_status() == T.ERR_TIMEOUT
+    At = workloads.gaussian(10000, 16, seed=1)
+    R = T.tsqr_r(At.cuda().T)
+    torch.cuda.synchronize()
+    assert T.tsqr_get_device_status() == T.SUCCESS
+    _check(oracle, oracle.from_torch_colmajor(At), R.cpu().numpy())
