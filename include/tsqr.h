@@ -96,7 +96,7 @@ tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double 
 
 /* tsqr_r for A and R in HOST memory, FP64: the copy of A to the device overlaps the leaf
  * factorizations.  TSQR streams naturally (Section 2: each row block is factorized on its own
- * and only the n x n factors meet in the tree).  With page-locked A, A is copied in up to 8 row
+ * and only the n x n factors meet in the tree).  With page-locked A, A is copied in up to 16 row
  * pieces on a second stream while ONE launch already folds the pieces that have arrived: its
  * leaves take the work units round-robin (leaf l: units l, l + L, l + 2L, ...), wait for a
  * piece's arrival flag before loading from it (a bounded wait; on timeout the device status

@@ -519,7 +519,7 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
-    const int P = (int)std::min<int64_t>(8, p.nunits);
+    const int P = (int)std::min<int64_t>(16, p.nunits);
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
     const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
@@ -878,7 +878,7 @@ int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_ite
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
-    const int P = (int)std::min<int64_t>(8, p.nunits);
+    const int P = (int)std::min<int64_t>(16, p.nunits);
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
     const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
