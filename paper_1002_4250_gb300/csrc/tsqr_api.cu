@@ -81,6 +81,27 @@ struct F64Plan {
     int64_t nodes = 0;
 };
 
+// Kernel arguments for a plan: A (leading dimension lda), m, n and the plan's shape; the
+// workspace, R and status pointers are the caller's to set.  Every other field is zero.
+F64Args plan_args(const F64Plan &p, const double *A, int64_t m, int64_t n, int64_t lda) {
+    F64Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.A = A;
+    a.m = m;
+    a.lda = lda;
+    a.n = (int)n;
+    a.unit = p.unit;
+    a.nunits = p.nunits;
+    a.nleaves = p.nleaves;
+    a.arity = p.arity;
+    a.h = p.h;
+    a.hs = p.hs;
+    a.blk = p.blk;
+    a.vec = p.vec;
+    a.ldS = p.ldS;
+    return a;
+}
+
 tsqr_status_t build_tree(int64_t leaves, int arity, TreeShape *t, int64_t *nodes) {
     std::memset(t, 0, sizeof(*t));
     int64_t c = leaves, off = 0;
@@ -338,20 +359,7 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
     Workspace *ws = nullptr;
     st = get_workspace(stream, cnt_bytes + slot_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
-    F64Args a;
-    a.A = A;
-    a.m = m;
-    a.lda = lda;
-    a.n = (int)n;
-    a.unit = p.unit;
-    a.nunits = p.nunits;
-    a.nleaves = p.nleaves;
-    a.arity = p.arity;
-    a.h = p.h;
-    a.hs = p.hs;
-    a.blk = p.blk;
-    a.vec = p.vec;
-    a.ldS = p.ldS;
+    F64Args a = plan_args(p, A, m, n, lda);
     a.counters = (unsigned int *)ws->base;
     a.slots = (double *)((char *)ws->base + cnt_bytes);
     a.R = R;
@@ -411,21 +419,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
                                    blk_bytes + sgn_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
     char *base = (char *)ws->base;
-    F64Args a;
-    std::memset(&a, 0, sizeof(a));
-    a.A = A;
-    a.m = m;
-    a.lda = lda;
-    a.n = (int)n;
-    a.unit = p.unit;
-    a.nunits = p.nunits;
-    a.nleaves = p.nleaves;
-    a.arity = p.arity;
-    a.h = p.h;
-    a.hs = p.hs;
-    a.blk = p.blk;
-    a.vec = p.vec;
-    a.ldS = p.ldS;
+    F64Args a = plan_args(p, A, m, n, lda);
     a.counters = (unsigned int *)base;
     a.slots = (double *)(base + cnt_bytes);
     a.R = R;
@@ -544,21 +538,7 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
     double *Ad = (double *)(base + cnt_bytes + slot_bytes + flag_bytes);
     double *Rd = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
-    F64Args a;
-    std::memset(&a, 0, sizeof(a));
-    a.A = Ad;
-    a.m = m;
-    a.lda = m;
-    a.n = (int)n;
-    a.unit = p.unit;
-    a.nunits = p.nunits;
-    a.nleaves = p.nleaves;
-    a.arity = p.arity;
-    a.h = p.h;
-    a.hs = p.hs;
-    a.blk = p.blk;
-    a.vec = p.vec;
-    a.ldS = p.ldS;
+    F64Args a = plan_args(p, Ad, m, n, m);
     a.counters = (unsigned int *)base;
     a.slots = (double *)(base + cnt_bytes);
     a.R = Rd;
@@ -630,19 +610,7 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     if (st != TSQR_SUCCESS) return st;
     MixedArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.base.A = nullptr;
-    a.base.m = m;
-    a.base.lda = lda;
-    a.base.n = (int)n;
-    a.base.unit = p.unit;
-    a.base.nunits = p.nunits;
-    a.base.nleaves = p.nleaves;
-    a.base.arity = p.arity;
-    a.base.h = p.h;
-    a.base.hs = p.hs;
-    a.base.blk = p.blk;
-    a.base.vec = p.vec;
-    a.base.ldS = p.ldS;
+    a.base = plan_args(p, nullptr, m, n, lda);
     a.base.counters = (unsigned int *)ws->base;
     a.base.slots = (double *)((char *)ws->base + cnt_bytes);
     a.base.R = R;
@@ -805,18 +773,7 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
     F64Plan p;
     const tsqr_status_t st = plan_f64(m, n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
-    std::memset(a, 0, sizeof(*a));
-    a->m = m;
-    a->n = n;
-    a->unit = p.unit;
-    a->nunits = p.nunits;
-    a->nleaves = p.nleaves;
-    a->arity = p.arity;
-    a->h = p.h;
-    a->hs = p.hs;
-    a->blk = p.blk;
-    a->vec = p.vec;
-    a->ldS = p.ldS;
+    *a = plan_args(p, nullptr, m, n, 0);
     *warps = p.warps;
     *smem = p.smem;
     *nodes = p.nodes;
@@ -888,21 +845,7 @@ int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_ite
     st = get_workspace(s, cnt_bytes + slot_bytes + flag_bytes + a_bytes + r_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
     char *base = (char *)ws->base;
-    F64Args a;
-    std::memset(&a, 0, sizeof(a));
-    a.A = (double *)(base + cnt_bytes + slot_bytes + flag_bytes);
-    a.m = m;
-    a.lda = m;
-    a.n = (int)n;
-    a.unit = p.unit;
-    a.nunits = p.nunits;
-    a.nleaves = p.nleaves;
-    a.arity = p.arity;
-    a.h = p.h;
-    a.hs = p.hs;
-    a.blk = p.blk;
-    a.vec = p.vec;
-    a.ldS = p.ldS;
+    F64Args a = plan_args(p, (double *)(base + cnt_bytes + slot_bytes + flag_bytes), m, n, m);
     a.counters = (unsigned int *)base;
     a.slots = (double *)(base + cnt_bytes);
     a.R = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
