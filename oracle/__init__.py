@@ -15,6 +15,8 @@ skinny matrices using MPI_Reduce" (arXiv:1002.4250) they follow:
   then the diag(R) >= 0 sign convention of Section 2;
 * ``householder_qr`` -- the same factorization plus the thin Q factor, formed by applying the
   reflectors to the identity (Section 3, the remark on computing Q);
+* ``lstsq``          -- least squares through that thin QR: X = R^-1 (Q^T B) (Section 3, the
+  remark on applying the Householder transformations to a matrix);
 * ``qr_uppers``      -- Section 2 / Table 3, the reduction operator qr(R1, R2);
 * ``tsqr_r``         -- Section 2 (local QR per tile, then the reduction) with the binary,
   flat and hybrid trees of Section 1 and Fig. 1;
@@ -146,6 +148,31 @@ def householder_qr(A, nthreads: int = 1, lib=None):
                                                   _ptr(R), max(n, 1), int(nthreads)),
            "householder_qr")
     return Q, R
+
+
+def back_substitute(R, C) -> np.ndarray:
+    """X with R X = C for R upper triangular (n x n, nonzero diagonal), C (n, k): the rows
+    solved last to first, each from the already solved rows below it."""
+    R = np.asarray(R, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    n = R.shape[0]
+    X = np.zeros_like(C)
+    for i in range(n - 1, -1, -1):
+        X[i] = (C[i] - R[i, i + 1:] @ X[i + 1:]) / R[i, i]
+    return X
+
+
+def lstsq(A, B, nthreads: int = 1, lib=None) -> np.ndarray:
+    """X minimizing ||A X - B||_F for A (m x n, m >= n) of full column rank and B (m x k): the
+    thin QR of A (householder_qr, Q formed from the Householder reflectors), then
+    X = R^-1 (Q^T B) by back substitution (Section 3: the stored Householder transformations
+    applied to a matrix instead of to the identity)."""
+    Q, R = householder_qr(A, nthreads=nthreads, lib=lib)
+    B = np.asarray(B, dtype=np.float64)
+    vec = B.ndim == 1
+    C = Q.T @ (B[:, None] if vec else B)
+    X = back_substitute(R, C)
+    return X[:, 0] if vec else X
 
 
 def qr_uppers(R1, R2, count_flops: bool = False, lib=None):
