@@ -351,7 +351,31 @@ def bench_extras(dev):
     out["widths_2e24"] = bench_widths(dev, ms64)
     out["varlen_batch"] = bench_batched(dev)
     out["thin_qr"] = bench_qr(dev)
+    out["lstsq"] = bench_lstsq(dev)
     return out
+
+
+def bench_lstsq(dev):
+    """tsqr_lstsq on 4,194,304 x 32 FP64 with k = 1 right-hand side (the augmented
+    factorization of [A | B]) and k = 32 and 100 (Q^T B through the stored reflectors), beside
+    tsqr_r alone."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    m, n = 4194304, 32
+    A = workloads.gaussian(m, n, seed=0, device=dev).T
+    R = T.empty_r(n, dev)
+    res = {"r_only_ms": time_call(lambda: T.tsqr_r(A, R=R), reps=5, warmup=1)}
+    for k in (1, 32, 100):
+        g = torch.Generator(device=dev).manual_seed(k)
+        B = torch.randn(k, m, generator=g, dtype=torch.float64, device=dev).T
+        X = torch.empty(k, n, dtype=torch.float64, device=dev).T
+        res[f"k{k}_ms"] = time_call(lambda: T.tsqr_lstsq(A, B, X=X, R=R), reps=3, warmup=1)
+        del B, X
+    res["path"] = {"k1": "augmented [A | B]", "k32": "stored reflectors", "k100": "stored reflectors"}
+    del A
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_qr(dev):

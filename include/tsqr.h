@@ -155,6 +155,28 @@ tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double
                       int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
                       tsqr_stream_t stream);
 
+/* Least squares: X minimizing ||A X - B||_F column by column, for A of full column rank, FP64.
+ * Section 3 notes that the reduction's Householder transformations, once stored, can be applied
+ * to another matrix (there: the trailing matrix of a blocked QR).  This call applies Q^T to B:
+ * the factorization is tsqr_qr's with the reflectors kept; each leaf folds its rows of B into the n rows of Q^T B that belong to its R
+ * and the tree combines them with the stored node reflectors; then R X = (Q^T B)(0:n, :).  Q is
+ * never formed.
+ *   A : device, column-major m x n, lda >= m, m >= n >= 1; read only.
+ *   B : device, column-major m x k, ldb >= m, k >= 0; read only.
+ *   X : device, column-major n x k, ldx >= n.
+ *   R : device n x n (ldr >= n) receiving R, or NULL.
+ *   plan as for tsqr_qr (NULL = AUTO).
+ * With few right-hand sides (k <= max(1, n / 4) and n + k <= TSQR_MAX_N) the augmented matrix
+ * [A | B] is factorized instead (its R holds R and (Q^T B)(0:n, :) side by side) and one
+ * triangular solve follows; R then equals tsqr_r's up to rounding.  Otherwise the columns of B
+ * go k_g = min(k, n) at a time (two launches per group after the factorization) and R is
+ * tsqr_r's bit for bit.
+ * A zero on R's diagonal (rank deficiency) makes X non-finite and the device status
+ * TSQR_STATUS_NONFINITE.  Returns TSQR_ERR_UNSUPPORTED where tsqr_qr does. */
+tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
+                         int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
+                         const tsqr_plan_t *plan, tsqr_stream_t stream);
+
 /* Varlen batch of independent problems: R_i = R factor of A_i for i < count.
  *   ptrs    : host array of `count` device pointers; A_i is column-major m_i x n_i with
  *             lda_i = m_i (e.g. all pointing into one packed buffer).

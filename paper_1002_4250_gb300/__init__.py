@@ -78,6 +78,9 @@ def _load():
     capi.tsqr_autotune_reset.restype = None
     capi.tsqr_r_host.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p]
     capi.tsqr_r_host.restype = _i32
+    capi.tsqr_lstsq.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64,
+                                ctypes.POINTER(Plan), _p]
+    capi.tsqr_lstsq.restype = _i32
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -96,7 +99,7 @@ def __getattr__(name):
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
                "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
-               "tsqr_autotune_reset", "tsqr_r_host")
+               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq")
 
 
 class TsqrError(RuntimeError):
@@ -198,6 +201,29 @@ def tsqr_qr(A, Q=None, R=None, plan: Plan | None = None, stream=None):
     check(_load().tsqr_qr(A.data_ptr(), m, n, lda, Q.data_ptr(), ldq, R.data_ptr(),
                           max(R.stride(1), n, 1), pp, _stream_ptr(stream)), "tsqr_qr")
     return Q, R
+
+
+def tsqr_lstsq(A, B, X=None, R=None, plan: Plan | None = None, stream=None):
+    """Least squares min ||A X - B||_F for logical (m, n) A and (m, k) B, column-major FP64
+    CUDA tensors (B may also be a vector of length m).  Returns (X, R): X (n, k) (or (n,)),
+    R (n, n) as from tsqr_r."""
+    import torch
+    m, n, lda = _colmajor_dims(A)
+    vec = B.dim() == 1
+    B2 = B[:, None] if vec else B
+    mb, k, ldb = _colmajor_dims(B2, "B")
+    if mb != m:
+        raise ValueError("A and B must have the same number of rows")
+    if X is None:
+        X = torch.empty(k, n, dtype=torch.float64, device=A.device).T
+    _, _, ldx = _colmajor_dims(X, "X")
+    if R is None:
+        R = empty_r(n, A.device)
+    pp = ctypes.byref(plan) if plan is not None else None
+    check(_load().tsqr_lstsq(A.data_ptr(), m, n, lda, B2.data_ptr(), ldb, k, X.data_ptr(),
+                             max(ldx, n), R.data_ptr(), max(R.stride(1), n, 1), pp,
+                             _stream_ptr(stream)), "tsqr_lstsq")
+    return (X[:, 0] if vec else X), R
 
 
 def tsqr_r_host(A, R=None, stream=None):

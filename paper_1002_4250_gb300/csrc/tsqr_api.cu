@@ -14,6 +14,12 @@
 #include "tsqr_qr.cuh"
 
 namespace tsqr {
+// Q^T B and the triangular solve of tsqr_lstsq (tsqr_qr.cu)
+size_t qt_smem_bytes(int n, int k, int ldS, int warps);
+cudaError_t qt_prepare(size_t smem_bytes);
+cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes, cudaStream_t stream);
+cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t ldc, double *X,
+                        int64_t ldx, int n, int k, int *status, cudaStream_t stream);
 // Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
 cudaError_t f64_stream_prepare(size_t smem_bytes);
 cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
@@ -594,6 +600,193 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     return TSQR_SUCCESS;
 }
 
+// Least squares with few right-hand sides (k <= max(1, n / 4), n + k <= TSQR_MAX_N): the R factor of the augmented
+// matrix [A | B] holds R in its leading n x n block and (Q^T B)(0:n, :) beside it (the first n
+// reflectors are A's own; the sign convention negates whole rows, which keeps R X = C), so one
+// factorization of [A | B] and one triangular solve give X.  Workspace: counters | slots |
+// [A | B] (ld m) | R of [A | B].
+tsqr_status_t run_lstsq_augmented(const double *A, int64_t m, int64_t n, int64_t lda,
+                                  const double *B, int64_t ldb, int64_t k, double *X, int64_t ldx,
+                                  double *R, int64_t ldr, const tsqr_plan_t *over,
+                                  cudaStream_t stream) {
+    const int64_t na = n + k;
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)na, over, &p);
+    if (st != TSQR_SUCCESS) return st;
+    if (f64_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)na * na * sizeof(double), 256);
+    const size_t aug_bytes = align_up((size_t)m * (size_t)na * sizeof(double), 256);
+    const size_t ra_bytes = (size_t)na * na * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, cnt_bytes + slot_bytes + aug_bytes + ra_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *base = (char *)ws->base;
+    double *aug = (double *)(base + cnt_bytes + slot_bytes);
+    double *Ra = (double *)(base + cnt_bytes + slot_bytes + aug_bytes);
+    if (cudaMemcpy2DAsync(aug, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                          (size_t)m * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice,
+                          stream) != cudaSuccess ||
+        cudaMemcpy2DAsync(aug + n * m, (size_t)m * sizeof(double), B, (size_t)ldb * sizeof(double),
+                          (size_t)m * sizeof(double), (size_t)k, cudaMemcpyDeviceToDevice,
+                          stream) != cudaSuccess ||
+        cudaMemsetAsync(base, 0, (size_t)p.nodes * sizeof(unsigned int), stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    F64Args a = plan_args(p, aug, m, na, m);
+    a.counters = (unsigned int *)base;
+    a.slots = (double *)(base + cnt_bytes);
+    a.R = Ra;
+    a.ldr = na;
+    a.status = ws->status;
+    if (f64_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (R && cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Ra, (size_t)na * sizeof(double),
+                               (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice,
+                               stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (trsm_launch(Ra, na, Ra + n * na, na, X, ldx, (int)n, (int)k, ws->status, stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    g_last_launches = 2;
+    return TSQR_SUCCESS;
+}
+
+// Least squares: the factorization with its reflectors kept (as tsqr_qr's, with the tails in
+// the workspace), then per group of at most n columns of B: Q^T B's first n rows (one launch,
+// tsqr_qr.cu) and R X = those rows (one launch).  Workspace: counters | slots | tails |
+// chunk scalars | node tails | node scalars | signs | apply counters | apply slots | C | R.
+// With k <= max(1, n / 4) and n + k <= TSQR_MAX_N the augmented factorization above is used.
+tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
+                        int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
+                        const tsqr_plan_t *over, cudaStream_t stream) {
+    g_last_launches = 0;
+    // the augmented factorization costs ~(n + k)^2 per row against n^2 plus the apply pass:
+    // cheaper up to k ~ n / 4 (4,194,304 x 32: k = 1 11.3 against 15.2 ms, k = 32 49.0 against
+    // 41.1 ms)
+    if (k > 0 && k <= std::max<int64_t>(1, n / 4) && n + k <= TSQR_MAX_N)
+        return run_lstsq_augmented(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, over, stream);
+    F64Plan p;
+    tsqr_status_t st = plan_f64(m, (int)n, over, &p);
+    if (st != TSQR_SUCCESS) return st;
+    if (p.unit % p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    const int kg = (int)std::min<int64_t>(k, n);  // columns of B per apply launch
+    // the apply pass has no serial reflector chain: more, shorter warps (as the Q leaf pass)
+    int qwarps = p.warps;
+    for (int c : {12, 8})
+        if (c > qwarps && p.hs % (32 * c) == 0) {
+            qwarps = c;
+            break;
+        }
+    int qblk = 1;
+    for (int c = 4; c >= 1; --c)
+        if ((p.hs / (32 * qwarps)) % c == 0) {
+            qblk = c;
+            break;
+        }
+    const size_t qt_smem = qt_smem_bytes((int)n, kg, p.ldS, qwarps);
+    if (qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
+    if (qr_prepare(p.smem, q_leaf_smem_bytes((int)n, p.ldS, p.warps),
+                   q_tree_smem_bytes((int)n, p.arity)) != cudaSuccess ||
+        qt_prepare(qt_smem) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    const int64_t nchunks = (m + p.h - 1) / p.h;
+    const size_t nn = (size_t)n * (size_t)n;
+    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
+    const size_t slot_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
+    const size_t v_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
+    const size_t csc_bytes = align_up((size_t)nchunks * 2 * n * sizeof(double), 256);
+    const size_t nv_bytes = align_up((size_t)p.nodes * (p.arity - 1) * nn * sizeof(double), 256);
+    const size_t nsc_bytes = align_up((size_t)p.nodes * 2 * n * sizeof(double), 256);
+    const size_t sgn_bytes = align_up((size_t)n * sizeof(double), 256);
+    const size_t qslot_bytes = align_up((size_t)p.nodes * (size_t)n * kg * sizeof(double), 256);
+    const size_t c_bytes = align_up((size_t)n * kg * sizeof(double), 256);
+    const size_t r_bytes = R ? 0 : nn * sizeof(double);
+    Workspace *ws = nullptr;
+    st = get_workspace(stream, 2 * cnt_bytes + slot_bytes + v_bytes + csc_bytes + nv_bytes +
+                                   nsc_bytes + sgn_bytes + qslot_bytes + c_bytes + r_bytes, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *base = (char *)ws->base;
+    size_t o = 0;
+    unsigned int *counters = (unsigned int *)(base + o);
+    o += cnt_bytes;
+    double *slots = (double *)(base + o);
+    o += slot_bytes;
+    double *V = (double *)(base + o);
+    o += v_bytes;
+    double *csc = (double *)(base + o);
+    o += csc_bytes;
+    double *nV = (double *)(base + o);
+    o += nv_bytes;
+    double *nsc = (double *)(base + o);
+    o += nsc_bytes;
+    double *signs = (double *)(base + o);
+    o += sgn_bytes;
+    unsigned int *qcounters = (unsigned int *)(base + o);
+    o += cnt_bytes;
+    double *qslots = (double *)(base + o);
+    o += qslot_bytes;
+    double *C = (double *)(base + o);
+    o += c_bytes;
+    if (!R) {
+        R = (double *)(base + o);
+        ldr = n;
+    }
+    F64Args a = plan_args(p, A, m, n, lda);
+    a.counters = counters;
+    a.slots = slots;
+    a.R = R;
+    a.ldr = ldr;
+    a.status = ws->status;
+    a.q.V = V;
+    a.q.ldv = m;
+    a.q.chunk_sc = csc;
+    a.q.node_V = nV;
+    a.q.node_sc = nsc;
+    a.q.signs = signs;
+    if (cudaMemsetAsync(counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+            cudaSuccess ||
+        qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    int launches = 1;
+    for (int64_t q0 = 0; q0 < k; q0 += kg) {
+        const int kc = (int)std::min<int64_t>(kg, k - q0);
+        QtArgs t;
+        std::memset(&t, 0, sizeof(t));
+        t.V = V;
+        t.ldv = m;
+        t.B = B + q0 * ldb;
+        t.m = m;
+        t.ldb = ldb;
+        t.n = (int)n;
+        t.k = kc;
+        t.unit = p.unit;
+        t.nunits = p.nunits;
+        t.nleaves = p.nleaves;
+        t.h = p.h;
+        t.hs = p.hs;
+        t.ldS = p.ldS;
+        t.arity = p.arity;
+        t.chunk_sc = csc;
+        t.node_V = nV;
+        t.node_sc = nsc;
+        t.signs = signs;
+        t.slots = qslots;
+        t.counters = qcounters;
+        t.C = C;
+        if (cudaMemsetAsync(qcounters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+                cudaSuccess ||
+            qt_launch(t, qblk, qwarps, qt_smem, stream) != cudaSuccess ||
+            trsm_launch(R, ldr, C, n, X + q0 * ldx, ldx, (int)n, kc, ws->status, stream) !=
+                cudaSuccess)
+            return TSQR_ERR_CUDA;
+        launches += 2;
+    }
+    g_last_launches = launches;
+    return TSQR_SUCCESS;
+}
+
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
@@ -857,6 +1050,18 @@ int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_ite
         f64_stream_launch(a, flags, P, p.warps, p.smem, (long long)wait_iters, s) != cudaSuccess)
         return TSQR_ERR_CUDA;
     return TSQR_SUCCESS;
+}
+
+tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
+                         int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
+                         const tsqr_plan_t *plan, tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, std::max<int64_t>(ldr, n)) || n < 1 || m < n || k < 0 ||
+        ldb < std::max<int64_t>(1, m) || ldx < n || (R && ldr < n))
+        return TSQR_ERR_INVALID_ARG;
+    if (!A || (k > 0 && (!B || !X))) return TSQR_ERR_INVALID_ARG;
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    return run_lstsq(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, plan, (cudaStream_t)stream);
 }
 
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,

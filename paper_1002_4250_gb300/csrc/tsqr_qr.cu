@@ -114,13 +114,14 @@ __global__ void __launch_bounds__(256) tsqr_q_tree_kernel(const QTreeArgs a) {
 // ------------------------------------------------------------------------------------------
 // Software pipelined: the next block's operands are loaded before the current block is
 // updated and stored (the two blocks never overlap: different rows, or the next column).
+// ncols: the columns of Z (n for the Q leaf pass, k for the Q^T B pass).
 template <int B>
-__device__ __forceinline__ void q_sweep(const int lane, const int n, const int r, const int Hw,
+__device__ __forceinline__ void q_sweep(const int lane, const int ncols, const int r, const int Hw,
                                         double *__restrict__ Z, const int ldS, const int r0,
                                         const double *__restrict__ xu,
                                         const double *__restrict__ xd,
                                         const double *__restrict__ g, double *__restrict__ seg) {
-    const int run = n * r;
+    const int run = ncols * r;
     const int nblk = run / B;
     const int p = lane * run;
     int kk = p / Hw;
@@ -166,7 +167,7 @@ __device__ __forceinline__ void q_sweep(const int lane, const int n, const int r
             if (cross) {
                 seg[lane + kk] = acc;
                 acc = 0.0;
-                gk = g[min(kk2, n - 1)];
+                gk = g[min(kk2, ncols - 1)];
             }
             i = i2;
             kk = kk2;
@@ -322,6 +323,205 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Q^T B (tsqr_lstsq).  One CTA per leaf, as the leaf pass: per chunk, first to last, X = the
+// chunk's tails, Z = the chunk's rows of B and T the leaf's block (zero at the start, the rows
+// of the zero triangle the first chunk was folded under); for J = 0 .. n-1 the bulk sweep
+// applies reflector J-1's update Z(:,q) -= g_q x_{J-1} and forms x_J . Z(:,q) for every column
+// q of Z; the reducer forms w_q = T(J,q) + c_J d_q, T(J,q) -= tau_J w_q, g_q = tau_J c_J w_q.
+// Z is dropped after the chunk: only T (the rows of Q^T B that belong to R) goes on.  The leaf
+// then climbs the factorization's tree with its T, and the last child to arrive at a node
+// applies the node's reflectors, first to last, to [T_0; T_1; ...] (row J of T_0 and rows 0..J
+// of every other block).  The root writes D T (D: the row signs) to C.
+// ------------------------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n, kc = a.k, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Wb = (blockDim.x >> 5) - 1;
+    const bool reducer = (warp == Wb);
+    const int Hw = a.hs / Wb, r = Hw >> 5, r0 = warp * Hw;
+    const QtLayout L = qt_layout(n, kc, a.ldS, Wb + 1);
+    double *X = smem + L.X;
+    double *Z = smem + L.Z;
+    double *top = smem + L.top;
+    double *g = smem + L.g;
+    double *sc = smem + L.sc;
+    const int ss = seg_stride(kc);
+    double *seg_all = smem + L.seg;
+    double *seg = seg_all + warp * ss;
+    double *tot = smem + L.tot;
+    unsigned int *flag = reinterpret_cast<unsigned int *>(smem + L.flag);
+    const int nslot = 32 + kc;
+    constexpr int kGroups = 4;
+    const int leaf = blockIdx.x;
+
+    for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) top[idx] = 0.0;
+    const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
+    const int64_t rbeg = u0 * a.unit;
+    const int64_t rend = (u1 * a.unit < a.m) ? u1 * a.unit : a.m;
+    const int64_t nchunks = (rend - rbeg + a.h - 1) / a.h;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int64_t row0 = rbeg + c * a.h;
+        const int rows = (int)((rend - row0 < a.h) ? rend - row0 : a.h);
+        __syncthreads();  // the previous chunk's X and Z are no longer read
+        for (int idx = threadIdx.x; idx < a.hs * n; idx += blockDim.x) {
+            const int col = idx / a.hs, i = idx - col * a.hs;
+            X[i + (size_t)col * a.ldS] = (i < rows) ? a.V[row0 + i + (int64_t)col * a.ldv] : 0.0;
+        }
+        for (int idx = threadIdx.x; idx < a.hs * kc; idx += blockDim.x) {
+            const int col = idx / a.hs, i = idx - col * a.hs;
+            Z[i + (size_t)col * a.ldS] = (i < rows) ? a.B[row0 + i + (int64_t)col * a.ldb] : 0.0;
+        }
+        const double *csc = a.chunk_sc + (row0 / a.h) * 2 * n;
+        for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) sc[j] = csc[j];
+        __syncthreads();
+        for (int J = 0; J < n; ++J) {
+            if (!reducer) {
+                for (int id = lane; id < nslot; id += 32) seg[id] = 0.0;
+                __syncwarp();
+                q_sweep<B>(lane, kc, r, Hw, Z, a.ldS, r0,
+                           (J > 0) ? X + (size_t)(J - 1) * a.ldS + r0 : nullptr,
+                           X + (size_t)J * a.ldS + r0, g, seg);
+            }
+            __syncthreads();
+            for (int base = 0; base < nslot * kGroups; base += blockDim.x) {
+                const int t = base + threadIdx.x;
+                const int id = t / kGroups, gi = t - id * kGroups;
+                double v = 0.0;
+                if (id < nslot) {
+                    const int w0 = (gi * Wb) / kGroups, w1 = ((gi + 1) * Wb) / kGroups;
+                    for (int w = w0; w < w1; ++w) v += seg_all[w * ss + id];
+                }
+#pragma unroll
+                for (int o = kGroups >> 1; o > 0; o >>= 1)
+                    v += __shfl_xor_sync(0xffffffffu, v, o, kGroups);
+                if (id < nslot && gi == 0) tot[id] = v;
+            }
+            __syncthreads();
+            if (reducer) {
+                const double tau = sc[2 * J], cj = sc[2 * J + 1];
+                const int Nw = kc * Hw;
+                for (int q = lane; q < kc; q += 32) {
+                    const int la = (32 * (q * Hw + 1) - 1) / Nw;
+                    const int lb = (32 * (q + 1) * Hw - 1) / Nw;
+                    double d0 = tot[q + la], d1 = 0.0;
+                    for (int l = la + 1; l + 1 <= lb; l += 2) {
+                        d0 += tot[q + l];
+                        d1 += tot[q + l + 1];
+                    }
+                    if (((lb - la) & 1) == 1) d0 += tot[q + lb];
+                    const double w = fma(cj, d0 + d1, top[J + q * n]);
+                    top[J + q * n] = fma(-tau, w, top[J + q * n]);
+                    g[q] = tau * cj * w;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // the tree: the same shape, node ids and stored reflectors as the factorization's
+    const int k = a.arity;
+    int cnt = a.nleaves, off = 0, t = leaf;
+    for (;;) {
+        if (cnt == 1) {
+            for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
+                a.C[idx] = a.signs[idx % n] * top[idx];
+            return;
+        }
+        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
+        const int parent = t / k, first = parent * k;
+        const int nchild = min(k, cnt - first);
+        if (nchild == 1) {
+            off = next_off;
+            cnt = next_cnt;
+            t = parent;
+            continue;
+        }
+        double *mine = a.slots + (size_t)(off + t) * n * kc;
+        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) mine[idx] = top[idx];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + parent], 1u);
+        __syncthreads();
+        if (flag[0] + 1 < (unsigned)nchild) return;
+        __threadfence();
+        // the children's blocks in index order: the first on top, the others stacked in X
+        const int cs = nchild - 1, ldY = cs * n;
+        double *Y = X;
+        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
+            top[idx] = __ldcg(a.slots + (size_t)(off + first) * n * kc + idx);
+        for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
+            const int col = idx / (cs * n), rr = idx - col * (cs * n);
+            const int tt = rr / n, i = rr - tt * n;
+            Y[rr + (size_t)col * ldY] =
+                __ldcg(a.slots + (size_t)(off + first + 1 + tt) * n * kc + i + (size_t)col * n);
+        }
+        __syncthreads();
+        const size_t id = (size_t)next_off + parent;
+        const int ldX = (k - 1) * n;
+        const double *Xn = a.node_V + id * (size_t)ldX * n;
+        const double *nsc = a.node_sc + id * 2 * n;
+        int tpc = 1;  // lanes per column: a power of two <= 32 with tpc kc <= blockDim
+        while (tpc < 32 && 2 * tpc * kc <= (int)blockDim.x) tpc *= 2;
+        const int q0 = threadIdx.x / tpc, sub = threadIdx.x - q0 * tpc;
+        const bool active = q0 < kc;
+        const int q = active ? q0 : kc - 1;
+        for (int J = 0; J < n; ++J) {
+            const double tau = nsc[2 * J], cj = nsc[2 * J + 1];
+            if (tau == 0.0) continue;
+            const int h1 = J + 1, E = cs * h1;
+            double d = 0.0;
+            for (int e = sub; e < E; e += tpc) {
+                const int tt = e / h1, i = e - tt * h1;
+                d = fma(Xn[tt * n + i + (size_t)J * ldX], Y[tt * n + i + (size_t)q * ldY], d);
+            }
+            for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
+            const double w = fma(cj, d, top[J + q * n]);
+            __syncwarp();
+            if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
+            const double gq = tau * cj * w;
+            if (active) {
+                for (int e = sub; e < E; e += tpc) {
+                    const int tt = e / h1, i = e - tt * h1;
+                    Y[tt * n + i + (size_t)q * ldY] = fma(-gq, Xn[tt * n + i + (size_t)J * ldX],
+                                                          Y[tt * n + i + (size_t)q * ldY]);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        off = next_off;
+        cnt = next_cnt;
+        t = parent;
+    }
+}
+
+// R X = C for R upper triangular (n x n), C (n x k, leading dimension ldc): one warp per column,
+// rows last to first, each row's sum over the solved rows split across the lanes (a fixed
+// butterfly).  A zero or non-finite result is noted in the status word.
+__global__ void __launch_bounds__(1024) tsqr_trsm_kernel(const double *R, int64_t ldr,
+                                                         const double *C, int64_t ldc, double *X,
+                                                         int64_t ldx, int n, int k, int *status) {
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= k) return;
+    double *x = X + (int64_t)q * ldx;
+    bool bad = false;
+    for (int i = n - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int j = i + 1 + lane; j < n; j += 32) s = fma(R[i + (int64_t)j * ldr], x[j], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double v = (C[i + (int64_t)q * ldc] - s) / R[i + (int64_t)i * ldr];
+        if (lane == 0) x[i] = v;
+        bad |= !isfinite(v);
+        __syncwarp();
+    }
+    if (bad && lane == 0 && status) atomicOr(status, kStatusNonfiniteBit);
+}
+
 namespace {
 const void *q_leaf_fn(int blk) {
     switch (blk) {
@@ -341,6 +541,38 @@ size_t q_leaf_smem_bytes(int n, int ldS, int warps) {
 }
 
 size_t q_tree_smem_bytes(int n, int arity) { return sizeof(double) * (size_t)arity * n * n; }
+
+size_t qt_smem_bytes(int n, int k, int ldS, int warps) {
+    return sizeof(double) * (size_t)qt_layout(n, k, ldS, warps + 1).total;
+}
+
+cudaError_t qt_prepare(size_t smem_bytes) {
+    cudaError_t e = set_smem_attrs(tsqr_qt_kernel<4>, smem_bytes);
+    if (e == cudaSuccess) e = set_smem_attrs(tsqr_qt_kernel<3>, smem_bytes);
+    if (e == cudaSuccess) e = set_smem_attrs(tsqr_qt_kernel<2>, smem_bytes);
+    if (e == cudaSuccess) e = set_smem_attrs(tsqr_qt_kernel<1>, smem_bytes);
+    return e;
+}
+
+cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes,
+                      cudaStream_t stream) {
+    const dim3 grid(a.nleaves), block((warps + 1) * 32);
+    switch (blk) {
+        case 4: tsqr_qt_kernel<4><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 3: tsqr_qt_kernel<3><<<grid, block, smem_bytes, stream>>>(a); break;
+        case 2: tsqr_qt_kernel<2><<<grid, block, smem_bytes, stream>>>(a); break;
+        default: tsqr_qt_kernel<1><<<grid, block, smem_bytes, stream>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t ldc, double *X,
+                        int64_t ldx, int n, int k, int *status, cudaStream_t stream) {
+    const int warps = 8;
+    tsqr_trsm_kernel<<<(k + warps - 1) / warps, warps * 32, 0, stream>>>(R, ldr, C, ldc, X, ldx,
+                                                                        n, k, status);
+    return cudaGetLastError();
+}
 
 cudaError_t qr_prepare(size_t factor_smem, size_t leaf_smem, size_t tree_smem) {
     for (int b = 1; b <= 4; ++b) {

@@ -55,4 +55,49 @@ __host__ __device__ inline QLeafLayout q_leaf_layout(int n, int ldS, int warps_t
     return L;
 }
 
+// Q^T applied to B (tsqr_lstsq): the factorization's leaf partition and chunk shape, its stored
+// reflectors, and B (m x k, leading dimension ldb).  Each leaf folds its chunks of B, first to
+// last, into a k-column block T (the rows of Q^T B that belong to its R); the leaves then
+// climb the factorization's tree, where the last child to arrive applies the node's reflectors
+// to its children's stacked blocks.  The root's block, with the sign convention's row signs,
+// is the first n rows of Q^T B, written to C.
+struct QtArgs {
+    const double *V;          // the chunks' tails (QStore::V), leading dimension ldv
+    int64_t ldv;
+    const double *B;          // m x k, leading dimension ldb
+    int64_t m, ldb;
+    int n, k;
+    int64_t unit, nunits;
+    int nleaves, h, hs, ldS, arity;
+    const double *chunk_sc;   // per chunk: tau_J, c_J
+    const double *node_V;     // per node id: stacked tails, leading dimension (arity-1) n
+    const double *node_sc;    // per node id: tau_J, c_J
+    const double *signs;      // the root's row signs
+    double *slots;            // per node id: n x k block, leading dimension n
+    unsigned int *counters;   // per node id: arrivals (zeroed per call)
+    double *C;                // out: n x k, leading dimension n
+};
+
+// Offsets in doubles: the tails X (ldS x n), B's chunk Z (ldS x k), the block T (n x k), the
+// stacked children's blocks during the climb (reusing X and Z), the factors g, the chunk's
+// scalars, the partial-sum slots and their sums, and one word for the climb's counter value.
+struct QtLayout {
+    int X, Z, top, g, sc, seg, tot, flag, total;
+};
+
+__host__ __device__ inline QtLayout qt_layout(int n, int k, int ldS, int warps_total) {
+    QtLayout L;
+    int o = 0;
+    L.X = o;    o += ldS * n;
+    L.Z = o;    o += ldS * k;
+    L.top = o;  o += n * k;
+    L.g = o;    o += k + 1;
+    L.sc = o;   o += 2 * n;
+    L.seg = o;  o += warps_total * seg_stride(k);
+    L.tot = o;  o += 2 * seg_stride(k);
+    L.flag = o; o += 1;
+    L.total = o;
+    return L;
+}
+
 }  // namespace tsqr
