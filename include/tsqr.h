@@ -147,10 +147,12 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
  *   plan : NULL = AUTO, or as for tsqr_r_ex.  The plan's chunking must put every chunk
  *          boundary at a multiple of its chunk height (AUTO and HYBRID/FLAT plans do; a BINARY
  *          tile taller than one chunk that is not a multiple of it does not).
- * Returns TSQR_ERR_UNSUPPORTED when the Q pass's chunk buffers (two chunks and an n x n block
- * in shared memory) do not fit: with the AUTO plan every n <= 64 fits.  Workspace: about
- * (2 + arity) n^2 doubles per tree node plus 2n per chunk, from the per-stream pool.
- * Launches: the factorization, one per tree level below the root, and the leaf pass. */
+ * Every n <= TSQR_MAX_N is supported: where a chunk of tails, the Q rows and the carried block
+ * do not fit shared memory together (n above about 64 with the AUTO plan), the passes take Q's
+ * columns in groups and the tails go to workspace instead of Q.  Workspace: about (2 + arity)
+ * n^2 doubles per tree node plus 2n per chunk, plus m x n when grouped, from the per-stream
+ * pool.  Launches: the factorization, one per tree level below the root, and one leaf pass per
+ * column group. */
 tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q,
                       int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
                       tsqr_stream_t stream);
@@ -176,6 +178,28 @@ tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double
 tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
                          int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                          const tsqr_plan_t *plan, tsqr_stream_t stream);
+
+/* R of a general tall m x n matrix (n not limited to TSQR_MAX_N), FP64, by the communication-
+ * avoiding QR that Section 5 describes: the first `panel` columns (the panel) are factorized by
+ * the TSQR reduction with their Householder reflectors kept, Q^T of that panel is applied to
+ * the columns right of it (its first `panel` rows are R's next block row), and the rows left
+ * below form the next panel's matrix; and so on to the last column.
+ *   A     : device, column-major m x n, lda >= m, m >= n >= 1; read only.
+ *   R     : device, column-major n x n, ldr >= n; the upper triangle with diag(R) >= 0, the
+ *           strict lower triangle written as 0.  Must not overlap A.
+ *   panel : panel width, 1 .. TSQR_MAX_N; 0 = 32 (or n if smaller).
+ *   plan  : NULL = AUTO, else the plan used for every panel's factorization (as for tsqr_qr).
+ * Each panel's update keeps every row of the panel's matrix and adds the n-row blocks its tree
+ * nodes leave behind: a panel factorized on L leaves adds (L - 1) panel rows to the next
+ * matrix (the rows' order does not change R).  Workspace: the matrix right of the first panel
+ * with those rows added (about 8 (m + (n / panel) (L - 1) panel) n bytes), the panel's stored
+ * reflectors (8 m panel bytes) and small tree buffers, from the per-stream pool.  Launches: two
+ * per panel (the factorization and the update) except the last (one).  Returns
+ * TSQR_ERR_INVALID_ARG for bad sizes, TSQR_ERR_UNSUPPORTED for a panel above TSQR_MAX_N or a
+ * plan tsqr_qr would refuse, TSQR_ERR_ALLOC when the workspace cannot be had. */
+tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                          int64_t ldr, int64_t panel, const tsqr_plan_t *plan,
+                          tsqr_stream_t stream);
 
 /* Varlen batch of independent problems: R_i = R factor of A_i for i < count.
  *   ptrs    : host array of `count` device pointers; A_i is column-major m_i x n_i with

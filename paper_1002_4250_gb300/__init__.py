@@ -81,6 +81,8 @@ def _load():
     capi.tsqr_lstsq.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64,
                                 ctypes.POINTER(Plan), _p]
     capi.tsqr_lstsq.restype = _i32
+    capi.tsqr_caqr_r.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _i64, ctypes.POINTER(Plan), _p]
+    capi.tsqr_caqr_r.restype = _i32
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -99,7 +101,7 @@ def __getattr__(name):
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
                "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
-               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq")
+               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq", "tsqr_caqr_r")
 
 
 class TsqrError(RuntimeError):
@@ -224,6 +226,19 @@ def tsqr_lstsq(A, B, X=None, R=None, plan: Plan | None = None, stream=None):
                              max(ldx, n), R.data_ptr(), max(R.stride(1), n, 1), pp,
                              _stream_ptr(stream)), "tsqr_lstsq")
     return (X[:, 0] if vec else X), R
+
+
+def tsqr_caqr_r(A, panel: int = 0, R=None, plan: Plan | None = None, stream=None):
+    """R (n, n), diag(R) >= 0, of a logical (m, n) column-major FP64 CUDA tensor of any width
+    n <= m, by panels of `panel` columns (0 = the default width): each panel factorized by TSQR,
+    then its Q^T applied to the columns right of it (Section 5)."""
+    m, n, lda = _colmajor_dims(A)
+    if R is None:
+        R = empty_r(n, A.device)
+    pp = ctypes.byref(plan) if plan is not None else None
+    check(_load().tsqr_caqr_r(A.data_ptr(), m, n, lda, R.data_ptr(), max(R.stride(1), n, 1),
+                              int(panel), pp, _stream_ptr(stream)), "tsqr_caqr_r")
+    return R
 
 
 def tsqr_r_host(A, R=None, stream=None):

@@ -406,10 +406,18 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
             qblk = c;
             break;
         }
-    const size_t leaf_smem = q_leaf_smem_bytes((int)n, p.ldS, qwarps);
-    const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity);
+    // column groups: Q's columns (and the carried blocks') are independent, so the leaf pass
+    // takes them qn at a time and the tree pass qg at a time where all n do not fit
+    int qn = (int)n, qg = (int)n;
+    while (qn > 8 && q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps) > di.smem_block_optin)
+        qn = (qn + 1) / 2;
+    while (qg > 8 && q_tree_smem_bytes((int)n, p.arity, qg) > di.smem_block_optin)
+        qg = (qg + 1) / 2;
+    const size_t leaf_smem = q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps);
+    const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity, qg);
     if (leaf_smem > di.smem_block_optin || tree_smem > di.smem_block_optin)
         return TSQR_ERR_UNSUPPORTED;
+    const bool grouped = qn < n;  // then the tails cannot live in Q: later groups still read them
     if (qr_prepare(p.smem, leaf_smem, tree_smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t nchunks = (m + p.h - 1) / p.h;
     const size_t nn = (size_t)n * (size_t)n;
@@ -420,9 +428,10 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     const size_t nsc_bytes = align_up((size_t)p.nodes * 2 * n * sizeof(double), 256);
     const size_t blk_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
     const size_t sgn_bytes = align_up((size_t)n * sizeof(double), 256);
+    const size_t v_bytes = grouped ? align_up((size_t)m * (size_t)n * sizeof(double), 256) : 0;
     Workspace *ws = nullptr;
     st = get_workspace(stream, cnt_bytes + slot_bytes + csc_bytes + nv_bytes + nsc_bytes +
-                                   blk_bytes + sgn_bytes, &ws);
+                                   blk_bytes + sgn_bytes + v_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
     char *base = (char *)ws->base;
     F64Args a = plan_args(p, A, m, n, lda);
@@ -443,6 +452,11 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     double *blocks = (double *)(base + o);
     o += blk_bytes;
     a.q.signs = (double *)(base + o);
+    o += sgn_bytes;
+    if (grouped) {
+        a.q.V = (double *)(base + o);
+        a.q.ldv = m;
+    }
     if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
         cudaSuccess)
         return TSQR_ERR_CUDA;
@@ -462,6 +476,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
         t.node_sc = a.q.node_sc;
         t.signs = a.q.signs;
         t.B = blocks;
+        t.qg = qg;
         if (q_tree_launch(t, sh.count[L], tree_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
         ++launches;
     }
@@ -480,8 +495,15 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     l.B = blocks;
     l.signs = a.q.signs;
     l.single = (sh.levels == 1) ? 1 : 0;
-    if (q_leaf_launch(l, qblk, qwarps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
-    g_last_launches = launches + 1;
+    l.V = a.q.V;
+    l.ldv = a.q.ldv;
+    for (int q0 = 0; q0 < n; q0 += qn) {
+        l.q0 = q0;
+        l.qn = (int)std::min<int64_t>(qn, n - q0);
+        if (q_leaf_launch(l, qblk, qwarps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+        ++launches;
+    }
+    g_last_launches = launches;
     return TSQR_SUCCESS;
 }
 
@@ -687,8 +709,7 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
         }
     const size_t qt_smem = qt_smem_bytes((int)n, kg, p.ldS, qwarps);
     if (qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
-    if (qr_prepare(p.smem, q_leaf_smem_bytes((int)n, p.ldS, p.warps),
-                   q_tree_smem_bytes((int)n, p.arity)) != cudaSuccess ||
+    if (qr_prepare(p.smem, 0, 0) != cudaSuccess ||
         qt_prepare(qt_smem) != cudaSuccess)
         return TSQR_ERR_CUDA;
     const int64_t nchunks = (m + p.h - 1) / p.h;
@@ -775,6 +796,8 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
         t.slots = qslots;
         t.counters = qcounters;
         t.C = C;
+        t.ldc = n;
+        t.ktot = kc;
         if (cudaMemsetAsync(qcounters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
                 cudaSuccess ||
             qt_launch(t, qblk, qwarps, qt_smem, stream) != cudaSuccess ||
@@ -782,6 +805,170 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
                 cudaSuccess)
             return TSQR_ERR_CUDA;
         launches += 2;
+    }
+    g_last_launches = launches;
+    return TSQR_SUCCESS;
+}
+
+// Communication-avoiding QR of a general m x N matrix (Section 5): panels of nb columns, each
+// factorized by the TSQR factorization with its reflectors kept, then Q^T applied to the
+// columns right of it.  The rows that update leaves behind form the next panel's matrix: every
+// row of the old one (its chunks' rows of Q^T B, in place) and the n-row blocks its tree nodes
+// left behind (appended below), so a panel on L leaves adds (L - 1) nb rows.
+constexpr int64_t kCaqrPanel = 32;  // the default panel width
+
+struct CaqrPanel {
+    F64Plan p;
+    int64_t j0, M;  // first column, rows of the panel's matrix
+    int w, kc;      // panel width, trailing columns per update CTA (kc <= w)
+    int qwarps, qblk;
+    size_t qt_smem;
+};
+
+tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, double *R,
+                       int64_t ldr, int64_t nb, const tsqr_plan_t *over, cudaStream_t stream) {
+    g_last_launches = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    std::vector<CaqrPanel> panels;
+    int64_t M = m;
+    size_t max_fsmem = 0, max_qt = 0;
+    size_t cnt_max = 0, slot_max = 0, v_max = 0, csc_max = 0, nv_max = 0, nsc_max = 0;
+    size_t qcnt_max = 0, qslot_max = 0;
+    for (int64_t j0 = 0; j0 < N; j0 += nb) {
+        CaqrPanel c;
+        c.j0 = j0;
+        c.M = M;
+        c.w = (int)std::min<int64_t>(nb, N - j0);
+        tsqr_status_t st = plan_f64(M, c.w, over, &c.p);
+        if (st != TSQR_SUCCESS) return st;
+        if (c.p.unit % c.p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
+        c.qwarps = c.p.warps;
+        for (int w : {12, 8})
+            if (w > c.qwarps && c.p.hs % (32 * w) == 0) {
+                c.qwarps = w;
+                break;
+            }
+        c.qblk = 1;
+        for (int b = 4; b >= 1; --b)
+            if ((c.p.hs / (32 * c.qwarps)) % b == 0) {
+                c.qblk = b;
+                break;
+            }
+        // the update's columns are independent: as many per CTA as fit beside the chunk
+        c.kc = c.w;
+        while (c.kc > 8 && qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps) > di.smem_block_optin)
+            c.kc = (c.kc + 1) / 2;
+        c.qt_smem = qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps);
+        if (c.qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
+        const size_t ww = (size_t)c.w * c.w, nodes = (size_t)c.p.nodes;
+        const int64_t trail = N - j0 - c.w;
+        const size_t groups = trail > 0 ? (size_t)((trail + c.kc - 1) / c.kc) : 0;
+        if (groups > 65535) return TSQR_ERR_UNSUPPORTED;  // one grid row per column group
+        max_fsmem = std::max(max_fsmem, c.p.smem);
+        max_qt = std::max(max_qt, c.qt_smem);
+        cnt_max = std::max(cnt_max, nodes * sizeof(unsigned int));
+        slot_max = std::max(slot_max, nodes * ww * sizeof(double));
+        v_max = std::max(v_max, (size_t)M * c.w * sizeof(double));
+        csc_max = std::max(csc_max, (size_t)((M + c.p.h - 1) / c.p.h) * 2 * c.w * sizeof(double));
+        nv_max = std::max(nv_max, nodes * (c.p.arity - 1) * ww * sizeof(double));
+        nsc_max = std::max(nsc_max, nodes * 2 * c.w * sizeof(double));
+        qcnt_max = std::max(qcnt_max, groups * nodes * sizeof(unsigned int));
+        qslot_max = std::max(qslot_max, groups * nodes * c.w * c.kc * sizeof(double));
+        panels.push_back(c);
+        M += (int64_t)(c.p.nleaves - 1) * c.w;
+    }
+    const int64_t w0 = panels[0].w;
+    const int64_t ldC = (M + 3) / 4 * 4;  // the last panel's rows, rounded to 32 bytes
+    const size_t c_bytes = (size_t)ldC * (size_t)(N - w0) * sizeof(double);
+    if (qr_prepare(max_fsmem, 0, 0) != cudaSuccess ||
+        qt_prepare(max_qt) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    const size_t sizes[] = {cnt_max, slot_max,  v_max,    csc_max, nv_max, nsc_max,
+                            (size_t)nb * sizeof(double), qcnt_max, qslot_max, c_bytes};
+    size_t total = 0;
+    for (size_t b : sizes) total += align_up(b, 256);
+    Workspace *ws = nullptr;
+    tsqr_status_t st = get_workspace(stream, total, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *base = (char *)ws->base;
+    void *bufs[10];
+    size_t o = 0;
+    for (int i = 0; i < 10; ++i) {
+        bufs[i] = base + o;
+        o += align_up(sizes[i], 256);
+    }
+    unsigned int *counters = (unsigned int *)bufs[0];
+    double *slots = (double *)bufs[1], *V = (double *)bufs[2], *csc = (double *)bufs[3];
+    double *nV = (double *)bufs[4], *nsc = (double *)bufs[5], *signs = (double *)bufs[6];
+    unsigned int *qcounters = (unsigned int *)bufs[7];
+    double *qslots = (double *)bufs[8], *C = (double *)bufs[9];
+    // R's rows below each diagonal block stay zero; the kernels write the rest
+    if (cudaMemset2DAsync(R, (size_t)ldr * sizeof(double), 0, (size_t)N * sizeof(double),
+                          (size_t)N, stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    int launches = 0;
+    for (size_t pi = 0; pi < panels.size(); ++pi) {
+        const CaqrPanel &c = panels[pi];
+        // the panel's matrix: A itself for the first panel, then C (column j of the matrix is
+        // column j - w0 of C)
+        const double *src = pi == 0 ? A : C + (c.j0 - w0) * ldC;
+        const int64_t lds = pi == 0 ? lda : ldC;
+        F64Args a = plan_args(c.p, src, c.M, c.w, lds);
+        a.counters = counters;
+        a.slots = slots;
+        a.R = R + c.j0 + c.j0 * ldr;
+        a.ldr = ldr;
+        a.status = ws->status;
+        a.q.V = V;
+        a.q.ldv = c.M;
+        a.q.chunk_sc = csc;
+        a.q.node_V = nV;
+        a.q.node_sc = nsc;
+        a.q.signs = signs;
+        if (cudaMemsetAsync(counters, 0, (size_t)c.p.nodes * sizeof(unsigned int), stream) !=
+                cudaSuccess ||
+            qr_factor_launch(a, c.p.warps, c.p.smem, stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        ++launches;
+        const int64_t trail = N - c.j0 - c.w;
+        if (trail == 0) break;
+        QtArgs t;
+        std::memset(&t, 0, sizeof(t));
+        t.V = V;
+        t.ldv = c.M;
+        t.B = src + c.w * lds;
+        t.m = c.M;
+        t.ldb = lds;
+        t.n = c.w;
+        t.k = c.kc;
+        t.ktot = (int)trail;
+        t.unit = c.p.unit;
+        t.nunits = c.p.nunits;
+        t.nleaves = c.p.nleaves;
+        t.h = c.p.h;
+        t.hs = c.p.hs;
+        t.ldS = c.p.ldS;
+        t.arity = c.p.arity;
+        t.chunk_sc = csc;
+        t.node_V = nV;
+        t.node_sc = nsc;
+        t.signs = signs;
+        t.slots = qslots;
+        t.counters = qcounters;
+        t.nodes = c.p.nodes;
+        t.C = R + c.j0 + (c.j0 + c.w) * ldr;
+        t.ldc = ldr;
+        t.Cout = C + (c.j0 + c.w - w0) * ldC;
+        t.ldco = ldC;
+        t.grow0 = c.M;
+        const size_t groups = (size_t)((trail + c.kc - 1) / c.kc);
+        if (cudaMemsetAsync(qcounters, 0, groups * (size_t)c.p.nodes * sizeof(unsigned int),
+                            stream) != cudaSuccess ||
+            qt_launch(t, c.qblk, c.qwarps, c.qt_smem, stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        ++launches;
     }
     g_last_launches = launches;
     return TSQR_SUCCESS;
@@ -1062,6 +1249,17 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
     if (!A || (k > 0 && (!B || !X))) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     return run_lstsq(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, plan, (cudaStream_t)stream);
+}
+
+tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                          int64_t ldr, int64_t panel, const tsqr_plan_t *plan,
+                          tsqr_stream_t stream) {
+    g_last_launches = 0;
+    if (bad_dims(m, n, lda, ldr) || n < 1 || m < n || panel < 0 || !A || !R)
+        return TSQR_ERR_INVALID_ARG;
+    if (panel > TSQR_MAX_N || n > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
+    const int64_t nb = panel > 0 ? panel : std::min<int64_t>(n, kCaqrPanel);
+    return run_caqr(A, m, n, lda, R, ldr, nb, plan, (cudaStream_t)stream);
 }
 
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,

@@ -51,8 +51,8 @@ cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, s
 // Thin QR (tsqr_qr.cu)
 struct QTreeArgs;
 struct QLeafArgs;
-size_t q_leaf_smem_bytes(int n, int ldS, int warps);
-size_t q_tree_smem_bytes(int n, int arity);
+size_t q_leaf_smem_bytes(int n, int qn, int ldS, int warps);
+size_t q_tree_smem_bytes(int n, int arity, int qg);
 cudaError_t qr_prepare(size_t factor_smem, size_t leaf_smem, size_t tree_smem);
 cudaError_t qr_factor_launch(const F64Args &a, int warps, size_t smem_bytes, cudaStream_t stream);
 cudaError_t q_tree_launch(const QTreeArgs &a, int grid, size_t smem_bytes, cudaStream_t stream);

@@ -49,57 +49,68 @@ __global__ void __launch_bounds__(256) tsqr_q_tree_kernel(const QTreeArgs a) {
     const int first = t * k;
     const int nchild = min(k, a.child_cnt - first);
     const size_t id = (size_t)a.level_off + t;
-    double *top = smem;          // n x n, leading dimension n
-    double *T = smem + n * n;    // (nchild-1) n x n, leading dimension (nchild-1) n
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int col = idx / n, row = idx - col * n;
-        top[idx] = a.is_root ? ((row == col) ? a.signs[row] : 0.0) : a.B[id * n * n + idx];
-    }
+    const double *Bin = a.B + id * n * n;
     if (nchild == 1) {  // a promoted lone child: its block is the node's
-        __syncthreads();
         double *dst = a.B + ((size_t)a.child_off + first) * n * n;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) dst[idx] = top[idx];
-        return;
-    }
-    const int c = nchild - 1, ldT = c * n, ldX = (k - 1) * n;
-    for (int idx = threadIdx.x; idx < ldT * n; idx += blockDim.x) T[idx] = 0.0;
-    __syncthreads();
-    const double *X = a.node_V + id * (size_t)ldX * n;
-    const double *sc = a.node_sc + id * 2 * n;
-    int tpc = 1;  // lanes per column: a power of two <= 32 with tpc n <= blockDim
-    while (tpc < 32 && 2 * tpc * n <= (int)blockDim.x) tpc *= 2;
-    const int q0 = threadIdx.x / tpc, sub = threadIdx.x - q0 * tpc;
-    const bool active = q0 < n;
-    const int q = active ? q0 : n - 1;  // idle lanes shadow the last column, writing nothing
-    for (int J = n - 1; J >= 0; --J) {
-        const double tau = sc[2 * J], cj = sc[2 * J + 1];
-        if (tau == 0.0) continue;
-        const int h1 = J + 1, E = c * h1;
-        double d = 0.0;
-        for (int e = sub; e < E; e += tpc) {
-            const int tt = e / h1, i = e - tt * h1;
-            d = fma(X[tt * n + i + (size_t)J * ldX], T[tt * n + i + q * ldT], d);
-        }
-        for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
-        const double w = fma(cj, d, top[J + q * n]);
-        __syncwarp();
-        if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
-        const double gq = tau * cj * w;
-        if (active) {
-            for (int e = sub; e < E; e += tpc) {
-                const int tt = e / h1, i = e - tt * h1;
-                T[tt * n + i + q * ldT] = fma(-gq, X[tt * n + i + (size_t)J * ldX],
-                                              T[tt * n + i + q * ldT]);
-            }
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int ch = 0; ch < nchild; ++ch) {
-        double *dst = a.B + ((size_t)a.child_off + first + ch) * n * n;
         for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
             const int col = idx / n, row = idx - col * n;
-            dst[idx] = (ch == 0) ? top[idx] : T[(ch - 1) * n + row + col * ldT];
+            dst[idx] = a.is_root ? ((row == col) ? a.signs[row] : 0.0) : Bin[idx];
+        }
+        return;
+    }
+    const int c = nchild - 1, ldX = (k - 1) * n;
+    const double *X = a.node_V + id * (size_t)ldX * n;
+    const double *sc = a.node_sc + id * 2 * n;
+    const int qg = a.qg;
+    const int ldT = c * n;
+    double *top = smem;           // n x qg, leading dimension n
+    double *T = smem + n * qg;    // (nchild-1) n x qg, leading dimension (nchild-1) n
+    int tpc = 1;  // lanes per column: a power of two <= 32 with tpc qg <= blockDim
+    while (tpc < 32 && 2 * tpc * qg <= (int)blockDim.x) tpc *= 2;
+    const int q0t = threadIdx.x / tpc, sub = threadIdx.x - q0t * tpc;
+    for (int g0 = 0; g0 < n; g0 += qg) {
+        const int gn = min(qg, n - g0);
+        __syncthreads();  // the previous group's blocks are written out
+        for (int idx = threadIdx.x; idx < n * gn; idx += blockDim.x) {
+            const int col = idx / n, row = idx - col * n;
+            top[idx] = a.is_root ? ((row == g0 + col) ? a.signs[row] : 0.0)
+                                 : Bin[row + (size_t)(g0 + col) * n];
+        }
+        for (int idx = threadIdx.x; idx < ldT * gn; idx += blockDim.x) T[idx] = 0.0;
+        __syncthreads();
+        const bool active = q0t < gn;
+        const int q = active ? q0t : gn - 1;  // idle lanes shadow the last column, writing nothing
+        for (int J = n - 1; J >= 0; --J) {
+            const double tau = sc[2 * J], cj = sc[2 * J + 1];
+            if (tau == 0.0) continue;
+            const int h1 = J + 1, E = c * h1;
+            double d = 0.0;
+            for (int e = sub; e < E; e += tpc) {
+                const int tt = e / h1, i = e - tt * h1;
+                d = fma(X[tt * n + i + (size_t)J * ldX], T[tt * n + i + q * ldT], d);
+            }
+            for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
+            const double w = fma(cj, d, top[J + q * n]);
+            __syncwarp();
+            if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
+            const double gq = tau * cj * w;
+            if (active) {
+                for (int e = sub; e < E; e += tpc) {
+                    const int tt = e / h1, i = e - tt * h1;
+                    T[tt * n + i + q * ldT] = fma(-gq, X[tt * n + i + (size_t)J * ldX],
+                                                  T[tt * n + i + q * ldT]);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int ch = 0; ch < nchild; ++ch) {
+            double *dst = a.B + ((size_t)a.child_off + first + ch) * n * n;
+            for (int idx = threadIdx.x; idx < n * gn; idx += blockDim.x) {
+                const int col = idx / n, row = idx - col * n;
+                dst[row + (size_t)(g0 + col) * n] =
+                    (ch == 0) ? top[idx] : T[(ch - 1) * n + row + col * ldT];
+            }
         }
     }
 }
@@ -224,24 +235,25 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
     const int Wb = (blockDim.x >> 5) - 1;
     const bool reducer = (warp == Wb);
     const int Hw = a.hs / Wb, r = Hw >> 5, r0 = warp * Hw;
-    const QLeafLayout L = q_leaf_layout(n, a.ldS, Wb + 1);
+    const int qn = a.qn, q0 = a.q0;
+    const QLeafLayout L = q_leaf_layout(n, qn, a.ldS, Wb + 1);
     double *X = smem + L.X;
     double *Z = smem + L.Z;
     double *top = smem + L.top;
     double *g = smem + L.g;
     double *sc = smem + L.sc;
-    const int ss = seg_stride(n);
+    const int ss = seg_stride(qn);
     double *seg_all = smem + L.seg;
     double *seg = seg_all + warp * ss;
     double *tot = smem + L.tot;
-    const int nslot = 32 + n;
+    const int nslot = 32 + qn;
     constexpr int kGroups = 4;
     const int leaf = blockIdx.x;
 
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < n * qn; idx += blockDim.x) {
         const int col = idx / n, row = idx - col * n;
-        top[idx] = a.single ? ((row == col) ? a.signs[row] : 0.0)
-                            : a.B[(size_t)leaf * n * n + idx];
+        top[idx] = a.single ? ((row == q0 + col) ? a.signs[row] : 0.0)
+                            : a.B[(size_t)leaf * n * n + row + (size_t)(q0 + col) * n];
     }
     const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
     const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
@@ -254,7 +266,10 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
         __syncthreads();  // the previous chunk's X and Z are no longer read
         for (int idx = threadIdx.x; idx < a.hs * n; idx += blockDim.x) {
             const int col = idx / a.hs, i = idx - col * a.hs;
-            X[i + (size_t)col * a.ldS] = (i < rows) ? a.Q[row0 + i + (int64_t)col * a.ldq] : 0.0;
+            X[i + (size_t)col * a.ldS] = (i < rows) ? a.V[row0 + i + (int64_t)col * a.ldv] : 0.0;
+        }
+        for (int idx = threadIdx.x; idx < a.hs * qn; idx += blockDim.x) {
+            const int col = idx / a.hs, i = idx - col * a.hs;
             Z[i + (size_t)col * a.ldS] = 0.0;
         }
         const double *csc = a.chunk_sc + (row0 / a.h) * 2 * n;
@@ -262,9 +277,9 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
         __syncthreads();
         for (int J = n - 1; J >= 0; --J) {
             if (!reducer) {
-                for (int id = lane; id < 32 + n; id += 32) seg[id] = 0.0;
+                for (int id = lane; id < nslot; id += 32) seg[id] = 0.0;
                 __syncwarp();
-                q_sweep<B>(lane, n, r, Hw, Z, a.ldS, r0,
+                q_sweep<B>(lane, qn, r, Hw, Z, a.ldS, r0,
                            (J + 1 < n) ? X + (size_t)(J + 1) * a.ldS + r0 : nullptr,
                            X + (size_t)J * a.ldS + r0, g, seg);
             }
@@ -288,8 +303,8 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
             __syncthreads();
             if (reducer) {
                 const double tau = sc[2 * J], cj = sc[2 * J + 1];
-                const int Nw = n * Hw;
-                for (int q = lane; q < n; q += 32) {
+                const int Nw = qn * Hw;
+                for (int q = lane; q < qn; q += 32) {
                     // column q's partials: slots q + la .. q + lb (as in the leaf fold)
                     const int la = (32 * (q * Hw + 1) - 1) / Nw;
                     const int lb = (32 * (q + 1) * Hw - 1) / Nw;
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
             __syncthreads();
         }
         if (!reducer) {  // reflector 0's update
-            for (int q = 0; q < n; ++q) {
+            for (int q = 0; q < qn; ++q) {
                 const double gq = g[q];
                 for (int t = 0; t < r; ++t) {
                     const int i = r0 + lane + 32 * t;
@@ -316,28 +331,37 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
             }
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < rows * qn; idx += blockDim.x) {
             const int col = idx / rows, i = idx - col * rows;
-            a.Q[row0 + i + (int64_t)col * a.ldq] = Z[i + (size_t)col * a.ldS];
+            a.Q[row0 + i + (int64_t)(q0 + col) * a.ldq] = Z[i + (size_t)col * a.ldS];
         }
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// Q^T B (tsqr_lstsq).  One CTA per leaf, as the leaf pass: per chunk, first to last, X = the
+// Q^T B (tsqr_lstsq, tsqr_caqr_r).  One CTA per leaf and column group, as the leaf pass: per
+// chunk, first to last, X = the
 // chunk's tails, Z = the chunk's rows of B and T the leaf's block (zero at the start, the rows
 // of the zero triangle the first chunk was folded under); for J = 0 .. n-1 the bulk sweep
 // applies reflector J-1's update Z(:,q) -= g_q x_{J-1} and forms x_J . Z(:,q) for every column
 // q of Z; the reducer forms w_q = T(J,q) + c_J d_q, T(J,q) -= tau_J w_q, g_q = tau_J c_J w_q.
-// Z is dropped after the chunk: only T (the rows of Q^T B that belong to R) goes on.  The leaf
-// then climbs the factorization's tree with its T, and the last child to arrive at a node
-// applies the node's reflectors, first to last, to [T_0; T_1; ...] (row J of T_0 and rows 0..J
-// of every other block).  The root writes D T (D: the row signs) to C.
+// Only T (the rows of Q^T B that belong to R) goes on; Z, after reflector n-1's update, is the
+// chunk's rows of Q^T B, written to Cout where the whole product is wanted (a panel's trailing
+// update) and otherwise dropped.  The leaf then climbs the factorization's tree with its T, and
+// the last child to arrive at a node applies the node's reflectors, first to last, to
+// [T_0; T_1; ...] (row J of T_0 and rows 0..J of every other block); T_1, T_2, ... then stay
+// behind (to Cout) and T_0 goes up.  The root writes D T (D: the row signs) to C.
 // ------------------------------------------------------------------------------------------
 template <int B>
 __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
     extern __shared__ __align__(16) double smem[];
-    const int n = a.n, kc = a.k, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y, kc = min(a.k, a.ktot - grp * a.k);
+    const double *Bg = a.B + (int64_t)grp * a.k * a.ldb;
+    double *Cg = a.C + (int64_t)grp * a.k * a.ldc;
+    double *Og = a.Cout ? a.Cout + (int64_t)grp * a.k * a.ldco : nullptr;
+    unsigned int *counters = a.counters + grp * a.nodes;
+    double *slots = a.slots + grp * a.nodes * n * a.k;
     const int Wb = (blockDim.x >> 5) - 1;
     const bool reducer = (warp == Wb);
     const int Hw = a.hs / Wb, r = Hw >> 5, r0 = warp * Hw;
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
         }
         for (int idx = threadIdx.x; idx < a.hs * kc; idx += blockDim.x) {
             const int col = idx / a.hs, i = idx - col * a.hs;
-            Z[i + (size_t)col * a.ldS] = (i < rows) ? a.B[row0 + i + (int64_t)col * a.ldb] : 0.0;
+            Z[i + (size_t)col * a.ldS] = (i < rows) ? Bg[row0 + i + (int64_t)col * a.ldb] : 0.0;
         }
         const double *csc = a.chunk_sc + (row0 / a.h) * 2 * n;
         for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) sc[j] = csc[j];
@@ -419,31 +443,52 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
             }
             __syncthreads();
         }
+        if (Og) {
+            if (!reducer) {  // reflector n-1's update: Z is then the chunk's rows of Q^T B
+                const double *xl = X + (size_t)(n - 1) * a.ldS;
+                for (int q = 0; q < kc; ++q) {
+                    const double gq = g[q];
+                    for (int t = 0; t < r; ++t) {
+                        const int i = r0 + lane + 32 * t;
+                        Z[i + (size_t)q * a.ldS] = fma(-gq, xl[i], Z[i + (size_t)q * a.ldS]);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < rows * kc; idx += blockDim.x) {
+                const int col = idx / rows, i = idx - col * rows;
+                Og[row0 + i + (int64_t)col * a.ldco] = Z[i + (size_t)col * a.ldS];
+            }
+        }
     }
 
     // the tree: the same shape, node ids and stored reflectors as the factorization's
     const int k = a.arity;
     int cnt = a.nleaves, off = 0, t = leaf;
+    int64_t left = 0;  // n-row blocks left behind by the levels below (cnt - next_cnt each)
     for (;;) {
         if (cnt == 1) {
-            for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
-                a.C[idx] = a.signs[idx % n] * top[idx];
+            for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) {
+                const int col = idx / n, i = idx - col * n;
+                Cg[i + (int64_t)col * a.ldc] = a.signs[i] * top[idx];
+            }
             return;
         }
         const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
         const int parent = t / k, first = parent * k;
         const int nchild = min(k, cnt - first);
         if (nchild == 1) {
+            left += cnt - next_cnt;
             off = next_off;
             cnt = next_cnt;
             t = parent;
             continue;
         }
-        double *mine = a.slots + (size_t)(off + t) * n * kc;
+        double *mine = slots + (size_t)(off + t) * n * kc;
         for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) mine[idx] = top[idx];
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) flag[0] = atomicAdd(&a.counters[next_off + parent], 1u);
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&counters[next_off + parent], 1u);
         __syncthreads();
         if (flag[0] + 1 < (unsigned)nchild) return;
         __threadfence();
@@ -451,12 +496,12 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
         const int cs = nchild - 1, ldY = cs * n;
         double *Y = X;
         for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
-            top[idx] = __ldcg(a.slots + (size_t)(off + first) * n * kc + idx);
+            top[idx] = __ldcg(slots + (size_t)(off + first) * n * kc + idx);
         for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
             const int col = idx / (cs * n), rr = idx - col * (cs * n);
             const int tt = rr / n, i = rr - tt * n;
             Y[rr + (size_t)col * ldY] =
-                __ldcg(a.slots + (size_t)(off + first + 1 + tt) * n * kc + i + (size_t)col * n);
+                __ldcg(slots + (size_t)(off + first + 1 + tt) * n * kc + i + (size_t)col * n);
         }
         __syncthreads();
         const size_t id = (size_t)next_off + parent;
@@ -492,6 +537,14 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
             __syncwarp();
         }
         __syncthreads();
+        if (Og) {  // the blocks of children 1 .. cs stay behind: the node's n-row blocks
+            const int64_t rb = a.grow0 + (left + (int64_t)parent * (k - 1)) * n;
+            for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
+                const int col = idx / (cs * n), rr = idx - col * (cs * n);
+                Og[rb + rr + (int64_t)col * a.ldco] = Y[rr + (size_t)col * ldY];
+            }
+        }
+        left += cnt - next_cnt;
         off = next_off;
         cnt = next_cnt;
         t = parent;
@@ -536,11 +589,13 @@ const void *q_leaf_fn(int blk) {
 // ------------------------------------------------------------------------------------------
 // host-side launchers
 // ------------------------------------------------------------------------------------------
-size_t q_leaf_smem_bytes(int n, int ldS, int warps) {
-    return sizeof(double) * (size_t)q_leaf_layout(n, ldS, warps + 1).total;
+size_t q_leaf_smem_bytes(int n, int qn, int ldS, int warps) {
+    return sizeof(double) * (size_t)q_leaf_layout(n, qn, ldS, warps + 1).total;
 }
 
-size_t q_tree_smem_bytes(int n, int arity) { return sizeof(double) * (size_t)arity * n * n; }
+size_t q_tree_smem_bytes(int n, int arity, int qg) {
+    return sizeof(double) * (size_t)arity * n * qg;
+}
 
 size_t qt_smem_bytes(int n, int k, int ldS, int warps) {
     return sizeof(double) * (size_t)qt_layout(n, k, ldS, warps + 1).total;
@@ -556,7 +611,7 @@ cudaError_t qt_prepare(size_t smem_bytes) {
 
 cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes,
                       cudaStream_t stream) {
-    const dim3 grid(a.nleaves), block((warps + 1) * 32);
+    const dim3 grid(a.nleaves, (a.ktot + a.k - 1) / a.k), block((warps + 1) * 32);
     switch (blk) {
         case 4: tsqr_qt_kernel<4><<<grid, block, smem_bytes, stream>>>(a); break;
         case 3: tsqr_qt_kernel<3><<<grid, block, smem_bytes, stream>>>(a); break;
@@ -574,14 +629,15 @@ cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t l
     return cudaGetLastError();
 }
 
+// leaf_smem / tree_smem = 0: the caller launches no Q pass (the attribute is left alone).
 cudaError_t qr_prepare(size_t factor_smem, size_t leaf_smem, size_t tree_smem) {
     for (int b = 1; b <= 4; ++b) {
         cudaError_t e = set_smem_attrs(qr_factor_fn(b), factor_smem);
         if (e != cudaSuccess) return e;
-        e = set_smem_attrs(q_leaf_fn(b), leaf_smem);
+        if (leaf_smem > 0) e = set_smem_attrs(q_leaf_fn(b), leaf_smem);
         if (e != cudaSuccess) return e;
     }
-    return set_smem_attrs(tsqr_q_tree_kernel, tree_smem);
+    return tree_smem > 0 ? set_smem_attrs(tsqr_q_tree_kernel, tree_smem) : cudaSuccess;
 }
 
 cudaError_t qr_factor_launch(const F64Args &a, int warps, size_t smem_bytes,

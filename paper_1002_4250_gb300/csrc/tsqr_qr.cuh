@@ -19,13 +19,18 @@ struct QTreeArgs {
     const double *node_sc;    // per node id: tau_J, c_J
     const double *signs;
     double *B;                // per node id: n x n block, leading dimension n (in and out)
+    int qg;                   // columns per group: the blocks' columns are independent, and
+                              // the kernel takes them qg at a time to bound shared memory
 };
 
 // The leaf pass: the leaf partition of the factorization (m, unit, nunits, nleaves, h) and
 // its chunk buffer shape (hs rows, leading dimension ldS).
 struct QLeafArgs {
-    double *Q;                // in: the chunks' tails (QStore::V); out: Q
+    double *Q;                // out: columns q0 .. q0+qn-1 of Q
     int64_t m, ldq;
+    const double *V;          // the chunks' tails (QStore::V, Q itself when qn = n)
+    int64_t ldv;
+    int q0, qn;               // the column group of this launch (columns are independent)
     int n;
     int64_t unit, nunits;
     int nleaves, h, hs, ldS;
@@ -35,22 +40,23 @@ struct QLeafArgs {
     int single;               // one leaf: its block is diag(signs)
 };
 
-// Offsets in doubles: the tails X and the Q rows Z (ldS x n each), the carried block (n x n),
-// the update factors g, the chunk's scalars, the partial-sum slots and their sums.
+// Offsets in doubles: the tails X (ldS x n), the Q rows Z of the column group (ldS x qn), the
+// carried block's columns (n x qn), the update factors g, the chunk's scalars, the
+// partial-sum slots and their sums.
 struct QLeafLayout {
     int X, Z, top, g, sc, seg, tot, total;
 };
 
-__host__ __device__ inline QLeafLayout q_leaf_layout(int n, int ldS, int warps_total) {
+__host__ __device__ inline QLeafLayout q_leaf_layout(int n, int qn, int ldS, int warps_total) {
     QLeafLayout L;
     int o = 0;
     L.X = o;    o += ldS * n;
-    L.Z = o;    o += ldS * n;
-    L.top = o;  o += n * n;
-    L.g = o;    o += n + 1;
+    L.Z = o;    o += ldS * qn;
+    L.top = o;  o += n * qn;
+    L.g = o;    o += qn + 1;
     L.sc = o;   o += 2 * n;
-    L.seg = o;  o += warps_total * seg_stride(n);
-    L.tot = o;  o += 2 * seg_stride(n);
+    L.seg = o;  o += warps_total * seg_stride(qn);
+    L.tot = o;  o += 2 * seg_stride(qn);
     L.total = o;
     return L;
 }
@@ -75,7 +81,18 @@ struct QtArgs {
     const double *signs;      // the root's row signs
     double *slots;            // per node id: n x k block, leading dimension n
     unsigned int *counters;   // per node id: arrivals (zeroed per call)
-    double *C;                // out: n x k, leading dimension n
+    double *C;                // out: n x k, leading dimension ldc
+    int64_t ldc;
+    // Column groups: blockIdx.y takes columns y k .. y k + k - 1 of the ktot columns of B (and
+    // of Cout and C); each group has its own counters and slots, nodes apart.
+    int ktot;
+    int64_t nodes;
+    // The whole of Q^T B (the trailing update of a panel factorization), when Cout is set: each
+    // chunk's rows of Q^T B go to the same rows of Cout (B itself is allowed), and the rows a
+    // tree node leaves behind (every child's block but the first) to rows grow0 .. of Cout, in
+    // a fixed order.  Together with the n rows in C they are Q^T B up to a row permutation.
+    double *Cout;
+    int64_t ldco, grow0;
 };
 
 // Offsets in doubles: the tails X (ldS x n), B's chunk Z (ldS x k), the block T (n x k), the

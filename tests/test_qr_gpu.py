@@ -50,6 +50,13 @@ def test_qr_gaussian(oracle, T, m, n):
     _check(oracle, T, workloads.gaussian(m, n, seed=m % 101))
 
 
+@pytest.mark.parametrize("m,n", [(100003, 128), (65537, 96), (30011, 80)])
+def test_qr_wide_column_groups(oracle, T, m, n):
+    """Widths whose chunk, Q rows and carried block do not fit shared memory together: the
+    passes take the columns in groups (and the tails live outside Q)."""
+    _check(oracle, T, workloads.gaussian(m, n, seed=n))
+
+
 @pytest.mark.parametrize("tree,b,ctas,arity", [("binary", 256, 0, 0), ("flat", 0, 0, 0),
                                                ("hybrid", 0, 37, 2), ("hybrid", 0, 61, 5),
                                                ("hybrid", 0, 100, 8)])
@@ -111,12 +118,11 @@ def test_qr_argument_errors(T):
     with pytest.raises(T.TsqrError) as e:
         T.tsqr_qr(torch.zeros(8, 4, dtype=torch.float64, device="cuda").T)  # m = 4 < n = 8
     assert e.value.status == T.ERR_INVALID_ARG
+    # a binary tile of 20,001 rows is taller than any chunk (a multiple of 32 W rows), so it is
+    # folded in chunks that do not divide it
     with pytest.raises(T.TsqrError) as e:
-        T.tsqr_qr(torch.zeros(128, 1000, dtype=torch.float64, device="cuda").T)
-    assert e.value.status == T.ERR_UNSUPPORTED
-    with pytest.raises(T.TsqrError) as e:  # a binary tile of 600 rows is folded in chunks of 384
-        T.tsqr_qr(workloads.gaussian(5000, 32, seed=1).cuda().T,
-                  plan=T.make_plan("binary", tile_rows=600))
+        T.tsqr_qr(workloads.gaussian(50000, 32, seed=1).cuda().T,
+                  plan=T.make_plan("binary", tile_rows=20001))
     assert e.value.status == T.ERR_UNSUPPORTED
 
 
