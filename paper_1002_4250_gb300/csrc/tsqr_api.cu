@@ -8,6 +8,7 @@
 #include <numeric>
 #include <utility>
 #include <vector>
+#include <cmath>
 
 #include "tsqr.h"
 #include "tsqr_internal.h"
@@ -843,6 +844,23 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         c.w = (int)std::min<int64_t>(nb, N - j0);
         tsqr_status_t st = plan_f64(M, c.w, over, &c.p);
         if (st != TSQR_SUCCESS) return st;
+        const int64_t trail = N - j0 - c.w;
+        if (plan_is_auto(over) && trail > 0) {
+            // Fewer leaves than the AUTO plan's: the panel's factorization runs on fewer CTAs
+            // (its time ~ 2 M w^2 (2 SMs) / (L P) at a GPU rate P), but every later panel's
+            // matrix has (L - 1) w rows more (their cost ~ w sum_{q > p} 4 w trail_q / P ~
+            // 2 w trail^2 / P per leaf).  The two balance at L = sqrt(2 SMs M w) / trail.
+            const double best = std::sqrt(2.0 * di.sms * (double)M * c.w) / (double)trail;
+            const int leaves = (int)std::max(1.0, std::ceil(best));
+            if (leaves < c.p.nleaves) {
+                tsqr_plan_t o;
+                std::memset(&o, 0, sizeof(o));
+                o.tree = TSQR_TREE_HYBRID;
+                o.ctas = leaves;
+                st = plan_f64(M, c.w, &o, &c.p);
+                if (st != TSQR_SUCCESS) return st;
+            }
+        }
         if (c.p.unit % c.p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
         c.qwarps = c.p.warps;
         for (int w : {12, 8})
@@ -863,7 +881,6 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         c.qt_smem = qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps);
         if (c.qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
         const size_t ww = (size_t)c.w * c.w, nodes = (size_t)c.p.nodes;
-        const int64_t trail = N - j0 - c.w;
         const size_t groups = trail > 0 ? (size_t)((trail + c.kc - 1) / c.kc) : 0;
         if (groups > 65535) return TSQR_ERR_UNSUPPORTED;  // one grid row per column group
         max_fsmem = std::max(max_fsmem, c.p.smem);
