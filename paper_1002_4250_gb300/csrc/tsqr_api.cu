@@ -19,6 +19,12 @@ namespace tsqr {
 size_t qt_smem_bytes(int n, int k, int ldS, int warps);
 cudaError_t qt_prepare(size_t smem_bytes);
 cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes, cudaStream_t stream);
+size_t wy_smem_bytes(int n, int ldX);
+cudaError_t wy_launch(const WyArgs &a, size_t smem_bytes, int grid, cudaStream_t stream);
+size_t qt_wy_smem_bytes(int n, int kc, int ldS);
+size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS);
+cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t stream);
+cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream);
 cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t ldc, double *X,
                         int64_t ldx, int n, int k, int *status, cudaStream_t stream);
 // Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
@@ -410,18 +416,32 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     // column groups: Q's columns (and the carried blocks') are independent, so the leaf pass
     // takes them qn at a time and the tree pass qg at a time where all n do not fit
     int qn = (int)n, qg = (int)n;
-    while (qn > 8 && q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps) > di.smem_block_optin)
-        qn = (qn + 1) / 2;
+    // the blocked leaf pass (compact WY factors per chunk) where a chunk's tails and two n x n
+    // blocks fit one CTA, else the sweep
+    const int ldX = p.h | 1;
+    const size_t wy_smem = wy_smem_bytes((int)n, ldX);
+    bool wyq = wy_smem <= di.smem_block_optin;
+    if (wyq) {
+        while (qn > 8 && q_leaf_wy_smem_bytes((int)n, qn, p.ldS) > di.smem_block_optin)
+            qn = (qn + 1) / 2;
+        wyq = q_leaf_wy_smem_bytes((int)n, qn, p.ldS) <= di.smem_block_optin;
+        if (!wyq) qn = (int)n;
+    }
+    if (!wyq)
+        while (qn > 8 && q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps) > di.smem_block_optin)
+            qn = (qn + 1) / 2;
     while (qg > 8 && q_tree_smem_bytes((int)n, p.arity, qg) > di.smem_block_optin)
         qg = (qg + 1) / 2;
-    const size_t leaf_smem = q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps);
+    const size_t leaf_smem = wyq ? q_leaf_wy_smem_bytes((int)n, qn, p.ldS)
+                                 : q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps);
     const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity, qg);
     if (leaf_smem > di.smem_block_optin || tree_smem > di.smem_block_optin)
         return TSQR_ERR_UNSUPPORTED;
     const bool grouped = qn < n;  // then the tails cannot live in Q: later groups still read them
-    if (qr_prepare(p.smem, leaf_smem, tree_smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (qr_prepare(p.smem, wyq ? 0 : leaf_smem, tree_smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t nchunks = (m + p.h - 1) / p.h;
     const size_t nn = (size_t)n * (size_t)n;
+    const size_t wys_bytes = wyq ? align_up((size_t)nchunks * nn * sizeof(double), 256) : 0;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
     const size_t csc_bytes = align_up((size_t)nchunks * 2 * n * sizeof(double), 256);
@@ -432,7 +452,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     const size_t v_bytes = grouped ? align_up((size_t)m * (size_t)n * sizeof(double), 256) : 0;
     Workspace *ws = nullptr;
     st = get_workspace(stream, cnt_bytes + slot_bytes + csc_bytes + nv_bytes + nsc_bytes +
-                                   blk_bytes + sgn_bytes + v_bytes, &ws);
+                                   blk_bytes + sgn_bytes + v_bytes + wys_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
     char *base = (char *)ws->base;
     F64Args a = plan_args(p, A, m, n, lda);
@@ -458,11 +478,28 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
         a.q.V = (double *)(base + o);
         a.q.ldv = m;
     }
+    o += v_bytes;
+    double *wyS = (double *)(base + o);
     if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
         cudaSuccess)
         return TSQR_ERR_CUDA;
     if (qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     int launches = 1;
+    if (wyq) {
+        WyArgs wa;
+        wa.V = a.q.V;
+        wa.ldv = a.q.ldv;
+        wa.m = m;
+        wa.n = (int)n;
+        wa.h = p.h;
+        wa.ldX = ldX;
+        wa.nchunks = nchunks;
+        wa.chunk_sc = a.q.chunk_sc;
+        wa.S = wyS;
+        const int grid = (int)std::min<int64_t>(nchunks, 4LL * di.sms);
+        if (wy_launch(wa, wy_smem, grid, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+        ++launches;
+    }
     // tree pass, from the root's level down to level 1 (whose children are the leaves)
     const TreeShape &sh = p.shape;
     for (int L = sh.levels - 1; L >= 1; --L) {
@@ -498,10 +535,13 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     l.single = (sh.levels == 1) ? 1 : 0;
     l.V = a.q.V;
     l.ldv = a.q.ldv;
+    l.wyS = wyS;
     for (int q0 = 0; q0 < n; q0 += qn) {
         l.q0 = q0;
         l.qn = (int)std::min<int64_t>(qn, n - q0);
-        if (q_leaf_launch(l, qblk, qwarps, leaf_smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+        if ((wyq ? q_leaf_wy_launch(l, leaf_smem, stream)
+                 : q_leaf_launch(l, qblk, qwarps, leaf_smem, stream)) != cudaSuccess)
+            return TSQR_ERR_CUDA;
         ++launches;
     }
     g_last_launches = launches;
@@ -678,6 +718,131 @@ tsqr_status_t run_lstsq_augmented(const double *A, int64_t m, int64_t n, int64_t
 // tsqr_qr.cu) and R X = those rows (one launch).  Workspace: counters | slots | tails |
 // chunk scalars | node tails | node scalars | signs | apply counters | apply slots | C | R.
 // With k <= max(1, n / 4) and n + k <= TSQR_MAX_N the augmented factorization above is used.
+// Compact WY factors fit when a chunk's scaled tails and two n x n blocks fit one CTA; the
+// blocked apply then takes as many update columns per CTA as fit beside the chunk.
+bool plan_wy(int w, const F64Plan &p, const DeviceInfo &di, int *ldX, size_t *wy_smem, int *kc,
+             size_t *qt_smem) {
+    *ldX = p.h | 1;
+    *wy_smem = wy_smem_bytes(w, *ldX);
+    if (*wy_smem > di.smem_block_optin) return false;
+    int k = w;
+    while (k > 8 && qt_wy_smem_bytes(w, k, p.ldS) > di.smem_block_optin) k = (k + 1) / 2;
+    *kc = k;
+    *qt_smem = qt_wy_smem_bytes(w, k, p.ldS);
+    return *qt_smem <= di.smem_block_optin;
+}
+
+// tsqr_lstsq's stored-reflector path with each chunk's reflectors applied as one compact WY
+// block: the factorization, the chunks' S factors, one apply launch over every column of B
+// (groups of kg on the grid; only T is kept, so the chunk's rows of Q^T B are never formed)
+// and one triangular solve.
+tsqr_status_t run_lstsq_wy(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
+                           int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
+                           const F64Plan &p, int ldX, size_t wy_smem, int kg, size_t qtw_smem,
+                           const DeviceInfo &di, cudaStream_t stream) {
+    if (qr_prepare(p.smem, 0, 0) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int64_t nchunks = (m + p.h - 1) / p.h;
+    const int64_t groups = k > 0 ? (k + kg - 1) / kg : 0;
+    if (groups > 65535) return TSQR_ERR_UNSUPPORTED;  // one grid row per column group
+    const size_t nn = (size_t)n * (size_t)n;
+    const size_t sizes[] = {
+        (size_t)p.nodes * sizeof(unsigned int),                    // factorization counters
+        (size_t)p.nodes * nn * sizeof(double),                     // factorization slots
+        (size_t)m * (size_t)n * sizeof(double),                    // chunk tails
+        (size_t)nchunks * 2 * n * sizeof(double),                  // chunk tau, c
+        (size_t)p.nodes * (p.arity - 1) * nn * sizeof(double),     // node tails
+        (size_t)p.nodes * 2 * n * sizeof(double),                  // node tau, c
+        (size_t)n * sizeof(double),                                // root signs
+        (size_t)groups * p.nodes * sizeof(unsigned int),           // apply counters
+        (size_t)groups * p.nodes * n * kg * sizeof(double),        // apply slots
+        (size_t)n * (size_t)k * sizeof(double),                    // (Q^T B)(0:n, :)
+        (size_t)nchunks * nn * sizeof(double),                     // S per chunk
+        R ? (size_t)0 : nn * sizeof(double)};                      // R when the caller has none
+    constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
+    size_t total = 0;
+    for (size_t b : sizes) total += align_up(b, 256);
+    Workspace *ws = nullptr;
+    tsqr_status_t st = get_workspace(stream, total, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    char *bufs[kBufs];
+    size_t o = 0;
+    for (int i = 0; i < kBufs; ++i) {
+        bufs[i] = (char *)ws->base + o;
+        o += align_up(sizes[i], 256);
+    }
+    if (!R) {
+        R = (double *)bufs[11];
+        ldr = n;
+    }
+    F64Args a = plan_args(p, A, m, n, lda);
+    a.counters = (unsigned int *)bufs[0];
+    a.slots = (double *)bufs[1];
+    a.R = R;
+    a.ldr = ldr;
+    a.status = ws->status;
+    a.q.V = (double *)bufs[2];
+    a.q.ldv = m;
+    a.q.chunk_sc = (double *)bufs[3];
+    a.q.node_V = (double *)bufs[4];
+    a.q.node_sc = (double *)bufs[5];
+    a.q.signs = (double *)bufs[6];
+    WyArgs wa;
+    wa.V = a.q.V;
+    wa.ldv = m;
+    wa.m = m;
+    wa.n = (int)n;
+    wa.h = p.h;
+    wa.ldX = ldX;
+    wa.nchunks = nchunks;
+    wa.chunk_sc = a.q.chunk_sc;
+    wa.S = (double *)bufs[10];
+    QtArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.V = a.q.V;
+    t.ldv = m;
+    t.B = B;
+    t.m = m;
+    t.ldb = ldb;
+    t.n = (int)n;
+    t.k = kg;
+    t.ktot = (int)k;
+    t.unit = p.unit;
+    t.nunits = p.nunits;
+    t.nleaves = p.nleaves;
+    t.h = p.h;
+    t.hs = p.hs;
+    t.ldS = p.ldS;
+    t.arity = p.arity;
+    t.chunk_sc = a.q.chunk_sc;
+    t.node_V = a.q.node_V;
+    t.node_sc = a.q.node_sc;
+    t.signs = a.q.signs;
+    t.counters = (unsigned int *)bufs[7];
+    t.slots = (double *)bufs[8];
+    t.nodes = p.nodes;
+    t.C = (double *)bufs[9];
+    t.ldc = n;
+    t.wyS = wa.S;
+    const int grid = (int)std::min<int64_t>(nchunks, 4LL * di.sms);
+    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+        cudaSuccess)
+        return TSQR_ERR_CUDA;
+    if (k == 0) {  // R alone
+        if (qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+        g_last_launches = 1;
+        return TSQR_SUCCESS;
+    }
+    if (cudaMemsetAsync(t.counters, 0, (size_t)groups * p.nodes * sizeof(unsigned int),
+                        stream) != cudaSuccess ||
+        qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess ||
+        wy_launch(wa, wy_smem, grid, stream) != cudaSuccess ||
+        qt_wy_launch(t, qtw_smem, stream) != cudaSuccess ||
+        trsm_launch(R, ldr, t.C, n, X, ldx, (int)n, (int)k, ws->status, stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    g_last_launches = 4;
+    return TSQR_SUCCESS;
+}
+
 tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
                         int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                         const tsqr_plan_t *over, cudaStream_t stream) {
@@ -708,6 +873,12 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
             qblk = c;
             break;
         }
+    int ldX = 0, kw = 0;
+    size_t wy_smem = 0, qtw_smem = 0;
+    const bool wy = plan_wy((int)n, p, di, &ldX, &wy_smem, &kw, &qtw_smem);
+    if (wy) return run_lstsq_wy(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, p, ldX, wy_smem,
+                                (int)std::max<int64_t>(1, std::min<int64_t>(k, kw)), qtw_smem,
+                                di, stream);
     const size_t qt_smem = qt_smem_bytes((int)n, kg, p.ldS, qwarps);
     if (qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
     if (qr_prepare(p.smem, 0, 0) != cudaSuccess ||
@@ -824,7 +995,11 @@ struct CaqrPanel {
     int w, kc;      // panel width, trailing columns per update CTA (kc <= w)
     int qwarps, qblk;
     size_t qt_smem;
+    bool wy;        // the update applies each chunk's reflectors as one compact WY block
+    size_t wy_smem;
+    int ldX;
 };
+
 
 tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, double *R,
                        int64_t ldr, int64_t nb, const tsqr_plan_t *over, cudaStream_t stream) {
@@ -836,7 +1011,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
     int64_t M = m;
     size_t max_fsmem = 0, max_qt = 0;
     size_t cnt_max = 0, slot_max = 0, v_max = 0, csc_max = 0, nv_max = 0, nsc_max = 0;
-    size_t qcnt_max = 0, qslot_max = 0;
+    size_t qcnt_max = 0, qslot_max = 0, wys_max = 0;
     for (int64_t j0 = 0; j0 < N; j0 += nb) {
         CaqrPanel c;
         c.j0 = j0;
@@ -874,11 +1049,15 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
                 c.qblk = b;
                 break;
             }
-        // the update's columns are independent: as many per CTA as fit beside the chunk
-        c.kc = c.w;
-        while (c.kc > 8 && qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps) > di.smem_block_optin)
-            c.kc = (c.kc + 1) / 2;
-        c.qt_smem = qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps);
+        c.wy = plan_wy(c.w, c.p, di, &c.ldX, &c.wy_smem, &c.kc, &c.qt_smem);
+        if (!c.wy) {
+            // the reflector-by-reflector update; its columns are independent too: as many per
+            // CTA as fit beside the chunk
+            c.kc = c.w;
+            while (c.kc > 8 && qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps) > di.smem_block_optin)
+                c.kc = (c.kc + 1) / 2;
+            c.qt_smem = qt_smem_bytes(c.w, c.kc, c.p.ldS, c.qwarps);
+        }
         if (c.qt_smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
         const size_t ww = (size_t)c.w * c.w, nodes = (size_t)c.p.nodes;
         const size_t groups = trail > 0 ? (size_t)((trail + c.kc - 1) / c.kc) : 0;
@@ -891,6 +1070,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         csc_max = std::max(csc_max, (size_t)((M + c.p.h - 1) / c.p.h) * 2 * c.w * sizeof(double));
         nv_max = std::max(nv_max, nodes * (c.p.arity - 1) * ww * sizeof(double));
         nsc_max = std::max(nsc_max, nodes * 2 * c.w * sizeof(double));
+        if (c.wy) wys_max = std::max(wys_max, (size_t)((M + c.p.h - 1) / c.p.h) * ww * sizeof(double));
         qcnt_max = std::max(qcnt_max, groups * nodes * sizeof(unsigned int));
         qslot_max = std::max(qslot_max, groups * nodes * c.w * c.kc * sizeof(double));
         panels.push_back(c);
@@ -899,20 +1079,20 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
     const int64_t w0 = panels[0].w;
     const int64_t ldC = (M + 3) / 4 * 4;  // the last panel's rows, rounded to 32 bytes
     const size_t c_bytes = (size_t)ldC * (size_t)(N - w0) * sizeof(double);
-    if (qr_prepare(max_fsmem, 0, 0) != cudaSuccess ||
-        qt_prepare(max_qt) != cudaSuccess)
+    if (qr_prepare(max_fsmem, 0, 0) != cudaSuccess || qt_prepare(max_qt) != cudaSuccess)
         return TSQR_ERR_CUDA;
-    const size_t sizes[] = {cnt_max, slot_max,  v_max,    csc_max, nv_max, nsc_max,
-                            (size_t)nb * sizeof(double), qcnt_max, qslot_max, c_bytes};
+    const size_t sizes[] = {cnt_max, slot_max,  v_max,    csc_max, nv_max,  nsc_max,
+                            (size_t)nb * sizeof(double), qcnt_max, qslot_max, c_bytes, wys_max};
+    constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
     size_t total = 0;
     for (size_t b : sizes) total += align_up(b, 256);
     Workspace *ws = nullptr;
     tsqr_status_t st = get_workspace(stream, total, &ws);
     if (st != TSQR_SUCCESS) return st;
     char *base = (char *)ws->base;
-    void *bufs[10];
+    void *bufs[kBufs];
     size_t o = 0;
-    for (int i = 0; i < 10; ++i) {
+    for (int i = 0; i < kBufs; ++i) {
         bufs[i] = base + o;
         o += align_up(sizes[i], 256);
     }
@@ -920,7 +1100,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
     double *slots = (double *)bufs[1], *V = (double *)bufs[2], *csc = (double *)bufs[3];
     double *nV = (double *)bufs[4], *nsc = (double *)bufs[5], *signs = (double *)bufs[6];
     unsigned int *qcounters = (unsigned int *)bufs[7];
-    double *qslots = (double *)bufs[8], *C = (double *)bufs[9];
+    double *qslots = (double *)bufs[8], *C = (double *)bufs[9], *wyS = (double *)bufs[10];
     // R's rows below each diagonal block stay zero; the kernels write the rest
     if (cudaMemset2DAsync(R, (size_t)ldr * sizeof(double), 0, (size_t)N * sizeof(double),
                           (size_t)N, stream) != cudaSuccess)
@@ -982,10 +1162,30 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         t.grow0 = c.M;
         const size_t groups = (size_t)((trail + c.kc - 1) / c.kc);
         if (cudaMemsetAsync(qcounters, 0, groups * (size_t)c.p.nodes * sizeof(unsigned int),
-                            stream) != cudaSuccess ||
-            qt_launch(t, c.qblk, c.qwarps, c.qt_smem, stream) != cudaSuccess)
+                            stream) != cudaSuccess)
             return TSQR_ERR_CUDA;
-        ++launches;
+        if (c.wy) {
+            WyArgs wa;
+            wa.V = V;
+            wa.ldv = c.M;
+            wa.m = c.M;
+            wa.n = c.w;
+            wa.h = c.p.h;
+            wa.ldX = c.ldX;
+            wa.nchunks = (c.M + c.p.h - 1) / c.p.h;
+            wa.chunk_sc = csc;
+            wa.S = wyS;
+            t.wyS = wyS;
+            const int grid = (int)std::min<int64_t>(wa.nchunks, 4LL * di.sms);
+            if (wy_launch(wa, c.wy_smem, grid, stream) != cudaSuccess ||
+                qt_wy_launch(t, c.qt_smem, stream) != cudaSuccess)
+                return TSQR_ERR_CUDA;
+            launches += 2;
+        } else {
+            if (qt_launch(t, c.qblk, c.qwarps, c.qt_smem, stream) != cudaSuccess)
+                return TSQR_ERR_CUDA;
+            ++launches;
+        }
     }
     g_last_launches = launches;
     return TSQR_SUCCESS;

@@ -338,6 +338,102 @@ __global__ void __launch_bounds__(416, 1) tsqr_q_leaf_kernel(const QLeafArgs a) 
     }
 }
 
+// The climb of the Q^T apply: the leaf's block T (top, n x kc) goes up the factorization's tree
+// (same shape, node ids and stored reflectors); the last child to arrive at a node applies the
+// node's reflectors to the children's stacked blocks (X's space holds all but the first), the
+// others stay behind (to Og), and the root writes D T to Cg.
+__device__ __forceinline__ void qt_climb(const QtArgs &a, const int leaf, const int kc, double *X,
+                                         double *top, unsigned int *flag, double *Cg, double *Og,
+                                         unsigned int *counters, double *slots) {
+    const int n = a.n;
+    const int k = a.arity;
+    int cnt = a.nleaves, off = 0, t = leaf;
+    int64_t left = 0;  // n-row blocks left behind by the levels below (cnt - next_cnt each)
+    for (;;) {
+        if (cnt == 1) {
+            for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) {
+                const int col = idx / n, i = idx - col * n;
+                Cg[i + (int64_t)col * a.ldc] = a.signs[i] * top[idx];
+            }
+            return;
+        }
+        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
+        const int parent = t / k, first = parent * k;
+        const int nchild = min(k, cnt - first);
+        if (nchild == 1) {
+            left += cnt - next_cnt;
+            off = next_off;
+            cnt = next_cnt;
+            t = parent;
+            continue;
+        }
+        double *mine = slots + (size_t)(off + t) * n * kc;
+        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) mine[idx] = top[idx];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) flag[0] = atomicAdd(&counters[next_off + parent], 1u);
+        __syncthreads();
+        if (flag[0] + 1 < (unsigned)nchild) return;
+        __threadfence();
+        // the children's blocks in index order: the first on top, the others stacked in X
+        const int cs = nchild - 1, ldY = cs * n;
+        double *Y = X;
+        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
+            top[idx] = __ldcg(slots + (size_t)(off + first) * n * kc + idx);
+        for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
+            const int col = idx / (cs * n), rr = idx - col * (cs * n);
+            const int tt = rr / n, i = rr - tt * n;
+            Y[rr + (size_t)col * ldY] =
+                __ldcg(slots + (size_t)(off + first + 1 + tt) * n * kc + i + (size_t)col * n);
+        }
+        __syncthreads();
+        const size_t id = (size_t)next_off + parent;
+        const int ldX = (k - 1) * n;
+        const double *Xn = a.node_V + id * (size_t)ldX * n;
+        const double *nsc = a.node_sc + id * 2 * n;
+        int tpc = 1;  // lanes per column: a power of two <= 32 with tpc kc <= blockDim
+        while (tpc < 32 && 2 * tpc * kc <= (int)blockDim.x) tpc *= 2;
+        const int q0 = threadIdx.x / tpc, sub = threadIdx.x - q0 * tpc;
+        const bool active = q0 < kc;
+        const int q = active ? q0 : kc - 1;
+        for (int J = 0; J < n; ++J) {
+            const double tau = nsc[2 * J], cj = nsc[2 * J + 1];
+            if (tau == 0.0) continue;
+            const int h1 = J + 1, E = cs * h1;
+            double d = 0.0;
+            for (int e = sub; e < E; e += tpc) {
+                const int tt = e / h1, i = e - tt * h1;
+                d = fma(Xn[tt * n + i + (size_t)J * ldX], Y[tt * n + i + (size_t)q * ldY], d);
+            }
+            for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
+            const double w = fma(cj, d, top[J + q * n]);
+            __syncwarp();
+            if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
+            const double gq = tau * cj * w;
+            if (active) {
+                for (int e = sub; e < E; e += tpc) {
+                    const int tt = e / h1, i = e - tt * h1;
+                    Y[tt * n + i + (size_t)q * ldY] = fma(-gq, Xn[tt * n + i + (size_t)J * ldX],
+                                                          Y[tt * n + i + (size_t)q * ldY]);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (Og) {  // the blocks of children 1 .. cs stay behind: the node's n-row blocks
+            const int64_t rb = a.grow0 + (left + (int64_t)parent * (k - 1)) * n;
+            for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
+                const int col = idx / (cs * n), rr = idx - col * (cs * n);
+                Og[rb + rr + (int64_t)col * a.ldco] = Y[rr + (size_t)col * ldY];
+            }
+        }
+        left += cnt - next_cnt;
+        off = next_off;
+        cnt = next_cnt;
+        t = parent;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Q^T B (tsqr_lstsq, tsqr_caqr_r).  One CTA per leaf and column group, as the leaf pass: per
 // chunk, first to last, X = the
@@ -462,92 +558,309 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
         }
     }
 
-    // the tree: the same shape, node ids and stored reflectors as the factorization's
-    const int k = a.arity;
-    int cnt = a.nleaves, off = 0, t = leaf;
-    int64_t left = 0;  // n-row blocks left behind by the levels below (cnt - next_cnt each)
-    for (;;) {
-        if (cnt == 1) {
-            for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) {
-                const int col = idx / n, i = idx - col * n;
-                Cg[i + (int64_t)col * a.ldc] = a.signs[i] * top[idx];
+    qt_climb(a, leaf, kc, X, top, flag, Cg, Og, counters, slots);
+}
+
+// ------------------------------------------------------------------------------------------
+// Compact WY factors.  One CTA per chunk (grid-strided): the scaled tails X diag(c) in shared
+// memory, G(i,J) = (c_i x_i) . (c_J x_J) for i < J over the chunk's rows, then S column by
+// column, S(0:J,J) = -tau_J S(0:J,0:J) G(0:J,J): row i of S needs only row i's earlier entries,
+// so a lane owns a row.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tsqr_wy_kernel(const WyArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n, ldX = a.ldX;
+    double *X = smem;               // ldX x n
+    double *G = smem + ldX * n;     // n x n (strict upper triangle used)
+    double *S = G + n * n;          // n x n
+    const int npairs = n * (n - 1) / 2;
+    for (int64_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
+        const int64_t row0 = c * a.h;
+        const int rows = (int)((a.m - row0 < a.h) ? a.m - row0 : a.h);
+        const double *sc = a.chunk_sc + c * 2 * n;
+        __syncthreads();  // the previous chunk's S is written out
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+            const int J = idx / rows, i = idx - J * rows;
+            X[i + J * ldX] = sc[2 * J + 1] * a.V[row0 + i + (int64_t)J * a.ldv];
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+            // pair p -> (i, J), i < J, column by column: J = the largest with J(J-1)/2 <= p
+            int J = (int)((1.0 + sqrt(1.0 + 8.0 * p)) * 0.5);
+            while (J * (J - 1) / 2 > p) --J;
+            while ((J + 1) * J / 2 <= p) ++J;
+            const int i = p - J * (J - 1) / 2;
+            const double *xi = X + i * ldX, *xj = X + J * ldX;
+            double d0 = 0.0, d1 = 0.0;
+            int r = 0;
+            for (; r + 1 < rows; r += 2) {
+                d0 = fma(xi[r], xj[r], d0);
+                d1 = fma(xi[r + 1], xj[r + 1], d1);
             }
-            return;
-        }
-        const int next_off = off + cnt, next_cnt = (cnt + k - 1) / k;
-        const int parent = t / k, first = parent * k;
-        const int nchild = min(k, cnt - first);
-        if (nchild == 1) {
-            left += cnt - next_cnt;
-            off = next_off;
-            cnt = next_cnt;
-            t = parent;
-            continue;
-        }
-        double *mine = slots + (size_t)(off + t) * n * kc;
-        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) mine[idx] = top[idx];
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) flag[0] = atomicAdd(&counters[next_off + parent], 1u);
-        __syncthreads();
-        if (flag[0] + 1 < (unsigned)nchild) return;
-        __threadfence();
-        // the children's blocks in index order: the first on top, the others stacked in X
-        const int cs = nchild - 1, ldY = cs * n;
-        double *Y = X;
-        for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x)
-            top[idx] = __ldcg(slots + (size_t)(off + first) * n * kc + idx);
-        for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
-            const int col = idx / (cs * n), rr = idx - col * (cs * n);
-            const int tt = rr / n, i = rr - tt * n;
-            Y[rr + (size_t)col * ldY] =
-                __ldcg(slots + (size_t)(off + first + 1 + tt) * n * kc + i + (size_t)col * n);
+            if (r < rows) d0 = fma(xi[r], xj[r], d0);
+            G[i + J * n] = d0 + d1;
         }
         __syncthreads();
-        const size_t id = (size_t)next_off + parent;
-        const int ldX = (k - 1) * n;
-        const double *Xn = a.node_V + id * (size_t)ldX * n;
-        const double *nsc = a.node_sc + id * 2 * n;
-        int tpc = 1;  // lanes per column: a power of two <= 32 with tpc kc <= blockDim
-        while (tpc < 32 && 2 * tpc * kc <= (int)blockDim.x) tpc *= 2;
-        const int q0 = threadIdx.x / tpc, sub = threadIdx.x - q0 * tpc;
-        const bool active = q0 < kc;
-        const int q = active ? q0 : kc - 1;
-        for (int J = 0; J < n; ++J) {
-            const double tau = nsc[2 * J], cj = nsc[2 * J + 1];
-            if (tau == 0.0) continue;
-            const int h1 = J + 1, E = cs * h1;
-            double d = 0.0;
-            for (int e = sub; e < E; e += tpc) {
-                const int tt = e / h1, i = e - tt * h1;
-                d = fma(Xn[tt * n + i + (size_t)J * ldX], Y[tt * n + i + (size_t)q * ldY], d);
+        // S column by column; column J's rows i < J each by a team of tpr lanes (the sum over
+        // k = i .. J-1 strided over the team, then a fixed butterfly)
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            for (int i = 0; i < n; ++i) S[i + idx * n] = (i == idx) ? sc[2 * idx] : 0.0;
+        }
+        for (int J = 1; J < n; ++J) {
+            __syncthreads();  // columns 0 .. J-1 are complete
+            int tpr = 1;
+            while (tpr < 32 && 2 * tpr * J <= (int)blockDim.x) tpr *= 2;
+            const int team = threadIdx.x / tpr, sub = threadIdx.x - team * tpr;
+            const int i = team < J ? team : J - 1;  // spare teams shadow the last row
+            double v = 0.0;
+            for (int k = i + sub; k < J; k += tpr) v = fma(S[i + k * n], G[k + J * n], v);
+            for (int o = tpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, tpr);
+            if (team < J && sub == 0) S[i + J * n] = -sc[2 * J] * v;
+        }
+        __syncthreads();
+        double *out = a.S + c * (int64_t)n * n;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = S[idx];
+    }
+}
+
+// W = T + X^T Z over the chunk's first `rows` rows (X ldS x n, Z ldS x kc; T, W n x kc).
+// Thread tiles of 2 x 2 outputs; where they are fewer than the threads, the rows are split in
+// slices whose partial sums are added in slice order.
+__device__ __forceinline__ void wy_xtz(const double *X, const double *Z, const int ldS,
+                                       const int rows, const int n, const int kc,
+                                       const double *T, double *W, double *part) {
+    const int NT = blockDim.x;
+    const int ti = (n + 1) >> 1, tq = (kc + 1) >> 1, tiles = ti * tq;
+    const int slices = tiles >= NT ? 1 : NT / tiles;
+    const int rs = (rows + slices - 1) / slices;
+    for (int u = threadIdx.x; u < tiles * slices; u += NT) {
+        const int tile = u % tiles, sl = u / tiles;
+        const int i0 = 2 * (tile % ti), q0 = 2 * (tile / ti);
+        const int i1 = min(i0 + 1, n - 1), q1 = min(q0 + 1, kc - 1);
+        const int ra = sl * rs, rb = min(rows, ra + rs);
+        const double *x0 = X + (size_t)i0 * ldS, *x1 = X + (size_t)i1 * ldS;
+        const double *z0 = Z + (size_t)q0 * ldS, *z1 = Z + (size_t)q1 * ldS;
+        double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+        for (int r = ra; r < rb; ++r) {
+            const double xa = x0[r], xb = x1[r], za = z0[r], zb = z1[r];
+            a00 = fma(xa, za, a00);
+            a01 = fma(xa, zb, a01);
+            a10 = fma(xb, za, a10);
+            a11 = fma(xb, zb, a11);
+        }
+        if (slices == 1) {
+            W[i0 + q0 * n] = T[i0 + q0 * n] + a00;
+            if (q0 + 1 < kc) W[i0 + (q0 + 1) * n] = T[i0 + (q0 + 1) * n] + a01;
+            if (i0 + 1 < n) W[i0 + 1 + q0 * n] = T[i0 + 1 + q0 * n] + a10;
+            if (i0 + 1 < n && q0 + 1 < kc) W[i0 + 1 + (q0 + 1) * n] = T[i0 + 1 + (q0 + 1) * n] + a11;
+        } else {
+            double *pp = part + 4 * (size_t)(sl * tiles + tile);
+            pp[0] = a00;
+            pp[1] = a01;
+            pp[2] = a10;
+            pp[3] = a11;
+        }
+    }
+    if (slices > 1) {
+        __syncthreads();
+        for (int o = threadIdx.x; o < n * kc; o += NT) {
+            const int i = o % n, q = o / n;
+            const int tile = (i >> 1) + (q >> 1) * ti, e = 2 * (i & 1) + (q & 1);
+            double v = T[o];
+            for (int sl = 0; sl < slices; ++sl) v += part[4 * (size_t)(sl * tiles + tile) + e];
+            W[o] = v;
+        }
+    }
+}
+
+// Y = S^T W (trans) or S W, S upper triangular (n x n); T -= Y.
+__device__ __forceinline__ void wy_sw(const double *S, const double *W, double *Y, double *T,
+                                      const int n, const int kc, const bool trans) {
+    for (int o = threadIdx.x; o < n * kc; o += blockDim.x) {
+        const int i = o % n, q = o / n;
+        const double *w = W + q * n;
+        double v = 0.0;
+        if (trans) {
+            for (int j = 0; j <= i; ++j) v = fma(S[j + i * n], w[j], v);
+        } else {
+            for (int j = i; j < n; ++j) v = fma(S[i + j * n], w[j], v);
+        }
+        Y[o] = v;
+        T[o] -= v;
+    }
+}
+
+// Z(r, q) -= sum_j X(r, j) Y(j, q) for r < rows: thread tiles of 4 rows (tr apart, so that a
+// warp's lanes read consecutive rows) by 2 columns.
+__device__ __forceinline__ void wy_zupdate(double *Z, const double *X, const int ldS,
+                                           const int rows, const int n, const int kc,
+                                           const double *Y) {
+    const int tr = (rows + 3) >> 2, tq = (kc + 1) >> 1;
+    for (int u = threadIdx.x; u < tr * tq; u += blockDim.x) {
+        const int rr = u % tr, q0 = 2 * (u / tr), q1 = min(q0 + 1, kc - 1);
+        int rw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rw[k] = min(rr + k * tr, rows - 1);
+        double z0[4], z1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            z0[k] = Z[rw[k] + (size_t)q0 * ldS];
+            z1[k] = Z[rw[k] + (size_t)q1 * ldS];
+        }
+        for (int j = 0; j < n; ++j) {
+            const double y0 = Y[j + q0 * n], y1 = Y[j + q1 * n];
+            const double *xj = X + (size_t)j * ldS;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double x = xj[rw[k]];
+                z0[k] = fma(-x, y0, z0[k]);
+                z1[k] = fma(-x, y1, z1[k]);
             }
-            for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o, tpc);
-            const double w = fma(cj, d, top[J + q * n]);
-            __syncwarp();
-            if (active && sub == 0) top[J + q * n] = fma(-tau, w, top[J + q * n]);
-            const double gq = tau * cj * w;
-            if (active) {
-                for (int e = sub; e < E; e += tpc) {
-                    const int tt = e / h1, i = e - tt * h1;
-                    Y[tt * n + i + (size_t)q * ldY] = fma(-gq, Xn[tt * n + i + (size_t)J * ldX],
-                                                          Y[tt * n + i + (size_t)q * ldY]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (rr + k * tr < rows) {
+                Z[rw[k] + (size_t)q0 * ldS] = z0[k];
+                if (q0 + 1 < kc) Z[rw[k] + (size_t)q1 * ldS] = z1[k];
+            }
+        }
+    }
+}
+
+// The Q^T apply with each chunk's reflectors as one blocked transformation: per chunk, first to
+// last, W = T + (X diag(c))^T Z, Y = S^T W, T -= Y and (where the whole product is wanted)
+// Z -= X diag(c) Y, written to Cout.  Then the same climb.  Two passes over the chunk's rows
+// in place of n fused sweeps, and no per-reflector barriers.
+__global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n;
+    const int grp = blockIdx.y, kc = min(a.k, a.ktot - grp * a.k);
+    const double *Bg = a.B + (int64_t)grp * a.k * a.ldb;
+    double *Cg = a.C + (int64_t)grp * a.k * a.ldc;
+    double *Og = a.Cout ? a.Cout + (int64_t)grp * a.k * a.ldco : nullptr;
+    unsigned int *counters = a.counters + grp * a.nodes;
+    double *slots = a.slots + grp * a.nodes * n * a.k;
+    const WyLayout L = wy_layout(n, kc, a.ldS, blockDim.x);
+    double *X = smem + L.X;
+    double *Z = smem + L.Z;
+    double *top = smem + L.top;
+    double *S = smem + L.S;
+    double *W = smem + L.W;
+    double *part = smem + L.part;
+    unsigned int *flag = reinterpret_cast<unsigned int *>(smem + L.flag);
+    const int leaf = blockIdx.x;
+
+    for (int idx = threadIdx.x; idx < n * kc; idx += blockDim.x) top[idx] = 0.0;
+    const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
+    const int64_t rbeg = u0 * a.unit;
+    const int64_t rend = (u1 * a.unit < a.m) ? u1 * a.unit : a.m;
+    const int64_t nchunks = (rend - rbeg + a.h - 1) / a.h;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int64_t row0 = rbeg + c * a.h;
+        const int rows = (int)((rend - row0 < a.h) ? rend - row0 : a.h);
+        const int64_t cid = row0 / a.h;
+        const double *csc = a.chunk_sc + cid * 2 * n;
+        __syncthreads();  // the previous chunk's buffers are no longer read
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+            const int col = idx / rows, i = idx - col * rows;
+            X[i + (size_t)col * a.ldS] = csc[2 * col + 1] * a.V[row0 + i + (int64_t)col * a.ldv];
+        }
+        for (int idx = threadIdx.x; idx < rows * kc; idx += blockDim.x) {
+            const int col = idx / rows, i = idx - col * rows;
+            Z[i + (size_t)col * a.ldS] = Bg[row0 + i + (int64_t)col * a.ldb];
+        }
+        const double *Sg = a.wyS + cid * (int64_t)n * n;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) S[idx] = Sg[idx];
+        __syncthreads();
+        wy_xtz(X, Z, a.ldS, rows, n, kc, top, W, part);
+        __syncthreads();
+        wy_sw(S, W, part, top, n, kc, true);
+        if (Og) {
+            __syncthreads();
+            wy_zupdate(Z, X, a.ldS, rows, n, kc, part);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < rows * kc; idx += blockDim.x) {
+                const int col = idx / rows, i = idx - col * rows;
+                Og[row0 + i + (int64_t)col * a.ldco] = Z[i + (size_t)col * a.ldS];
+            }
+        }
+    }
+    __syncthreads();
+    qt_climb(a, leaf, kc, X, top, flag, Cg, Og, counters, slots);
+}
+
+// The leaf pass with each chunk's reflectors as one blocked transformation: the chunk's rows of
+// [T; 0] under H_0 H_1 ... H_{n-1} = I - V S V^T are T - S T on top and -X diag(c) S T below.
+// Per chunk, last to first: Y = S T, T -= Y, and the chunk's rows of Q, -X diag(c) Y, are
+// written straight from registers.  Only half the flops of the sweep (no dot products with
+// the chunk's rows, which are zero before the chunk's reflectors reach them).
+__global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs a) {
+    extern __shared__ __align__(16) double smem[];
+    const int n = a.n, qn = a.qn, q0 = a.q0;
+    const QLeafWyLayout L = q_leaf_wy_layout(n, qn, a.ldS);
+    double *X = smem + L.X;
+    double *top = smem + L.top;
+    double *S = smem + L.S;
+    double *Y = smem + L.Y;
+    const int leaf = blockIdx.x;
+    for (int idx = threadIdx.x; idx < n * qn; idx += blockDim.x) {
+        const int col = idx / n, row = idx - col * n;
+        top[idx] = a.single ? ((row == q0 + col) ? a.signs[row] : 0.0)
+                            : a.B[(size_t)leaf * n * n + row + (size_t)(q0 + col) * n];
+    }
+    const int64_t u0 = ((int64_t)leaf * a.nunits) / a.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * a.nunits) / a.nleaves;
+    const int64_t rbeg = u0 * a.unit;
+    const int64_t rend = (u1 * a.unit < a.m) ? u1 * a.unit : a.m;
+    const int64_t nchunks = (rend - rbeg + a.h - 1) / a.h;
+    for (int64_t c = nchunks - 1; c >= 0; --c) {
+        const int64_t row0 = rbeg + c * a.h;
+        const int rows = (int)((rend - row0 < a.h) ? rend - row0 : a.h);
+        const int64_t cid = row0 / a.h;
+        const double *csc = a.chunk_sc + cid * 2 * n;
+        __syncthreads();  // the previous chunk's X, S and Y are no longer read
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+            const int col = idx / rows, i = idx - col * rows;
+            X[i + (size_t)col * a.ldS] = csc[2 * col + 1] * a.V[row0 + i + (int64_t)col * a.ldv];
+        }
+        const double *Sg = a.wyS + cid * (int64_t)n * n;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) S[idx] = Sg[idx];
+        __syncthreads();
+        for (int o = threadIdx.x; o < n * qn; o += blockDim.x) {  // Y = S T (S upper)
+            const int i = o % n, q = o / n;
+            double v = 0.0;
+            for (int j = i; j < n; ++j) v = fma(S[i + j * n], top[j + q * n], v);
+            Y[o] = v;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < n * qn; o += blockDim.x) top[o] -= Y[o];
+        // Q rows: thread tiles of 4 rows (tr apart) by 2 columns, -sum_j X(r, j) Y(j, q)
+        const int tr = (rows + 3) >> 2, tq = (qn + 1) >> 1;
+        for (int u = threadIdx.x; u < tr * tq; u += blockDim.x) {
+            const int rr = u % tr, qa = 2 * (u / tr), qb = min(qa + 1, qn - 1);
+            int rw[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rw[k] = min(rr + k * tr, rows - 1);
+            double z0[4] = {0.0, 0.0, 0.0, 0.0}, z1[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int j = 0; j < n; ++j) {
+                const double y0 = Y[j + qa * n], y1 = Y[j + qb * n];
+                const double *xj = X + (size_t)j * a.ldS;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double x = xj[rw[k]];
+                    z0[k] = fma(-x, y0, z0[k]);
+                    z1[k] = fma(-x, y1, z1[k]);
                 }
             }
-            __syncwarp();
-        }
-        __syncthreads();
-        if (Og) {  // the blocks of children 1 .. cs stay behind: the node's n-row blocks
-            const int64_t rb = a.grow0 + (left + (int64_t)parent * (k - 1)) * n;
-            for (int idx = threadIdx.x; idx < cs * n * kc; idx += blockDim.x) {
-                const int col = idx / (cs * n), rr = idx - col * (cs * n);
-                Og[rb + rr + (int64_t)col * a.ldco] = Y[rr + (size_t)col * ldY];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (rr + k * tr < rows) {
+                    a.Q[row0 + rw[k] + (int64_t)(q0 + qa) * a.ldq] = z0[k];
+                    if (qa + 1 < qn) a.Q[row0 + rw[k] + (int64_t)(q0 + qa + 1) * a.ldq] = z1[k];
+                }
             }
         }
-        left += cnt - next_cnt;
-        off = next_off;
-        cnt = next_cnt;
-        t = parent;
     }
 }
 
@@ -618,6 +931,42 @@ cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes,
         case 2: tsqr_qt_kernel<2><<<grid, block, smem_bytes, stream>>>(a); break;
         default: tsqr_qt_kernel<1><<<grid, block, smem_bytes, stream>>>(a); break;
     }
+    return cudaGetLastError();
+}
+
+size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS) {
+    return sizeof(double) * (size_t)q_leaf_wy_layout(n, qn, ldS).total;
+}
+
+cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t stream) {
+    cudaError_t e = set_smem_attrs(tsqr_q_leaf_wy_kernel, smem_bytes);
+    if (e != cudaSuccess) return e;
+    tsqr_q_leaf_wy_kernel<<<a.nleaves, 256, smem_bytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+size_t wy_smem_bytes(int n, int ldX) {
+    return sizeof(double) * ((size_t)ldX * n + 2 * (size_t)n * n);
+}
+
+cudaError_t wy_launch(const WyArgs &a, size_t smem_bytes, int grid, cudaStream_t stream) {
+    cudaError_t e = set_smem_attrs(tsqr_wy_kernel, smem_bytes);
+    if (e != cudaSuccess) return e;
+    tsqr_wy_kernel<<<grid, 256, smem_bytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+constexpr int kWyThreads = 256;
+
+size_t qt_wy_smem_bytes(int n, int kc, int ldS) {
+    return sizeof(double) * (size_t)wy_layout(n, kc, ldS, kWyThreads).total;
+}
+
+cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream) {
+    cudaError_t e = set_smem_attrs(tsqr_qt_wy_kernel, smem_bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(a.nleaves, (a.ktot + a.k - 1) / a.k);
+    tsqr_qt_wy_kernel<<<grid, kWyThreads, smem_bytes, stream>>>(a);
     return cudaGetLastError();
 }
 

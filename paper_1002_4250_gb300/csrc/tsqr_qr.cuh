@@ -38,6 +38,7 @@ struct QLeafArgs {
     const double *B;          // per leaf: n x n block, leading dimension n
     const double *signs;      // the root's row signs (used when the only leaf is the root)
     int single;               // one leaf: its block is diag(signs)
+    const double *wyS;        // the chunks' compact WY factors (the blocked leaf pass)
 };
 
 // Offsets in doubles: the tails X (ldS x n), the Q rows Z of the column group (ldS x qn), the
@@ -93,7 +94,45 @@ struct QtArgs {
     // a fixed order.  Together with the n rows in C they are Q^T B up to a row permutation.
     double *Cout;
     int64_t ldco, grow0;
+    // The chunks' compact WY factors (per chunk id, n x n, from tsqr_wy_kernel), for the
+    // blocked leaf part; unused by the reflector-by-reflector one.
+    const double *wyS;
 };
+
+// Compact WY form of each chunk's reflectors.  Reflector J of a chunk is v_J = [e_J; c_J x_J]
+// (row J of the carried triangle, then the chunk's rows), so with V = [I; X diag(c)] the
+// product H_0 H_1 ... H_{n-1} is I - V S V^T with S upper triangular (forward accumulation:
+// S(J,J) = tau_J, S(0:J,J) = -tau_J S(0:J,0:J) V(:,0:J)^T v_J, and V(:,i)^T v_J = c_i c_J x_i . x_J
+// for i < J).  One S per chunk id, n x n with leading dimension n.
+struct WyArgs {
+    const double *V;          // the chunks' tails, leading dimension ldv
+    int64_t ldv, m;
+    int n, h, ldX;            // chunk rows and the shared-memory leading dimension (>= h)
+    int64_t nchunks;
+    const double *chunk_sc;   // per chunk: tau_J, c_J
+    double *S;                // out
+};
+
+// Blocked leaf part of the Q^T apply: the scaled tails X diag(c) (ldS x n), B's chunk Z
+// (ldS x kc), the carried block T (n x kc), S (n x n), W = V^T [T; Z] (n x kc), the partial
+// sums of W's row slices (which then hold S^T W), and the climb's counter word.
+struct WyLayout {
+    int X, Z, top, S, W, part, flag, total;
+};
+
+__host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthreads) {
+    WyLayout L;
+    int o = 0;
+    L.X = o;    o += ldS * n;
+    L.Z = o;    o += ldS * kc;
+    L.top = o;  o += n * kc;
+    L.S = o;    o += n * n;
+    L.W = o;    o += n * kc;
+    L.part = o; o += (4 * nthreads > n * kc) ? 4 * nthreads : n * kc;
+    L.flag = o; o += 1;
+    L.total = o;
+    return L;
+}
 
 // Offsets in doubles: the tails X (ldS x n), B's chunk Z (ldS x k), the block T (n x k), the
 // stacked children's blocks during the climb (reusing X and Z), the factors g, the chunk's
@@ -113,6 +152,23 @@ __host__ __device__ inline QtLayout qt_layout(int n, int k, int ldS, int warps_t
     L.seg = o;  o += warps_total * seg_stride(k);
     L.tot = o;  o += 2 * seg_stride(k);
     L.flag = o; o += 1;
+    L.total = o;
+    return L;
+}
+
+// Blocked leaf pass: the scaled tails X diag(c) (ldS x n), the carried block's columns T
+// (n x qn), S (n x n) and Y = S T (n x qn).
+struct QLeafWyLayout {
+    int X, top, S, Y, total;
+};
+
+__host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS) {
+    QLeafWyLayout L;
+    int o = 0;
+    L.X = o;    o += ldS * n;
+    L.top = o;  o += n * qn;
+    L.S = o;    o += n * n;
+    L.Y = o;    o += n * qn;
     L.total = o;
     return L;
 }
