@@ -623,7 +623,8 @@ __global__ void __launch_bounds__(256) tsqr_wy_kernel(const WyArgs a) {
     }
 }
 
-// W = T + X^T Z over the chunk's first `rows` rows (X ldS x n, Z ldS x kc; T, W n x kc).
+// W = T + X^T Z over the chunk's first `rows` rows (X ldS x n, the scaled tails; Z ldS x kc;
+// T, W n x kc).
 // Thread tiles of 2 x 2 outputs; where they are fewer than the threads, the rows are split in
 // slices whose partial sums are added in slice order.
 __device__ __forceinline__ void wy_xtz(const double *X, const double *Z, const int ldS,
@@ -728,8 +729,8 @@ __device__ __forceinline__ void wy_zupdate(double *Z, const double *X, const int
 }
 
 // The Q^T apply with each chunk's reflectors as one blocked transformation: per chunk, first to
-// last, W = T + (X diag(c))^T Z, Y = S^T W, T -= Y and (where the whole product is wanted)
-// Z -= X diag(c) Y, written to Cout.  Then the same climb.  Two passes over the chunk's rows
+// last (the tails copied asynchronously with B's rows and S, then scaled), W = T + (X diag(c))^T Z,
+// Y = S^T W, T -= Y and (where the whole product is wanted) Z -= X diag(c) Y, written to Cout.  Then the same climb.  Two passes over the chunk's rows
 // in place of n fused sweeps, and no per-reflector barriers.
 __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
     extern __shared__ __align__(16) double smem[];
@@ -747,6 +748,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
     double *S = smem + L.S;
     double *W = smem + L.W;
     double *part = smem + L.part;
+    double *cs = smem + L.cs;
     unsigned int *flag = reinterpret_cast<unsigned int *>(smem + L.flag);
     const int leaf = blockIdx.x;
 
@@ -762,16 +764,27 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
         const int64_t cid = row0 / a.h;
         const double *csc = a.chunk_sc + cid * 2 * n;
         __syncthreads();  // the previous chunk's buffers are no longer read
+        // asynchronous copies of the tails, B's rows and S; each thread then scales the tails
+        // it copied (X diag(c), whose entries are at most 1 in magnitude, is the well-scaled
+        // form: c alone overflows where a chunk's rank runs out and the tails become tiny)
         for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
             const int col = idx / rows, i = idx - col * rows;
-            X[i + (size_t)col * a.ldS] = csc[2 * col + 1] * a.V[row0 + i + (int64_t)col * a.ldv];
+            cp_async8(X + i + (size_t)col * a.ldS, a.V + row0 + i + (int64_t)col * a.ldv, 8);
         }
         for (int idx = threadIdx.x; idx < rows * kc; idx += blockDim.x) {
             const int col = idx / rows, i = idx - col * rows;
-            Z[i + (size_t)col * a.ldS] = Bg[row0 + i + (int64_t)col * a.ldb];
+            cp_async8(Z + i + (size_t)col * a.ldS, Bg + row0 + i + (int64_t)col * a.ldb, 8);
         }
         const double *Sg = a.wyS + cid * (int64_t)n * n;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) S[idx] = Sg[idx];
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) cp_async8(S + idx, Sg + idx, 8);
+        cp_async_commit();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) cs[j] = csc[2 * j + 1];
+        cp_async_wait_all();
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
+            const int col = idx / rows, i = idx - col * rows;
+            X[i + (size_t)col * a.ldS] *= cs[col];
+        }
         __syncthreads();
         wy_xtz(X, Z, a.ldS, rows, n, kc, top, W, part);
         __syncthreads();
@@ -803,6 +816,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs 
     double *top = smem + L.top;
     double *S = smem + L.S;
     double *Y = smem + L.Y;
+    double *cs = smem + L.cs;
     const int leaf = blockIdx.x;
     for (int idx = threadIdx.x; idx < n * qn; idx += blockDim.x) {
         const int col = idx / n, row = idx - col * n;
@@ -822,11 +836,18 @@ __global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs 
         __syncthreads();  // the previous chunk's X, S and Y are no longer read
         for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
             const int col = idx / rows, i = idx - col * rows;
-            X[i + (size_t)col * a.ldS] = csc[2 * col + 1] * a.V[row0 + i + (int64_t)col * a.ldv];
+            cp_async8(X + i + (size_t)col * a.ldS, a.V + row0 + i + (int64_t)col * a.ldv, 8);
         }
         const double *Sg = a.wyS + cid * (int64_t)n * n;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) S[idx] = Sg[idx];
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) cp_async8(S + idx, Sg + idx, 8);
+        cp_async_commit();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) cs[j] = csc[2 * j + 1];
+        cp_async_wait_all();
         __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {  // X diag(c)
+            const int col = idx / rows, i = idx - col * rows;
+            X[i + (size_t)col * a.ldS] *= cs[col];
+        }
         for (int o = threadIdx.x; o < n * qn; o += blockDim.x) {  // Y = S T (S upper)
             const int i = o % n, q = o / n;
             double v = 0.0;

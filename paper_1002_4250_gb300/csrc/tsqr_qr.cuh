@@ -113,11 +113,11 @@ struct WyArgs {
     double *S;                // out
 };
 
-// Blocked leaf part of the Q^T apply: the scaled tails X diag(c) (ldS x n), B's chunk Z
-// (ldS x kc), the carried block T (n x kc), S (n x n), W = V^T [T; Z] (n x kc), the partial
-// sums of W's row slices (which then hold S^T W), and the climb's counter word.
+// Blocked leaf part of the Q^T apply: the tails X diag(c) (ldS x n), B's chunk Z (ldS x kc),
+// the carried block T (n x kc), S (n x n), W = V^T [T; Z] (n x kc), the partial sums of W's row
+// slices (which then hold S^T W), the chunk's c, and the climb's counter word.
 struct WyLayout {
-    int X, Z, top, S, W, part, flag, total;
+    int X, Z, top, S, W, part, cs, flag, total;
 };
 
 __host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthreads) {
@@ -129,6 +129,7 @@ __host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthrea
     L.S = o;    o += n * n;
     L.W = o;    o += n * kc;
     L.part = o; o += (4 * nthreads > n * kc) ? 4 * nthreads : n * kc;
+    L.cs = o;   o += n;
     L.flag = o; o += 1;
     L.total = o;
     return L;
@@ -156,10 +157,10 @@ __host__ __device__ inline QtLayout qt_layout(int n, int k, int ldS, int warps_t
     return L;
 }
 
-// Blocked leaf pass: the scaled tails X diag(c) (ldS x n), the carried block's columns T
-// (n x qn), S (n x n) and Y = S T (n x qn).
+// Blocked leaf pass: the tails X diag(c) (ldS x n), the carried block's columns T (n x qn),
+// S (n x n), Y = S T (n x qn), and the chunk's c.
 struct QLeafWyLayout {
-    int X, top, S, Y, total;
+    int X, top, S, Y, cs, total;
 };
 
 __host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS) {
@@ -169,6 +170,7 @@ __host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS
     L.top = o;  o += n * qn;
     L.S = o;    o += n * n;
     L.Y = o;    o += n * qn;
+    L.cs = o;   o += n;
     L.total = o;
     return L;
 }

@@ -46,7 +46,7 @@ def _check(oracle, T, At, panel=0, plan=None):
 
 @pytest.mark.parametrize("m,n,panel", [(20000, 200, 32), (30011, 150, 0), (5000, 300, 64),
                                        (12345, 100, 48), (40000, 97, 16), (9000, 129, 128),
-                                       (65537, 256, 32)])
+                                       (65537, 256, 32), (385, 200, 32), (257, 130, 64)])
 def test_caqr_gaussian(oracle, T, m, n, panel):
     _check(oracle, T, workloads.gaussian(m, n, seed=n), panel=panel)
 

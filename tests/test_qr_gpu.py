@@ -69,8 +69,11 @@ def test_qr_conditioned(oracle, T):
     _check(oracle, T, workloads.conditioned(200000, 32, 1e8, seed=0))
 
 
-@pytest.mark.parametrize("m,n", [(32, 32), (300, 32), (129, 64), (1, 1), (5, 5)])
+@pytest.mark.parametrize("m,n", [(32, 32), (300, 32), (129, 64), (1, 1), (5, 5), (130, 64),
+                                 (133, 64), (386, 32)])
 def test_qr_single_leaf_and_square(oracle, T, m, n):
+    """Also shapes whose last leaf holds one to five rows: a chunk that runs out of rank, with
+    tiny tails and huge scales c in its later reflectors."""
     _check(oracle, T, workloads.gaussian(m, n, seed=3))
 
 
