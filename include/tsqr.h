@@ -187,7 +187,7 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
  *   A     : device, column-major m x n, lda >= m, m >= n >= 1; read only.
  *   R     : device, column-major n x n, ldr >= n; the upper triangle with diag(R) >= 0, the
  *           strict lower triangle written as 0.  Must not overlap A.
- *   panel : panel width, 1 .. TSQR_MAX_N; 0 = 32 (or n if smaller).
+ *   panel : panel width, 1 .. TSQR_MAX_N; 0 = 16 (or n if smaller).
  *   plan  : NULL = AUTO, else the plan used for every panel's factorization (as for tsqr_qr).
  * Each panel's update keeps every row of the panel's matrix and adds the n-row blocks its tree
  * nodes leave behind: a panel factorized on L leaves adds (L - 1) panel rows to the next

@@ -987,7 +987,7 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
 // columns right of it.  The rows that update leaves behind form the next panel's matrix: every
 // row of the old one (its chunks' rows of Q^T B, in place) and the n-row blocks its tree nodes
 // left behind (appended below), so a panel on L leaves adds (L - 1) nb rows.
-constexpr int64_t kCaqrPanel = 32;  // the default panel width
+constexpr int64_t kCaqrPanel = 16;  // the default panel width (measured: 16 >= 24, 32, 48)
 
 struct CaqrPanel {
     F64Plan p;
