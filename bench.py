@@ -352,7 +352,24 @@ def bench_extras(dev):
     out["varlen_batch"] = bench_batched(dev)
     out["thin_qr"] = bench_qr(dev)
     out["lstsq"] = bench_lstsq(dev)
+    out["caqr"] = bench_caqr(dev)
     return out
+
+
+def bench_caqr(dev):
+    """tsqr_caqr_r (R of a general m x n matrix by TSQR panels and trailing updates) on
+    262,144 x 1,024 FP64 N(0,1) with the default panel: time and GFLOP/s (2mn^2 - 2n^3/3)."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import workloads
+    m, n = 262144, 1024
+    A = workloads.gaussian(m, n, seed=0, device=dev).T
+    R = T.empty_r(n, dev)
+    ms = time_call(lambda: T.tsqr_caqr_r(A, R=R), reps=2, warmup=1)
+    del A
+    torch.cuda.empty_cache()
+    return {"workload": f"{m:,} x {n:,} N(0,1) seed 0, default panel", "ms": ms,
+            "gflops": flops(m, n) / ms / 1e6}
 
 
 def bench_lstsq(dev):
@@ -381,8 +398,8 @@ def bench_lstsq(dev):
 def bench_qr(dev):
     """tsqr_qr (thin Q and R, FP64) on 4,194,304 x 32 and 16,777,216 x 64: time, GFLOP/s with
     LAPACK's counts (geqrf 2mn^2 - 2n^3/3 plus orgqr 2mn^2 - 2n^3/3), the Q passes' share
-    (tsqr_qr minus tsqr_r with the same plan), and the Q passes' FP64 rate on the flops they
-    execute (4mn^2: every leaf reflector meets all n columns of the carried block)."""
+    (tsqr_qr minus tsqr_r with the same plan), and the Q passes' FP64 rate on the flops the
+    blocked form executes (3mn^2: mn^2 for the chunks' S factors, 2mn^2 for the leaf pass)."""
     import torch
     import paper_1002_4250_gb300 as T
     import workloads
@@ -397,7 +414,7 @@ def bench_qr(dev):
         fl = 4.0 * m * n * n - 4.0 * n ** 3 / 3
         res[f"{m}x{n}"] = {"ms": ms_qr, "gflops_lapack_count": fl / ms_qr / 1e6,
                            "r_only_ms": ms_r, "q_passes_ms": ms_qr - ms_r,
-                           "q_passes_gflops_executed": 4.0 * m * n * n / (ms_qr - ms_r) / 1e6}
+                           "q_passes_gflops_executed": 3.0 * m * n * n / (ms_qr - ms_r) / 1e6}
         del A, Q
         torch.cuda.empty_cache()
     return res
