@@ -581,7 +581,13 @@ __global__ void __launch_bounds__(256) tsqr_wy_kernel(const WyArgs a) {
         __syncthreads();  // the previous chunk's S is written out
         for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {
             const int J = idx / rows, i = idx - J * rows;
-            X[i + J * ldX] = sc[2 * J + 1] * a.V[row0 + i + (int64_t)J * a.ldv];
+            cp_async8(X + i + J * ldX, a.V + row0 + i + (int64_t)J * a.ldv, 8);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {  // X diag(c), own copies
+            const int J = idx / rows, i = idx - J * rows;
+            X[i + J * ldX] *= sc[2 * J + 1];
         }
         __syncthreads();
         for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
