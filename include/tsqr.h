@@ -132,7 +132,9 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
  * Section 3 notes that the Q factor is obtained by applying the Householder transformations
  * of the reduction to the identity, which requires keeping every node's Householder vectors
  * and the shape of the tree.  This call does that: the factorization is tsqr_r's (same plan,
- * same kernels, the same R bit for bit) with the reflectors of every leaf chunk and tree node
+ * same kernels, the same R bit for bit; with the AUTO plan, except at widths where tsqr_r's
+ * chunks are too tall for the Q passes' buffers, which take the four-warp plan instead:
+ * tsqr_last_plan reports the plan used) with the reflectors of every leaf chunk and tree node
  * kept, then Q = H [I_n; 0] (with the sign convention applied to Q's columns) is formed top-down
  * through the tree and backwards through each leaf's chunks.  Q is unique for A of full rank
  * (as R is); with Householder reflectors it is then orthonormal to working accuracy however
@@ -247,7 +249,7 @@ tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda,
  *   A, m, n, lda, dtype, prec, R, ldr as for tsqr_r_ex; R is overwritten (the last candidate's
  *   result).  best: optional, receives the chosen plan.
  *   Candidates: HYBRID slabs as tall as fit 1, 2 or 3 CTAs per SM, and half as tall, with that
- *   many CTAs per SM on every SM; 4 or 12 bulk warps for FP64, 4, 8 or 12 for the mixed path.
+ *   many CTAs per SM on every SM; 4, 8 or 12 bulk warps.
  *   Each is timed over three calls with CUDA events on `stream`.
  *   Synchronizes `stream`; not for use under stream capture.  Returns TSQR_ERR_UNSUPPORTED if
  *   no candidate runs. */
@@ -269,6 +271,12 @@ void tsqr_release_workspace(void);
 
 /* Static description of a status code. */
 const char *tsqr_status_string(int32_t status);
+
+/* The plan of the factorization the last call on this host thread ran (the first panel's for
+ * tsqr_caqr_r), in the form tsqr_r_ex accepts: passed back as a plan it gives the same
+ * partition, kernels and bytes.  All fields zero when that call ran no factorization.
+ *   out : host pointer, required.  Returns TSQR_ERR_INVALID_ARG when NULL. */
+tsqr_status_t tsqr_last_plan(tsqr_plan_t *out);
 
 /* The plan AUTO (or `plan`) resolves to for an (m, n, dtype, prec) problem on the current
  * device, written to *out.  Host only; enqueues nothing. */

@@ -83,6 +83,8 @@ def _load():
     capi.tsqr_lstsq.restype = _i32
     capi.tsqr_caqr_r.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _i64, ctypes.POINTER(Plan), _p]
     capi.tsqr_caqr_r.restype = _i32
+    capi.tsqr_last_plan.argtypes = [ctypes.POINTER(Plan)]
+    capi.tsqr_last_plan.restype = _i32
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
@@ -101,7 +103,7 @@ def __getattr__(name):
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
                "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
-               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq", "tsqr_caqr_r")
+               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq", "tsqr_caqr_r", "tsqr_last_plan")
 
 
 class TsqrError(RuntimeError):
@@ -311,6 +313,13 @@ def tsqr_get_device_status(stream=None) -> int:
 
 def tsqr_release_workspace() -> None:
     _load().tsqr_release_workspace()
+
+
+def last_plan() -> Plan:
+    """The plan of the factorization the last call on this thread ran (tsqr_last_plan)."""
+    out = Plan()
+    check(_load().tsqr_last_plan(ctypes.byref(out)), "tsqr_last_plan")
+    return out
 
 
 def tsqr_resolve_plan(m, n, dtype=F64, prec=PREC_F64, plan: Plan | None = None) -> Plan:

@@ -38,6 +38,7 @@ using namespace tsqr;
 namespace {
 
 thread_local int g_last_launches = 0;
+thread_local tsqr_plan_t g_last_plan{};  // the plan of the last call's (first) factorization
 
 struct Workspace {
     void *base = nullptr;   // counters + slots (grown on demand)
@@ -93,6 +94,17 @@ struct F64Plan {
     TreeShape shape{};
     int64_t nodes = 0;
 };
+
+// The public form of a plan: passed back as a plan it gives the same partition and kernels.
+tsqr_plan_t public_plan(const F64Plan &p) {
+    tsqr_plan_t o;
+    o.tree = p.tree;
+    o.tile_rows = (int32_t)p.unit;
+    o.ctas = p.nleaves;
+    o.warps = p.warps;
+    o.arity = p.arity;
+    return o;
+}
 
 // Kernel arguments for a plan: A (leading dimension lda), m, n and the plan's shape; the
 // workspace, R and status pointers are the caller's to set.  Every other field is zero.
@@ -171,6 +183,8 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
 tsqr_status_t plan_f64(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     return plan_leaf(m, n, over, false, p);
 }
+
+tsqr_status_t plan_store(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p);
 
 // Shared memory of a leaf CTA holding an hs-row chunk with leading dimension ld.
 size_t leaf_smem_bytes(int n, int hs, int ld, int warps, bool mixed) {
@@ -288,6 +302,18 @@ tsqr_status_t plan_with_r(int64_t m, int n, const tsqr_plan_t *over, bool mixed,
     return build_tree(leaves, p->arity, &p->shape, &p->nodes);
 }
 
+// FP64 bulk warps of the AUTO plan, by width: from a sweep of every n = 2 .. 128 at 4,194,304
+// rows with 4, 8 and 12 bulk warps, a width takes 8 or 12 where that was at least 2% faster
+// than 4 (n = 13: +23%, 49-51: +9%, 80-90: +40%, where four warps drop to one CTA per SM;
+// 56-64 with 12: +4-5%).  Every other width keeps 4, the best or within 2% of it.
+int f64_auto_warps(int n) {
+    if (n == 5 || n == 8 || n == 13 || (n >= 22 && n <= 25) || (n >= 49 && n <= 51) ||
+        (n >= 80 && n <= 90))
+        return 8;
+    if (n == 35 || (n >= 56 && n <= 64)) return 12;
+    return 4;
+}
+
 tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -297,9 +323,9 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     if (plan_is_auto(over) && tuned_plan(dev, m, n, mixed, &tuned)) over = &tuned;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
-    // bulk warps: 4; 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep
-    // gains from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms)
-    p->warps = (mixed && n >= 48) ? 8 : 4;
+    // bulk warps: 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep gains
+    // from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms); FP64 by width
+    p->warps = mixed ? (n >= 48 ? 8 : 4) : f64_auto_warps(n);
     if (over && over->warps) {
         if (over->warps != 2 && over->warps != 4 && over->warps != 8 && over->warps != 12)
             return TSQR_ERR_INVALID_ARG;
@@ -361,11 +387,13 @@ tsqr_status_t zero_r(double *R, int64_t n, int64_t ldr, cudaStream_t stream) {
 tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
                       const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) return zero_r(R, n, ldr, stream);
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     if (f64_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = (size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double);
@@ -391,9 +419,11 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
 tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double *Q, int64_t ldq,
                      double *R, int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     F64Plan p;
-    tsqr_status_t st = plan_f64(m, (int)n, over, &p);
+    tsqr_status_t st = plan_store(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     if (p.unit % p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -569,6 +599,7 @@ const unsigned int *host_ones() {
 tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                            int64_t ldr, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) {
         for (int64_t c = 0; c < n; ++c)
@@ -582,6 +613,7 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     const int P = (int)std::min<int64_t>(16, p.nunits);
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
@@ -676,6 +708,7 @@ tsqr_status_t run_lstsq_augmented(const double *A, int64_t m, int64_t n, int64_t
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)na, over, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     if (f64_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)na * na * sizeof(double), 256);
@@ -730,6 +763,26 @@ bool plan_wy(int w, const F64Plan &p, const DeviceInfo &di, int *ldX, size_t *wy
     *kc = k;
     *qt_smem = qt_wy_smem_bytes(w, k, p.ldS);
     return *qt_smem <= di.smem_block_optin;
+}
+
+// The plan of a factorization whose reflectors the Q and Q^T passes apply: tsqr_r's, unless
+// that is the AUTO plan and its chunks are too tall for the blocked passes' buffers (some wide
+// n where the AUTO plan takes 8 or 12 bulk warps); then the four-warp plan.  tsqr_last_plan
+// reports which.
+tsqr_status_t plan_store(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    tsqr_status_t st = plan_f64(m, n, over, p);
+    if (st != TSQR_SUCCESS || !plan_is_auto(over) || p->warps == 4) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    int ldX = 0, kc = 0;
+    size_t wy = 0, qt = 0;
+    if (plan_wy(n, *p, di, &ldX, &wy, &kc, &qt) &&
+        q_leaf_wy_smem_bytes(n, std::min(n, 8), p->ldS) <= di.smem_block_optin)
+        return st;
+    tsqr_plan_t w4{};
+    w4.warps = 4;
+    return plan_f64(m, n, &w4, p);
 }
 
 // tsqr_lstsq's stored-reflector path with each chunk's reflectors applied as one compact WY
@@ -847,14 +900,16 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
                         int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                         const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     // the augmented factorization costs ~(n + k)^2 per row against n^2 plus the apply pass:
     // cheaper up to k ~ n / 4 (4,194,304 x 32: k = 1 11.3 against 15.2 ms, k = 32 49.0 against
     // 41.1 ms)
     if (k > 0 && k <= std::max<int64_t>(1, n / 4) && n + k <= TSQR_MAX_N)
         return run_lstsq_augmented(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, over, stream);
     F64Plan p;
-    tsqr_status_t st = plan_f64(m, (int)n, over, &p);
+    tsqr_status_t st = plan_store(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     if (p.unit % p.h != 0) return TSQR_ERR_UNSUPPORTED;  // chunk ids = first row / h
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -1004,6 +1059,7 @@ struct CaqrPanel {
 tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, double *R,
                        int64_t ldr, int64_t nb, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
@@ -1017,7 +1073,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         c.j0 = j0;
         c.M = M;
         c.w = (int)std::min<int64_t>(nb, N - j0);
-        tsqr_status_t st = plan_f64(M, c.w, over, &c.p);
+        tsqr_status_t st = plan_store(M, c.w, over, &c.p);
         if (st != TSQR_SUCCESS) return st;
         const int64_t trail = N - j0 - c.w;
         if (plan_is_auto(over) && trail > 0) {
@@ -1032,6 +1088,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
                 std::memset(&o, 0, sizeof(o));
                 o.tree = TSQR_TREE_HYBRID;
                 o.ctas = leaves;
+                o.warps = c.p.warps;
                 st = plan_f64(M, c.w, &o, &c.p);
                 if (st != TSQR_SUCCESS) return st;
             }
@@ -1073,6 +1130,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         if (c.wy) wys_max = std::max(wys_max, (size_t)((M + c.p.h - 1) / c.p.h) * ww * sizeof(double));
         qcnt_max = std::max(qcnt_max, groups * nodes * sizeof(unsigned int));
         qslot_max = std::max(qslot_max, groups * nodes * c.w * c.kc * sizeof(double));
+        if (panels.empty()) g_last_plan = public_plan(c.p);
         panels.push_back(c);
         M += (int64_t)(c.p.nleaves - 1) * c.w;
     }
@@ -1194,11 +1252,13 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) return zero_r(R, n, ldr, stream);
     F64Plan p;
     tsqr_status_t st = plan_leaf(m, (int)n, over, true, &p);
     if (st != TSQR_SUCCESS) return st;
+    g_last_plan = public_plan(p);
     if (mixed_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = (size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double);
@@ -1234,6 +1294,7 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
                           const int64_t *offsets, int32_t count, double *R_packed, int dt,
                           cudaStream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
@@ -1399,6 +1460,7 @@ int32_t tsqr_last_launch_count(void) { return g_last_launches; }
 tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
                      tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
@@ -1409,6 +1471,7 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
                         int64_t lda, double *R, int64_t ldr, const tsqr_plan_t *plan,
                         tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
     if (dtype < TSQR_F64 || dtype > TSQR_BF16 || prec < TSQR_PREC_F64 || prec > TSQR_PREC_MIXED)
         return TSQR_ERR_INVALID_ARG;
@@ -1460,6 +1523,7 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
                          int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                          const tsqr_plan_t *plan, tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, std::max<int64_t>(ldr, n)) || n < 1 || m < n || k < 0 ||
         ldb < std::max<int64_t>(1, m) || ldx < n || (R && ldr < n))
         return TSQR_ERR_INVALID_ARG;
@@ -1472,6 +1536,7 @@ tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, do
                           int64_t ldr, int64_t panel, const tsqr_plan_t *plan,
                           tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr) || n < 1 || m < n || panel < 0 || !A || !R)
         return TSQR_ERR_INVALID_ARG;
     if (panel > TSQR_MAX_N || n > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
@@ -1482,6 +1547,7 @@ tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, do
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                           int64_t ldr, tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
@@ -1492,6 +1558,7 @@ tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double
                       int64_t ldq, double *R, int64_t ldr, const tsqr_plan_t *plan,
                       tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr) || n < 1 || m < n || ldq < m) return TSQR_ERR_INVALID_ARG;
     if (!A || !Q || !R) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
@@ -1502,6 +1569,7 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
                              int64_t ld2, double *R, int64_t ldr, int32_t normalize,
                              tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (n < 0 || ld1 < std::max<int64_t>(1, n) || ld2 < std::max<int64_t>(1, n) ||
         ldr < std::max<int64_t>(1, n))
         return TSQR_ERR_INVALID_ARG;
@@ -1527,6 +1595,7 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (count < 0) return TSQR_ERR_INVALID_ARG;
     if (count == 0) return TSQR_SUCCESS;
     if (!ptrs || !ms || !ns || !offsets || !R_packed) return TSQR_ERR_INVALID_ARG;
@@ -1577,6 +1646,12 @@ void tsqr_release_workspace(void) {
     cudaSetDevice(cur);
 }
 
+tsqr_status_t tsqr_last_plan(tsqr_plan_t *out) {
+    if (!out) return TSQR_ERR_INVALID_ARG;
+    *out = g_last_plan;
+    return TSQR_SUCCESS;
+}
+
 tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t prec,
                                 const tsqr_plan_t *plan, tsqr_plan_t *out) {
     if (!out || m < 0 || n < 1) return TSQR_ERR_INVALID_ARG;
@@ -1599,6 +1674,7 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
                             int64_t lda, double *R, int64_t ldr, tsqr_plan_t *best,
                             tsqr_stream_t stream) {
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr) || n < 1 || m < 1 || !A || !R) return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
@@ -1610,10 +1686,10 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     const cudaStream_t s = (cudaStream_t)stream;
     // candidates: HYBRID slabs as tall as fit k CTAs per SM (k = 1, 2, 3), and half as tall,
-    // with 4 or 12 bulk warps (FP64) or 4, 12 and 8 (mixed); k CTAs per SM on every SM
+    // with 4, 12 or 8 bulk warps; k CTAs per SM on every SM
     std::vector<tsqr_plan_t> cands;
     const int warps_opts[3] = {4, 12, 8};
-    for (int wi = 0; wi < (mixed ? 3 : 2); ++wi) {
+    for (int wi = 0; wi < 3; ++wi) {
         const int W = warps_opts[wi];
         for (int k = 1; k <= 3; ++k) {
             const size_t reserve = 1024;
@@ -1666,6 +1742,7 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
     if (st != TSQR_SUCCESS) return st;
     if (best_ms < 0.0f) return TSQR_ERR_UNSUPPORTED;
     {

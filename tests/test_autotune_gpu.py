@@ -33,7 +33,7 @@ def test_autotune_fp64(oracle, T):
     default = T.tsqr_resolve_plan(m, n)
     other = T.tsqr_resolve_plan(m, 16)
     best = T.tsqr_autotune(Ad)
-    assert best.tree == T.TREE_HYBRID and best.warps == 4 and best.tile_rows >= n
+    assert best.tree == T.TREE_HYBRID and best.warps in (4, 8, 12) and best.tile_rows >= n
     assert _fields(T.tsqr_resolve_plan(m, n)) == _fields(best)
     assert _fields(T.tsqr_resolve_plan(m + 12345, n)) == _fields(best)  # same log2 bucket
     assert _fields(T.tsqr_resolve_plan(m, 16)) == _fields(other)        # other n untouched

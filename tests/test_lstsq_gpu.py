@@ -40,11 +40,14 @@ def _check(oracle, T, At, Bt, plan=None):
     m, n = A.shape
     k = Bn.shape[1]
     X, R = T.tsqr_lstsq(At.cuda().T, Bt.cuda().T, plan=plan)
-    Rr = T.tsqr_r_ex(At.cuda().T, plan=plan).cpu().numpy()
+    augmented = k <= max(1, n // 4) and n + k <= 128
+    # the stored-reflector path's factorization plan gives a bit-identical R
+    used = plan if plan is not None or augmented else T.last_plan()
+    Rr = T.tsqr_r_ex(At.cuda().T, plan=used).cpu().numpy()
     Xh = X.cpu().numpy()
     Xo = oracle.lstsq(A, Bn, nthreads=16)
     kap = oracle.kappa_from_r(oracle.householder_r(A, nthreads=16))
-    if not (k <= max(1, n // 4) and n + k <= 128):
+    if not augmented:
         assert np.array_equal(R.cpu().numpy(), Rr)
     else:
         np.testing.assert_allclose(R.cpu().numpy(), Rr, rtol=0,

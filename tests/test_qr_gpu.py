@@ -32,7 +32,8 @@ def _check(oracle, T, At, plan=None, nthreads=16):
     m, n = A.shape
     Ad = At.cuda().T
     Q, R = T.tsqr_qr(Ad, plan=plan)
-    Rr = T.tsqr_r_ex(Ad, plan=plan)
+    used = T.last_plan()  # the AUTO plan, or the four-warp one where its chunks are too tall
+    Rr = T.tsqr_r_ex(Ad, plan=plan if plan is not None else used)
     Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
     assert np.array_equal(Rh, Rr.cpu().numpy()), "R differs from tsqr_r's under the same plan"
     Qo, Ro = oracle.householder_qr(A, nthreads=nthreads)
@@ -146,3 +147,27 @@ def test_qr_rank_deficient(oracle, T):
     Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
     assert oracle.gram_residual(A, Rh) <= 1e-13
     assert np.linalg.norm(A - Qh @ Rh) / np.linalg.norm(A) <= _c(50000) * 6 * U
+
+
+def test_last_plan(T):
+    """tsqr_last_plan: tsqr_r's is the resolved AUTO plan and, passed back, gives the same bytes;
+    at n = 64, where the AUTO plan's twelve-warp chunks are too tall for the Q passes, tsqr_qr
+    factorizes with four warps and reports it; a call that fails reports a zero plan."""
+    import torch
+    m = 200003
+    Ad = workloads.gaussian(m, 64, seed=12).cuda().T
+    R1 = T.tsqr_r(Ad).clone()
+    p = T.last_plan()
+    auto = T.tsqr_resolve_plan(m, 64)
+    assert (p.tree, p.tile_rows, p.ctas, p.warps, p.arity) == \
+        (auto.tree, auto.tile_rows, auto.ctas, auto.warps, auto.arity)
+    assert torch.equal(T.tsqr_r_ex(Ad, plan=p), R1)
+    Q, R = T.tsqr_qr(Ad)
+    q = T.last_plan()
+    assert q.warps == 4 and auto.warps == 12
+    assert torch.equal(T.tsqr_r_ex(Ad, plan=q), R)
+    with pytest.raises(T.TsqrError):
+        T.tsqr_qr(torch.zeros(8, 4, dtype=torch.float64, device="cuda").T)
+    z = T.last_plan()
+    assert (z.tree, z.tile_rows, z.ctas, z.warps, z.arity) == (0, 0, 0, 0, 0)
+
