@@ -64,9 +64,17 @@ typedef enum { TSQR_PREC_F64 = 0, TSQR_PREC_MIXED = 1 } tsqr_prec_t;
  * FLAT:   one CTA folds every tile in row order, R <- R([R; A_t]) (the tile algorithms' tree).
  * HYBRID: `ctas` CTAs each fold a contiguous run of tiles flat, their R factors then reduced
  *         by a fixed tree of `arity` children per node (children in index order, the lowest on
- *         top; a lone last child promoted unchanged).  AUTO picks HYBRID.                    */
+ *         top; a lone last child promoted unchanged).
+ * PANELS: FP64 R only (tsqr_r, tsqr_r_ex with F64/F64): the columns in panels of `tile_rows`
+ *         columns (0 = 16), each panel's R by its own TSQR reduction (AUTO plan, reflectors
+ *         kept) and its Q^T applied to the columns right of it, as tsqr_caqr_r does (Section
+ *         5's panel and update).  R equals one reduction's up to rounding.
+ * AUTO picks HYBRID, or PANELS for FP64 R with n >= 56 and m >= 8 n, where it measured faster
+ * (4,194,304 rows, n = 56 / 64 / 96 / 128: 775 / 828 / 863 / 887 against 727 / 750 / 555 / 586
+ * GFLOP/s; at n = 48 one reduction is faster, 826 against 802).                           */
 typedef enum {
-    TSQR_TREE_AUTO = 0, TSQR_TREE_BINARY = 1, TSQR_TREE_FLAT = 2, TSQR_TREE_HYBRID = 3
+    TSQR_TREE_AUTO = 0, TSQR_TREE_BINARY = 1, TSQR_TREE_FLAT = 2, TSQR_TREE_HYBRID = 3,
+    TSQR_TREE_PANELS = 4
 } tsqr_tree_t;
 
 /* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic

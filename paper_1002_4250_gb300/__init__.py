@@ -25,9 +25,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtsqr.so")
 SUCCESS, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, STATUS_NONFINITE = range(7)
 F64, F32, BF16 = 0, 1, 2
 PREC_F64, PREC_MIXED = 0, 1
-TREE_AUTO, TREE_BINARY, TREE_FLAT, TREE_HYBRID = 0, 1, 2, 3
+TREE_AUTO, TREE_BINARY, TREE_FLAT, TREE_HYBRID, TREE_PANELS = 0, 1, 2, 3, 4
 MAX_N = 128
-_TREES = {"auto": TREE_AUTO, "binary": TREE_BINARY, "flat": TREE_FLAT, "hybrid": TREE_HYBRID}
+_TREES = {"auto": TREE_AUTO, "binary": TREE_BINARY, "flat": TREE_FLAT, "hybrid": TREE_HYBRID,
+          "panels": TREE_PANELS}
 
 
 class Plan(ctypes.Structure):

@@ -320,7 +320,9 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     const DeviceInfo di = device_info(dev);
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     tsqr_plan_t tuned;
-    if (plan_is_auto(over) && tuned_plan(dev, m, n, mixed, &tuned)) over = &tuned;
+    if (plan_is_auto(over) && tuned_plan(dev, m, n, mixed, &tuned) &&
+        tuned.tree != TSQR_TREE_PANELS)
+        over = &tuned;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
     // bulk warps: 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep gains
@@ -384,12 +386,48 @@ tsqr_status_t zero_r(double *R, int64_t n, int64_t ldr, cudaStream_t stream) {
     return TSQR_SUCCESS;
 }
 
+tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, double *R,
+                       int64_t ldr, int64_t nb, const tsqr_plan_t *over, cudaStream_t stream);
+
+// Panels (TSQR_TREE_PANELS): the AUTO plan of a tall FP64 matrix from n = 56 on, where the one
+// reduction's leaves hold one CTA per SM and n reflectors per chunk, while panels of 16 columns
+// (each a TSQR reduction of its own, then Q^T applied to the columns right of it) keep the
+// leaves small and the updates blocked: 4,194,304 rows, n = 56 / 64 / 96 / 128: 775 / 828 /
+// 863 / 887 against 727 / 750 / 555 / 586 GFLOP/s (n = 48: 802 against 826, so one reduction
+// below 56).  Returns the panel width, or 0 for one reduction.
+constexpr int kPanelsMinN = 56;
+constexpr int kPanelsWidth = 16;
+
+int64_t panels_width(int64_t m, int64_t n, const tsqr_plan_t *over, int dev) {
+    tsqr_plan_t tuned;
+    if (plan_is_auto(over) && tuned_plan(dev, m, (int)n, false, &tuned)) over = &tuned;
+    if (over && over->tree == TSQR_TREE_PANELS)
+        return over->tile_rows > 0 ? over->tile_rows : kPanelsWidth;
+    if (plan_is_auto(over) && n >= kPanelsMinN && m >= 8 * n) return kPanelsWidth;
+    return 0;
+}
+
 tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
                       const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
     g_last_plan = tsqr_plan_t{};
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) return zero_r(R, n, ldr, stream);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+        const int64_t nb = panels_width(m, n, over, dev);
+        if (nb > 0) {
+            if (nb > TSQR_MAX_N || m < n) return TSQR_ERR_INVALID_ARG;
+            const tsqr_status_t st = run_caqr(A, m, n, lda, R, ldr, nb, nullptr, stream);
+            g_last_plan = tsqr_plan_t{};
+            if (st == TSQR_SUCCESS) {
+                g_last_plan.tree = TSQR_TREE_PANELS;
+                g_last_plan.tile_rows = (int32_t)nb;
+            }
+            return st;
+        }
+    }
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
@@ -1659,6 +1697,17 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
     const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
     const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
     if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
+    if (f64 && m > 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+        const int64_t nb = panels_width(m, n, plan, dev);
+        if (nb > 0) {
+            *out = tsqr_plan_t{};
+            out->tree = TSQR_TREE_PANELS;
+            out->tile_rows = (int32_t)nb;
+            return TSQR_SUCCESS;
+        }
+    }
     F64Plan p;
     tsqr_status_t st = plan_leaf(m, (int)n, plan, mixed, &p);
     if (st != TSQR_SUCCESS) return st;
@@ -1710,6 +1759,8 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
             }
         }
     }
+    if (f64 && n >= 48 && m >= 8 * n)
+        for (int32_t nb : {16, 32}) cands.push_back(tsqr_plan_t{TSQR_TREE_PANELS, nb, 0, 0, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return TSQR_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {

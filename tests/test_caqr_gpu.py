@@ -128,6 +128,24 @@ def test_caqr_large_properties(oracle, T):
     assert np.all(np.abs(Gr - G) <= tol * np.outer(cn, cn))
 
 
+def test_caqr_rank_deficient_and_nonfinite(oracle, T):
+    """Rank-deficient A (a zero column, two equal columns) has no unique R beyond the rank, but
+    R^T R = A^T A still holds; a NaN in A is reported as TSQR_STATUS_NONFINITE."""
+    import torch
+    At = workloads.gaussian(30000, 70, seed=13)
+    At[5] = 0.0
+    At[40] = At[7]
+    A = oracle.from_torch_colmajor(At)
+    R = T.tsqr_caqr_r(At.cuda().T, panel=16).cpu().numpy()
+    assert np.all(np.isfinite(R)) and np.all(np.diag(R) >= 0.0)
+    assert oracle.gram_residual(A, R, nthreads=16) <= 1e-13
+    T.tsqr_get_device_status()  # clears the status word
+    At[3, 1234] = float("nan")
+    T.tsqr_caqr_r(At.cuda().T, panel=16)
+    torch.cuda.synchronize()
+    assert T.tsqr_get_device_status() == T.STATUS_NONFINITE
+
+
 def test_caqr_argument_errors(T):
     import torch
     A = torch.zeros(8, 100, dtype=torch.float64, device="cuda").T

@@ -140,6 +140,30 @@ def test_bit_reproducible(T):
         assert torch.equal(a, b), tree
 
 
+@pytest.mark.parametrize("m,n", [(40000, 64), (100003, 96), (65537, 128), (30011, 80)])
+def test_auto_panels_wide(oracle, T, m, n):
+    """From n = 64 on, the AUTO plan of a tall FP64 matrix takes the columns in panels of 16
+    (each a TSQR reduction, then the update of the columns right of it): the resolved plan says
+    so, R keeps parity with the oracle, equals the explicit panels plan's bytes, and the one
+    reduction (an explicit HYBRID plan) keeps parity too."""
+    import torch
+    At = workloads.gaussian(m, n, seed=n + 1)
+    A = oracle.from_torch_colmajor(At)
+    p = T.tsqr_resolve_plan(m, n)
+    assert p.tree == T.TREE_PANELS and p.tile_rows == 16
+    R = T.tsqr_r(_gpu(At))
+    Ro = oracle.householder_r(A, nthreads=16)
+    _assert_parity(oracle, A, R, R_ref=Ro, nthreads=16)
+    assert torch.equal(T.tsqr_r_ex(_gpu(At), plan=T.make_plan("panels", tile_rows=16)), R)
+    l = T.last_plan()
+    assert (l.tree, l.tile_rows) == (T.TREE_PANELS, 16)
+    _assert_parity(oracle, A, T.tsqr_r_ex(_gpu(At), plan=T.make_plan("hybrid")), R_ref=Ro,
+                   nthreads=16)
+    assert T.tsqr_resolve_plan(4 * n, n).tree == T.TREE_HYBRID  # not tall enough: one reduction
+    with pytest.raises(T.TsqrError):  # panels are for FP64 R only
+        T.tsqr_qr(_gpu(At), plan=T.make_plan("panels"))
+
+
 def test_tree_independence(T, oracle):
     """Section 2: the tree changes neither the result (beyond rounding) nor its stability."""
     At = workloads.gaussian(100000, 24, seed=2)

@@ -150,9 +150,10 @@ def test_qr_rank_deficient(oracle, T):
 
 
 def test_last_plan(T):
-    """tsqr_last_plan: tsqr_r's is the resolved AUTO plan and, passed back, gives the same bytes;
-    at n = 64, where the AUTO plan's twelve-warp chunks are too tall for the Q passes, tsqr_qr
-    factorizes with four warps and reports it; a call that fails reports a zero plan."""
+    """tsqr_last_plan: tsqr_r's is the resolved AUTO plan (panels at n = 64) and, passed back,
+    gives the same bytes; tsqr_qr factorizes with one reduction, and where that plan's
+    twelve-warp chunks are too tall for the Q passes (n = 64) with four warps, and reports it; a
+    call that fails reports a zero plan."""
     import torch
     m = 200003
     Ad = workloads.gaussian(m, 64, seed=12).cuda().T
@@ -164,7 +165,9 @@ def test_last_plan(T):
     assert torch.equal(T.tsqr_r_ex(Ad, plan=p), R1)
     Q, R = T.tsqr_qr(Ad)
     q = T.last_plan()
-    assert q.warps == 4 and auto.warps == 12
+    assert auto.tree == T.TREE_PANELS and auto.tile_rows == 16
+    assert q.tree == T.TREE_HYBRID and q.warps == 4
+    assert T.tsqr_resolve_plan(m, 64, plan=T.make_plan("hybrid")).warps == 12
     assert torch.equal(T.tsqr_r_ex(Ad, plan=q), R)
     with pytest.raises(T.TsqrError):
         T.tsqr_qr(torch.zeros(8, 4, dtype=torch.float64, device="cuda").T)
