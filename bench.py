@@ -398,7 +398,8 @@ def bench_lstsq(dev):
 def bench_qr(dev):
     """tsqr_qr (thin Q and R, FP64) on 4,194,304 x 32 and 16,777,216 x 64: time, GFLOP/s with
     LAPACK's counts (geqrf 2mn^2 - 2n^3/3 plus orgqr 2mn^2 - 2n^3/3), the Q passes' share
-    (tsqr_qr minus tsqr_r with the same plan), and the Q passes' FP64 rate on the flops the
+    (tsqr_qr minus tsqr_r_ex with the plan tsqr_qr's factorization used), and the Q passes'
+    FP64 rate on the flops the
     blocked form executes (3mn^2: mn^2 for the chunks' S factors, 2mn^2 for the leaf pass)."""
     import torch
     import paper_1002_4250_gb300 as T
@@ -410,7 +411,8 @@ def bench_qr(dev):
         R = T.empty_r(n, dev)
         reps = 5 if n <= 32 else 2
         ms_qr = time_call(lambda: T.tsqr_qr(A, Q=Q, R=R), reps=reps, warmup=1)
-        ms_r = time_call(lambda: T.tsqr_r(A, R=R), reps=reps, warmup=1)
+        used = T.last_plan()  # the factorization's plan: R alone timed with the same one
+        ms_r = time_call(lambda: T.tsqr_r_ex(A, R=R, plan=used), reps=reps, warmup=1)
         fl = 4.0 * m * n * n - 4.0 * n ** 3 / 3
         res[f"{m}x{n}"] = {"ms": ms_qr, "gflops_lapack_count": fl / ms_qr / 1e6,
                            "r_only_ms": ms_r, "q_passes_ms": ms_qr - ms_r,
