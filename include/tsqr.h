@@ -96,7 +96,8 @@ typedef void *tsqr_stream_t; /* a cudaStream_t */
 /* R factor of the m x n FP64 matrix A (Section 2, steps 1 and 2).
  *   A   : device, column-major, lda >= max(1, m); read only.
  *   m   : rows, m >= 0 (m = 0 gives R = 0; m < n gives rows m..n-1 of R equal to zero).
- *   n   : columns, 0 <= n <= TSQR_MAX_N (n = 0 does nothing).
+ *   n   : columns, 0 <= n <= TSQR_MAX_N (n = 0 does nothing); above TSQR_MAX_N, any n <= m,
+ *         by panels (the PANELS tree, as tsqr_caqr_r), else TSQR_ERR_UNSUPPORTED.
  *   R   : device, column-major n x n, ldr >= max(1, n); fully written.
  * Uses the AUTO plan.  Returns TSQR_SUCCESS once the work is enqueued.                     */
 tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
@@ -183,8 +184,13 @@ tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double
  * triangular solve follows; R then equals tsqr_r's up to rounding.  Otherwise the columns of B
  * go k_g = min(k, n) at a time (two launches per group after the factorization) and R is
  * tsqr_r's bit for bit.
+ * Above TSQR_MAX_N columns (AUTO plan only) [A | B] is copied to a buffer allocated for the
+ * call (stream-ordered, m (n + k) doubles, plus (n + k)^2 for its R) and factorized by panels
+ * as tsqr_caqr_r does; its R holds R and (Q^T B)(0:n, :) side by side, then one triangular
+ * solve.  R then equals tsqr_caqr_r's on A up to rounding.
  * A zero on R's diagonal (rank deficiency) makes X non-finite and the device status
- * TSQR_STATUS_NONFINITE.  Returns TSQR_ERR_UNSUPPORTED where tsqr_qr does. */
+ * TSQR_STATUS_NONFINITE.  Returns TSQR_ERR_UNSUPPORTED where tsqr_qr does (n <= TSQR_MAX_N), or
+ * for an explicit plan above TSQR_MAX_N columns. */
 tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
                          int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                          const tsqr_plan_t *plan, tsqr_stream_t stream);

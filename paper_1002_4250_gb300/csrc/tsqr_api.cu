@@ -403,7 +403,8 @@ int64_t panels_width(int64_t m, int64_t n, const tsqr_plan_t *over, int dev) {
     if (plan_is_auto(over) && tuned_plan(dev, m, (int)n, false, &tuned)) over = &tuned;
     if (over && over->tree == TSQR_TREE_PANELS)
         return over->tile_rows > 0 ? over->tile_rows : kPanelsWidth;
-    if (plan_is_auto(over) && n >= kPanelsMinN && m >= 8 * n) return kPanelsWidth;
+    if (plan_is_auto(over) && (n > TSQR_MAX_N || (n >= kPanelsMinN && m >= 8 * n)))
+        return kPanelsWidth;  // past TSQR_MAX_N only panels run
     return 0;
 }
 
@@ -418,7 +419,8 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
         if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
         const int64_t nb = panels_width(m, n, over, dev);
         if (nb > 0) {
-            if (nb > TSQR_MAX_N || m < n) return TSQR_ERR_INVALID_ARG;
+            if (nb > TSQR_MAX_N) return TSQR_ERR_INVALID_ARG;
+            if (m < n) return n > TSQR_MAX_N ? TSQR_ERR_UNSUPPORTED : TSQR_ERR_INVALID_ARG;
             const tsqr_status_t st = run_caqr(A, m, n, lda, R, ldr, nb, nullptr, stream);
             g_last_plan = tsqr_plan_t{};
             if (st == TSQR_SUCCESS) {
@@ -428,6 +430,7 @@ tsqr_status_t run_f64(const double *A, int64_t m, int64_t n, int64_t lda, double
             return st;
         }
     }
+    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
@@ -784,11 +787,6 @@ tsqr_status_t run_lstsq_augmented(const double *A, int64_t m, int64_t n, int64_t
     return TSQR_SUCCESS;
 }
 
-// Least squares: the factorization with its reflectors kept (as tsqr_qr's, with the tails in
-// the workspace), then per group of at most n columns of B: Q^T B's first n rows (one launch,
-// tsqr_qr.cu) and R X = those rows (one launch).  Workspace: counters | slots | tails |
-// chunk scalars | node tails | node scalars | signs | apply counters | apply slots | C | R.
-// With k <= max(1, n / 4) and n + k <= TSQR_MAX_N the augmented factorization above is used.
 // Compact WY factors fit when a chunk's scaled tails and two n x n blocks fit one CTA; the
 // blocked apply then takes as many update columns per CTA as fit beside the chunk.
 bool plan_wy(int w, const F64Plan &p, const DeviceInfo &di, int *ldX, size_t *wy_smem, int *kc,
@@ -934,6 +932,11 @@ tsqr_status_t run_lstsq_wy(const double *A, int64_t m, int64_t n, int64_t lda, c
     return TSQR_SUCCESS;
 }
 
+// Least squares: the factorization with its reflectors kept (as tsqr_qr's, with the tails in
+// the workspace), then Q^T B's first n rows and R X = those rows: with the blocked apply, one
+// launch over every column of B (run_lstsq_wy); otherwise per group of at most n columns of B,
+// two launches.  With k <= max(1, n / 4) and n + k <= TSQR_MAX_N the augmented factorization
+// above is used, and above TSQR_MAX_N columns the panels of run_lstsq_panels.
 tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
                         int64_t ldb, int64_t k, double *X, int64_t ldx, double *R, int64_t ldr,
                         const tsqr_plan_t *over, cudaStream_t stream) {
@@ -1287,6 +1290,49 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
     return TSQR_SUCCESS;
 }
 
+// Least squares above TSQR_MAX_N columns: [A | B] (copied to a buffer of this call) by panels,
+// as tsqr_caqr_r; its R holds R and (Q^T B)(0:n, :) side by side (the sign convention negates
+// whole rows, which keeps R X = C), then R X = C.  The copy and the augmented R are allocated
+// stream-ordered for the call, since the panels take the stream's pooled workspace themselves.
+tsqr_status_t run_lstsq_panels(const double *A, int64_t m, int64_t n, int64_t lda,
+                               const double *B, int64_t ldb, int64_t k, double *X, int64_t ldx,
+                               double *R, int64_t ldr, cudaStream_t stream) {
+    const int64_t na = n + k;
+    double *aug = nullptr, *Ra = nullptr;
+    if (cudaMallocAsync((void **)&aug, (size_t)m * na * sizeof(double), stream) != cudaSuccess)
+        return TSQR_ERR_ALLOC;
+    if (cudaMallocAsync((void **)&Ra, (size_t)na * na * sizeof(double), stream) != cudaSuccess) {
+        cudaFreeAsync(aug, stream);
+        return TSQR_ERR_ALLOC;
+    }
+    tsqr_status_t st = TSQR_SUCCESS;
+    if (cudaMemcpy2DAsync(aug, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                          (size_t)m * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice,
+                          stream) != cudaSuccess ||
+        (k > 0 && cudaMemcpy2DAsync(aug + n * m, (size_t)m * sizeof(double), B,
+                                    (size_t)ldb * sizeof(double), (size_t)m * sizeof(double),
+                                    (size_t)k, cudaMemcpyDeviceToDevice, stream) != cudaSuccess))
+        st = TSQR_ERR_CUDA;
+    int launches = 0;
+    if (st == TSQR_SUCCESS) {
+        st = run_caqr(aug, m, na, m, Ra, na, kCaqrPanel, nullptr, stream);
+        launches = g_last_launches;
+    }
+    Workspace *ws = nullptr;
+    if (st == TSQR_SUCCESS) st = get_workspace(stream, 0, &ws);
+    if (st == TSQR_SUCCESS &&
+        ((R && cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Ra, (size_t)na * sizeof(double),
+                                 (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice,
+                                 stream) != cudaSuccess) ||
+         (k > 0 && trsm_launch(Ra, na, Ra + n * na, na, X, ldx, (int)n, (int)k, ws->status,
+                               stream) != cudaSuccess)))
+        st = TSQR_ERR_CUDA;
+    cudaFreeAsync(aug, stream);
+    cudaFreeAsync(Ra, stream);
+    g_last_launches = st == TSQR_SUCCESS ? launches + (k > 0 ? 1 : 0) : 0;
+    return st;
+}
+
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
@@ -1500,7 +1546,7 @@ tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double 
     g_last_launches = 0;
     g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
-    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > TSQR_MAX_N && (m < n || n > 0x7fffffffLL)) return TSQR_ERR_UNSUPPORTED;
     if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
     return run_f64(A, m, n, lda, R, ldr, nullptr, (cudaStream_t)stream);
 }
@@ -1513,10 +1559,10 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
     if (dtype < TSQR_F64 || dtype > TSQR_BF16 || prec < TSQR_PREC_F64 || prec > TSQR_PREC_MIXED)
         return TSQR_ERR_INVALID_ARG;
-    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    const bool f64 = dtype == TSQR_F64 && prec == TSQR_PREC_F64;
+    if (n > TSQR_MAX_N && (!f64 || m < n || n > 0x7fffffffLL)) return TSQR_ERR_UNSUPPORTED;
     if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
-    if (dtype == TSQR_F64 && prec == TSQR_PREC_F64)
-        return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
+    if (f64) return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
     if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
     return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
 }
@@ -1566,7 +1612,10 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
         ldb < std::max<int64_t>(1, m) || ldx < n || (R && ldr < n))
         return TSQR_ERR_INVALID_ARG;
     if (!A || (k > 0 && (!B || !X))) return TSQR_ERR_INVALID_ARG;
-    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > TSQR_MAX_N) {
+        if (!plan_is_auto(plan) || n + k > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
+        return run_lstsq_panels(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, (cudaStream_t)stream);
+    }
     return run_lstsq(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, plan, (cudaStream_t)stream);
 }
 
@@ -1693,8 +1742,8 @@ tsqr_status_t tsqr_last_plan(tsqr_plan_t *out) {
 tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t prec,
                                 const tsqr_plan_t *plan, tsqr_plan_t *out) {
     if (!out || m < 0 || n < 1) return TSQR_ERR_INVALID_ARG;
-    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
     const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
+    if (n > TSQR_MAX_N && (!f64 || m < n)) return TSQR_ERR_UNSUPPORTED;
     const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
     if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
     if (f64 && m > 0) {

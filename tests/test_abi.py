@@ -53,6 +53,7 @@ def test_host_side_argument_errors(lib):
     ]
     for A, m, n, lda, R, ldr in bad:
         assert c.tsqr_r(A, m, n, lda, R, ldr, None) == lib.ERR_INVALID_ARG
+    # above TSQR_MAX_N columns only tall matrices (by panels) are supported
     assert c.tsqr_r(None, 10, 129, 10, None, 129, None) == lib.ERR_UNSUPPORTED
     # n == 0 is a no-op
     assert c.tsqr_r(None, 10, 0, 10, None, 1, None) == lib.SUCCESS

@@ -146,6 +146,23 @@ def test_caqr_rank_deficient_and_nonfinite(oracle, T):
     assert T.tsqr_get_device_status() == T.STATUS_NONFINITE
 
 
+def test_tsqr_r_beyond_128_columns_is_panels(oracle, T):
+    """tsqr_r and tsqr_r_ex take any tall n by panels: above 128 columns the AUTO plan is
+    PANELS, and R equals tsqr_caqr_r's with the default panel byte for byte."""
+    import torch
+    At = workloads.gaussian(25000, 200, seed=14)
+    Ad = At.cuda().T
+    R = T.tsqr_r(Ad)
+    assert torch.equal(R, T.tsqr_caqr_r(Ad))
+    assert torch.equal(T.tsqr_r_ex(Ad), R)
+    p = T.tsqr_resolve_plan(25000, 200)
+    assert (p.tree, p.tile_rows) == (T.TREE_PANELS, 16)
+    _check(oracle, T, At)
+    with pytest.raises(T.TsqrError) as e:  # wide (m < n) above 128 columns
+        T.tsqr_r(torch.zeros(200, 150, dtype=torch.float64, device="cuda").T)
+    assert e.value.status == T.ERR_UNSUPPORTED
+
+
 def test_caqr_argument_errors(T):
     import torch
     A = torch.zeros(8, 100, dtype=torch.float64, device="cuda").T

@@ -99,6 +99,27 @@ def test_lstsq_vector_and_more_columns_than_n(oracle, T):
     _check(oracle, T, At, _bmat(30000, 130, seed=4))
 
 
+@pytest.mark.parametrize("m,n,k", [(20000, 200, 3), (30011, 150, 40), (5000, 129, 1)])
+def test_lstsq_wide_by_panels(oracle, T, m, n, k):
+    """Above 128 columns [A | B] is factorized by panels (as tsqr_caqr_r) and R X = C solved:
+    X within the least-squares bound of the oracle's, with c(m, n) = max(50, 2 sqrt(m n / 32))
+    as for the panels' R."""
+    At = workloads.gaussian(m, n, seed=n)
+    Bt = _bmat(m, k, seed=k)
+    A = oracle.from_torch_colmajor(At)
+    Bn = oracle.from_torch_colmajor(Bt)
+    X, R = T.tsqr_lstsq(At.cuda().T, Bt.cuda().T)
+    Xh = X.cpu().numpy()
+    Xo = oracle.lstsq(A, Bn, nthreads=16)
+    Ro = oracle.householder_r(A, nthreads=16)
+    kap = oracle.kappa_from_r(Ro)
+    c = max(50.0, 2.0 * np.sqrt(m * n / 32.0))
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, rtol=0, atol=c * kap * U * np.linalg.norm(Ro))
+    res = np.linalg.norm(Bn - A @ Xo)
+    tol = c * (kap + kap ** 2 * res / (np.linalg.norm(A, 2) * np.linalg.norm(Xo))) * U
+    assert np.linalg.norm(Xh - Xo) <= tol * np.linalg.norm(Xo)
+
+
 def test_lstsq_rank_deficient_and_errors(T):
     import torch
     At = workloads.gaussian(5000, 4, seed=1)
