@@ -111,7 +111,9 @@ tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double 
  * piece's arrival flag before loading from it (a bounded wait; on timeout the device status
  * becomes TSQR_ERR_TIMEOUT and R is not written), and then climb the usual tree.  With pageable
  * A, A is copied whole and the ordinary kernel runs.  The plan is the AUTO plan; the
- * round-robin rows give an R equal to tsqr_r's up to rounding (not bit for bit).
+ * round-robin rows give an R equal to tsqr_r's up to rounding (not bit for bit).  Where the
+ * AUTO plan runs by panels (n >= 56, m >= 8 n), A is copied whole to a buffer of the call
+ * (stream-ordered) and the panels run on it, as tsqr_r does (R then equals tsqr_r's bytes).
  *   A : host, column-major m x n, lda >= m.
  *   R : host, column-major n x n, ldr >= n, written as by tsqr_r.
  * Asynchronous on `stream` like tsqr_r: A must not be modified, nor R read, until the stream

@@ -637,6 +637,45 @@ const unsigned int *host_ones() {
 // pieces on a copy stream while one streaming launch (tsqr_host.cu) already folds the pieces
 // that have arrived; otherwise A is copied whole and the ordinary kernel runs.  The plan is the
 // AUTO plan.  Workspace: counters | tree slots | piece flags | A (ld m) | R (ld n).
+// Host input where the AUTO plan runs by panels (n >= 56, tall): A copied whole into a buffer
+// of this call (stream-ordered; the panels take the stream's pooled workspace themselves), the
+// panels, and R copied back.  The panels' updates need every column, so there is no piece-wise
+// overlap as in the one reduction's streaming kernel.
+tsqr_status_t run_host_panels(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
+                              int64_t ldr, int64_t nb, cudaStream_t stream) {
+    double *Ad = nullptr, *Rd = nullptr;
+    if (cudaMallocAsync((void **)&Ad, (size_t)m * n * sizeof(double), stream) != cudaSuccess)
+        return TSQR_ERR_ALLOC;
+    if (cudaMallocAsync((void **)&Rd, (size_t)n * n * sizeof(double), stream) != cudaSuccess) {
+        cudaFreeAsync(Ad, stream);
+        return TSQR_ERR_ALLOC;
+    }
+    tsqr_status_t st = TSQR_SUCCESS;
+    if (cudaMemcpy2DAsync(Ad, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                          (size_t)m * sizeof(double), (size_t)n, cudaMemcpyHostToDevice,
+                          stream) != cudaSuccess)
+        st = TSQR_ERR_CUDA;
+    int launches = 0;
+    if (st == TSQR_SUCCESS) {
+        st = run_caqr(Ad, m, n, m, Rd, n, nb, nullptr, stream);
+        launches = g_last_launches;
+    }
+    if (st == TSQR_SUCCESS &&
+        cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Rd, (size_t)n * sizeof(double),
+                          (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost,
+                          stream) != cudaSuccess)
+        st = TSQR_ERR_CUDA;
+    cudaFreeAsync(Ad, stream);
+    cudaFreeAsync(Rd, stream);
+    g_last_launches = st == TSQR_SUCCESS ? launches : 0;
+    g_last_plan = tsqr_plan_t{};
+    if (st == TSQR_SUCCESS) {
+        g_last_plan.tree = TSQR_TREE_PANELS;
+        g_last_plan.tile_rows = (int32_t)nb;
+    }
+    return st;
+}
+
 tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                            int64_t ldr, cudaStream_t stream) {
     g_last_launches = 0;
@@ -646,6 +685,12 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
         for (int64_t c = 0; c < n; ++c)
             for (int64_t i = 0; i < n; ++i) R[i + c * ldr] = 0.0;
         return TSQR_SUCCESS;
+    }
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+        const int64_t nb = panels_width(m, n, nullptr, dev);
+        if (nb > 0) return run_host_panels(A, m, n, lda, R, ldr, nb, stream);
     }
     cudaPointerAttributes attr;
     const bool pinned = cudaPointerGetAttributes(&attr, A) == cudaSuccess &&
@@ -1636,7 +1681,7 @@ tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, do
     g_last_launches = 0;
     g_last_plan = tsqr_plan_t{};
     if (bad_dims(m, n, lda, ldr)) return TSQR_ERR_INVALID_ARG;
-    if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
+    if (n > TSQR_MAX_N && (m < n || n > 0x7fffffffLL)) return TSQR_ERR_UNSUPPORTED;
     if (n > 0 && (!R || (m > 0 && !A))) return TSQR_ERR_INVALID_ARG;
     return run_f64_host(A, m, n, lda, R, ldr, (cudaStream_t)stream);
 }

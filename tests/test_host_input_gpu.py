@@ -42,6 +42,24 @@ def test_host_input_parity(oracle, T, m, n, pinned):
     _check(oracle, oracle.from_torch_colmajor(At), R.numpy())
 
 
+@pytest.mark.parametrize("m,n,pinned", [(200003, 96, True), (50000, 200, False)])
+def test_host_input_by_panels(oracle, T, m, n, pinned):
+    """Where the AUTO plan runs by panels (n >= 56, tall; and every n above 128), host A is
+    copied whole and the panels run on it: R equals tsqr_r's bytes on the device copy."""
+    import torch
+    At = workloads.gaussian(m, n, seed=n)
+    Ah = At.pin_memory() if pinned else At
+    R = T.tsqr_r_host(Ah.T)
+    torch.cuda.synchronize()
+    p = T.last_plan()
+    assert (p.tree, p.tile_rows) == (T.TREE_PANELS, 16)
+    assert torch.equal(R, T.tsqr_r(At.cuda().T).cpu())
+    Ro = oracle.householder_r(oracle.from_torch_colmajor(At), nthreads=16)
+    c = max(50.0, 2.0 * np.sqrt(m * n / 32.0))
+    np.testing.assert_allclose(R.numpy(), Ro, rtol=0,
+                               atol=c * oracle.kappa_from_r(Ro) * U * np.linalg.norm(Ro))
+
+
 def test_host_input_leading_dimensions_and_empty(oracle, T):
     import torch
     m, n = 123457, 20
