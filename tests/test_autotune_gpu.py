@@ -60,3 +60,21 @@ def test_autotune_mixed(oracle, T):
     A = oracle.from_torch_colmajor(At.to(torch.float64))
     assert oracle.gram_residual(A, R, nthreads=16) <= 2e-6
     T.tsqr_autotune_reset()
+
+
+def test_autotune_wide_considers_panels(oracle, T):
+    """From n = 48 on the FP64 candidates include panels of 16 and 32 columns; whatever wins,
+    later AUTO calls of the bucket return its bytes, with parity; tsqr_qr keeps one reduction."""
+    import torch
+    m, n = 1 << 19, 96
+    At = workloads.gaussian(m, n, seed=23)
+    Ad = At.cuda().T
+    best = T.tsqr_autotune(Ad)
+    R = T.tsqr_r(Ad)
+    assert torch.equal(R, T.tsqr_r_ex(Ad, plan=best))
+    A = oracle.from_torch_colmajor(At)
+    assert oracle.gram_residual(A, R.cpu().numpy(), nthreads=16) <= 1e-13
+    T.tsqr_qr(Ad)
+    assert T.last_plan().tree == T.TREE_HYBRID
+    T.tsqr_autotune_reset()
+
