@@ -1193,6 +1193,38 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
                 break;
             }
         c.wy = plan_wy(c.w, c.p, di, &c.ldX, &c.wy_smem, &c.kc, &c.qt_smem);
+        if (plan_is_auto(over) && trail > 0 && c.wy) {
+            // The update's grid is L x G CTAs of equal work (G column groups), whole waves of
+            // SMs x (CTAs per SM) at a time: a leaf count within 15% of L that fills the last
+            // wave better wins (262,144 x 512: 2,288 CTAs in 15.05 waves of 152 left the
+            // sixteenth wave almost empty).
+            const int64_t G = (trail + c.kc - 1) / c.kc;
+            const int64_t slots =
+                (int64_t)di.sms * std::max<int64_t>(1, (int64_t)(di.smem_sm / (c.qt_smem + 1024)));
+            const int L = c.p.nleaves;
+            auto eff = [&](int64_t l) {
+                const int64_t ctas = l * G;
+                return (double)ctas / (double)(((ctas + slots - 1) / slots) * slots);
+            };
+            int bestL = L;
+            const int lo = std::max(1, (int)(0.85 * L)), hi = (int)std::min<int64_t>(
+                                                             c.p.nunits, (int64_t)(1.15 * L) + 1);
+            for (int l = lo; l <= hi; ++l)
+                if (eff(l) > eff(bestL) + 1e-9 ||
+                    (eff(l) > eff(bestL) - 1e-9 && std::abs(l - L) < std::abs(bestL - L)))
+                    bestL = l;
+            if (bestL != L) {
+                tsqr_plan_t o;
+                std::memset(&o, 0, sizeof(o));
+                o.tree = TSQR_TREE_HYBRID;
+                o.ctas = bestL;
+                o.warps = c.p.warps;
+                st = plan_f64(M, c.w, &o, &c.p);
+                if (st != TSQR_SUCCESS) return st;
+                if (c.p.unit % c.p.h != 0) return TSQR_ERR_UNSUPPORTED;
+                c.wy = plan_wy(c.w, c.p, di, &c.ldX, &c.wy_smem, &c.kc, &c.qt_smem);
+            }
+        }
         if (!c.wy) {
             // the reflector-by-reflector update; its columns are independent too: as many per
             // CTA as fit beside the chunk
