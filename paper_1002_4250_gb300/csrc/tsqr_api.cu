@@ -22,7 +22,7 @@ cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes, cu
 size_t wy_smem_bytes(int n, int ldX);
 cudaError_t wy_launch(const WyArgs &a, size_t smem_bytes, int grid, cudaStream_t stream);
 size_t qt_wy_smem_bytes(int n, int kc, int ldS);
-size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS);
+size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS, bool fused);
 cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t stream);
 cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream);
 cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t ldc, double *X,
@@ -493,9 +493,9 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     const size_t wy_smem = wy_smem_bytes((int)n, ldX);
     bool wyq = wy_smem <= di.smem_block_optin;
     if (wyq) {
-        while (qn > 8 && q_leaf_wy_smem_bytes((int)n, qn, p.ldS) > di.smem_block_optin)
+        while (qn > 8 && q_leaf_wy_smem_bytes((int)n, qn, p.ldS, false) > di.smem_block_optin)
             qn = (qn + 1) / 2;
-        wyq = q_leaf_wy_smem_bytes((int)n, qn, p.ldS) <= di.smem_block_optin;
+        wyq = q_leaf_wy_smem_bytes((int)n, qn, p.ldS, false) <= di.smem_block_optin;
         if (!wyq) qn = (int)n;
     }
     if (!wyq)
@@ -503,7 +503,10 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
             qn = (qn + 1) / 2;
     while (qg > 8 && q_tree_smem_bytes((int)n, p.arity, qg) > di.smem_block_optin)
         qg = (qg + 1) / 2;
-    const size_t leaf_smem = wyq ? q_leaf_wy_smem_bytes((int)n, qn, p.ldS)
+    // one column group: the leaf pass forms each chunk's S itself from the tails it loads anyway
+    const bool fuse = wyq && qn == n &&
+                      q_leaf_wy_smem_bytes((int)n, qn, p.ldS, true) <= di.smem_block_optin;
+    const size_t leaf_smem = wyq ? q_leaf_wy_smem_bytes((int)n, qn, p.ldS, fuse)
                                  : q_leaf_smem_bytes((int)n, qn, p.ldS, qwarps);
     const size_t tree_smem = q_tree_smem_bytes((int)n, p.arity, qg);
     if (leaf_smem > di.smem_block_optin || tree_smem > di.smem_block_optin)
@@ -512,7 +515,8 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     if (qr_prepare(p.smem, wyq ? 0 : leaf_smem, tree_smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t nchunks = (m + p.h - 1) / p.h;
     const size_t nn = (size_t)n * (size_t)n;
-    const size_t wys_bytes = wyq ? align_up((size_t)nchunks * nn * sizeof(double), 256) : 0;
+    const size_t wys_bytes =
+        (wyq && !fuse) ? align_up((size_t)nchunks * nn * sizeof(double), 256) : 0;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * nn * sizeof(double), 256);
     const size_t csc_bytes = align_up((size_t)nchunks * 2 * n * sizeof(double), 256);
@@ -556,7 +560,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
         return TSQR_ERR_CUDA;
     if (qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     int launches = 1;
-    if (wyq) {
+    if (wyq && !fuse) {
         WyArgs wa;
         wa.V = a.q.V;
         wa.ldv = a.q.ldv;
@@ -606,7 +610,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     l.single = (sh.levels == 1) ? 1 : 0;
     l.V = a.q.V;
     l.ldv = a.q.ldv;
-    l.wyS = wyS;
+    l.wyS = fuse ? nullptr : wyS;
     for (int q0 = 0; q0 < n; q0 += qn) {
         l.q0 = q0;
         l.qn = (int)std::min<int64_t>(qn, n - q0);
@@ -859,7 +863,7 @@ tsqr_status_t plan_store(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) 
     int ldX = 0, kc = 0;
     size_t wy = 0, qt = 0;
     if (plan_wy(n, *p, di, &ldX, &wy, &kc, &qt) &&
-        q_leaf_wy_smem_bytes(n, std::min(n, 8), p->ldS) <= di.smem_block_optin)
+        q_leaf_wy_smem_bytes(n, std::min(n, 8), p->ldS, false) <= di.smem_block_optin)
         return st;
     tsqr_plan_t w4{};
     w4.warps = 4;

@@ -567,13 +567,57 @@ __global__ void __launch_bounds__(416, 1) tsqr_qt_kernel(const QtArgs a) {
 // column, S(0:J,J) = -tau_J S(0:J,0:J) G(0:J,J): row i of S needs only row i's earlier entries,
 // so a lane owns a row.
 // ------------------------------------------------------------------------------------------
+// G(i,J) = x_i . x_J for i < J over the first `rows` rows of the scaled tails X (ldX x n): one
+// pair per thread, column by column, two accumulators.
+__device__ __forceinline__ void wy_gram(const double *X, const int ldX, const int rows,
+                                        const int n, double *G) {
+    const int npairs = n * (n - 1) / 2;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        // pair p -> (i, J), i < J, column by column: J = the largest with J(J-1)/2 <= p
+        int J = (int)((1.0 + sqrt(1.0 + 8.0 * p)) * 0.5);
+        while (J * (J - 1) / 2 > p) --J;
+        while ((J + 1) * J / 2 <= p) ++J;
+        const int i = p - J * (J - 1) / 2;
+        const double *xi = X + i * ldX, *xj = X + J * ldX;
+        double d0 = 0.0, d1 = 0.0;
+        int r = 0;
+        for (; r + 1 < rows; r += 2) {
+            d0 = fma(xi[r], xj[r], d0);
+            d1 = fma(xi[r + 1], xj[r + 1], d1);
+        }
+        if (r < rows) d0 = fma(xi[r], xj[r], d0);
+        G[i + J * n] = d0 + d1;
+    }
+}
+
+// S from G and the chunk's tau (sc[2J]), column by column: column J's rows i < J each by a team
+// of tpr lanes (the sum over k = i .. J-1 strided over the team, then a fixed butterfly).  G must
+// be complete (a barrier before); S is complete after the call's last barrier.
+__device__ __forceinline__ void wy_s_from_g(const double *G, const double *sc, const int n,
+                                            double *S) {
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        for (int i = 0; i < n; ++i) S[i + idx * n] = (i == idx) ? sc[2 * idx] : 0.0;
+    }
+    for (int J = 1; J < n; ++J) {
+        __syncthreads();  // columns 0 .. J-1 are complete
+        int tpr = 1;
+        while (tpr < 32 && 2 * tpr * J <= (int)blockDim.x) tpr *= 2;
+        const int team = threadIdx.x / tpr, sub = threadIdx.x - team * tpr;
+        const int i = team < J ? team : J - 1;  // spare teams shadow the last row
+        double v = 0.0;
+        for (int k = i + sub; k < J; k += tpr) v = fma(S[i + k * n], G[k + J * n], v);
+        for (int o = tpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, tpr);
+        if (team < J && sub == 0) S[i + J * n] = -sc[2 * J] * v;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) tsqr_wy_kernel(const WyArgs a) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n, ldX = a.ldX;
     double *X = smem;               // ldX x n
     double *G = smem + ldX * n;     // n x n (strict upper triangle used)
     double *S = G + n * n;          // n x n
-    const int npairs = n * (n - 1) / 2;
     for (int64_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
         const int64_t row0 = c * a.h;
         const int rows = (int)((a.m - row0 < a.h) ? a.m - row0 : a.h);
@@ -590,40 +634,9 @@ __global__ void __launch_bounds__(256) tsqr_wy_kernel(const WyArgs a) {
             X[i + J * ldX] *= sc[2 * J + 1];
         }
         __syncthreads();
-        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-            // pair p -> (i, J), i < J, column by column: J = the largest with J(J-1)/2 <= p
-            int J = (int)((1.0 + sqrt(1.0 + 8.0 * p)) * 0.5);
-            while (J * (J - 1) / 2 > p) --J;
-            while ((J + 1) * J / 2 <= p) ++J;
-            const int i = p - J * (J - 1) / 2;
-            const double *xi = X + i * ldX, *xj = X + J * ldX;
-            double d0 = 0.0, d1 = 0.0;
-            int r = 0;
-            for (; r + 1 < rows; r += 2) {
-                d0 = fma(xi[r], xj[r], d0);
-                d1 = fma(xi[r + 1], xj[r + 1], d1);
-            }
-            if (r < rows) d0 = fma(xi[r], xj[r], d0);
-            G[i + J * n] = d0 + d1;
-        }
+        wy_gram(X, ldX, rows, n, G);
         __syncthreads();
-        // S column by column; column J's rows i < J each by a team of tpr lanes (the sum over
-        // k = i .. J-1 strided over the team, then a fixed butterfly)
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            for (int i = 0; i < n; ++i) S[i + idx * n] = (i == idx) ? sc[2 * idx] : 0.0;
-        }
-        for (int J = 1; J < n; ++J) {
-            __syncthreads();  // columns 0 .. J-1 are complete
-            int tpr = 1;
-            while (tpr < 32 && 2 * tpr * J <= (int)blockDim.x) tpr *= 2;
-            const int team = threadIdx.x / tpr, sub = threadIdx.x - team * tpr;
-            const int i = team < J ? team : J - 1;  // spare teams shadow the last row
-            double v = 0.0;
-            for (int k = i + sub; k < J; k += tpr) v = fma(S[i + k * n], G[k + J * n], v);
-            for (int o = tpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, tpr);
-            if (team < J && sub == 0) S[i + J * n] = -sc[2 * J] * v;
-        }
-        __syncthreads();
+        wy_s_from_g(G, sc, n, S);
         double *out = a.S + c * (int64_t)n * n;
         for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = S[idx];
     }
@@ -817,7 +830,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
 __global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs a) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n, qn = a.qn, q0 = a.q0;
-    const QLeafWyLayout L = q_leaf_wy_layout(n, qn, a.ldS);
+    const QLeafWyLayout L = q_leaf_wy_layout(n, qn, a.ldS, a.wyS == nullptr);
     double *X = smem + L.X;
     double *top = smem + L.top;
     double *S = smem + L.S;
@@ -844,8 +857,11 @@ __global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs 
             const int col = idx / rows, i = idx - col * rows;
             cp_async8(X + i + (size_t)col * a.ldS, a.V + row0 + i + (int64_t)col * a.ldv, 8);
         }
-        const double *Sg = a.wyS + cid * (int64_t)n * n;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) cp_async8(S + idx, Sg + idx, 8);
+        if (a.wyS) {
+            const double *Sg = a.wyS + cid * (int64_t)n * n;
+            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+                cp_async8(S + idx, Sg + idx, 8);
+        }
         cp_async_commit();
         for (int j = threadIdx.x; j < n; j += blockDim.x) cs[j] = csc[2 * j + 1];
         cp_async_wait_all();
@@ -853,6 +869,12 @@ __global__ void __launch_bounds__(256, 1) tsqr_q_leaf_wy_kernel(const QLeafArgs 
         for (int idx = threadIdx.x; idx < rows * n; idx += blockDim.x) {  // X diag(c)
             const int col = idx / rows, i = idx - col * rows;
             X[i + (size_t)col * a.ldS] *= cs[col];
+        }
+        if (!a.wyS) {  // one column group: the chunk's S here, from the tails just loaded
+            __syncthreads();
+            wy_gram(X, a.ldS, rows, n, smem + L.G);
+            __syncthreads();
+            wy_s_from_g(smem + L.G, csc, n, S);
         }
         for (int o = threadIdx.x; o < n * qn; o += blockDim.x) {  // Y = S T (S upper)
             const int i = o % n, q = o / n;
@@ -961,8 +983,8 @@ cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes,
     return cudaGetLastError();
 }
 
-size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS) {
-    return sizeof(double) * (size_t)q_leaf_wy_layout(n, qn, ldS).total;
+size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS, bool fused) {
+    return sizeof(double) * (size_t)q_leaf_wy_layout(n, qn, ldS, fused).total;
 }
 
 cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t stream) {

@@ -38,7 +38,8 @@ struct QLeafArgs {
     const double *B;          // per leaf: n x n block, leading dimension n
     const double *signs;      // the root's row signs (used when the only leaf is the root)
     int single;               // one leaf: its block is diag(signs)
-    const double *wyS;        // the chunks' compact WY factors (the blocked leaf pass)
+    const double *wyS;        // the chunks' compact WY factors (the blocked leaf pass), or
+                              // NULL: the pass forms them itself (one column group)
 };
 
 // Offsets in doubles: the tails X (ldS x n), the Q rows Z of the column group (ldS x qn), the
@@ -160,10 +161,11 @@ __host__ __device__ inline QtLayout qt_layout(int n, int k, int ldS, int warps_t
 // Blocked leaf pass: the tails X diag(c) (ldS x n), the carried block's columns T (n x qn),
 // S (n x n), Y = S T (n x qn), and the chunk's c.
 struct QLeafWyLayout {
-    int X, top, S, Y, cs, total;
+    int X, top, S, Y, cs, G, total;
 };
 
-__host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS) {
+// fused: the pass forms each chunk's S itself (one column group), with G (n x n) beside it.
+__host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS, bool fused) {
     QLeafWyLayout L;
     int o = 0;
     L.X = o;    o += ldS * n;
@@ -171,6 +173,7 @@ __host__ __device__ inline QLeafWyLayout q_leaf_wy_layout(int n, int qn, int ldS
     L.S = o;    o += n * n;
     L.Y = o;    o += n * qn;
     L.cs = o;   o += n;
+    L.G = o;    o += fused ? n * n : 0;
     L.total = o;
     return L;
 }

@@ -109,9 +109,9 @@ def test_qr_bit_reproducible_and_launches(T):
     while c > 1:
         c = (c + p.arity - 1) // p.arity
         levels += 1
-    # the factorization, the chunks' compact WY factors, one tree pass per level below the
-    # root and the leaf pass
-    assert n_launch == 1 + 1 + (levels - 1) + 1
+    # the factorization, one tree pass per level below the root and the leaf pass (which forms
+    # the chunks' compact WY factors itself when Q's columns form one group)
+    assert n_launch == 1 + (levels - 1) + 1
 
 
 def test_qr_full_size_4m_x_32(oracle, T):
