@@ -21,7 +21,7 @@ cudaError_t qt_prepare(size_t smem_bytes);
 cudaError_t qt_launch(const QtArgs &a, int blk, int warps, size_t smem_bytes, cudaStream_t stream);
 size_t wy_smem_bytes(int n, int ldX);
 cudaError_t wy_launch(const WyArgs &a, size_t smem_bytes, int grid, cudaStream_t stream);
-size_t qt_wy_smem_bytes(int n, int kc, int ldS);
+size_t qt_wy_smem_bytes(int n, int kc, int ldS, bool fused = false);
 size_t q_leaf_wy_smem_bytes(int n, int qn, int ldS, bool fused);
 cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t stream);
 cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream);
@@ -962,6 +962,12 @@ tsqr_status_t run_lstsq_wy(const double *A, int64_t m, int64_t n, int64_t lda, c
     t.ldc = n;
     t.wyS = wa.S;
     const int grid = (int)std::min<int64_t>(nchunks, 4LL * di.sms);
+    // one column group: the apply forms each chunk's S itself from the tails it loads anyway
+    const bool fuse = groups == 1 && qt_wy_smem_bytes((int)n, kg, p.ldS, true) <= di.smem_block_optin;
+    if (fuse) {
+        t.wyS = nullptr;
+        qtw_smem = qt_wy_smem_bytes((int)n, kg, p.ldS, true);
+    }
     if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
         cudaSuccess)
         return TSQR_ERR_CUDA;
@@ -973,11 +979,11 @@ tsqr_status_t run_lstsq_wy(const double *A, int64_t m, int64_t n, int64_t lda, c
     if (cudaMemsetAsync(t.counters, 0, (size_t)groups * p.nodes * sizeof(unsigned int),
                         stream) != cudaSuccess ||
         qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess ||
-        wy_launch(wa, wy_smem, grid, stream) != cudaSuccess ||
+        (!fuse && wy_launch(wa, wy_smem, grid, stream) != cudaSuccess) ||
         qt_wy_launch(t, qtw_smem, stream) != cudaSuccess ||
         trsm_launch(R, ldr, t.C, n, X, ldx, (int)n, (int)k, ws->status, stream) != cudaSuccess)
         return TSQR_ERR_CUDA;
-    g_last_launches = 4;
+    g_last_launches = fuse ? 3 : 4;
     return TSQR_SUCCESS;
 }
 

@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
     double *Og = a.Cout ? a.Cout + (int64_t)grp * a.k * a.ldco : nullptr;
     unsigned int *counters = a.counters + grp * a.nodes;
     double *slots = a.slots + grp * a.nodes * n * a.k;
-    const WyLayout L = wy_layout(n, kc, a.ldS, blockDim.x);
+    const WyLayout L = wy_layout(n, kc, a.ldS, blockDim.x, a.wyS == nullptr);
     double *X = smem + L.X;
     double *Z = smem + L.Z;
     double *top = smem + L.top;
@@ -794,8 +794,11 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
             const int col = idx / rows, i = idx - col * rows;
             cp_async8(Z + i + (size_t)col * a.ldS, Bg + row0 + i + (int64_t)col * a.ldb, 8);
         }
-        const double *Sg = a.wyS + cid * (int64_t)n * n;
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) cp_async8(S + idx, Sg + idx, 8);
+        if (a.wyS) {
+            const double *Sg = a.wyS + cid * (int64_t)n * n;
+            for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+                cp_async8(S + idx, Sg + idx, 8);
+        }
         cp_async_commit();
         for (int j = threadIdx.x; j < n; j += blockDim.x) cs[j] = csc[2 * j + 1];
         cp_async_wait_all();
@@ -805,6 +808,11 @@ __global__ void __launch_bounds__(256, 1) tsqr_qt_wy_kernel(const QtArgs a) {
             X[i + (size_t)col * a.ldS] *= cs[col];
         }
         __syncthreads();
+        if (!a.wyS) {  // one column group: the chunk's S here (G in the part region, free now)
+            wy_gram(X, a.ldS, rows, n, part);
+            __syncthreads();
+            wy_s_from_g(part, csc, n, S);
+        }
         wy_xtz(X, Z, a.ldS, rows, n, kc, top, W, part);
         __syncthreads();
         wy_sw(S, W, part, top, n, kc, true);
@@ -1007,8 +1015,8 @@ cudaError_t wy_launch(const WyArgs &a, size_t smem_bytes, int grid, cudaStream_t
 
 constexpr int kWyThreads = 256;
 
-size_t qt_wy_smem_bytes(int n, int kc, int ldS) {
-    return sizeof(double) * (size_t)wy_layout(n, kc, ldS, kWyThreads).total;
+size_t qt_wy_smem_bytes(int n, int kc, int ldS, bool fused) {
+    return sizeof(double) * (size_t)wy_layout(n, kc, ldS, kWyThreads, fused).total;
 }
 
 cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream) {

@@ -121,7 +121,9 @@ struct WyLayout {
     int X, Z, top, S, W, part, cs, flag, total;
 };
 
-__host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthreads) {
+// fused: the apply forms each chunk's S itself (one column group), its G in the part region.
+__host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthreads,
+                                              bool fused = false) {
     WyLayout L;
     int o = 0;
     L.X = o;    o += ldS * n;
@@ -129,7 +131,9 @@ __host__ __device__ inline WyLayout wy_layout(int n, int kc, int ldS, int nthrea
     L.top = o;  o += n * kc;
     L.S = o;    o += n * n;
     L.W = o;    o += n * kc;
-    L.part = o; o += (4 * nthreads > n * kc) ? 4 * nthreads : n * kc;
+    int part = (4 * nthreads > n * kc) ? 4 * nthreads : n * kc;
+    if (fused && part < n * n) part = n * n;
+    L.part = o; o += part;
     L.cs = o;   o += n;
     L.flag = o; o += 1;
     L.total = o;
