@@ -29,8 +29,9 @@ cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t l
                         int64_t ldx, int n, int k, int *status, cudaStream_t stream);
 // Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
 cudaError_t f64_stream_prepare(size_t smem_bytes);
-cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
-                              size_t smem_bytes, long long wait_iters, cudaStream_t stream);
+cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces,
+                              int64_t first, int warps, size_t smem_bytes, long long wait_iters,
+                              cudaStream_t stream);
 }  // namespace tsqr
 
 using namespace tsqr;
@@ -704,7 +705,10 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
     g_last_plan = public_plan(p);
-    const int P = (int)std::min<int64_t>(16, p.nunits);
+    // pieces: the leaves' first round alone (every leaf starts after the smallest copy), then
+    // the rest in up to 15 equal pieces
+    const int64_t first = std::min<int64_t>(p.nleaves, p.nunits);
+    const int P = (int)std::min<int64_t>(16, 1 + (p.nunits - first));
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
     const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
@@ -759,11 +763,15 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
                 cudaSuccess)
             return TSQR_ERR_CUDA;
         if (f64_stream_prepare(p.smem) != cudaSuccess ||
-            f64_stream_launch(a, flags, P, p.warps, p.smem, 1LL << 23, stream) != cudaSuccess)
+            f64_stream_launch(a, flags, P, first, p.warps, p.smem, 1LL << 23, stream) !=
+                cudaSuccess)
             return TSQR_ERR_CUDA;
+        const int64_t rest = p.nunits - first;
         for (int q = 0; q < P; ++q) {
-            const int64_t r0 = std::min<int64_t>(((int64_t)q * p.nunits / P) * p.unit, m);
-            const int64_t r1 = std::min<int64_t>(((int64_t)(q + 1) * p.nunits / P) * p.unit, m);
+            const int64_t u0 = q == 0 ? 0 : first + ((int64_t)(q - 1) * rest) / (P - 1);
+            const int64_t u1 = q == 0 ? first : first + ((int64_t)q * rest) / (P - 1);
+            const int64_t r0 = std::min<int64_t>(u0 * p.unit, m);
+            const int64_t r1 = std::min<int64_t>(u1 * p.unit, m);
             // one contiguous copy per column segment (copy engines), then the piece's flag
             for (int64_t c = 0; c < n && r1 > r0; ++c)
                 if (cudaMemcpyAsync(Ad + r0 + c * m, A + r0 + c * lda,
@@ -1666,7 +1674,8 @@ int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_ite
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
-    const int P = (int)std::min<int64_t>(16, p.nunits);
+    const int64_t first = std::min<int64_t>(p.nleaves, p.nunits);
+    const int P = (int)std::min<int64_t>(16, 1 + (p.nunits - first));
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
     const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
@@ -1685,7 +1694,8 @@ int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_ite
     unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
     if (cudaMemsetAsync(base, 0, cnt_bytes + slot_bytes + flag_bytes + a_bytes, s) != cudaSuccess ||
         f64_stream_prepare(p.smem) != cudaSuccess ||
-        f64_stream_launch(a, flags, P, p.warps, p.smem, (long long)wait_iters, s) != cudaSuccess)
+        f64_stream_launch(a, flags, P, first, p.warps, p.smem, (long long)wait_iters, s) !=
+            cudaSuccess)
         return TSQR_ERR_CUDA;
     return TSQR_SUCCESS;
 }

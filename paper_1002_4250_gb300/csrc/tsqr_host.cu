@@ -18,12 +18,18 @@ namespace tsqr {
 namespace {
 
 
-// Piece q holds work units [q nunits / P, (q+1) nunits / P).
-__device__ __forceinline__ int piece_of(const int64_t u, const int64_t nunits, const int P) {
-    int q = (int)((u * P) / nunits);
-    while (q + 1 < P && ((int64_t)(q + 1) * nunits) / P <= u) ++q;
-    while (q > 0 && ((int64_t)q * nunits) / P > u) --q;
-    return q;
+// Piece 0 holds work units [0, first): the leaves' first round, so that every leaf can start
+// after the smallest copy.  Piece q >= 1 holds [first + (q-1) R / (P-1), first + q R / (P-1)),
+// R = nunits - first.
+__device__ __forceinline__ int piece_of(const int64_t u, const int64_t nunits, const int P,
+                                        const int64_t first) {
+    if (u < first || P == 1) return 0;
+    const int64_t r = u - first, R = nunits - first;
+    const int Q = P - 1;
+    int q = (int)((r * Q) / R);
+    while (q + 1 < Q && ((int64_t)(q + 1) * R) / Q <= r) ++q;
+    while (q > 0 && ((int64_t)q * R) / Q > r) --q;
+    return 1 + q;
 }
 
 __device__ __forceinline__ unsigned int load_flag(const unsigned int *p) {
@@ -65,7 +71,7 @@ __device__ __forceinline__ Chunk<double> unit_chunk(const F64Args &a, const int6
 template <int B>
 __global__ void __launch_bounds__(416, 1)
     tsqr_f64_stream_kernel(const F64Args a, const unsigned int *flags, const int pieces,
-                           const long long wait_iters) {
+                           const int64_t first, const long long wait_iters) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n;
     const SmemLayout L = smem_layout(n, a.hs, a.ldS, blockDim.x >> 5);
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(416, 1)
     const int64_t stride = a.nleaves;
     int64_t u = leaf;
     if (u < a.nunits) {
-        if (!piece_arrived(flags, piece_of(u, a.nunits, pieces), true, wait_iters, pflag)) {
+        if (!piece_arrived(flags, piece_of(u, a.nunits, pieces, first), true, wait_iters, pflag)) {
             if (threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusTimeoutBit);
             return;
         }
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(416, 1)
         for (;;) {
             const int64_t nx = u + stride;
             const bool have = nx < a.nunits;
-            const bool pre = have && piece_arrived(flags, piece_of(nx, a.nunits, pieces), false, 0,
+            const bool pre = have && piece_arrived(flags, piece_of(nx, a.nunits, pieces, first), false, 0,
                                                   pflag);
             Chunk<double> next;
             next.src = nullptr;
@@ -104,7 +110,7 @@ __global__ void __launch_bounds__(416, 1)
                                                    next);
             if (!have) break;
             if (!pre) {
-                if (!piece_arrived(flags, piece_of(nx, a.nunits, pieces), true, wait_iters,
+                if (!piece_arrived(flags, piece_of(nx, a.nunits, pieces, first), true, wait_iters,
                                    pflag)) {
                     if (threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusTimeoutBit);
                     return;
@@ -129,21 +135,22 @@ cudaError_t f64_stream_prepare(size_t smem_bytes) {
 }
 
 // wait_iters: polls per wait (1 << 23 in tsqr_r_host: seconds before a timeout)
-cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces, int warps,
-                              size_t smem_bytes, long long wait_iters, cudaStream_t stream) {
+cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces,
+                              int64_t first, int warps, size_t smem_bytes, long long wait_iters,
+                              cudaStream_t stream) {
     const dim3 grid(a.nleaves), block((warps + 1) * 32);
     switch (a.blk) {
         case 4:
-            tsqr_f64_stream_kernel<4><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            tsqr_f64_stream_kernel<4><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, first, wait_iters);
             break;
         case 3:
-            tsqr_f64_stream_kernel<3><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            tsqr_f64_stream_kernel<3><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, first, wait_iters);
             break;
         case 2:
-            tsqr_f64_stream_kernel<2><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            tsqr_f64_stream_kernel<2><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, first, wait_iters);
             break;
         default:
-            tsqr_f64_stream_kernel<1><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, wait_iters);
+            tsqr_f64_stream_kernel<1><<<grid, block, smem_bytes, stream>>>(a, flags, pieces, first, wait_iters);
             break;
     }
     return cudaGetLastError();
