@@ -96,6 +96,51 @@ struct F64Plan {
     int64_t nodes = 0;
 };
 
+// Arguments of the Q^T apply for a factorization with storage `q` under plan p: B (m x ktot,
+// leading dimension ldb) in groups of k columns; the apply's counters, slots, outputs and S
+// factors are the caller's to set.  Every other field is zero.
+QtArgs qt_args(const F64Plan &p, const QStore &q, int64_t m, int n, const double *B,
+               int64_t ldb, int k, int ktot) {
+    QtArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.V = q.V;
+    t.ldv = q.ldv;
+    t.B = B;
+    t.m = m;
+    t.ldb = ldb;
+    t.n = n;
+    t.k = k;
+    t.ktot = ktot;
+    t.unit = p.unit;
+    t.nunits = p.nunits;
+    t.nleaves = p.nleaves;
+    t.h = p.h;
+    t.hs = p.hs;
+    t.ldS = p.ldS;
+    t.arity = p.arity;
+    t.chunk_sc = q.chunk_sc;
+    t.node_V = q.node_V;
+    t.node_sc = q.node_sc;
+    t.signs = q.signs;
+    t.nodes = p.nodes;
+    return t;
+}
+
+// Arguments of the compact WY factor kernel for the chunks of a factorization with storage q.
+WyArgs wy_args(const F64Plan &p, const QStore &q, int64_t m, int n, int ldX, double *S) {
+    WyArgs w;
+    w.V = q.V;
+    w.ldv = q.ldv;
+    w.m = m;
+    w.n = n;
+    w.h = p.h;
+    w.ldX = ldX;
+    w.nchunks = (m + p.h - 1) / p.h;
+    w.chunk_sc = q.chunk_sc;
+    w.S = S;
+    return w;
+}
+
 // The public form of a plan: passed back as a plan it gives the same partition and kernels.
 tsqr_plan_t public_plan(const F64Plan &p) {
     tsqr_plan_t o;
@@ -562,16 +607,7 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     if (qr_factor_launch(a, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     int launches = 1;
     if (wyq && !fuse) {
-        WyArgs wa;
-        wa.V = a.q.V;
-        wa.ldv = a.q.ldv;
-        wa.m = m;
-        wa.n = (int)n;
-        wa.h = p.h;
-        wa.ldX = ldX;
-        wa.nchunks = nchunks;
-        wa.chunk_sc = a.q.chunk_sc;
-        wa.S = wyS;
+        const WyArgs wa = wy_args(p, a.q, m, (int)n, ldX, wyS);
         const int grid = (int)std::min<int64_t>(nchunks, 4LL * di.sms);
         if (wy_launch(wa, wy_smem, grid, stream) != cudaSuccess) return TSQR_ERR_CUDA;
         ++launches;
@@ -932,40 +968,10 @@ tsqr_status_t run_lstsq_wy(const double *A, int64_t m, int64_t n, int64_t lda, c
     a.q.node_V = (double *)bufs[4];
     a.q.node_sc = (double *)bufs[5];
     a.q.signs = (double *)bufs[6];
-    WyArgs wa;
-    wa.V = a.q.V;
-    wa.ldv = m;
-    wa.m = m;
-    wa.n = (int)n;
-    wa.h = p.h;
-    wa.ldX = ldX;
-    wa.nchunks = nchunks;
-    wa.chunk_sc = a.q.chunk_sc;
-    wa.S = (double *)bufs[10];
-    QtArgs t;
-    std::memset(&t, 0, sizeof(t));
-    t.V = a.q.V;
-    t.ldv = m;
-    t.B = B;
-    t.m = m;
-    t.ldb = ldb;
-    t.n = (int)n;
-    t.k = kg;
-    t.ktot = (int)k;
-    t.unit = p.unit;
-    t.nunits = p.nunits;
-    t.nleaves = p.nleaves;
-    t.h = p.h;
-    t.hs = p.hs;
-    t.ldS = p.ldS;
-    t.arity = p.arity;
-    t.chunk_sc = a.q.chunk_sc;
-    t.node_V = a.q.node_V;
-    t.node_sc = a.q.node_sc;
-    t.signs = a.q.signs;
+    const WyArgs wa = wy_args(p, a.q, m, (int)n, ldX, (double *)bufs[10]);
+    QtArgs t = qt_args(p, a.q, m, (int)n, B, ldb, kg, (int)k);
     t.counters = (unsigned int *)bufs[7];
     t.slots = (double *)bufs[8];
-    t.nodes = p.nodes;
     t.C = (double *)bufs[9];
     t.ldc = n;
     t.wyS = wa.S;
@@ -1104,31 +1110,11 @@ tsqr_status_t run_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, cons
     int launches = 1;
     for (int64_t q0 = 0; q0 < k; q0 += kg) {
         const int kc = (int)std::min<int64_t>(kg, k - q0);
-        QtArgs t;
-        std::memset(&t, 0, sizeof(t));
-        t.V = V;
-        t.ldv = m;
-        t.B = B + q0 * ldb;
-        t.m = m;
-        t.ldb = ldb;
-        t.n = (int)n;
-        t.k = kc;
-        t.unit = p.unit;
-        t.nunits = p.nunits;
-        t.nleaves = p.nleaves;
-        t.h = p.h;
-        t.hs = p.hs;
-        t.ldS = p.ldS;
-        t.arity = p.arity;
-        t.chunk_sc = csc;
-        t.node_V = nV;
-        t.node_sc = nsc;
-        t.signs = signs;
+        QtArgs t = qt_args(p, a.q, m, (int)n, B + q0 * ldb, ldb, kc, kc);
         t.slots = qslots;
         t.counters = qcounters;
         t.C = C;
         t.ldc = n;
-        t.ktot = kc;
         if (cudaMemsetAsync(qcounters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
                 cudaSuccess ||
             qt_launch(t, qblk, qwarps, qt_smem, stream) != cudaSuccess ||
@@ -1325,30 +1311,9 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
         ++launches;
         const int64_t trail = N - c.j0 - c.w;
         if (trail == 0) break;
-        QtArgs t;
-        std::memset(&t, 0, sizeof(t));
-        t.V = V;
-        t.ldv = c.M;
-        t.B = src + c.w * lds;
-        t.m = c.M;
-        t.ldb = lds;
-        t.n = c.w;
-        t.k = c.kc;
-        t.ktot = (int)trail;
-        t.unit = c.p.unit;
-        t.nunits = c.p.nunits;
-        t.nleaves = c.p.nleaves;
-        t.h = c.p.h;
-        t.hs = c.p.hs;
-        t.ldS = c.p.ldS;
-        t.arity = c.p.arity;
-        t.chunk_sc = csc;
-        t.node_V = nV;
-        t.node_sc = nsc;
-        t.signs = signs;
+        QtArgs t = qt_args(c.p, a.q, c.M, c.w, src + c.w * lds, lds, c.kc, (int)trail);
         t.slots = qslots;
         t.counters = qcounters;
-        t.nodes = c.p.nodes;
         t.C = R + c.j0 + (c.j0 + c.w) * ldr;
         t.ldc = ldr;
         t.Cout = C + (c.j0 + c.w - w0) * ldC;
@@ -1359,16 +1324,7 @@ tsqr_status_t run_caqr(const double *A, int64_t m, int64_t N, int64_t lda, doubl
                             stream) != cudaSuccess)
             return TSQR_ERR_CUDA;
         if (c.wy) {
-            WyArgs wa;
-            wa.V = V;
-            wa.ldv = c.M;
-            wa.m = c.M;
-            wa.n = c.w;
-            wa.h = c.p.h;
-            wa.ldX = c.ldX;
-            wa.nchunks = (c.M + c.p.h - 1) / c.p.h;
-            wa.chunk_sc = csc;
-            wa.S = wyS;
+            const WyArgs wa = wy_args(c.p, a.q, c.M, c.w, c.ldX, wyS);
             t.wyS = wyS;
             const int grid = (int)std::min<int64_t>(wa.nchunks, 4LL * di.sms);
             if (wy_launch(wa, c.wy_smem, grid, stream) != cudaSuccess ||
