@@ -1435,12 +1435,18 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const DeviceInfo di = device_info(dev);
     if (di.sms <= 0) return TSQR_ERR_CUDA;
     const bool mixed = dt != 0;
-    const int W = 4;
+    int nmax = 1;
+    for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
     const size_t reserve = 1024 + 256;  // per-CTA reserve plus the kernel's static shared memory
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
-    int nmax = 1;
-    for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
+    // bulk warps: 4, or 12 for an FP64 batch with widths from 48 on whose widest chunk fits
+    // with 12 warps: it runs one CTA per SM and hides the wide problems' reflector chains
+    // behind more warps (the varlen batch of 4096 problems with widths up to 64: 716 ms with 4,
+    // 640 with 8, 626 with 12)
+    const int W = (!mixed && nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, false) >= 1)
+                      ? 12
+                      : 4;
     // two CTAs per SM when the widest problem's chunk fits at two rows per lane (one CTA per
     // SM with taller chunks measured faster on the varlen batch otherwise: 717 against
     // 1010 ms for FP64 with widths up to 64)

@@ -56,7 +56,7 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
     }
 }
 
-__global__ void __launch_bounds__(256, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(416, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
     batched_body<double, double>(b);
 }
 __global__ void __launch_bounds__(256, 1) tsqr_batched_f32_kernel(const BatchArgs b) {
