@@ -1471,8 +1471,9 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], ld_for(hs_of[n], vec_of[n]), W,
                                               mixed));
     }
-    if (batched_prepare(dt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
-    const int per_sm = std::max(1, batched_blocks_per_sm(dt, W, smem));
+    const int kdt = (dt == 0 && W == 12) ? 3 : dt;  // the 12-warp FP64 kernel
+    if (batched_prepare(kdt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int per_sm = std::max(1, batched_blocks_per_sm(kdt, W, smem));
     const int64_t ctas = (int64_t)di.sms * per_sm;
     // leaf size: about 6 leaves per CTA over the whole batch
     double work = 0.0;
@@ -1552,7 +1553,7 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         cudaSuccess)
         return TSQR_ERR_CUDA;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)items.size());
-    if (batched_launch(dt, b, grid, W, smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (batched_launch(kdt, b, grid, W, smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     g_last_launches = 1;
     return TSQR_SUCCESS;
 }

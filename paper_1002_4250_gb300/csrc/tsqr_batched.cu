@@ -56,7 +56,12 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
     }
 }
 
-__global__ void __launch_bounds__(416, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(256, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
+    batched_body<double, double>(b);
+}
+// FP64 with 12 bulk warps (wide batches): its own 416-thread bound, so that the 4-warp kernel
+// keeps the 256-thread bound's register budget
+__global__ void __launch_bounds__(416, 1) tsqr_batched_f64w_kernel(const BatchArgs b) {
     batched_body<double, double>(b);
 }
 __global__ void __launch_bounds__(256, 1) tsqr_batched_f32_kernel(const BatchArgs b) {
@@ -68,13 +73,15 @@ __global__ void __launch_bounds__(256, 1) tsqr_batched_bf16_kernel(const BatchAr
 
 namespace {
 const void *batched_fn(int dtype) {
-    return dtype == 0 ? (const void *)tsqr_batched_f64_kernel
-                      : dtype == 1 ? (const void *)tsqr_batched_f32_kernel
-                                   : (const void *)tsqr_batched_bf16_kernel;
+    return dtype == 0   ? (const void *)tsqr_batched_f64_kernel
+           : dtype == 1 ? (const void *)tsqr_batched_f32_kernel
+           : dtype == 2 ? (const void *)tsqr_batched_bf16_kernel
+                        : (const void *)tsqr_batched_f64w_kernel;
 }
 }  // namespace
 
-// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); `warps` counts bulk warps (+1 reducer).
+// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed), 3 FP64 with 12 bulk warps; `warps` counts
+// bulk warps (+1 reducer).
 cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
     return set_smem_attrs(batched_fn(dtype), smem_bytes);
 }
@@ -92,6 +99,8 @@ cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, s
     const int threads = (warps + 1) * 32;
     if (dtype == 0)
         tsqr_batched_f64_kernel<<<grid, threads, smem_bytes, stream>>>(b);
+    else if (dtype == 3)
+        tsqr_batched_f64w_kernel<<<grid, threads, smem_bytes, stream>>>(b);
     else if (dtype == 1)
         tsqr_batched_f32_kernel<<<grid, threads, smem_bytes, stream>>>(b);
     else
