@@ -7,7 +7,9 @@
  *          tree by the operator qr(R_i, R_j) = R factor of [R_i; R_j], which does no arithmetic
  *          on the known zeros of the two triangles.
  * The tree is fixed per call (binary, flat or hybrid; Section 1 and Fig. 1), so a call is
- * bit-reproducible: same inputs and same plan give the same bytes.
+ * bit-reproducible: same inputs and same plan give the same bytes.  Wide tall matrices (and,
+ * through tsqr_caqr_r, any width) run by panels of columns, each a reduction of its own
+ * followed by an update of the columns right of it (Section 5).
  *
  * Conventions shared by every entry point:
  *   - Matrices are column-major: element (i, j) of A is A[i + j*lda].
@@ -23,8 +25,10 @@
  *   - Workspace (tree-node slots and counters) is allocated by the library, per device and
  *     stream, with stream-ordered allocation, grown when needed and reused across calls;
  *     tsqr_release_workspace() returns it.  Calls on the same stream may follow each other
- *     freely; the first call on a stream should not be made under stream capture.
- *   - n is limited to TSQR_MAX_N.
+ *     freely; the first call on a stream should not be made under stream capture.  A few
+ *     calls also allocate a buffer for the call itself, stream-ordered, as each one states.
+ *   - n is limited to TSQR_MAX_N except where a call says otherwise (the FP64 R calls by
+ *     panels, tsqr_caqr_r and tsqr_lstsq take any n <= m).
  */
 #ifndef LIBTSQR_TSQR_H
 #define LIBTSQR_TSQR_H
