@@ -1440,13 +1440,11 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const size_t reserve = 1024 + 256;  // per-CTA reserve plus the kernel's static shared memory
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
-    // bulk warps: 4, or 12 for an FP64 batch with widths from 48 on whose widest chunk fits
-    // with 12 warps: it runs one CTA per SM and hides the wide problems' reflector chains
-    // behind more warps (the varlen batch of 4096 problems with widths up to 64: 716 ms with 4,
-    // 640 with 8, 626 with 12)
-    const int W = (!mixed && nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, false) >= 1)
-                      ? 12
-                      : 4;
+    // bulk warps: 4, or 12 for a batch with widths from 48 on whose widest chunk fits with 12
+    // warps: it runs one CTA per SM and hides the wide problems' reflector chains behind more
+    // warps (the varlen batch of 4096 problems with widths up to 64: FP64 716 ms with 4, 640
+    // with 8, 626 with 12; mixed FP32 304 ms with 4, 224 with 12)
+    const int W = (nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, mixed) >= 1) ? 12 : 4;
     // two CTAs per SM when the widest problem's chunk fits at two rows per lane (one CTA per
     // SM with taller chunks measured faster on the varlen batch otherwise: 717 against
     // 1010 ms for FP64 with widths up to 64)
@@ -1471,7 +1469,7 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], ld_for(hs_of[n], vec_of[n]), W,
                                               mixed));
     }
-    const int kdt = (dt == 0 && W == 12) ? 3 : dt;  // the 12-warp FP64 kernel
+    const int kdt = (W == 12) ? dt + 3 : dt;  // the 12-warp kernels
     if (batched_prepare(kdt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int per_sm = std::max(1, batched_blocks_per_sm(kdt, W, smem));
     const int64_t ctas = (int64_t)di.sms * per_sm;

@@ -59,8 +59,8 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
 __global__ void __launch_bounds__(256, 1) tsqr_batched_f64_kernel(const BatchArgs b) {
     batched_body<double, double>(b);
 }
-// FP64 with 12 bulk warps (wide batches): its own 416-thread bound, so that the 4-warp kernel
-// keeps the 256-thread bound's register budget
+// 12 bulk warps (wide batches; FP64 here, FP32 and BF16 below): their own 416-thread bound, so
+// that the 4-warp kernels keep the 256-thread bound's register budget
 __global__ void __launch_bounds__(416, 1) tsqr_batched_f64w_kernel(const BatchArgs b) {
     batched_body<double, double>(b);
 }
@@ -70,18 +70,28 @@ __global__ void __launch_bounds__(256, 1) tsqr_batched_f32_kernel(const BatchArg
 __global__ void __launch_bounds__(256, 1) tsqr_batched_bf16_kernel(const BatchArgs b) {
     batched_body<float, __nv_bfloat16>(b);
 }
+__global__ void __launch_bounds__(416, 1) tsqr_batched_f32w_kernel(const BatchArgs b) {
+    batched_body<float, float>(b);
+}
+__global__ void __launch_bounds__(416, 1) tsqr_batched_bf16w_kernel(const BatchArgs b) {
+    batched_body<float, __nv_bfloat16>(b);
+}
 
 namespace {
 const void *batched_fn(int dtype) {
-    return dtype == 0   ? (const void *)tsqr_batched_f64_kernel
-           : dtype == 1 ? (const void *)tsqr_batched_f32_kernel
-           : dtype == 2 ? (const void *)tsqr_batched_bf16_kernel
-                        : (const void *)tsqr_batched_f64w_kernel;
+    switch (dtype) {
+        case 0: return (const void *)tsqr_batched_f64_kernel;
+        case 1: return (const void *)tsqr_batched_f32_kernel;
+        case 2: return (const void *)tsqr_batched_bf16_kernel;
+        case 3: return (const void *)tsqr_batched_f64w_kernel;
+        case 4: return (const void *)tsqr_batched_f32w_kernel;
+        default: return (const void *)tsqr_batched_bf16w_kernel;
+    }
 }
 }  // namespace
 
-// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed), 3 FP64 with 12 bulk warps; `warps` counts
-// bulk warps (+1 reducer).
+// dtype: 0 FP64, 1 FP32 (mixed), 2 BF16 (mixed); 3, 4, 5 the same with 12 bulk warps; `warps`
+// counts bulk warps (+1 reducer).
 cudaError_t batched_prepare(int dtype, size_t smem_bytes) {
     return set_smem_attrs(batched_fn(dtype), smem_bytes);
 }
@@ -97,14 +107,14 @@ int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes) {
 cudaError_t batched_launch(int dtype, const BatchArgs &b, int grid, int warps, size_t smem_bytes,
                            cudaStream_t stream) {
     const int threads = (warps + 1) * 32;
-    if (dtype == 0)
-        tsqr_batched_f64_kernel<<<grid, threads, smem_bytes, stream>>>(b);
-    else if (dtype == 3)
-        tsqr_batched_f64w_kernel<<<grid, threads, smem_bytes, stream>>>(b);
-    else if (dtype == 1)
-        tsqr_batched_f32_kernel<<<grid, threads, smem_bytes, stream>>>(b);
-    else
-        tsqr_batched_bf16_kernel<<<grid, threads, smem_bytes, stream>>>(b);
+    switch (dtype) {
+        case 0: tsqr_batched_f64_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+        case 1: tsqr_batched_f32_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+        case 2: tsqr_batched_bf16_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+        case 3: tsqr_batched_f64w_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+        case 4: tsqr_batched_f32w_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+        default: tsqr_batched_bf16w_kernel<<<grid, threads, smem_bytes, stream>>>(b); break;
+    }
     return cudaGetLastError();
 }
 
