@@ -372,8 +372,10 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
     // bulk warps: 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep gains
-    // from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms); FP64 by width
-    p->warps = mixed ? (n >= 48 ? 8 : 4) : f64_auto_warps(n);
+    // from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms with 4, 52.1 with
+    // 12), and 12 from n = 96 on where they fit (2^24 x 96: FP32 143.6 against 177.4 ms, BF16
+    // 156.5 against 197.7); FP64 by width
+    p->warps = mixed ? (n >= 96 ? 12 : n >= 48 ? 8 : 4) : f64_auto_warps(n);
     if (over && over->warps) {
         if (over->warps != 2 && over->warps != 4 && over->warps != 8 && over->warps != 12)
             return TSQR_ERR_INVALID_ARG;
@@ -381,12 +383,18 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     }
     if (over && (over->tile_rows < 0 || over->ctas < 0 || over->arity < 0))
         return TSQR_ERR_INVALID_ARG;
-    const int W = p->warps;
+    int W = p->warps;
     const size_t reserve = 1024;
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
-    const int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
-    const int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
+    int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
+    int r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
+    if (mixed && W == 12 && !(over && over->warps) && r1 < 1) {  // 12 warps do not fit: 8
+        W = 8;
+        p->warps = 8;
+        r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
+        r1 = max_rows_per_lane_p(n, W, one_per_sm, mixed);
+    }
     // FP64: two CTAs per SM hide each other's per-column serial work (the reflector chain,
     // the barriers), which pays even at one row per lane (measured at n = 16, 32, 64).
     // Mixed: the FP32 bulk is cheap, so what counts is the number of rows sharing each
