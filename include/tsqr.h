@@ -126,8 +126,12 @@ tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double 
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                           int64_t ldr, tsqr_stream_t stream);
 
-/* tsqr_r with the storage type of A, the leaf arithmetic and an optional plan (NULL = AUTO).
- * (dtype, prec) must be (F64, F64), (F32, MIXED) or (BF16, MIXED).  lda counts elements. */
+/* tsqr_r (Section 2, steps 1 and 2) with the storage type of A, the leaf arithmetic and an
+ * optional plan (NULL = AUTO): the plan fixes the tree (Section 1: any reduction tree works),
+ * the tile rows, the leaves, the bulk warps and the arity.
+ * (dtype, prec) must be (F64, F64), (F32, MIXED) or (BF16, MIXED).  lda counts elements.
+ * MIXED keeps A in its storage type on chip and does the leaves' bulk arithmetic in FP32,
+ * with the reflector norms and scalars, R and the tree in FP64; R is always FP64. */
 tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
                         int64_t lda, double *R, int64_t ldr, const tsqr_plan_t *plan,
                         tsqr_stream_t stream);
@@ -215,15 +219,17 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
  * nodes leave behind: a panel factorized on L leaves adds (L - 1) panel rows to the next
  * matrix (the rows' order does not change R).  Workspace: the matrix right of the first panel
  * with those rows added (about 8 (m + (n / panel) (L - 1) panel) n bytes), the panel's stored
- * reflectors (8 m panel bytes) and small tree buffers, from the per-stream pool.  Launches: two
- * per panel (the factorization and the update) except the last (one).  Returns
+ * reflectors (8 m panel bytes) and small tree buffers, from the per-stream pool.  Launches:
+ * three per panel (the factorization, its chunks' compact WY factors and the update; two where
+ * the blocked update does not fit) except the last (the factorization alone).  Returns
  * TSQR_ERR_INVALID_ARG for bad sizes, TSQR_ERR_UNSUPPORTED for a panel above TSQR_MAX_N or a
  * plan tsqr_qr would refuse, TSQR_ERR_ALLOC when the workspace cannot be had. */
 tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                           int64_t ldr, int64_t panel, const tsqr_plan_t *plan,
                           tsqr_stream_t stream);
 
-/* Varlen batch of independent problems: R_i = R factor of A_i for i < count.
+/* Varlen batch of independent problems: R_i = R factor of A_i for i < count, each the TSQR of
+ * Section 2 (steps 1 and 2) with its own leaves and tree, all in one persistent launch.
  *   ptrs    : host array of `count` device pointers; A_i is column-major m_i x n_i with
  *             lda_i = m_i (e.g. all pointing into one packed buffer).
  *   ms, ns  : host arrays of count rows (>= 0) and columns (1..TSQR_MAX_N).

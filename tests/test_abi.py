@@ -29,6 +29,27 @@ def test_header_declares_the_entry_points():
         assert must in names
 
 
+def test_every_entry_point_is_documented():
+    """Each declaration in the header is preceded by its own comment block, and the compute
+    entry points cite the passage of the paper they implement (a Section, Table or Fig.)."""
+    text = open(os.path.join(ROOT, "include", "tsqr.h")).read()
+    decl = re.compile(r"(?:tsqr_status_t|int32_t|const char \*|void)\s+(tsqr_[a-z_]+)\s*\(")
+    cited = re.compile(r"Section \d|Table \d|Fig\. \d")
+    compute = {"tsqr_r", "tsqr_r_ex", "tsqr_r_host", "tsqr_qr", "tsqr_qr_uppers", "tsqr_lstsq",
+               "tsqr_caqr_r", "tsqr_r_batched"}
+    seen = set()
+    for mt in decl.finditer(text):
+        name = mt.group(1)
+        comment_end = text.rfind("*/", 0, mt.start())
+        comment_start = text.rfind("/*", 0, comment_end)
+        between = text[comment_end + 2:mt.start()]
+        assert comment_end > 0 and ";" not in between, f"{name} has no comment of its own"
+        if name in compute:
+            assert cited.search(text[comment_start:comment_end]), f"{name} cites no passage"
+        seen.add(name)
+    assert compute <= seen
+
+
 def test_every_declared_symbol_is_exported(lib):
     raw = ctypes.CDLL(lib.LIB_PATH)
     for name in _declared_functions():
