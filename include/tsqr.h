@@ -47,8 +47,7 @@ typedef enum {
     TSQR_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. n > TSQR_MAX_N)              */
     TSQR_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, allocation, copy)      */
     TSQR_ERR_ALLOC = 4,         /* workspace could not be allocated                           */
-    TSQR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (tsqr_r_host's wait for
-                                   a piece of A that never arrived; read by
+    TSQR_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (read by
                                    tsqr_get_device_status)                                    */
     TSQR_STATUS_NONFINITE = 6   /* R holds NaN or Inf (the input held NaN/Inf or overflowed)  */
 } tsqr_status_t;
@@ -81,6 +80,19 @@ typedef enum {
     TSQR_TREE_PANELS = 4
 } tsqr_tree_t;
 
+/* Leaf (tile) factorization of the MIXED path (TSQR_PREC_MIXED; the FP64 path has one leaf).
+ * FOLD:   the fused fold R <- R([R; chunk]) one reflector at a time, every reflector applied to
+ *         every later column by the CUDA cores (FP32 bulk arithmetic, FP64 R and scalars); any
+ *         n <= TSQR_MAX_N.
+ * PANELS: the same fold by panels of 16 columns: each panel factorized column by column in
+ *         registers (the reflector norms, sums and scalars in double-FP32, about 48 bits),
+ *         then applied to the columns right of it as one compact WY block (I - V S V^T) whose
+ *         two products run on the tensor cores as split-TF32 products with FP32 accumulation
+ *         (each as accurate as an FP32 dot product); R in double-FP32 in the leaf, FP64 in the
+ *         tree.  n <= 64; chunks of 256 or 512 rows (tile_rows).
+ * AUTO picks PANELS where it applies (n <= 64), else FOLD. */
+typedef enum { TSQR_LEAF_AUTO = 0, TSQR_LEAF_FOLD = 1, TSQR_LEAF_PANELS = 2 } tsqr_leaf_t;
+
 /* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic
  * order, so two calls with equal plans and inputs return identical bytes. */
 typedef struct {
@@ -93,6 +105,9 @@ typedef struct {
                            in one sweep (the R factor of [R_1; ...; R_c], equal to a sequence of
                            binary operators by associativity, Section 2).  0 = as many as the
                            kernel's shared memory holds.                                     */
+    int32_t leaf;       /* tsqr_leaf_t (mixed path only; 0 elsewhere).  With PANELS,
+                           tile_rows is the chunk height (256 or 512) of a HYBRID plan, warps
+                           is 8 (or 0).                                                      */
 } tsqr_plan_t;
 
 typedef void *tsqr_stream_t; /* a cudaStream_t */
@@ -107,22 +122,20 @@ typedef void *tsqr_stream_t; /* a cudaStream_t */
 tsqr_status_t tsqr_r(const double *A, int64_t m, int64_t n, int64_t lda, double *R, int64_t ldr,
                      tsqr_stream_t stream);
 
-/* tsqr_r for A and R in HOST memory, FP64: the copy of A to the device overlaps the leaf
- * factorizations.  TSQR streams naturally (Section 2: each row block is factorized on its own
- * and only the n x n factors meet in the tree).  With page-locked A, A is copied in up to 16 row
- * pieces on a second stream while ONE launch already folds the pieces that have arrived: its
- * leaves take the work units round-robin (leaf l: units l, l + L, l + 2L, ...), wait for a
- * piece's arrival flag before loading from it (a bounded wait; on timeout the device status
- * becomes TSQR_ERR_TIMEOUT and R is not written), and then climb the usual tree.  With pageable
- * A, A is copied whole and the ordinary kernel runs.  The plan is the AUTO plan; the
- * round-robin rows give an R equal to tsqr_r's up to rounding (not bit for bit).  Where the
- * AUTO plan runs by panels (n >= 56, m >= 8 n), A is copied whole to a buffer of the call
- * (stream-ordered) and the panels run on it, as tsqr_r does (R then equals tsqr_r's bytes).
+/* tsqr_r for A and R in HOST memory, FP64.  TSQR needs no copy of A before it starts (Section 2:
+ * each row block is factorized on its own and only the n x n factors meet in the tree), so
+ * page-locked A (cudaHostAlloc / cudaHostRegister with a device mapping) is read IN PLACE by
+ * tsqr_r's kernel through its device address: every leaf streams its rows from host memory
+ * while it factorizes them, with no second stream, flag or wait, so the result does not
+ * depend on copies and kernels running at the same time.  Plan, kernel and R are tsqr_r's, bit
+ * for bit.  Other host memory (pageable) is copied whole to a device buffer of the workspace
+ * first.  Where the AUTO plan runs by panels (n >= 56, m >= 8 n), A is copied whole to a buffer
+ * of the call (stream-ordered) and the panels run on it, as tsqr_r does (R equals tsqr_r's bytes).
  *   A : host, column-major m x n, lda >= m.
  *   R : host, column-major n x n, ldr >= n, written as by tsqr_r.
  * Asynchronous on `stream` like tsqr_r: A must not be modified, nor R read, until the stream
- * has been synchronized (for m = 0, R is zeroed before the call returns).  Workspace: A's size
- * on the device plus the tree's slots, from the per-stream pool. */
+ * has been synchronized (for m = 0, R is zeroed before the call returns).  Workspace: the tree's
+ * slots and R, plus A's size when A is copied, from the per-stream pool. */
 tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                           int64_t ldr, tsqr_stream_t stream);
 
@@ -249,12 +262,17 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
  * loop that must not allocate after start-up, or a process whose framework has already
  * reserved the device's memory for its own caching allocator.  The paper has no counterpart;
  * this is a deployment variant of tsqr_r.
- *   Same arguments, plan, kernel and result as tsqr_r (FP64, AUTO plan).  Instead of the
- *   per-stream workspace it uses one static device array of TSQR_NOALLOC_SCRATCH_BYTES that
- *   every GPU loading the library holds until the process exits.  It calls no cudaMalloc,
- *   cudaFree or other allocating routine.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *     make that first call before any stream capture on that device.
+ *   Same arguments as tsqr_r (FP64).  It always runs ONE reduction with the AUTO plan's
+ *   one-reduction partition (tsqr_resolve_plan's plan, or the tuned plan of the bucket): where
+ *   tsqr_r's AUTO plan runs by panels (n >= 56, m >= 8 n), this call does not, and its R equals
+ *   tsqr_r's within the parity tolerance, not bit for bit; elsewhere the plan, kernel and R are
+ *   tsqr_r's.  Instead of the per-stream workspace it uses one static device array of
+ *   TSQR_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ *   exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     and keeps it for the life of the process; make that first call before any stream capture
+ *     on that device.  The address does not survive cudaDeviceReset: do not call this
+ *     function on a device after resetting it.
  *   - All calls share the array and it keeps the last call's contents (each call clears the
  *     part that must start at zero): calls that overlap on the GPU, on any streams, race and
  *     must be serialized by the caller.
@@ -262,7 +280,8 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
  *     counter per tree node; with the AUTO plan every n <= 80 fits, n = 128 does not)
  *     returns TSQR_ERR_UNSUPPORTED before enqueuing anything.
  *   - No device status is recorded: NaN/Inf still propagate into R, but
- *     tsqr_get_device_status() does not report them for these calls.                       */
+ *     tsqr_get_device_status() does not report them for these calls.
+ *   - tsqr_last_plan and tsqr_last_launch_count describe the call like any other.           */
 tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                              int64_t ldr, tsqr_stream_t stream);
 

@@ -26,15 +26,17 @@ SUCCESS, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_ALLOC, ERR_TIMEOUT, STA
 F64, F32, BF16 = 0, 1, 2
 PREC_F64, PREC_MIXED = 0, 1
 TREE_AUTO, TREE_BINARY, TREE_FLAT, TREE_HYBRID, TREE_PANELS = 0, 1, 2, 3, 4
+LEAF_AUTO, LEAF_FOLD, LEAF_PANELS = 0, 1, 2
 MAX_N = 128
 _TREES = {"auto": TREE_AUTO, "binary": TREE_BINARY, "flat": TREE_FLAT, "hybrid": TREE_HYBRID,
           "panels": TREE_PANELS}
 
 
 class Plan(ctypes.Structure):
-    """tsqr_plan_t: tree, tile_rows, ctas, warps, arity (zeros mean "choose")."""
+    """tsqr_plan_t: tree, tile_rows, ctas, warps, arity, leaf (zeros mean "choose")."""
     _fields_ = [("tree", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("ctas", ctypes.c_int32), ("warps", ctypes.c_int32), ("arity", ctypes.c_int32)]
+                ("ctas", ctypes.c_int32), ("warps", ctypes.c_int32), ("arity", ctypes.c_int32),
+                ("leaf", ctypes.c_int32)]
 
 
 _capi = None
@@ -89,6 +91,11 @@ def _load():
     capi.tsqr_r_noalloc.restype = _i32
     capi.tsqr_last_launch_count.argtypes = []
     capi.tsqr_last_launch_count.restype = _i32
+    # measurement and self-test hooks (not part of include/tsqr.h)
+    capi.tsqr_internal_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
+    capi.tsqr_internal_measure_peaks.restype = _i32
+    capi.tsqr_internal_tc_layout_selftest.argtypes = [_p, _i32, _i32, _i32]
+    capi.tsqr_internal_tc_layout_selftest.restype = _i32
 
     _capi = capi
     return capi
@@ -148,9 +155,12 @@ def empty_r(n: int, device=None):
     return torch.empty((n, n), dtype=torch.float64, device=device).T
 
 
-def make_plan(tree="auto", tile_rows=0, ctas=0, warps=0, arity=0) -> Plan:
+_LEAVES = {"auto": LEAF_AUTO, "fold": LEAF_FOLD, "panels": LEAF_PANELS}
+
+
+def make_plan(tree="auto", tile_rows=0, ctas=0, warps=0, arity=0, leaf="auto") -> Plan:
     return Plan(_TREES[tree] if isinstance(tree, str) else int(tree), int(tile_rows), int(ctas),
-                int(warps), int(arity))
+                int(warps), int(arity), _LEAVES[leaf] if isinstance(leaf, str) else int(leaf))
 
 
 def tsqr_r(A, R=None, stream=None):
@@ -244,10 +254,13 @@ def tsqr_caqr_r(A, panel: int = 0, R=None, plan: Plan | None = None, stream=None
     return R
 
 
-def tsqr_r_host(A, R=None, stream=None):
-    """tsqr_r for a CPU FP64 tensor A (logical (m, n), column-major, ideally pinned): the copy to
-    the device overlaps the leaf factorizations.  Returns R as a CPU (n, n) column-major tensor;
-    synchronize the stream before reading it."""
+def tsqr_r_host(A, R=None, stream=None, sync=True):
+    """tsqr_r for a CPU FP64 tensor A (logical (m, n), column-major): page-locked A (``pin_memory``)
+    is read in place by the device, other memory is copied to the device first.  Returns R as
+    a CPU (n, n) column-major tensor.  With ``sync`` (the default) the stream is synchronized
+    and the device status read before returning: R is then ready, and a device-side error
+    raises TsqrError (non-finite values in R only warn, as R still holds them).  With
+    ``sync=False`` synchronize the stream before reading R."""
     import torch
     if A.dim() != 2 or A.is_cuda or A.dtype != torch.float64:
         raise ValueError("A must be a 2-D CPU float64 tensor")
@@ -260,6 +273,13 @@ def tsqr_r_host(A, R=None, stream=None):
     ldr = max(R.stride(1) if n > 1 else n, n, 1)
     check(_load().tsqr_r_host(A.data_ptr(), m, n, lda, R.data_ptr(), ldr, _stream_ptr(stream)),
           "tsqr_r_host")
+    if sync:
+        st = int(_load().tsqr_get_device_status(_stream_ptr(stream)))
+        if st == STATUS_NONFINITE:
+            import warnings
+            warnings.warn("tsqr_r_host: R holds NaN or Inf", RuntimeWarning, stacklevel=2)
+        elif st != SUCCESS:
+            raise TsqrError(st, "tsqr_r_host")
     return R
 
 
@@ -333,3 +353,15 @@ def tsqr_resolve_plan(m, n, dtype=F64, prec=PREC_F64, plan: Plan | None = None) 
 
 def tsqr_last_launch_count() -> int:
     return int(_load().tsqr_last_launch_count())
+
+
+PEAK_NAMES = ("fp64_dfma", "fp32_ffma", "tf32_mma_sync", "tf32_tcgen05", "bf16_tcgen05")
+
+
+def measure_peaks() -> dict:
+    """Pipe peaks of the current GPU in TFLOP/s, measured by libtsqr's microbenchmarks (dense;
+    2 flops per FMA): FP64 DFMA, FP32 FFMA, TF32 through the warp-level mma and through
+    tcgen05.mma, BF16 through tcgen05.mma.  Synchronizes the device (about a second)."""
+    out = (ctypes.c_double * len(PEAK_NAMES))()
+    check(_load().tsqr_internal_measure_peaks(out, len(PEAK_NAMES)), "measure_peaks")
+    return dict(zip(PEAK_NAMES, list(out)))

@@ -27,11 +27,6 @@ cudaError_t q_leaf_wy_launch(const QLeafArgs &a, size_t smem_bytes, cudaStream_t
 cudaError_t qt_wy_launch(const QtArgs &a, size_t smem_bytes, cudaStream_t stream);
 cudaError_t trsm_launch(const double *R, int64_t ldr, const double *C, int64_t ldc, double *X,
                         int64_t ldx, int n, int k, int *status, cudaStream_t stream);
-// Streaming leaf kernel of tsqr_r_host (tsqr_host.cu)
-cudaError_t f64_stream_prepare(size_t smem_bytes);
-cudaError_t f64_stream_launch(const F64Args &a, const unsigned int *flags, int pieces,
-                              int64_t first, int warps, size_t smem_bytes, long long wait_iters,
-                              cudaStream_t stream);
 }  // namespace tsqr
 
 using namespace tsqr;
@@ -48,9 +43,6 @@ struct Workspace {
     // batched calls: the problem table and work items last copied to base + table_off
     std::vector<char> table;
     size_t table_off = 0;
-    // host-input calls: the copy stream and the events ordering it with the call's stream
-    cudaStream_t copy_stream = nullptr;
-    std::vector<cudaEvent_t> events;
 };
 
 std::mutex g_mu;
@@ -84,6 +76,7 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct F64Plan {
     int tree = TSQR_TREE_HYBRID;
+    int leaf = 0;                  // mixed path: TSQR_LEAF_FOLD or TSQR_LEAF_PANELS
     int warps = 4;
     int64_t unit = 0, nunits = 0;  // rows per work unit (tile or slab) and their count
     int h = 0, hs = 0, ldS = 0;    // chunk rows, shared-memory rows, leading dimension
@@ -149,6 +142,7 @@ tsqr_plan_t public_plan(const F64Plan &p) {
     o.ctas = p.nleaves;
     o.warps = p.warps;
     o.arity = p.arity;
+    o.leaf = p.leaf;
     return o;
 }
 
@@ -273,7 +267,7 @@ int floor_log2(int64_t m) {
 
 bool plan_is_auto(const tsqr_plan_t *p) {
     return !p || (p->tree == 0 && p->tile_rows == 0 && p->ctas == 0 && p->warps == 0 &&
-                  p->arity == 0);
+                  p->arity == 0 && p->leaf == 0);
 }
 
 bool tuned_plan(int dev, int64_t m, int n, bool mixed, tsqr_plan_t *out) {
@@ -371,6 +365,9 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
         over = &tuned;
     p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
     if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
+    if (over && over->leaf != 0 && (!mixed || over->leaf != TSQR_LEAF_FOLD))
+        return TSQR_ERR_INVALID_ARG;
+    p->leaf = mixed ? TSQR_LEAF_FOLD : 0;
     // bulk warps: 8 for the mixed path from n = 48 on, whose latency-bound FP32 sweep gains
     // from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms with 4, 52.1 with
     // 12), and 12 from n = 96 on where they fit (2^24 x 96: FP32 143.6 against 177.4 ms, BF16
@@ -668,28 +665,11 @@ tsqr_status_t run_qr(const double *A, int64_t m, int64_t n, int64_t lda, double 
     return TSQR_SUCCESS;
 }
 
-// A page-locked host word holding 1 (the value of an arrived piece's flag), allocated once.
-const unsigned int *host_ones() {
-    static unsigned int *ones = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        if (cudaHostAlloc((void **)&ones, sizeof(unsigned int), cudaHostAllocPortable) ==
-            cudaSuccess)
-            *ones = 1u;
-        else
-            ones = nullptr;
-    });
-    return ones;
-}
-
-// Host-input FP64 call: A and R in host memory.  With page-locked A, A is copied in P row
-// pieces on a copy stream while one streaming launch (tsqr_host.cu) already folds the pieces
-// that have arrived; otherwise A is copied whole and the ordinary kernel runs.  The plan is the
-// AUTO plan.  Workspace: counters | tree slots | piece flags | A (ld m) | R (ld n).
+// Host-input FP64 call: A and R in host memory.
 // Host input where the AUTO plan runs by panels (n >= 56, tall): A copied whole into a buffer
 // of this call (stream-ordered; the panels take the stream's pooled workspace themselves), the
-// panels, and R copied back.  The panels' updates need every column, so there is no piece-wise
-// overlap as in the one reduction's streaming kernel.
+// panels, and R copied back.  The panels' updates read every column more than once, so A is
+// brought to HBM first.
 tsqr_status_t run_host_panels(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                               int64_t ldr, int64_t nb, cudaStream_t stream) {
     double *Ad = nullptr, *Rd = nullptr;
@@ -725,6 +705,23 @@ tsqr_status_t run_host_panels(const double *A, int64_t m, int64_t n, int64_t lda
     return st;
 }
 
+// The device address of page-locked host memory, or null for memory the device cannot address
+// in place (pageable memory, or a registration without a device mapping).
+const double *mapped_device_ptr(const double *A) {
+    cudaPointerAttributes attr;
+    const double *d = nullptr;
+    if (cudaPointerGetAttributes(&attr, A) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+        d = static_cast<const double *>(attr.devicePointer);
+    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    return d;
+}
+
+// One reduction (the AUTO plan, as tsqr_r) on host A.  Page-locked A is read in place: the
+// leaves' cp.async loads go through the device mapping of A's pages (NVLink-C2C on a Grace
+// host), so the transfer of A is spread over the whole factorization and overlaps it without a
+// second stream, flags or waits; the kernel is tsqr_r's, with tsqr_r's plan, so R is tsqr_r's
+// bit for bit.  Other host memory is copied whole to a device buffer of the workspace first.
+// Workspace: counters | tree slots | R (ld n) | [A (ld m), when staged].
 tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, double *R,
                            int64_t ldr, cudaStream_t stream) {
     g_last_launches = 0;
@@ -741,94 +738,42 @@ tsqr_status_t run_f64_host(const double *A, int64_t m, int64_t n, int64_t lda, d
         const int64_t nb = panels_width(m, n, nullptr, dev);
         if (nb > 0) return run_host_panels(A, m, n, lda, R, ldr, nb, stream);
     }
-    cudaPointerAttributes attr;
-    const bool pinned = cudaPointerGetAttributes(&attr, A) == cudaSuccess &&
-                        attr.type == cudaMemoryTypeHost;
-    cudaGetLastError();  // an unregistered pointer may leave an error behind
+    const double *Amapped = mapped_device_ptr(A);
     F64Plan p;
     tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
     g_last_plan = public_plan(p);
-    // pieces: the leaves' first round alone (every leaf starts after the smallest copy), then
-    // the rest in up to 15 equal pieces
-    const int64_t first = std::min<int64_t>(p.nleaves, p.nunits);
-    const int P = (int)std::min<int64_t>(16, 1 + (p.nunits - first));
+    if (f64_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
-    const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
-    const size_t a_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
-    const size_t r_bytes = (size_t)n * (size_t)n * sizeof(double);
+    const size_t r_bytes = align_up((size_t)n * (size_t)n * sizeof(double), 256);
+    const size_t a_bytes = Amapped ? 0 : (size_t)m * (size_t)n * sizeof(double);
     Workspace *ws = nullptr;
-    st = get_workspace(stream, cnt_bytes + slot_bytes + flag_bytes + a_bytes + r_bytes, &ws);
+    st = get_workspace(stream, cnt_bytes + slot_bytes + r_bytes + a_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!ws->copy_stream &&
-            cudaStreamCreateWithFlags(&ws->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
-            return TSQR_ERR_CUDA;
-        while (ws->events.size() < 2) {
-            cudaEvent_t e;
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-                return TSQR_ERR_CUDA;
-            ws->events.push_back(e);
-        }
-    }
     char *base = (char *)ws->base;
-    unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
-    double *Ad = (double *)(base + cnt_bytes + slot_bytes + flag_bytes);
-    double *Rd = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
-    F64Args a = plan_args(p, Ad, m, n, m);
+    double *Rd = (double *)(base + cnt_bytes + slot_bytes);
+    const double *Ain = Amapped;
+    int64_t ld_in = lda;
+    if (!Amapped) {
+        double *Ad = (double *)(base + cnt_bytes + slot_bytes + r_bytes);
+        if (cudaMemcpy2DAsync(Ad, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
+                              (size_t)m * sizeof(double), (size_t)n, cudaMemcpyHostToDevice,
+                              stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        Ain = Ad;
+        ld_in = m;
+    }
+    F64Args a = plan_args(p, Ain, m, n, ld_in);
     a.counters = (unsigned int *)base;
     a.slots = (double *)(base + cnt_bytes);
     a.R = Rd;
     a.ldr = n;
     a.status = ws->status;
-    if (!pinned || p.unit != p.h || !host_ones()) {
-        // staged copy of the whole of A, then the ordinary kernel
-        if (cudaMemcpy2DAsync(Ad, (size_t)m * sizeof(double), A, (size_t)lda * sizeof(double),
-                              (size_t)m * sizeof(double), (size_t)n, cudaMemcpyHostToDevice,
-                              stream) != cudaSuccess ||
-            cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
-                cudaSuccess)
-            return TSQR_ERR_CUDA;
-        if (f64_prepare(p.smem) != cudaSuccess ||
-            f64_launch(a, p.warps, p.smem, stream) != cudaSuccess)
-            return TSQR_ERR_CUDA;
-    } else {
-        cudaStream_t cs = ws->copy_stream;
-        // the copy stream starts after earlier work on `stream` (which may still read A) and
-        // zeroes the piece flags before the kernel, launched after that, can poll them
-        if (cudaEventRecord(ws->events[0], stream) != cudaSuccess ||
-            cudaStreamWaitEvent(cs, ws->events[0], 0) != cudaSuccess ||
-            cudaMemsetAsync(flags, 0, (size_t)P * sizeof(unsigned int), cs) != cudaSuccess ||
-            cudaEventRecord(ws->events[1], cs) != cudaSuccess ||
-            cudaStreamWaitEvent(stream, ws->events[1], 0) != cudaSuccess ||
-            cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
-                cudaSuccess)
-            return TSQR_ERR_CUDA;
-        if (f64_stream_prepare(p.smem) != cudaSuccess ||
-            f64_stream_launch(a, flags, P, first, p.warps, p.smem, 1LL << 23, stream) !=
-                cudaSuccess)
-            return TSQR_ERR_CUDA;
-        const int64_t rest = p.nunits - first;
-        for (int q = 0; q < P; ++q) {
-            const int64_t u0 = q == 0 ? 0 : first + ((int64_t)(q - 1) * rest) / (P - 1);
-            const int64_t u1 = q == 0 ? first : first + ((int64_t)q * rest) / (P - 1);
-            const int64_t r0 = std::min<int64_t>(u0 * p.unit, m);
-            const int64_t r1 = std::min<int64_t>(u1 * p.unit, m);
-            // one contiguous copy per column segment (copy engines), then the piece's flag
-            for (int64_t c = 0; c < n && r1 > r0; ++c)
-                if (cudaMemcpyAsync(Ad + r0 + c * m, A + r0 + c * lda,
-                                    (size_t)(r1 - r0) * sizeof(double), cudaMemcpyHostToDevice,
-                                    cs) != cudaSuccess)
-                    return TSQR_ERR_CUDA;
-            // the flag is copied from page-locked host memory: a copy-engine transfer, which
-            // needs no SM while the streaming kernel occupies them all
-            if (cudaMemcpyAsync(flags + q, host_ones(), sizeof(unsigned int),
-                                cudaMemcpyHostToDevice, cs) != cudaSuccess)
-                return TSQR_ERR_CUDA;
-        }
-    }
+    if (cudaMemsetAsync(a.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+            cudaSuccess ||
+        f64_launch(a, p.warps, p.smem, stream) != cudaSuccess)
+        return TSQR_ERR_CUDA;
     if (cudaMemcpy2DAsync(R, (size_t)ldr * sizeof(double), Rd, (size_t)n * sizeof(double),
                           (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost,
                           stream) != cudaSuccess)
@@ -1392,6 +1337,98 @@ tsqr_status_t run_lstsq_panels(const double *A, int64_t m, int64_t n, int64_t ld
     return st;
 }
 
+// Plan of the blocked mixed leaf (TSQR_LEAF_PANELS): chunks of h = 256 or 512 rows (AUTO: the
+// taller one that keeps two CTAs per SM, for two CTAs' reflector chains to hide each other;
+// else 256), work units of one chunk (HYBRID, FLAT) or one tile (BINARY), the largest tree
+// arity whose stacked FP64 triangles fit the chunk region.
+tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    const DeviceInfo di = device_info(dev);
+    if (di.sms <= 0) return TSQR_ERR_CUDA;
+    if (n < 1 || n > kMixedWyMaxN) return TSQR_ERR_UNSUPPORTED;
+    p->leaf = TSQR_LEAF_PANELS;
+    p->tree = (over && over->tree) ? over->tree : TSQR_TREE_HYBRID;
+    if (p->tree < TSQR_TREE_BINARY || p->tree > TSQR_TREE_HYBRID) return TSQR_ERR_INVALID_ARG;
+    if (over && (over->warps != 0 && over->warps != 8)) return TSQR_ERR_INVALID_ARG;
+    if (over && (over->tile_rows < 0 || over->ctas < 0 || over->arity < 0))
+        return TSQR_ERR_INVALID_ARG;
+    p->warps = 8;
+    const int64_t mm = std::max<int64_t>(m, 1);
+    const size_t reserve = 1024;
+    int h;
+    if (p->tree == TSQR_TREE_BINARY) {
+        p->unit = (over && over->tile_rows > 0) ? over->tile_rows : 256;
+        h = (p->unit >= 512 && p->unit % 512 == 0) ? 512 : 256;
+    } else if (over && over->tile_rows > 0) {
+        if (over->tile_rows != 256 && over->tile_rows != 512) return TSQR_ERR_INVALID_ARG;
+        h = over->tile_rows;
+        p->unit = h;
+    } else {
+        h = (2 * (mixed_wy_smem_bytes(n, 512) + reserve) <= di.smem_sm) ? 512 : 256;
+        p->unit = h;
+    }
+    p->h = h;
+    p->hs = h;
+    p->ldS = 0;
+    p->blk = h / 256;
+    p->vec = 1;
+    p->smem = mixed_wy_smem_bytes(n, h);
+    if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
+    p->nunits = (mm + p->unit - 1) / p->unit;
+    int64_t leaves;
+    if (p->tree == TSQR_TREE_FLAT) {
+        leaves = 1;
+    } else if (p->tree == TSQR_TREE_BINARY) {
+        leaves = p->nunits;
+    } else if (over && over->ctas > 0) {
+        leaves = over->ctas;
+    } else {
+        if (mixed_wy_prepare(p->smem) != cudaSuccess) return TSQR_ERR_CUDA;
+        leaves = (int64_t)di.sms * std::max(1, mixed_wy_blocks_per_sm(h, p->smem));
+    }
+    leaves = std::min<int64_t>(leaves, p->nunits);
+    if (leaves < 1 || leaves > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
+    p->nleaves = (int)leaves;
+    if (p->tree == TSQR_TREE_BINARY) {
+        p->arity = 2;
+    } else if (over && over->arity > 0) {
+        if (over->arity < 2 || over->arity > 8) return TSQR_ERR_INVALID_ARG;
+        p->arity = over->arity;
+    } else {
+        p->arity = mixed_wy_arity(n, h);
+    }
+    if (!mixed_wy_tree_fits(n, h, p->arity)) return TSQR_ERR_UNSUPPORTED;
+    p->ldSd = tree_ldsd(n, p->arity);
+    p->s_doubles = 0;
+    return build_tree(leaves, p->arity, &p->shape, &p->nodes);
+}
+
+// The mixed path's plan: the tuned plan of the bucket for AUTO calls, then the blocked leaf
+// where it applies (TSQR_LEAF_PANELS requested, or AUTO with n <= kMixedWyMaxN), else the fold.
+tsqr_status_t plan_mixed(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    tsqr_plan_t tuned;
+    if (plan_is_auto(over) && tuned_plan(dev, m, n, true, &tuned)) over = &tuned;
+    const int leaf = over ? over->leaf : 0;
+    // AUTO leaf: the panels where they apply and the plan's knobs are theirs (8 or 0 warps;
+    // chunks of 256 or 512 rows unless the tree is BINARY); else the fold
+    const bool wy_knobs =
+        !over || ((over->warps == 0 || over->warps == 8) &&
+                  (over->tree == TSQR_TREE_BINARY || over->tile_rows == 0 ||
+                   over->tile_rows == 256 || over->tile_rows == 512));
+    if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && n <= kMixedWyMaxN && wy_knobs)) {
+        tsqr_plan_t o = over ? *over : tsqr_plan_t{};
+        o.leaf = TSQR_LEAF_PANELS;
+        return plan_mixed_wy(m, n, &o, p);
+    }
+    if (leaf != 0 && leaf != TSQR_LEAF_FOLD) return TSQR_ERR_INVALID_ARG;
+    tsqr_plan_t o = over ? *over : tsqr_plan_t{};
+    o.leaf = 0;
+    return plan_leaf(m, n, plan_is_auto(&o) ? nullptr : &o, true, p);
+}
+
 tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t lda, double *R,
                         int64_t ldr, const tsqr_plan_t *over, cudaStream_t stream) {
     g_last_launches = 0;
@@ -1399,30 +1436,38 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) return zero_r(R, n, ldr, stream);
     F64Plan p;
-    tsqr_status_t st = plan_leaf(m, (int)n, over, true, &p);
+    tsqr_status_t st = plan_mixed(m, (int)n, over, &p);
     if (st != TSQR_SUCCESS) return st;
-    g_last_plan = public_plan(p);
-    if (mixed_prepare(p.smem) != cudaSuccess) return TSQR_ERR_CUDA;
+    const bool wy = p.leaf == TSQR_LEAF_PANELS;
+    if ((wy ? mixed_wy_prepare(p.smem) : mixed_prepare(p.smem)) != cudaSuccess)
+        return TSQR_ERR_CUDA;
     const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
     const size_t slot_bytes = (size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double);
     Workspace *ws = nullptr;
     st = get_workspace(stream, cnt_bytes + slot_bytes, &ws);
     if (st != TSQR_SUCCESS) return st;
-    MixedArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.base = plan_args(p, nullptr, m, n, lda);
-    a.base.counters = (unsigned int *)ws->base;
-    a.base.slots = (double *)((char *)ws->base + cnt_bytes);
-    a.base.R = R;
-    a.base.ldr = ldr;
-    a.base.status = ws->status;
-    a.A = A;
-    a.ldSd = p.ldSd;
-    a.s_doubles = p.s_doubles;
-    if (cudaMemsetAsync(a.base.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
+    F64Args base = plan_args(p, nullptr, m, n, lda);
+    base.counters = (unsigned int *)ws->base;
+    base.slots = (double *)((char *)ws->base + cnt_bytes);
+    base.R = R;
+    base.ldr = ldr;
+    base.status = ws->status;
+    if (cudaMemsetAsync(base.counters, 0, (size_t)p.nodes * sizeof(unsigned int), stream) !=
         cudaSuccess)
         return TSQR_ERR_CUDA;
-    if (mixed_launch(a, bf16, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (wy) {
+        if (mixed_wy_launch(base, A, bf16, p.ldSd, p.smem, stream) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+    } else {
+        MixedArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.base = base;
+        a.A = A;
+        a.ldSd = p.ldSd;
+        a.s_doubles = p.s_doubles;
+        if (mixed_launch(a, bf16, p.warps, p.smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    }
+    g_last_plan = public_plan(p);
     g_last_launches = 1;
     return TSQR_SUCCESS;
 }
@@ -1575,7 +1620,7 @@ namespace tsqr {
 // The AUTO plan of tsqr_r expressed as kernel arguments (A, R, workspace and status left for
 // the caller to fill), for entry points that bring their own workspace.
 tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,
-                            int64_t *nodes) {
+                            int64_t *nodes, tsqr_plan_t *plan) {
     F64Plan p;
     const tsqr_status_t st = plan_f64(m, n, nullptr, &p);
     if (st != TSQR_SUCCESS) return st;
@@ -1583,7 +1628,13 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
     *warps = p.warps;
     *smem = p.smem;
     *nodes = p.nodes;
+    *plan = public_plan(p);
     return TSQR_SUCCESS;
+}
+
+void set_last_call(int launches, const tsqr_plan_t &plan) {
+    g_last_launches = launches;
+    g_last_plan = plan;
 }
 
 }  // namespace tsqr
@@ -1629,44 +1680,6 @@ tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, i
     if (f64) return run_f64((const double *)A, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
     if (dtype == TSQR_F64 || prec == TSQR_PREC_F64) return TSQR_ERR_INVALID_ARG;
     return run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, plan, (cudaStream_t)stream);
-}
-
-// Test hook (not part of the C ABI's documented calls): one streaming launch over a device
-// buffer of m x n zeros whose pieces never arrive (their flags stay zero), each wait limited to
-// wait_iters polls; the CTAs give up, record the timeout in the status word and return, and
-// tsqr_get_device_status(stream) then reports TSQR_ERR_TIMEOUT.  Exercises the failure path of
-// tsqr_r_host's bounded waits without a fault or a hang.
-int tsqr_internal_stream_timeout_selftest(int64_t m, int64_t n, int64_t wait_iters,
-                                          tsqr_stream_t stream) {
-    if (m < 1 || n < 1 || n > TSQR_MAX_N || wait_iters < 1) return TSQR_ERR_INVALID_ARG;
-    const cudaStream_t s = (cudaStream_t)stream;
-    F64Plan p;
-    tsqr_status_t st = plan_f64(m, (int)n, nullptr, &p);
-    if (st != TSQR_SUCCESS) return st;
-    const int64_t first = std::min<int64_t>(p.nleaves, p.nunits);
-    const int P = (int)std::min<int64_t>(16, 1 + (p.nunits - first));
-    const size_t cnt_bytes = align_up((size_t)p.nodes * sizeof(unsigned int), 256);
-    const size_t slot_bytes = align_up((size_t)p.nodes * (size_t)n * (size_t)n * sizeof(double), 256);
-    const size_t flag_bytes = align_up((size_t)P * sizeof(unsigned int), 256);
-    const size_t a_bytes = align_up((size_t)m * (size_t)n * sizeof(double), 256);
-    const size_t r_bytes = (size_t)n * (size_t)n * sizeof(double);
-    Workspace *ws = nullptr;
-    st = get_workspace(s, cnt_bytes + slot_bytes + flag_bytes + a_bytes + r_bytes, &ws);
-    if (st != TSQR_SUCCESS) return st;
-    char *base = (char *)ws->base;
-    F64Args a = plan_args(p, (double *)(base + cnt_bytes + slot_bytes + flag_bytes), m, n, m);
-    a.counters = (unsigned int *)base;
-    a.slots = (double *)(base + cnt_bytes);
-    a.R = (double *)(base + cnt_bytes + slot_bytes + flag_bytes + a_bytes);
-    a.ldr = n;
-    a.status = ws->status;
-    unsigned int *flags = (unsigned int *)(base + cnt_bytes + slot_bytes);
-    if (cudaMemsetAsync(base, 0, cnt_bytes + slot_bytes + flag_bytes + a_bytes, s) != cudaSuccess ||
-        f64_stream_prepare(p.smem) != cudaSuccess ||
-        f64_stream_launch(a, flags, P, first, p.warps, p.smem, (long long)wait_iters, s) !=
-            cudaSuccess)
-        return TSQR_ERR_CUDA;
-    return TSQR_SUCCESS;
 }
 
 tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *B,
@@ -1792,8 +1805,6 @@ void tsqr_release_workspace(void) {
         cudaDeviceSynchronize();
         if (kv.second.base) cudaFree(kv.second.base);
         if (kv.second.status) cudaFree(kv.second.status);
-        for (cudaEvent_t e : kv.second.events) cudaEventDestroy(e);
-        if (kv.second.copy_stream) cudaStreamDestroy(kv.second.copy_stream);
     }
     g_ws.clear();
     cudaSetDevice(cur);
@@ -1824,13 +1835,9 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
         }
     }
     F64Plan p;
-    tsqr_status_t st = plan_leaf(m, (int)n, plan, mixed, &p);
+    tsqr_status_t st = mixed ? plan_mixed(m, (int)n, plan, &p) : plan_leaf(m, (int)n, plan, false, &p);
     if (st != TSQR_SUCCESS) return st;
-    out->tree = p.tree;
-    out->tile_rows = (int32_t)p.unit;
-    out->ctas = p.nleaves;
-    out->warps = p.warps;
-    out->arity = p.arity;
+    *out = public_plan(p);
     return TSQR_SUCCESS;
 }
 
@@ -1866,7 +1873,8 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
                 if (tile < n) continue;
                 const int64_t units = (m + tile - 1) / tile;
                 tsqr_plan_t c{TSQR_TREE_HYBRID, (int32_t)tile,
-                              (int32_t)std::min<int64_t>((int64_t)di.sms * k, units), W, 0};
+                              (int32_t)std::min<int64_t>((int64_t)di.sms * k, units), W, 0,
+                              mixed ? TSQR_LEAF_FOLD : 0};
                 bool dup = false;
                 for (const auto &o : cands)
                     dup |= (o.tile_rows == c.tile_rows && o.ctas == c.ctas && o.warps == c.warps);
@@ -1875,7 +1883,19 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
         }
     }
     if (f64 && n >= 48 && m >= 8 * n)
-        for (int32_t nb : {16, 32}) cands.push_back(tsqr_plan_t{TSQR_TREE_PANELS, nb, 0, 0, 0});
+        for (int32_t nb : {16, 32}) cands.push_back(tsqr_plan_t{TSQR_TREE_PANELS, nb, 0, 0, 0, 0});
+    // the blocked mixed leaf: chunks of 256 or 512 rows with as many CTAs as fit on every SM
+    if (mixed && n <= kMixedWyMaxN)
+        for (int32_t hh : {256, 512}) {
+            const size_t sm_b = mixed_wy_smem_bytes((int)n, hh);
+            if (sm_b > di.smem_block_optin || mixed_wy_prepare(sm_b) != cudaSuccess) continue;
+            const int per_sm = std::max(1, mixed_wy_blocks_per_sm(hh, sm_b));
+            const int64_t units = (m + hh - 1) / hh;
+            for (int k = 1; k <= per_sm; ++k)
+                cands.push_back(tsqr_plan_t{TSQR_TREE_HYBRID, hh,
+                                            (int32_t)std::min<int64_t>((int64_t)di.sms * k, units),
+                                            8, 0, TSQR_LEAF_PANELS});
+        }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return TSQR_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {

@@ -11,7 +11,7 @@
 namespace tsqr {
 
 constexpr int kStatusNonfiniteBit = 1;
-constexpr int kStatusTimeoutBit = 2;  // a bounded device-side wait gave up (tsqr_r_host)
+constexpr int kStatusTimeoutBit = 2;  // a bounded device-side wait gave up
 
 // Dynamic shared-memory size of a kernel, with the whole unified L1/shared array given to
 // shared memory (the kernels keep their working set there and read A past L1).
@@ -42,6 +42,17 @@ int mixed_blocks_per_sm(int warps, size_t smem_bytes);
 cudaError_t mixed_launch(const MixedArgs &a, bool bf16, int warps, size_t smem_bytes,
                          cudaStream_t stream);
 
+// Blocked mixed path (tsqr_mixed_wy.cu): panels of 16 columns, compact WY updates on the
+// tensor cores; n <= kMixedWyMaxN, chunks of h = 256 or 512 rows, 8 warps.
+constexpr int kMixedWyMaxN = 64;
+size_t mixed_wy_smem_bytes(int n, int h);
+int mixed_wy_arity(int n, int h);
+bool mixed_wy_tree_fits(int n, int h, int arity);
+cudaError_t mixed_wy_prepare(size_t smem_bytes);
+int mixed_wy_blocks_per_sm(int h, size_t smem_bytes);
+cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int ldSd,
+                            size_t smem_bytes, cudaStream_t stream);
+
 // Batched path (tsqr_batched.cu); dtype 0 FP64, 1 FP32, 2 BF16; `warps` counts bulk warps.
 cudaError_t batched_prepare(int dtype, size_t smem_bytes);
 int batched_blocks_per_sm(int dtype, int warps, size_t smem_bytes);
@@ -59,9 +70,13 @@ cudaError_t q_tree_launch(const QTreeArgs &a, int grid, size_t smem_bytes, cudaS
 cudaError_t q_leaf_launch(const QLeafArgs &a, int blk, int warps, size_t smem_bytes,
                           cudaStream_t stream);
 
-// The AUTO plan of tsqr_r as kernel arguments (tsqr_api.cu); A, R, workspace and status
-// pointers are left for the caller.
+// The AUTO plan of tsqr_r's one reduction as kernel arguments (tsqr_api.cu); A, R, workspace
+// and status pointers are left for the caller.  *plan receives its public form.
 tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *smem,
-                            int64_t *nodes);
+                            int64_t *nodes, tsqr_plan_t *plan);
+
+// What tsqr_last_launch_count and tsqr_last_plan report for the calling thread (tsqr_api.cu),
+// for entry points outside tsqr_api.cu.
+void set_last_call(int launches, const tsqr_plan_t &plan);
 
 }  // namespace tsqr

@@ -1,0 +1,797 @@
+// Blocked mixed-precision leaf of libtsqr (FP32 or BF16 A): the flat fold R <- R([R; chunk])
+// of Section 2's step 1 done by panels of 16 columns, each panel's reflectors applied to the
+// columns right of it as one compact WY block on the tensor cores.
+//
+// Per chunk of h rows (in shared memory as FP32) and per panel P of 16 columns:
+//   1. Panel factorization, column by column (the LAPACK dlarfg rule of the paper's operator,
+//      Table 3): each thread holds its rows of the panel in registers; for reflector J the
+//      threads update column J and the panel's later columns by reflector J-1 and form the
+//      16 dot products of column J with every panel column (its squared norm, the dot
+//      products with the earlier tails that the block's T factor needs, and those with the
+//      later columns).
+//      The per-lane partials are FP32 (one or two rows); every sum across lanes and warps and
+//      every reflector scalar (beta, tau, 1/(alpha - beta)) is in double-FP32 arithmetic
+//      (hi + lo pairs, about 44-48 bits) on the FP32 pipe.  Per reflector: every warp sums its
+//      lanes' partials, one barrier, warp 0 sums the warps' and forms the scalars, row J of R
+//      and the factors of the later columns, a second barrier.
+//   2. Compact WY form of the panel: with the tails x_J kept UNSCALED in the chunk and
+//      v_J = [e_J; c_J x_J], the product H_0 ... H_15 equals I - V S V^T (LAPACK's dlarft
+//      forward recurrence, S^-1 = diag(1 / tau) + strict_upper(G) in Joffrain et al.'s form),
+//      G(i, J) = c_i c_J x_i . x_J.  Column J - 1 of S is formed by warp 1 during reflector J's
+//      scalars.
+//   3. Trailing update of the columns T right of the panel (rows P of R, all rows of the
+//      chunk): Z = X^T C(:, T) (tensor cores), W = R(P, T) + diag(c) Z, Y = S^T W,
+//      R(P, T) -= Y, C(:, T) -= X (diag(c) Y) (tensor cores).
+// The tensor-core products are split-TF32 (compensated) products with FP32 accumulation: every
+// FP32 operand is exactly three TF32 parts (11 + 11 + 2 significant bits), diag(c) Y is split
+// into three too, and the six partial products down to 2^-22 of the leading one are summed
+// (the smallest first), so each product is as accurate as an FP32 dot product.  R is held in double-FP32 during the leaf and converted (exactly) to
+// FP64 for the FP64 tree (climb_tree / fold_stack, the paper's operator).
+//
+// Why this precision split: everything that multiplies the running triangle R (the reflector
+// scalars, S, the R rows) is accurate to far below FP32 rounding, so R's accumulated content
+// is transformed orthogonally to that accuracy chunk after chunk; the FP32 roundings land in
+// the chunk's rows.  The tails being exactly three TF32 parts makes the V the tensor cores use
+// and the V that S is built from the same matrix: the tails are used exactly as stored.
+#include <cuda_bf16.h>
+
+#include "tsqr_fold.cuh"
+#include "tsqr_tc.cuh"
+
+namespace tsqr {
+
+namespace wy {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = 8;
+constexpr int kPw = 16;       // panel width
+constexpr int kMaxUnits = 8;  // tensor-core units of the Z product (n-tile x row group)
+
+// ------------------------------------------------------------------------------------------
+// Double-FP32 ("df") arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2.  Error-free
+// transformations (Knuth's TwoSum, Dekker's fast TwoSum, TwoProduct by FMA) in round-to-nearest
+// intrinsics, which the compiler never contracts or reorders.
+// ------------------------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df mk(float h, float l = 0.f) {
+    df r;
+    r.hi = h;
+    r.lo = l;
+    return r;
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return mk(s, e);
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return mk(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df dadd(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df dneg(df a) { return mk(-a.hi, -a.lo); }
+__device__ __forceinline__ df dsub(df a, df b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return mk(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ df dmul(df a, df b) {
+    const df p = two_prod(a.hi, b.hi);
+    return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+// The hardware's approximate reciprocal and square root (about 2^-22 relative); one Newton
+// step in double-FP32 below makes either accurate to about 2^-44.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// 1/a: one Newton step y + y (1 - a y) from the approximate reciprocal y
+__device__ __forceinline__ df drecip(df a) {
+    const float y = rcp_approx(a.hi);
+    const df e = dsub(mk(1.f), dmul(a, mk(y)));
+    return fast_two_sum(y, __fmul_rn(y, e.hi));
+}
+// sqrt(a), a > 0: one Newton step y + (a - y^2) / (2 y) from the approximate square root
+__device__ __forceinline__ df dsqrt(df a) {
+    const float y = sqrt_approx(a.hi);
+    const df e = dsub(a, two_prod(y, y));
+    return fast_two_sum(y, __fmul_rn(e.hi, rcp_approx(__fmul_rn(2.f, y))));
+}
+__device__ __forceinline__ df shfl_df(df v, int src, int width = 32) {
+    return mk(__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width));
+}
+__device__ __forceinline__ df shfl_xor_df(df v, int m) {
+    return mk(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
+// Reflector J's scalars (the dlarfg rule: beta = -sign(alpha) sqrt(alpha^2 + sigma^2),
+// sign(0) = +1; an exactly zero tail gives the identity) in double-FP32.
+struct Refl {
+    df beta, tau, c, ib;
+    bool ident;
+};
+__device__ __forceinline__ Refl make_refl(const df alpha, const df sig2) {
+    Refl r;
+    r.ident = (sig2.hi == 0.f);
+    r.beta = alpha;
+    r.tau = mk(0.f);
+    r.c = mk(0.f);
+    r.ib = mk(0.f);
+    if (!r.ident) {
+        const df rt = dsqrt(dadd(dmul(alpha, alpha), sig2));
+        const bool pos = alpha.hi >= 0.f;
+        r.beta = pos ? dneg(rt) : rt;
+        r.ib = drecip(r.beta);
+        r.tau = dmul(dsub(r.beta, alpha), r.ib);
+        r.c = drecip(dsub(alpha, r.beta));
+    }
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// TF32 parts.  to_tf32 rounds to 11 significant bits (nearest, ties away).
+// ------------------------------------------------------------------------------------------
+// x (FP32, 24 bits) = h + m + l exactly
+__device__ __forceinline__ void split3(float x, float &h, float &m, float &l) {
+    h = tc::to_tf32(x);
+    const float r = __fsub_rn(x, h);
+    m = tc::to_tf32(r);
+    l = tc::to_tf32(__fsub_rn(r, m));
+}
+// a double-FP32 value to three TF32 parts (33 bits)
+__device__ __forceinline__ void split3_df(df x, float &h, float &m, float &l) {
+    h = tc::to_tf32(x.hi);
+    const df r = two_sum(__fsub_rn(x.hi, h), x.lo);
+    m = tc::to_tf32(r.hi);
+    l = tc::to_tf32(__fadd_rn(__fsub_rn(r.hi, m), r.lo));
+}
+
+// ------------------------------------------------------------------------------------------
+// The chunk in shared memory: FP32, in boxes of 32 rows x 16 columns (2 KB), box (i / 32,
+// col / 16) at ((i / 32) NP + col / 16) 2048 bytes; in a box, column col % 16 is one 128-byte
+// line, its 16-byte units XOR-swizzled by col % 8 (the layout of a 128-byte-swizzled TMA box):
+// a warp reading 32 consecutive rows of a column, or 4 consecutive rows of 8 columns, touches
+// 32 different banks.  Returns the float index.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int cidx(int i, int col, int NP) {
+    return ((((i >> 5) * NP + (col >> 4)) << 9) + ((col & 15) << 5) +
+            ((((i & 31) >> 2) ^ (col & 7)) << 2) + (i & 3));
+}
+
+// Shared-memory carve-up (bytes), identical on host and device.
+struct Layout {
+    int C;      // the chunk (h x 16 NP floats); the tree's FP64 stacked triangles afterwards
+    int R;      // R, packed upper triangle row by row, one df (8 bytes) per entry; FP64 later
+    int red;    // cross-warp partial sums: 2 buffers x 8 warps x 16 df
+    int tau;    // 16 df
+    int cc;     // 16 df
+    int G;      // 16 x 16 df: x_i . x_J (i < J), scaled by c_i c_J before S is formed
+    int S;      // 16 x 16 df (column-major)
+    int bar;    // the mbarrier (8 bytes) and the tensor-memory address (4 bytes)
+    int fsh;    // 16 floats: the factors f_k of the reflector just formed
+    int W;      // 16 x ntmax df: W, then Y
+    int B;      // diag(c) Y in three TF32 parts, K-major operands of 16 x ntmax16 each
+    int P;      // kMaxUnits x 16 x 8 floats: partial Z tiles
+    int f, seg, tot, flag;  // the tree's buffers (overlay W.. once the chunks are done)
+    int total;
+};
+
+__host__ __device__ inline int round_up_i(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline Layout layout(int n, int h) {
+    Layout L;
+    const int NP = (n + kPw - 1) / kPw;
+    const int ntmax = round_up_i(n, 8) - kPw > 0 ? round_up_i(n, 8) - kPw : 8;
+    const int ntmax16 = round_up_i(n, 16) - kPw > 0 ? round_up_i(n, 16) - kPw : 16;
+    int o = 0;
+    L.C = o;   o += h * NP * 64;
+    L.R = o;   o += round_up_i(n * (n + 1) / 2 * 8, 16);
+    L.red = o; o += 2 * kWarps * 16 * 8;
+    L.tau = o; o += 16 * 8;
+    L.cc = o;  o += 16 * 8;
+    L.G = o;   o += 16 * 16 * 8;
+    L.S = o;   o += 16 * 16 * 8;
+    L.bar = o; o += 16;
+    L.fsh = o; o += 16 * 4;
+    const int chunk_end_base = o;
+    L.W = o;   o += 16 * ntmax * 8;
+    L.B = o;   o += 3 * ntmax16 * 64;
+    L.P = o;   o += kMaxUnits * 16 * 8 * 4;
+    const int chunk_end = o;
+    // the tree (after the last chunk) reuses the region from W on
+    int t = chunk_end_base;
+    L.f = t;    t += (n + 1) * 8;
+    L.seg = t;  t += kWarps * seg_stride(n) * 8;
+    L.tot = t;  t += 2 * seg_stride(n) * 8;
+    L.flag = t; t += 16;
+    L.total = chunk_end > t ? chunk_end : t;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------------
+// Warp-wide sums of 16 FP32 partials per lane, in double-FP32: a transposing butterfly (each
+// level halves the values a lane keeps and exchanges the other half with its partner), five
+// levels, 16 exchanges.  Lane l ends with the sum of value idx(l) = 8 b4 + 4 b3 + 2 b2 + b1
+// (bi = bit i of l); lanes l and l ^ 1 hold the same bits.  Fixed order: bit-reproducible.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ df warp_sum16(const float (&v)[16], const int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    df a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = b4 ? v[i] : v[i + 8];
+        const float keep = b4 ? v[i + 8] : v[i];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
+        a[i] = b4 ? two_sum(recv, keep) : two_sum(keep, recv);
+    }
+    df b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const df send = b3 ? a[i] : a[i + 4];
+        const df keep = b3 ? a[i + 4] : a[i];
+        const df recv = shfl_xor_df(send, 8);
+        b[i] = b3 ? dadd(recv, keep) : dadd(keep, recv);
+    }
+    df c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const df send = b2 ? b[i] : b[i + 2];
+        const df keep = b2 ? b[i + 2] : b[i];
+        const df recv = shfl_xor_df(send, 4);
+        c[i] = b2 ? dadd(recv, keep) : dadd(keep, recv);
+    }
+    const df send = b1 ? c[0] : c[1];
+    const df keep = b1 ? c[1] : c[0];
+    const df recv = shfl_xor_df(send, 2);
+    const df d = b1 ? dadd(recv, keep) : dadd(keep, recv);
+    const df e = shfl_xor_df(d, 1);
+    return b0 ? dadd(e, d) : dadd(d, e);
+}
+__device__ __forceinline__ int sum16_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+// Column J of the panel's T factor S (the forward recurrence of LAPACK's dlarft on the compact
+// form): S(J, J) = tau_J, S(i, J) = -tau_J sum_{l = i..J-1} S(i, l) G(l, J) for i < J, with
+// G(l, J) = (c_l (x_l . x_J)) c_J scaled here in place first (|c x| <= 1: no intermediate
+// overflows).  One warp; lane i computes row i.  S is column-major (S[J * 16 + i]).
+__device__ __forceinline__ void s_column(const int J, const int lane, df *G, df *S, const df *tau,
+                                         const df *c) {
+    if (lane < J) G[lane * 16 + J] = dmul(dmul(c[lane], G[lane * 16 + J]), c[J]);
+    __syncwarp();
+    if (lane < 16) {
+        df v = mk(0.f);
+        if (lane == J) {
+            v = tau[J];
+        } else if (lane < J) {
+            df a0 = mk(0.f), a1 = mk(0.f);  // two chains
+            int l = lane;
+            for (; l + 1 < J; l += 2) {
+                a0 = dadd(a0, dmul(S[l * 16 + lane], G[l * 16 + J]));
+                a1 = dadd(a1, dmul(S[(l + 1) * 16 + lane], G[(l + 1) * 16 + J]));
+            }
+            if (l < J) a0 = dadd(a0, dmul(S[l * 16 + lane], G[l * 16 + J]));
+            v = dneg(dmul(tau[J], dadd(a0, a1)));
+        }
+        S[J * 16 + lane] = v;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------
+// Chunk load: rows [0, rows) of A's columns [0, n) at src (leading dimension lda) into the
+// chunk layout, zeros elsewhere (rows >= rows, columns >= n up to 16 NP): exact, since zero
+// rows leave R unchanged.  FP32 by cp.async (16 bytes where vec4, else 4), BF16 widened.
+// ------------------------------------------------------------------------------------------
+template <typename Tin>
+__device__ __forceinline__ void load_chunk(float *C, const Tin *src, int64_t lda, int rows, int n,
+                                           int h, int NP, bool vec4) {
+    const int cols = 16 * NP;
+    if constexpr (sizeof(Tin) == 4) {
+        if (vec4) {
+            const int groups = h / 4;
+            for (int idx = threadIdx.x; idx < groups * cols; idx += blockDim.x) {
+                const int col = idx / groups, i = 4 * (idx - col * groups);
+                float *dst = C + cidx(i, col, NP);
+                if (col < n) {
+                    const int nb = rows - i >= 4 ? 16 : (rows > i ? 4 * (rows - i) : 0);
+                    const void *g = nb ? (const void *)(src + (int64_t)col * lda + i) : (const void *)src;
+                    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(g),
+                                 "r"(nb)
+                                 : "memory");
+                } else {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < h * cols; idx += blockDim.x) {
+                const int col = idx / h, i = idx - col * h;
+                float *dst = C + cidx(i, col, NP);
+                if (col < n) {
+                    const bool ok = i < rows;
+                    cp_async4(dst, ok ? (const void *)(src + (int64_t)col * lda + i) : (const void *)src,
+                              ok ? 4 : 0);
+                } else {
+                    *dst = 0.f;
+                }
+            }
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+    } else {
+        for (int idx = threadIdx.x; idx < h * cols; idx += blockDim.x) {
+            const int col = idx / h, i = idx - col * h;
+            float v = 0.f;
+            if (col < n && i < rows) v = __bfloat162float(src[(int64_t)col * lda + i]);
+            C[cidx(i, col, NP)] = v;
+        }
+    }
+}
+
+struct WyArgs2 {
+    F64Args base;    // m, lda, n, unit, nunits, nleaves, arity, h, tree buffers, R, status
+    const void *A;   // FP32 or BF16
+    int ldSd;        // leading dimension of the tree's FP64 view of the chunk region
+    int vec4;        // FP32 A with 16-byte aligned columns (cp.async of 4 rows)
+};
+
+// ------------------------------------------------------------------------------------------
+// One panel: factorization (reflectors J = 0 .. pw-1 of columns J0 + J), S, and the update of
+// the columns right of it.  ROWS = h / 256 rows per thread in the factorization.
+// ------------------------------------------------------------------------------------------
+// Tensor memory of a CTA: for M-block b (rows 128 b .. 128 b + 127) the update's accumulator D_b
+// at columns [64 b, 64 b + 64) and the tails' three TF32 parts (A operand, 16 columns each) at
+// [64 MB + 48 b, 64 MB + 48 b + 48); MB = h / 128 M-blocks, 112 MB columns in all.
+struct Tmem {
+    uint32_t base;   // allocated address (lane 0)
+    uint64_t *bar;   // mbarrier the update's mma commit arrives on
+    uint32_t phase;  // parity of the next commit's phase
+    bool ok;         // false once a bounded wait gave up
+};
+__host__ __device__ constexpr uint32_t tmem_cols(int h) {
+    return (112 * (h / 128)) <= 256 ? 256u : 512u;
+}
+
+template <int ROWS>
+__device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, const int n,
+                                           const int NP, const int k, Tmem &tm, int *status) {
+    constexpr int h = 256 * ROWS;
+    float *C = reinterpret_cast<float *>(sm + L.C);
+    df *Rd = reinterpret_cast<df *>(sm + L.R);
+    df *red = reinterpret_cast<df *>(sm + L.red);
+    df *tau_s = reinterpret_cast<df *>(sm + L.tau);
+    df *c_s = reinterpret_cast<df *>(sm + L.cc);
+    df *G = reinterpret_cast<df *>(sm + L.G);
+    df *S = reinterpret_cast<df *>(sm + L.S);
+    df *W = reinterpret_cast<df *>(sm + L.W);
+    float *B = reinterpret_cast<float *>(sm + L.B);
+    float *P = reinterpret_cast<float *>(sm + L.P);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int J0 = kPw * k;
+    const int pw = min(kPw, n - J0);
+
+    // ---- 1. panel factorization in registers
+    float x[ROWS][kPw];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int i = 256 * q + 32 * warp + lane;
+#pragma unroll
+        for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
+    }
+    float *fsh = reinterpret_cast<float *>(sm + L.fsh);
+    // The loop over the panel's columns is not unrolled (one copy of its body keeps the
+    // instruction cache warm); the register columns are addressed with static indices and
+    // predicated by the column J.
+    float fv[kPw], xp[ROWS];
+#pragma unroll
+    for (int kk = 0; kk < kPw; ++kk) fv[kk] = 0.f;
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) xp[q] = 0.f;
+#pragma unroll 1
+    for (int J = 0; J < pw; ++J) {
+        // columns J.. get reflector J-1 (fv = 0 and xp = 0 at J = 0)
+#pragma unroll
+        for (int kk = 0; kk < kPw; ++kk)
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q)
+                x[q][kk] = (kk >= J) ? __fmaf_rn(-fv[kk], xp[q], x[q][kk]) : x[q][kk];
+        float xj[ROWS];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            float t = x[q][0];
+#pragma unroll
+            for (int kk = 1; kk < kPw; ++kk) t = (kk == J) ? x[q][kk] : t;
+            xj[q] = t;
+        }
+        float v[kPw];
+#pragma unroll
+        for (int kk = 0; kk < kPw; ++kk) {
+            float s = __fmul_rn(xj[0], x[0][kk]);
+#pragma unroll
+            for (int q = 1; q < ROWS; ++q) s = __fmaf_rn(xj[q], x[q][kk], s);
+            v[kk] = s;
+        }
+        const df ws = warp_sum16(v, lane);
+        df *rb = red + (J & 1) * kWarps * 16;
+        if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
+        __syncthreads();
+        if (warp == 0) {
+            // the cross-warp sums (lanes 0-15 over warps 0-3, 16-31 over warps 4-7, for value
+            // lane & 15), reflector J's scalars, row Jg of R and the factors f_k; the other
+            // warps wait for the factors at the next barrier
+            const int vi = lane & 15, half = lane >> 4;
+            const df s01 = dadd(rb[(4 * half) * 16 + vi], rb[(4 * half + 1) * 16 + vi]);
+            const df s23 = dadd(rb[(4 * half + 2) * 16 + vi], rb[(4 * half + 3) * 16 + vi]);
+            const df s = dadd(s01, s23);
+            const df o = shfl_xor_df(s, 16);
+            const df tot = half ? dadd(o, s) : dadd(s, o);  // lane l: value l & 15
+            const int Jg = J0 + J;
+            const df alpha = Rd[rowoff(n, Jg)];
+            const Refl rf = make_refl(alpha, shfl_df(tot, J));
+            float fk = 0.f;
+            if (lane < 16) {
+                if (vi > J && vi < pw && !rf.ident) {
+                    df *rjk = Rd + rowoff(n, Jg) + vi - J;
+                    const df wk = dadd(*rjk, dmul(rf.c, tot));
+                    *rjk = dsub(*rjk, dmul(rf.tau, wk));
+                    const df f = dneg(dmul(wk, rf.ib));
+                    fk = __fadd_rn(f.hi, f.lo);
+                }
+                fsh[vi] = fk;
+                if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled by warp 1 later)
+                if (vi == J) {
+                    tau_s[J] = rf.tau;
+                    c_s[J] = rf.c;
+                    Rd[rowoff(n, Jg)] = rf.beta;
+                }
+            }
+        } else if (warp == 1 && J > 0) {
+            s_column(J - 1, lane, G, S, tau_s, c_s);  // in the shadow of warp 0's scalars
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) xp[q] = xj[q];
+    }
+    if (warp == 1) s_column(pw - 1, lane, G, S, tau_s, c_s);
+    // the tails (unscaled, 22 bits) back to the chunk
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int i = 256 * q + 32 * warp + lane;
+#pragma unroll
+        for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = x[q][kk];
+    }
+    const int n8 = round_up_i(n, 8);
+    const int T0 = J0 + kPw;           // first trailing column
+    const int ntp = n8 - T0;           // trailing columns, padded to 8
+    if (ntp > 0) {
+        // the tails' two TF32 parts, this thread's rows, into tensor memory (the A operand of
+        // the update): row 256 q + 32 w + l is lane 32 (w % 4) + l of M-block 2 q + w / 4
+        constexpr int MB = h / 128;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int b = 2 * q + (warp >> 2);
+            float hi[8], mid[8], lo[8];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split3(x[q][8 * half + e], hi[e], mid[e], lo[e]);
+                const uint32_t col = (uint32_t)(64 * MB + 48 * b + 8 * half);
+                tc::tmem_st8(tm.base + lane_base + col, hi);
+                tc::tmem_st8(tm.base + lane_base + col + 16u, mid);
+                tc::tmem_st8(tm.base + lane_base + col + 32u, lo);
+            }
+        }
+        tc::tmem_st_wait();
+    }
+    __syncthreads();
+    if (ntp <= 0) return;
+
+    // ---- 2a. Z = X^T C(:, T) on the tensor cores (units: n-tile x row group)
+    const int NT8 = ntp / 8;
+    int KG = 1;
+    while (KG * 2 * NT8 <= kMaxUnits) KG *= 2;
+    const int g4 = lane >> 2, t4 = lane & 3;
+    if (warp < NT8 * KG) {
+        const int jt = warp % NT8, grp = warp / NT8;
+        const int c0 = T0 + 8 * jt;
+        const int r0 = grp * (h / KG), r1 = r0 + h / KG;
+        // six partial products in six accumulators (independent MMA chains), summed at the end
+        // smallest first
+        float d[6][4] = {};
+        for (int k0 = r0; k0 < r1; k0 += 8) {
+            const float xa[4] = {C[cidx(k0 + t4, J0 + g4, NP)], C[cidx(k0 + t4, J0 + g4 + 8, NP)],
+                                 C[cidx(k0 + t4 + 4, J0 + g4, NP)],
+                                 C[cidx(k0 + t4 + 4, J0 + g4 + 8, NP)]};
+            const float cb[2] = {C[cidx(k0 + t4, c0 + g4, NP)], C[cidx(k0 + t4 + 4, c0 + g4, NP)]};
+            float ah[4], am[4], al[4], bh[2], bm[2], bl[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) split3(xa[q], ah[q], am[q], al[q]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
+            tc::mma_m16n8k8(d[0], am, bm);
+            tc::mma_m16n8k8(d[1], al, bh);
+            tc::mma_m16n8k8(d[2], ah, bl);
+            tc::mma_m16n8k8(d[3], am, bh);
+            tc::mma_m16n8k8(d[4], ah, bm);
+            tc::mma_m16n8k8(d[5], ah, bh);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            d[4][q] = __fadd_rn(
+                __fadd_rn(__fadd_rn(__fadd_rn(d[0][q], d[1][q]), d[2][q]), __fadd_rn(d[3][q], d[4][q])),
+                d[5][q]);
+        float *pt = P + warp * 128;  // unit tile, 16 x 8 row-major
+        pt[g4 * 8 + 2 * t4] = d[4][0];
+        pt[g4 * 8 + 2 * t4 + 1] = d[4][1];
+        pt[(g4 + 8) * 8 + 2 * t4] = d[4][2];
+        pt[(g4 + 8) * 8 + 2 * t4 + 1] = d[4][3];
+    }
+    __syncthreads();
+
+    // ---- 2b. W = R(P, T) + diag(c) Z
+    for (int e = threadIdx.x; e < kPw * ntp; e += blockDim.x) {
+        const int J = e / ntp, cc = e - J * ntp;
+        const int col = T0 + cc;
+        df wv = mk(0.f);
+        if (J < pw && col < n) {
+            const int jt = cc >> 3, c8 = cc & 7;
+            df z = mk(P[jt * 128 + J * 8 + c8]);
+            for (int grp = 1; grp < KG; ++grp) z = dadd(z, mk(P[(grp * NT8 + jt) * 128 + J * 8 + c8]));
+            wv = dadd(Rd[rowoff(n, J0 + J) + col - (J0 + J)], dmul(c_s[J], z));
+        }
+        W[J * ntp + cc] = wv;
+    }
+    __syncthreads();
+
+    // ---- 2c. Y = S^T W; R(P, T) -= Y; diag(c) Y in three TF32 parts, each a K-major
+    //          operand of 16 (K) x ntp16 (N): core matrix (c / 8, J / 4) at (c / 8) 512 +
+    //          (J / 4) 128 bytes, row c % 8 at 16 bytes, element J % 4 at 4
+    const int ntp16 = round_up_i(ntp, 16);
+    const int part_bytes = ntp16 * 64;
+    for (int e = threadIdx.x; e < kPw * ntp16; e += blockDim.x) {
+        const int J = e / ntp16, cc = e - J * ntp16;
+        const int col = T0 + cc;
+        float bh = 0.f, bm = 0.f, bl = 0.f;
+        if (J < pw && col < n) {
+            df y0 = mk(0.f), y1 = mk(0.f);  // two chains: half the latency
+            int i = 0;
+            for (; i + 1 <= J; i += 2) {
+                y0 = dadd(y0, dmul(S[J * 16 + i], W[i * ntp + cc]));
+                y1 = dadd(y1, dmul(S[J * 16 + i + 1], W[(i + 1) * ntp + cc]));
+            }
+            if (i <= J) y0 = dadd(y0, dmul(S[J * 16 + i], W[i * ntp + cc]));
+            const df y = dadd(y0, y1);
+            df *r = Rd + rowoff(n, J0 + J) + col - (J0 + J);
+            *r = dsub(*r, y);
+            split3_df(dmul(c_s[J], y), bh, bm, bl);
+        }
+        const int off = (cc >> 3) * 512 + (J >> 2) * 128 + (cc & 7) * 16 + (J & 3) * 4;
+        *reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(B) + off) = bh;
+        *reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(B) + part_bytes + off) = bm;
+        *reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(B) + 2 * part_bytes + off) = bl;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    // ---- 2d. C(:, T) -= X (diag(c) Y) on the 5th-generation tensor cores: per M-block b,
+    //          D_b = X_lo B_mid + X_hi B_lo + X_lo B_hi + X_hi B_mid + X_hi B_hi (smallest
+    //          first, FP32 accumulation in tensor memory; X's parts in tensor memory, B's in
+    //          shared memory), issued by one thread; then every thread subtracts its rows of D
+    {
+        constexpr int MB = h / 128;
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, 128, ntp16, false, false);
+            const uint32_t bsm = tc::smem_u32(B);
+            // (A part, B part), 0 = hi, 1 = mid, 2 = lo; the products below 2^-33 are dropped
+            const int terms[6][2] = {{1, 1}, {2, 0}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+            for (int b = 0; b < MB; ++b) {
+                const uint32_t dcol = tm.base + (uint32_t)(64 * b);
+                const uint32_t acol = tm.base + (uint32_t)(64 * MB + 48 * b);
+                bool acc = false;
+                for (int t = 0; t < 6; ++t)
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const uint64_t bd = tc::smem_desc(
+                            bsm + (uint32_t)(terms[t][1] * part_bytes + 256 * s2), 128, 512,
+                            tc::kSwNone);
+                        tc::mma_tf32_ts(dcol, acol + (uint32_t)(16 * terms[t][0] + 8 * s2), bd,
+                                        idesc, acc);
+                        acc = true;
+                    }
+            }
+            tc::mma_commit(tm.bar);
+        }
+        // every thread polls (bounded); the CTA agrees on the outcome, so that all its threads
+        // take the same path
+        const bool done = __syncthreads_and(tc::mbar_wait(tm.bar, tm.phase, 1LL << 22) ? 1 : 0) != 0;
+        tm.phase ^= 1u;
+        if (!done) {
+            tm.ok = false;
+            if (status && threadIdx.x == 0) atomicOr(status, kStatusTimeoutBit);
+        }
+        tc::fence_after_sync();
+        if (done) {
+            const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+#pragma unroll
+            for (int q = 0; q < ROWS; ++q) {
+                const int i = 256 * q + 32 * warp + lane;
+                const int b = 2 * q + (warp >> 2);
+                for (int c0 = 0; c0 < ntp16; c0 += 8) {
+                    float v[8];
+                    tc::tmem_ld8(tm.base + lane_base + (uint32_t)(64 * b + c0), v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float *pc = C + cidx(i, T0 + c0 + e, NP);
+                        *pc = __fsub_rn(*pc, v[e]);
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+}
+
+// One row per thread (256-row chunks): two CTAs per SM (at most 128 registers a thread), so
+// that one CTA's reflector chain runs while the other's waits; two rows: one CTA per SM.
+template <typename Tin, int ROWS>
+__global__ void __launch_bounds__(kThreads, 3 - ROWS) tsqr_mixed_wy_kernel(const WyArgs2 a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int h = 256 * ROWS;
+    const F64Args &b = a.base;
+    const int n = b.n;
+    const int NP = (n + kPw - 1) / kPw;
+    const Layout L = layout(n, h);
+    df *Rd = reinterpret_cast<df *>(sm + L.R);
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) Rd[e] = mk(0.f);
+
+    const int leaf = blockIdx.x;
+    const int64_t u0 = ((int64_t)leaf * b.nunits) / b.nleaves;
+    const int64_t u1 = ((int64_t)(leaf + 1) * b.nunits) / b.nleaves;
+    const int64_t rbeg = u0 * b.unit;
+    const int64_t rend = (u1 * b.unit < b.m) ? u1 * b.unit : b.m;
+    // the update's mbarrier and tensor memory (released before the tree)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(sm + L.bar + 8);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(tbase, tmem_cols(h));
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    Tmem tm;
+    tm.base = *tbase;
+    tm.bar = bar;
+    tm.phase = 0;
+    tm.ok = true;
+
+    const Tin *A = static_cast<const Tin *>(a.A);
+    for (int64_t r0 = rbeg; r0 < rend && tm.ok; r0 += h) {
+        const int rows = (int)((rend - r0 < h) ? rend - r0 : h);
+        __syncthreads();  // the previous chunk's last reads of C are done
+        load_chunk<Tin>(reinterpret_cast<float *>(sm + L.C), A + r0, b.lda, rows, n, h, NP,
+                        a.vec4 != 0);
+        __syncthreads();
+        for (int k = 0; k < NP && tm.ok; ++k) panel_step<ROWS>(sm, L, n, NP, k, tm, b.status);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (!tm.ok) {
+        // a tensor-core wait gave up (recorded in the status word): wait once more, bounded, for
+        // the mma in flight, release the tensor memory and leave R unwritten
+        if (threadIdx.x == 0) tc::mbar_wait(bar, tm.phase, 1LL << 22);
+        __syncthreads();
+        if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(h));
+        return;
+    }
+    if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(h));
+    __syncthreads();
+    // R to FP64 (exact: hi + lo), in place, for the FP64 tree
+    double *Rp = reinterpret_cast<double *>(sm + L.R);
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
+        const df v = Rd[e];
+        Rp[e] = (double)v.hi + (double)v.lo;
+    }
+    __syncthreads();
+    climb_tree<false>(b, reinterpret_cast<double *>(sm + L.C), a.ldSd, Rp,
+                      reinterpret_cast<double *>(sm + L.f), reinterpret_cast<double *>(sm + L.seg),
+                      reinterpret_cast<double *>(sm + L.tot),
+                      reinterpret_cast<unsigned int *>(sm + L.flag), leaf);
+}
+
+}  // namespace wy
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+namespace {
+template <typename Tin>
+const void *wy_fn(int rows) {
+    return rows == 2 ? (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>
+                     : (const void *)wy::tsqr_mixed_wy_kernel<Tin, 1>;
+}
+}  // namespace
+
+size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total; }
+
+// Largest arity (<= 8) whose stacked FP64 triangles fit in the chunk region of an h-row leaf.
+int mixed_wy_arity(int n, int h) {
+    const int bytes = h * ((n + wy::kPw - 1) / wy::kPw) * 64;
+    int k = 2;
+    while (k < 8 && tree_ldsd(n, k + 1) * n * 8 <= bytes) ++k;
+    return k;
+}
+int mixed_wy_ldsd(int n, int arity) { return tree_ldsd(n, arity); }
+bool mixed_wy_tree_fits(int n, int h, int arity) {
+    return tree_ldsd(n, arity) * n * 8 <= h * ((n + wy::kPw - 1) / wy::kPw) * 64;
+}
+
+cudaError_t mixed_wy_prepare(size_t smem_bytes) {
+    const void *fns[4] = {wy_fn<float>(1), wy_fn<float>(2), wy_fn<__nv_bfloat16>(1),
+                          wy_fn<__nv_bfloat16>(2)};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int mixed_wy_blocks_per_sm(int h, size_t smem_bytes) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wy_fn<float>(h / 256), wy::kThreads,
+                                                      smem_bytes) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int ldSd,
+                            size_t smem_bytes, cudaStream_t stream) {
+    wy::WyArgs2 a;
+    a.base = base;
+    a.A = A;
+    a.ldSd = ldSd;
+    a.vec4 = !bf16 && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (base.lda % 4 == 0);
+    const dim3 grid(base.nleaves), block(wy::kThreads);
+    const int rows = base.h / 256;
+    if (bf16) {
+        if (rows == 2)
+            wy::tsqr_mixed_wy_kernel<__nv_bfloat16, 2><<<grid, block, smem_bytes, stream>>>(a);
+        else
+            wy::tsqr_mixed_wy_kernel<__nv_bfloat16, 1><<<grid, block, smem_bytes, stream>>>(a);
+    } else {
+        if (rows == 2)
+            wy::tsqr_mixed_wy_kernel<float, 2><<<grid, block, smem_bytes, stream>>>(a);
+        else
+            wy::tsqr_mixed_wy_kernel<float, 1><<<grid, block, smem_bytes, stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,6 +1,8 @@
 // tsqr_r_noalloc: the FP64 R factor with the reduction tree's scratch in a fixed,
 // statically allocated device array, for callers that cannot allocate device memory at call
-// time (see include/tsqr.h).  The kernel and the plan are those of tsqr_r.
+// time.  It runs tsqr_r's kernel on the AUTO plan's one-reduction partition (never the panels).
+// The device address of the array is looked up once per device and kept for the life of the
+// process; it is not valid after the device has been reset.
 #include <mutex>
 
 #include "tsqr.h"
@@ -38,6 +40,7 @@ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 extern "C" tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda,
                                         double *R, int64_t ldr, tsqr_stream_t stream) {
+    tsqr::set_last_call(0, tsqr_plan_t{});
     if (m < 0 || n < 0 || lda < (m > 1 ? m : 1) || ldr < (n > 1 ? n : 1))
         return TSQR_ERR_INVALID_ARG;
     if (n > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
@@ -51,7 +54,8 @@ extern "C" tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, i
     int warps = 0;
     size_t smem = 0;
     int64_t nodes = 0;
-    tsqr_status_t st = tsqr::f64_auto_args(m, (int)n, &a, &warps, &smem, &nodes);
+    tsqr_plan_t plan{};
+    tsqr_status_t st = tsqr::f64_auto_args(m, (int)n, &a, &warps, &smem, &nodes, &plan);
     if (st != TSQR_SUCCESS) return st;
     const size_t cnt_bytes = align256((size_t)nodes * sizeof(unsigned int));
     const size_t need = cnt_bytes + (size_t)nodes * (size_t)n * (size_t)n * sizeof(double);
@@ -71,5 +75,6 @@ extern "C" tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, i
     if (cudaMemsetAsync(a.counters, 0, (size_t)nodes * sizeof(unsigned int), s) != cudaSuccess)
         return TSQR_ERR_CUDA;
     if (tsqr::f64_launch(a, warps, smem, s) != cudaSuccess) return TSQR_ERR_CUDA;
+    tsqr::set_last_call(1, plan);
     return TSQR_SUCCESS;
 }

@@ -1,8 +1,10 @@
-"""tsqr_r_host (A and R in host memory; with page-locked A one streaming launch folds the row
-pieces as they arrive): parity with the oracle (every entry within c(m) kappa u ||R||_F,
-c(m) = max(50, 2 sqrt(m)), Gram residual <= 1e-13) on sizes with fewer work units than pieces
-and many more, with page-locked A (the streaming launch) and pageable A (copy, then the ordinary
-kernel), a padded lda and ldr, m = 0, and a clean device status afterwards."""
+"""tsqr_r_host (A and R in host memory; page-locked A is read in place by tsqr_r's kernel
+through its device mapping, other memory is copied first): parity with the oracle (every entry
+within c(m) kappa u ||R||_F, c(m) = max(50, 2 sqrt(m)), Gram residual <= 1e-13), R equal to
+tsqr_r's bytes (same plan and kernel), page-locked and pageable A, a padded lda and ldr, m = 0,
+a clean device status afterwards, and the same R with every launch serialized
+(CUDA_LAUNCH_BLOCKING=1), which a design that needs copies and kernels to run concurrently
+would fail."""
 import numpy as np
 import pytest
 
@@ -39,6 +41,7 @@ def test_host_input_parity(oracle, T, m, n, pinned):
     R = T.tsqr_r_host(Ah.T)
     assert T.capi.tsqr_last_launch_count() == 1
     assert T.tsqr_get_device_status() == T.SUCCESS
+    assert torch.equal(R, T.tsqr_r(At.cuda().T).cpu())
     _check(oracle, oracle.from_torch_colmajor(At), R.numpy())
 
 
@@ -75,20 +78,34 @@ def test_host_input_leading_dimensions_and_empty(oracle, T):
     assert np.all(T.tsqr_r_host(Z).numpy() == 0)
 
 
-def test_stream_wait_times_out_and_reports(oracle, T):
-    """The failure path of the streaming launch's bounded waits: pieces that never arrive (flags
-    nothing sets) with a ~1 ms wait limit.  Every CTA gives up and returns, the status word says
-    TSQR_ERR_TIMEOUT, and the context stays usable for the next call."""
-    import ctypes
+_SERIAL = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+import workloads, paper_1002_4250_gb300 as T
+At = workloads.gaussian({m}, {n}, seed=7)
+Rh = T.tsqr_r_host(At.pin_memory().T)
+Rd = T.tsqr_r(At.cuda().T).cpu()
+torch.cuda.synchronize()
+assert T.tsqr_get_device_status() == T.SUCCESS
+torch.save(Rh.T.contiguous(), {out!r})
+print("same" if torch.equal(Rh, Rd) else "differ")
+"""
+
+
+def test_host_input_serialized_launches(oracle, T, tmp_path):
+    """With CUDA_LAUNCH_BLOCKING=1 every launch and copy runs alone: R must still be tsqr_r's
+    R (no part of the call may depend on a copy and a kernel running at the same time)."""
+    import os
+    import subprocess
+    import sys
     import torch
-    fn = T.capi.tsqr_internal_stream_timeout_selftest
-    fn.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
-    fn.restype = ctypes.c_int
-    T.tsqr_get_device_status()  # clear
-    assert fn(200000, 16, 4096, T._stream_ptr(None)) == T.SUCCESS
-    assert T.tsqr_get_device_status() == T.ERR_TIMEOUT
-    At = workloads.gaussian(10000, 16, seed=1)
-    R = T.tsqr_r(At.cuda().T)
-    torch.cuda.synchronize()
-    assert T.tsqr_get_device_status() == T.SUCCESS
-    _check(oracle, oracle.from_torch_colmajor(At), R.cpu().numpy())
+    m, n = 1500000, 32
+    out = str(tmp_path / "R.pt")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_LAUNCH_BLOCKING="1")
+    r = subprocess.run([sys.executable, "-c", _SERIAL.format(root=root, m=m, n=n, out=out)],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().endswith("same")
+    R = torch.load(out).T.numpy()
+    _check(oracle, oracle.from_torch_colmajor(workloads.gaussian(m, n, seed=7)), R)

@@ -90,3 +90,77 @@ def test_mixed_full_size_kappa_1e6(oracle, T):
     import torch
     At = workloads.conditioned(1 << 24, 64, 1e6, seed=0, dtype=torch.float32)
     _check(oracle, T, At)
+
+
+# ---- the blocked leaf (TSQR_LEAF_PANELS: 16-column panels, compact WY updates on the tensor
+#      cores) explicitly, against the oracle; and the fold (TSQR_LEAF_FOLD) beside it
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("n", [1, 3, 8, 15, 16, 17, 31, 32, 33, 47, 48, 63, 64])
+@pytest.mark.parametrize("h", [256, 512])
+def test_panels_leaf_widths(oracle, T, dtype, n, h):
+    import torch
+    m = 70001 if n > 16 else 30011  # several chunks per leaf and a ragged last chunk
+    At = workloads.gaussian(m, n, seed=100 + n, dtype=getattr(torch, dtype))
+    plan = T.make_plan("hybrid", tile_rows=h, leaf="panels")
+    _check(oracle, T, At, plan=plan)
+    used = T.last_plan()
+    assert used.leaf == T.LEAF_PANELS and used.tile_rows == h
+
+
+@pytest.mark.parametrize("tree,b,ctas", [("binary", 256, 0), ("binary", 768, 0), ("flat", 0, 0),
+                                         ("hybrid", 256, 7), ("hybrid", 512, 3)])
+def test_panels_leaf_trees(oracle, T, tree, b, ctas):
+    import torch
+    At = workloads.gaussian(50000, 40, seed=7, dtype=torch.float32)
+    _check(oracle, T, At, plan=T.make_plan(tree, tile_rows=b, ctas=ctas, leaf="panels"))
+
+
+def test_panels_leaf_odd_leading_dimension(oracle, T):
+    """lda not a multiple of 4 floats: the chunk loads fall back from 16-byte copies."""
+    import torch
+    m, n = 33333, 48
+    At = workloads.gaussian(m, n, seed=9, dtype=torch.float32)
+    big = torch.zeros(n, m + 1, dtype=torch.float32)
+    big[:, :m] = At
+    R = T.tsqr_r_ex(big.cuda().T[:m, :], plan=T.make_plan(leaf="panels")).cpu().numpy()
+    A = oracle.from_torch_colmajor(At.to(torch.float64))
+    assert oracle.gram_residual(A, R) <= 2e-6
+    Ro = oracle.householder_r(A, nthreads=16)
+    np.testing.assert_allclose(R, Ro, rtol=0, atol=max(50.0, 2.0 * np.sqrt(m)) *
+                               oracle.kappa_from_r(Ro) * U32 * np.linalg.norm(Ro))
+
+
+def test_panels_leaf_rank_deficient(oracle, T):
+    """Zero and repeated columns (identity reflectors, zero pivots): R^T R = A^T A still."""
+    import torch
+    m, n = 40000, 40
+    At = workloads.gaussian(m, n, seed=11, dtype=torch.float32)
+    At[5] = 0.0
+    At[20] = At[3]
+    At[39] = 0.0
+    R = T.tsqr_r_ex(At.cuda().T, plan=T.make_plan(leaf="panels")).cpu().numpy()
+    A = oracle.from_torch_colmajor(At.to(torch.float64))
+    assert np.all(np.isfinite(R)) and np.all(np.diag(R) >= 0)
+    assert oracle.gram_residual(A, R) <= 2e-6
+
+
+def test_panels_leaf_bit_reproducible(T):
+    import torch
+    At = workloads.gaussian(400000, 64, seed=12, dtype=torch.float32).cuda().T
+    p = T.make_plan(leaf="panels")
+    a = T.tsqr_r_ex(At, plan=p).clone()
+    b = T.tsqr_r_ex(At, plan=p).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("leaf", ["fold", "panels"])
+def test_mixed_leaves_conditioned_report(oracle, T, leaf):
+    """Both mixed leaves at 2^20 x 64, kappa = 1e6, FP32: the Gram residual and the forward
+    error against the oracle, printed beside 50 kappa u32 (run with -s to see them)."""
+    import torch
+    At = workloads.conditioned(1 << 20, 64, 1e6, seed=0, dtype=torch.float32)
+    res, err, kap = _check(oracle, T, At, plan=T.make_plan(leaf=leaf))
+    print(f"\n{leaf}: gram residual {res:.3e}, |R - R_oracle|/|R_oracle| {err:.3e}, "
+          f"50 kappa u32 {50 * kap * U32:.3e}")

@@ -50,6 +50,9 @@ def test_noalloc_matches_tsqr_r_on_two_calls(T, m, n):
         R = T.empty_r(n, "cuda")
         R.fill_(float("nan"))
         assert _call_noalloc(T, A, R) == T.SUCCESS
+        assert T.tsqr_last_launch_count() == 1
+        used = T.last_plan()
+        assert used.tree == T.TREE_HYBRID and used.ctas > 0  # one reduction, never the panels
         torch.cuda.synchronize()
         np.testing.assert_allclose(R.cpu().numpy(), R_ref, rtol=0, atol=tol)
 
@@ -60,6 +63,7 @@ def test_noalloc_rejects_what_does_not_fit(T):
     A = torch.zeros(n, m, dtype=torch.float64, device="cuda").T
     R = T.empty_r(n, "cuda")
     assert _call_noalloc(T, A, R) == T.ERR_UNSUPPORTED
+    assert T.tsqr_last_launch_count() == 0 and T.last_plan().tree == 0
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert T.capi.tsqr_r_noalloc(A.data_ptr(), m, 129, m, R.data_ptr(), 129, stream) == T.ERR_UNSUPPORTED
     assert T.capi.tsqr_r_noalloc(A.data_ptr(), m, 8, m - 1, R.data_ptr(), 8, stream) == T.ERR_INVALID_ARG
