@@ -169,6 +169,19 @@ def run_cpu_baseline(At_cpu, threads, R_gpu, target_s=10.0, max_reps=40):
     return out
 
 
+def run_cpu_one_thread(At_cpu, rows=1 << 20):
+    """The oracle on one host thread, on the first `rows` rows of the workload (about as long as
+    the all-core run on the whole matrix)."""
+    import oracle
+    A = oracle.from_torch_colmajor(At_cpu[:, :rows].contiguous())
+    t0 = time.perf_counter()
+    oracle.householder_r(A, nthreads=1)
+    dt = time.perf_counter() - t0
+    return {"value": flops(rows, N) / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "seconds": dt, "sample": f"the first {rows:,} rows of the {M:,} x {N} workload, one "
+                                     f"unblocked Householder QR on one thread"}
+
+
 def bench_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -301,11 +314,12 @@ def bench_ours(args, world, rank, local):
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = bench_extras(dev)
+        extras = bench_extras(dev, os.cpu_count() or 1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(At_cpu, os.cpu_count() or 1, R.cpu().numpy())
+        cpu["one_thread"] = run_cpu_one_thread(At_cpu)
 
     if rank == 0:
         line = {"metric": "TSQR GFLOP/s (2mn^2-2n^3/3), FP64", "value": value, "unit": "GFLOP/s",
@@ -341,35 +355,130 @@ def time_call(fn, reps, warmup=2):
     return a.elapsed_time(b) / reps
 
 
-def bench_extras(dev):
-    """The mixed-precision path against the FP64 path on the mixed workload's shape
-    (16,777,216 x 64, N(0,1)): GFLOP/s, A-read GB/s and the speedup factor."""
+def bench_extras(dev, threads):
+    """One entry per workload of the method's configurations, each speed with its error:
+    the 10,000 x 16 binary-tree call, 4,194,304 x 32 by tree and at kappa = 1e8, the FP64 width
+    sweep at 2^24 rows, the mixed-precision path per kappa (FP32 and BF16) against the FP64 path,
+    the varlen batch (FP64 and mixed FP32) with graph replay, and the other entry points."""
     import torch
-    import paper_1002_4250_gb300 as T
-    import workloads
-    m, n = 1 << 24, 64
-    fl = flops(m, n)
-    out = {"workload": f"{m:,} x {n} N(0,1) seed 0 (generated on the GPU)"}
-    A64 = workloads.gaussian(m, n, seed=0, device=dev).T
-    R = T.empty_r(n, dev)
-    ms64 = time_call(lambda: T.tsqr_r(A64, R=R), reps=2, warmup=1)
-    out["fp64"] = {"ms": ms64, "gflops": fl / ms64 / 1e6, "frac_of_fp64_peak": fl / ms64 / 1e9 / peaks()["fp64_tflops"]}
-    for name, dt in (("mixed_fp32", torch.float32), ("mixed_bf16", torch.bfloat16)):
-        A = A64.T.to(dt).T
-        ms = time_call(lambda: T.tsqr_r_ex(A, R=R), reps=5)
-        bytes_a = A.element_size() * m * n
-        out[name] = {"ms": ms, "gflops": fl / ms / 1e6, "a_read_gbs": bytes_a / ms / 1e6,
-                     "a_read_frac_of_hbm": bytes_a / ms / 1e6 / peaks()["hbm_gbs"],
-                     "speedup_vs_fp64": ms64 / ms}
-        del A
-    del A64
-    torch.cuda.empty_cache()
-    out["widths_2e24"] = bench_widths(dev, ms64)
-    out["varlen_batch"] = bench_batched(dev)
+    out = {}
+    out["c1_10000x16_binary256"] = bench_c1(dev, threads)
+    out["c2_4194304x32"] = bench_c2(dev, threads)
+    widths = bench_widths(dev)
+    out["c3_widths_2e24"] = widths
+    out["c4_mixed_2e24x64"] = bench_mixed(dev, threads, widths["64"]["ms"])
+    out["c5_varlen_batch"] = bench_batched(dev, threads)
     out["thin_qr"] = bench_qr(dev)
     out["lstsq"] = bench_lstsq(dev)
     out["caqr"] = bench_caqr(dev)
+    torch.cuda.empty_cache()
     return out
+
+
+def _errors(A, R, Ro, threads, u):
+    """Forward error against the oracle's R, the Gram residual, and 50 kappa u."""
+    import oracle
+    kap = oracle.kappa_from_r(Ro)
+    return {"rel_err_vs_oracle": oracle.rel_err(R, Ro), "bound_50_kappa_u": 50.0 * kap * u,
+            "gram_residual": oracle.gram_residual(A, R, nthreads=threads), "kappa": kap}
+
+
+def bench_c1(dev, threads):
+    """10,000 x 16 FP64 N(0,1) seed 0, 256-row tiles, binary tree (the paper's tree): time per
+    call (launch-bound at this size) and the error against the oracle."""
+    import paper_1002_4250_gb300 as T
+    import oracle
+    import workloads
+    m, n = 10000, 16
+    At = workloads.gaussian(m, n, seed=0)
+    A = At.to(dev).T
+    R = T.empty_r(n, dev)
+    plan = T.make_plan("binary", tile_rows=256)
+    ms = time_call(lambda: T.tsqr_r_ex(A, plan=plan, R=R), reps=200, warmup=5)
+    An = oracle.from_torch_colmajor(At)
+    res = {"us_per_call": ms * 1e3, "gflops": flops(m, n) / ms / 1e6}
+    res.update(_errors(An, R.cpu().numpy(), oracle.householder_r(An, nthreads=threads), threads,
+                       2.0 ** -53))
+    return res
+
+
+def bench_c2(dev, threads):
+    """4,194,304 x 32 FP64: the binary (256-row tiles), flat (one CTA) and hybrid (AUTO) trees
+    on N(0,1) input, and the AUTO plan on A = G diag(sigma) V^T with kappa = 1e8, with errors."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import oracle
+    import workloads
+    m, n = 4194304, 32
+    fl = flops(m, n)
+    res = {}
+    At = workloads.gaussian(m, n, seed=0)
+    A = At.to(dev).T
+    R = T.empty_r(n, dev)
+    An = oracle.from_torch_colmajor(At)
+    Ro = oracle.householder_r(An, nthreads=threads)
+    for name, plan, reps in (("binary", T.make_plan("binary", tile_rows=256), 5),
+                             ("flat", T.make_plan("flat"), 1), ("hybrid_auto", None, 10)):
+        ms = time_call(lambda: T.tsqr_r_ex(A, plan=plan, R=R), reps=reps, warmup=1)
+        r = {"ms": ms, "gflops": fl / ms / 1e6}
+        r.update(_errors(An, R.cpu().numpy(), Ro, threads, 2.0 ** -53))
+        res[name] = r
+    del A
+    Ct = workloads.conditioned(m, n, 1e8, seed=0)
+    C = Ct.to(dev).T
+    ms = time_call(lambda: T.tsqr_r(C, R=R), reps=10, warmup=1)
+    Cn = oracle.from_torch_colmajor(Ct)
+    r = {"ms": ms, "gflops": fl / ms / 1e6}
+    r.update(_errors(Cn, R.cpu().numpy(), oracle.householder_r(Cn, nthreads=threads), threads,
+                     2.0 ** -53))
+    res["kappa_1e8_auto"] = r
+    del C
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_mixed(dev, threads, ms64):
+    """The mixed-precision path at 16,777,216 x 64 on A = G diag(sigma) V^T, kappa in {1e2, 1e4,
+    1e6}, FP32 and BF16 storage: time of the AUTO plan (the blocked leaf) and of the fold leaf,
+    the speedup over the FP64 path at 2^24 x 64 (N(0,1), ms64), and the errors against the FP64
+    oracle on the same recipe at 1,048,576 rows (the oracle's time at 2^24 rows is minutes)."""
+    import torch
+    import paper_1002_4250_gb300 as T
+    import oracle
+    import workloads
+    m, n = 1 << 24, 64
+    me = 1 << 20
+    fl = flops(m, n)
+    res = {"workload": f"{m:,} x {n}, A = G diag(sigma) V^T (G drawn on the GPU); errors on the "
+                       f"same recipe at {me:,} rows (G from the CPU generator, seed 0)",
+           "fp64_ms_2e24x64": ms64, "error_rows": me}
+    R = T.empty_r(n, dev)
+    u32 = 2.0 ** -24
+    for kappa in (1e2, 1e4, 1e6):
+        A64 = workloads.conditioned(m, n, kappa, seed=0, device=dev, device_draw=True).T
+        Ae = workloads.conditioned(me, n, kappa, seed=0)
+        for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+            A = A64.T.to(dt).T
+            ms = time_call(lambda: T.tsqr_r_ex(A, R=R), reps=5, warmup=1)
+            used = T.last_plan()
+            fold = T.make_plan(leaf="fold")
+            ms_fold = time_call(lambda: T.tsqr_r_ex(A, plan=fold, R=R), reps=2, warmup=1)
+            del A
+            Ael = Ae.to(dt)
+            An = oracle.from_torch_colmajor(Ael.to(torch.float64))
+            Ro = oracle.householder_r(An, nthreads=threads)
+            Rp = T.tsqr_r_ex(Ael.to(dev).T).cpu().numpy()
+            Rf = T.tsqr_r_ex(Ael.to(dev).T, plan=fold).cpu().numpy()
+            r = {"ms": ms, "gflops": fl / ms / 1e6, "speedup_vs_fp64": ms64 / ms,
+                 "a_read_gbs": torch.tensor([], dtype=dt).element_size() * m * n / ms / 1e6,
+                 "leaf": ["auto", "fold", "panels"][used.leaf], "fold_ms": ms_fold,
+                 "errors": _errors(An, Rp, Ro, threads, u32),
+                 "fold_errors": _errors(An, Rf, Ro, threads, u32),
+                 "gram_tol": 2e-6}
+            res[f"{name}_kappa_{kappa:.0e}"] = r
+        del A64
+        torch.cuda.empty_cache()
+    return res
 
 
 def bench_caqr(dev):
@@ -438,7 +547,7 @@ def bench_qr(dev):
     return res
 
 
-def bench_widths(dev, ms64=None):
+def bench_widths(dev):
     """FP64 at 16,777,216 x n for n in {4, 8, 16, 32, 64, 128}, N(0,1): GFLOP/s, A-read GB/s and
     the fraction of the roofline time max(bytes(A) / HBM, flops / FP64 peak)."""
     import torch
@@ -451,14 +560,11 @@ def bench_widths(dev, ms64=None):
         fl = flops(m, n)
         bytes_a = 8.0 * m * n
         t_roof = max(bytes_a / (pk["hbm_gbs"] * 1e9), fl / (pk["fp64_tflops"] * 1e12)) * 1e3
-        if n == 64 and ms64 is not None:
-            ms = ms64
-        else:
-            A = workloads.gaussian(m, n, seed=0, device=dev).T
-            R = T.empty_r(n, dev)
-            ms = time_call(lambda: T.tsqr_r(A, R=R), reps=2 if n >= 64 else 5, warmup=1)
-            del A
-            torch.cuda.empty_cache()
+        A = workloads.gaussian(m, n, seed=0, device=dev).T
+        R = T.empty_r(n, dev)
+        ms = time_call(lambda: T.tsqr_r(A, R=R), reps=2 if n >= 64 else 5, warmup=1)
+        del A
+        torch.cuda.empty_cache()
         res[str(n)] = {"ms": ms, "gflops": fl / ms / 1e6, "a_read_gbs": bytes_a / ms / 1e6,
                        "roofline_ms": t_roof, "frac_of_roofline": t_roof / ms,
                        "bound": "hbm" if bytes_a / (pk["hbm_gbs"] * 1e9) > fl / (pk["fp64_tflops"] * 1e12)
@@ -466,11 +572,16 @@ def bench_widths(dev, ms64=None):
     return res
 
 
-def bench_batched(dev):
+def bench_batched(dev, threads):
     """The varlen batch: 4096 problems, m log-uniform in [512, 262144], n uniform in
-    {8, 16, 32, 64}, packed in one buffer, one persistent launch per call; FP64 and mixed FP32."""
+    {8, 16, 32, 64}, packed in one buffer, one persistent launch per call; FP64 and mixed FP32.
+    Beside each time: the replay of the call captured in a CUDA graph, and the errors of a
+    sample of 24 problems (every 171st) against the oracle (the largest Gram residual and
+    forward error of the sample)."""
+    import numpy as np
     import torch
     import paper_1002_4250_gb300 as T
+    import oracle
     import workloads
     buf, ms, ns, offs = workloads.varlen_batch(4096, 512, 262144, seed=0, device=dev)
     fl = sum(flops(m, n) for m, n in zip(ms, ns))
@@ -479,14 +590,36 @@ def bench_batched(dev):
         roff.append(roff[-1] + n * n)
     Rp = torch.empty(roff[-1], dtype=torch.float64, device=dev)
     res = {"problems": len(ms), "elements": int(offs[-1]), "gflop_per_call": fl / 1e9}
-    for name, dt, code, prec in (("fp64", torch.float64, T.F64, T.PREC_F64),
-                                 ("mixed_fp32", torch.float32, T.F32, T.PREC_MIXED)):
+    sample = list(range(0, 4096, 171))
+    for name, dt, code, prec, u in (("fp64", torch.float64, T.F64, T.PREC_F64, 2.0 ** -53),
+                                    ("mixed_fp32", torch.float32, T.F32, T.PREC_MIXED, 2.0 ** -24)):
         b = buf if dt == torch.float64 else buf.to(dt)
         ptrs = [b.data_ptr() + b.element_size() * o for o in offs[:-1]]
-        ms_ = time_call(lambda: T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec),
-                        reps=2 if name == "fp64" else 5, warmup=1)
-        res[name] = {"ms": ms_, "gflops": fl / ms_ / 1e6,
-                     "a_read_gbs": b.element_size() * offs[-1] / ms_ / 1e6}
+        call = lambda: T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec)
+        ms_ = time_call(call, reps=2 if name == "fp64" else 5, warmup=1)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            call()  # workspace and problem table in place before the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec, stream=stream)
+        ms_graph = time_call(g.replay, reps=2 if name == "fp64" else 5, warmup=1)
+        torch.cuda.synchronize()
+        Rh = Rp.cpu().numpy()
+        gram, ferr = [], []
+        for i in sample:
+            m, n = ms[i], ns[i]
+            Ai = b[offs[i]:offs[i + 1]].view(n, m).to(torch.float64).cpu()
+            An = oracle.from_torch_colmajor(Ai)
+            Ri = Rh[roff[i]:roff[i] + n * n].reshape(n, n).T
+            gram.append(oracle.gram_residual(An, Ri, nthreads=threads))
+            ferr.append(oracle.rel_err(Ri, oracle.householder_r(An, nthreads=threads)))
+        res[name] = {"ms": ms_, "gflops": fl / ms_ / 1e6, "graph_replay_ms": ms_graph,
+                     "a_read_gbs": b.element_size() * offs[-1] / ms_ / 1e6,
+                     "sample_problems": len(sample), "max_gram_residual": float(np.max(gram)),
+                     "max_rel_err_vs_oracle": float(np.max(ferr)),
+                     "gram_tol": 1e-13 if name == "fp64" else 2e-6}
         del b
     res["mixed_speedup_vs_fp64"] = res["fp64"]["ms"] / res["mixed_fp32"]["ms"]
     del buf

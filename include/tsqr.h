@@ -89,8 +89,9 @@ typedef enum {
  *         then applied to the columns right of it as one compact WY block (I - V S V^T) whose
  *         two products run on the tensor cores as split-TF32 products with FP32 accumulation
  *         (each as accurate as an FP32 dot product); R in double-FP32 in the leaf, FP64 in the
- *         tree.  n <= 64; chunks of 256 or 512 rows (tile_rows).
- * AUTO picks PANELS where it applies (n <= 64), else FOLD. */
+ *         tree.  n <= 64; chunks of 256, 512, 768 or 1024 rows (tile_rows; AUTO: the
+ *         tallest the width's shared and tensor memory allow).
+ * AUTO picks PANELS for n <= 64 (FP32: from n = 13 on), where it measured faster, else FOLD. */
 typedef enum { TSQR_LEAF_AUTO = 0, TSQR_LEAF_FOLD = 1, TSQR_LEAF_PANELS = 2 } tsqr_leaf_t;
 
 /* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic
@@ -106,8 +107,8 @@ typedef struct {
                            binary operators by associativity, Section 2).  0 = as many as the
                            kernel's shared memory holds.                                     */
     int32_t leaf;       /* tsqr_leaf_t (mixed path only; 0 elsewhere).  With PANELS,
-                           tile_rows is the chunk height (256 or 512) of a HYBRID plan, warps
-                           is 8 (or 0).                                                      */
+                           tile_rows is the chunk height (256, 512, 768 or 1024) of a HYBRID
+                           plan, warps is 8 (or 0).                                          */
 } tsqr_plan_t;
 
 typedef void *tsqr_stream_t; /* a cudaStream_t */

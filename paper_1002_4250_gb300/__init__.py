@@ -94,7 +94,7 @@ def _load():
     # measurement and self-test hooks (not part of include/tsqr.h)
     capi.tsqr_internal_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), _i32]
     capi.tsqr_internal_measure_peaks.restype = _i32
-    capi.tsqr_internal_tc_layout_selftest.argtypes = [_p, _i32, _i32, _i32]
+    capi.tsqr_internal_tc_layout_selftest.argtypes = [_p, _i32, _i32]
     capi.tsqr_internal_tc_layout_selftest.restype = _i32
 
     _capi = capi

@@ -1356,22 +1356,41 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
     p->warps = 8;
     const int64_t mm = std::max<int64_t>(m, 1);
     const size_t reserve = 1024;
+    // AUTO chunk height: the tallest of 1024, 768, 512 rows that fits one CTA's shared memory
+    // and the SM's tensor memory (fewer reflector chains per row of A: 2^24 x 64 FP32 with
+    // 512-row chunks 24.3 ms, with 256-row chunks (two CTAs per SM) 49 ms)
+    auto fits = [&](int hh) {
+        return mixed_wy_smem_bytes(n, hh) + reserve <= di.smem_block_optin && mixed_wy_tmem_fits(n, hh);
+    };
+    int h_auto = 256;
+    for (int hh : {1024, 768, 512})
+        if (fits(hh)) {
+            h_auto = hh;
+            break;
+        }
     int h;
     if (p->tree == TSQR_TREE_BINARY) {
         p->unit = (over && over->tile_rows > 0) ? over->tile_rows : 256;
-        h = (p->unit >= 512 && p->unit % 512 == 0) ? 512 : 256;
+        h = 256;
+        for (int hh : {1024, 768, 512})
+            if (hh <= h_auto && p->unit % hh == 0) {
+                h = hh;
+                break;
+            }
     } else if (over && over->tile_rows > 0) {
-        if (over->tile_rows != 256 && over->tile_rows != 512) return TSQR_ERR_INVALID_ARG;
+        if (over->tile_rows % 256 != 0 || over->tile_rows > 1024 || !fits(over->tile_rows))
+            return TSQR_ERR_INVALID_ARG;
         h = over->tile_rows;
         p->unit = h;
     } else {
-        h = (2 * (mixed_wy_smem_bytes(n, 512) + reserve) <= di.smem_sm) ? 512 : 256;
+        h = h_auto;
         p->unit = h;
     }
     p->h = h;
     p->hs = h;
     p->ldS = 0;
     p->blk = h / 256;
+    (void)reserve;
     p->vec = 1;
     p->smem = mixed_wy_smem_bytes(n, h);
     if (p->smem > di.smem_block_optin) return TSQR_ERR_UNSUPPORTED;
@@ -1405,8 +1424,13 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
 }
 
 // The mixed path's plan: the tuned plan of the bucket for AUTO calls, then the blocked leaf
-// where it applies (TSQR_LEAF_PANELS requested, or AUTO with n <= kMixedWyMaxN), else the fold.
-tsqr_status_t plan_mixed(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+// where it applies (TSQR_LEAF_PANELS requested, or AUTO with n <= kMixedWyMaxN where it measured
+// faster), else the fold.  Measured at 2^24 rows (ms, FP32 / BF16, fold against panels):
+// n = 8: 0.81 / 1.79 against 1.24 / 1.71; n = 12: 1.63 / 3.07 against 1.79 / 2.37; n = 16:
+// 3.79 / 7.79 against 2.32 / 3.03; n = 32: 11.1 / 14.4 against 6.2 / 7.8; n = 64: 47.6 / 57.4
+// against 24.3 / 27.7.  So AUTO takes the panels from n = 13 on for FP32, and for every n for
+// BF16 (whose fold widens each chunk through registers).
+tsqr_status_t plan_mixed(int64_t m, int n, bool bf16, const tsqr_plan_t *over, F64Plan *p) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     tsqr_plan_t tuned;
@@ -1418,7 +1442,8 @@ tsqr_status_t plan_mixed(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) 
         !over || ((over->warps == 0 || over->warps == 8) &&
                   (over->tree == TSQR_TREE_BINARY || over->tile_rows == 0 ||
                    over->tile_rows == 256 || over->tile_rows == 512));
-    if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && n <= kMixedWyMaxN && wy_knobs)) {
+    const bool wy_auto = n <= kMixedWyMaxN && (bf16 || n > 12);
+    if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && wy_auto && wy_knobs)) {
         tsqr_plan_t o = over ? *over : tsqr_plan_t{};
         o.leaf = TSQR_LEAF_PANELS;
         return plan_mixed_wy(m, n, &o, p);
@@ -1436,7 +1461,7 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
     if (n == 0) return TSQR_SUCCESS;
     if (m == 0) return zero_r(R, n, ldr, stream);
     F64Plan p;
-    tsqr_status_t st = plan_mixed(m, (int)n, over, &p);
+    tsqr_status_t st = plan_mixed(m, (int)n, bf16, over, &p);
     if (st != TSQR_SUCCESS) return st;
     const bool wy = p.leaf == TSQR_LEAF_PANELS;
     if ((wy ? mixed_wy_prepare(p.smem) : mixed_prepare(p.smem)) != cudaSuccess)
@@ -1835,7 +1860,8 @@ tsqr_status_t tsqr_resolve_plan(int64_t m, int64_t n, int32_t dtype, int32_t pre
         }
     }
     F64Plan p;
-    tsqr_status_t st = mixed ? plan_mixed(m, (int)n, plan, &p) : plan_leaf(m, (int)n, plan, false, &p);
+    tsqr_status_t st = mixed ? plan_mixed(m, (int)n, dtype == TSQR_BF16, plan, &p)
+                             : plan_leaf(m, (int)n, plan, false, &p);
     if (st != TSQR_SUCCESS) return st;
     *out = public_plan(p);
     return TSQR_SUCCESS;

@@ -17,8 +17,7 @@
 //   2. Compact WY form of the panel: with the tails x_J kept UNSCALED in the chunk and
 //      v_J = [e_J; c_J x_J], the product H_0 ... H_15 equals I - V S V^T (LAPACK's dlarft
 //      forward recurrence, S^-1 = diag(1 / tau) + strict_upper(G) in Joffrain et al.'s form),
-//      G(i, J) = c_i c_J x_i . x_J.  Column J - 1 of S is formed by warp 1 during reflector J's
-//      scalars.
+//      G(i, J) = c_i c_J x_i . x_J.  S is formed after the panel's reflectors by 16-lane teams.
 //   3. Trailing update of the columns T right of the panel (rows P of R, all rows of the
 //      chunk): Z = X^T C(:, T) (tensor cores), W = R(P, T) + diag(c) Z, Y = S^T W,
 //      R(P, T) -= Y, C(:, T) -= X (diag(c) Y) (tensor cores).
@@ -45,7 +44,7 @@ namespace wy {
 constexpr int kThreads = 256;
 constexpr int kWarps = 8;
 constexpr int kPw = 16;       // panel width
-constexpr int kMaxUnits = 8;  // tensor-core units of the Z product (n-tile x row group)
+constexpr int kMaxPartials = 24;  // partial Z tiles (row group x n-tile) in shared memory
 
 // ------------------------------------------------------------------------------------------
 // Double-FP32 ("df") arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2.  Error-free
@@ -183,7 +182,7 @@ struct Layout {
     int fsh;    // 16 floats: the factors f_k of the reflector just formed
     int W;      // 16 x ntmax df: W, then Y
     int B;      // diag(c) Y in three TF32 parts, K-major operands of 16 x ntmax16 each
-    int P;      // kMaxUnits x 16 x 8 floats: partial Z tiles
+    int P;      // kMaxPartials x 16 x 8 floats: partial Z tiles
     int f, seg, tot, flag;  // the tree's buffers (overlay W.. once the chunks are done)
     int total;
 };
@@ -208,7 +207,7 @@ __host__ __device__ inline Layout layout(int n, int h) {
     const int chunk_end_base = o;
     L.W = o;   o += 16 * ntmax * 8;
     L.B = o;   o += 3 * ntmax16 * 64;
-    L.P = o;   o += kMaxUnits * 16 * 8 * 4;
+    L.P = o;   o += kMaxPartials * 16 * 8 * 4;
     const int chunk_end = o;
     // the tree (after the last chunk) reuses the region from W on
     int t = chunk_end_base;
@@ -263,31 +262,27 @@ __device__ __forceinline__ int sum16_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-// Column J of the panel's T factor S (the forward recurrence of LAPACK's dlarft on the compact
-// form): S(J, J) = tau_J, S(i, J) = -tau_J sum_{l = i..J-1} S(i, l) G(l, J) for i < J, with
-// G(l, J) = (c_l (x_l . x_J)) c_J scaled here in place first (|c x| <= 1: no intermediate
-// overflows).  One warp; lane i computes row i.  S is column-major (S[J * 16 + i]).
-__device__ __forceinline__ void s_column(const int J, const int lane, df *G, df *S, const df *tau,
-                                         const df *c) {
-    if (lane < J) G[lane * 16 + J] = dmul(dmul(c[lane], G[lane * 16 + J]), c[J]);
-    __syncwarp();
-    if (lane < 16) {
-        df v = mk(0.f);
-        if (lane == J) {
-            v = tau[J];
-        } else if (lane < J) {
-            df a0 = mk(0.f), a1 = mk(0.f);  // two chains
-            int l = lane;
-            for (; l + 1 < J; l += 2) {
-                a0 = dadd(a0, dmul(S[l * 16 + lane], G[l * 16 + J]));
-                a1 = dadd(a1, dmul(S[(l + 1) * 16 + lane], G[(l + 1) * 16 + J]));
-            }
-            if (l < J) a0 = dadd(a0, dmul(S[l * 16 + lane], G[l * 16 + J]));
-            v = dneg(dmul(tau[J], dadd(a0, a1)));
-        }
-        S[J * 16 + lane] = v;
+// The panel's T factor S (S^-1 = diag(1 / tau) + strict_upper(G), the compact form of LAPACK's
+// dlarft): 16 teams of 16 lanes, team Jc forms column Jc by back substitution,
+// S(Jc, Jc) = tau_Jc, S(i, Jc) = -tau_i sum_{l = i+1..Jc} G(i, l) S(l, Jc), with
+// G(i, l) = (c_i (x_i . x_l)) c_l scaled first (|c x| <= 1: no intermediate overflows).  Needs
+// 256 threads; S is column-major (S[Jc * 16 + i]); columns and rows from pw on are zero.
+__device__ __forceinline__ void s_factor(const int tid, const int pw, df *G, df *S,
+                                         const df *tau, const df *c) {
+    {
+        const int i = tid >> 4, J = tid & 15;
+        if (i < J && J < pw) G[i * 16 + J] = dmul(dmul(c[i], G[i * 16 + J]), c[J]);
     }
-    __syncwarp();
+    __syncthreads();
+    const int Jc = tid >> 4, i = tid & 15;
+    df acc = mk(0.f), s_mine = mk(0.f);
+    for (int l = 15; l >= 0; --l) {
+        if (l <= Jc && i == l) s_mine = (l == Jc) ? tau[l] : dneg(dmul(tau[l], acc));
+        const df sl = shfl_df(s_mine, l, 16);
+        if (l <= Jc && i < l) acc = dadd(acc, dmul(G[i * 16 + l], sl));
+    }
+    if (Jc >= pw || i > Jc) s_mine = mk(0.f);
+    S[Jc * 16 + i] = s_mine;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -353,16 +348,21 @@ struct WyArgs2 {
 // the columns right of it.  ROWS = h / 256 rows per thread in the factorization.
 // ------------------------------------------------------------------------------------------
 // Tensor memory of a CTA: for M-block b (rows 128 b .. 128 b + 127) the update's accumulator D_b
-// at columns [64 b, 64 b + 64) and the tails' three TF32 parts (A operand, 16 columns each) at
-// [64 MB + 48 b, 64 MB + 48 b + 48); MB = h / 128 M-blocks, 112 MB columns in all.
+// at columns [DW b, DW b + DW) (DW = the widest trailing block, 16 to 48 columns) and the tails'
+// three TF32 parts (A operand, 16 columns each) at [DW MB + 48 b, DW MB + 48 b + 48);
+// MB = h / 128 M-blocks, (DW + 48) MB <= 512 columns in all.
 struct Tmem {
     uint32_t base;   // allocated address (lane 0)
     uint64_t *bar;   // mbarrier the update's mma commit arrives on
     uint32_t phase;  // parity of the next commit's phase
     bool ok;         // false once a bounded wait gave up
 };
-__host__ __device__ constexpr uint32_t tmem_cols(int h) {
-    return (112 * (h / 128)) <= 256 ? 256u : 512u;
+__host__ __device__ constexpr int tmem_dw(int n) {
+    return ((n + 15) / 16) * 16 - 16 > 16 ? ((n + 15) / 16) * 16 - 16 : 16;
+}
+__host__ __device__ constexpr int tmem_need(int n, int h) { return (tmem_dw(n) + 48) * (h / 128); }
+__host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
+    return tmem_need(n, h) <= 256 ? 256u : 512u;
 }
 
 template <int ROWS>
@@ -458,8 +458,6 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                     Rd[rowoff(n, Jg)] = rf.beta;
                 }
             }
-        } else if (warp == 1 && J > 0) {
-            s_column(J - 1, lane, G, S, tau_s, c_s);  // in the shadow of warp 0's scalars
         }
         __syncthreads();
 #pragma unroll
@@ -467,7 +465,10 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
         for (int q = 0; q < ROWS; ++q) xp[q] = xj[q];
     }
-    if (warp == 1) s_column(pw - 1, lane, G, S, tau_s, c_s);
+    if (J0 + kPw < n) {  // S is needed only where columns right of the panel remain
+        __syncthreads();
+        s_factor(threadIdx.x, pw, G, S, tau_s, c_s);
+    }
     // the tails (unscaled, 22 bits) back to the chunk
 #pragma unroll
     for (int q = 0; q < ROWS; ++q) {
@@ -479,7 +480,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     const int T0 = J0 + kPw;           // first trailing column
     const int ntp = n8 - T0;           // trailing columns, padded to 8
     if (ntp > 0) {
-        // the tails' two TF32 parts, this thread's rows, into tensor memory (the A operand of
+        // the tails' three TF32 parts, this thread's rows, into tensor memory (the A operand of
         // the update): row 256 q + 32 w + l is lane 32 (w % 4) + l of M-block 2 q + w / 4
         constexpr int MB = h / 128;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
@@ -491,7 +492,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             for (int half = 0; half < 2; ++half) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) split3(x[q][8 * half + e], hi[e], mid[e], lo[e]);
-                const uint32_t col = (uint32_t)(64 * MB + 48 * b + 8 * half);
+                const uint32_t col = (uint32_t)(tmem_dw(n) * MB + 48 * b + 8 * half);
                 tc::tmem_st8(tm.base + lane_base + col, hi);
                 tc::tmem_st8(tm.base + lane_base + col + 16u, mid);
                 tc::tmem_st8(tm.base + lane_base + col + 32u, lo);
@@ -502,45 +503,57 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     __syncthreads();
     if (ntp <= 0) return;
 
-    // ---- 2a. Z = X^T C(:, T) on the tensor cores (units: n-tile x row group)
+    // ---- 2a. Z = X^T C(:, T) on the tensor cores.  The 8 warps are KG row groups x TS sets of
+    //          n-tiles (8 columns each): a warp splits its X fragments once per 8 rows and uses
+    //          them for every tile of its set.  Per tile two accumulators: the five smaller
+    //          partial products, and X_hi C_hi; partial tiles per row group go to P.
     const int NT8 = ntp / 8;
-    int KG = 1;
-    while (KG * 2 * NT8 <= kMaxUnits) KG *= 2;
+    const int TS = NT8 >= 4 ? 2 : 1;          // tile sets
+    const int TPS = (NT8 + TS - 1) / TS;      // tiles per set (<= 3 for n <= 64)
+    const int KG = kWarps / TS;               // row groups
     const int g4 = lane >> 2, t4 = lane & 3;
-    if (warp < NT8 * KG) {
-        const int jt = warp % NT8, grp = warp / NT8;
-        const int c0 = T0 + 8 * jt;
+    {
+        const int grp = warp / TS, set = warp % TS;
+        const int jt0 = set * TPS, jt1 = min(NT8, jt0 + TPS);
         const int r0 = grp * (h / KG), r1 = r0 + h / KG;
-        // six partial products in six accumulators (independent MMA chains), summed at the end
-        // smallest first
-        float d[6][4] = {};
+        float e[3][4] = {}, hh[3][4] = {};
         for (int k0 = r0; k0 < r1; k0 += 8) {
             const float xa[4] = {C[cidx(k0 + t4, J0 + g4, NP)], C[cidx(k0 + t4, J0 + g4 + 8, NP)],
                                  C[cidx(k0 + t4 + 4, J0 + g4, NP)],
                                  C[cidx(k0 + t4 + 4, J0 + g4 + 8, NP)]};
-            const float cb[2] = {C[cidx(k0 + t4, c0 + g4, NP)], C[cidx(k0 + t4 + 4, c0 + g4, NP)]};
-            float ah[4], am[4], al[4], bh[2], bm[2], bl[2];
+            float ah[4], am[4], al[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) split3(xa[q], ah[q], am[q], al[q]);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
-            tc::mma_m16n8k8(d[0], am, bm);
-            tc::mma_m16n8k8(d[1], al, bh);
-            tc::mma_m16n8k8(d[2], ah, bl);
-            tc::mma_m16n8k8(d[3], am, bh);
-            tc::mma_m16n8k8(d[4], ah, bm);
-            tc::mma_m16n8k8(d[5], ah, bh);
+            for (int t = 0; t < 3; ++t) {
+                const int jt = jt0 + t;
+                if (jt < jt1) {
+                    const int c0 = T0 + 8 * jt;
+                    const float cb[2] = {C[cidx(k0 + t4, c0 + g4, NP)],
+                                         C[cidx(k0 + t4 + 4, c0 + g4, NP)]};
+                    float bh[2], bm[2], bl[2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
+                    tc::mma_m16n8k8(e[t], am, bm);
+                    tc::mma_m16n8k8(e[t], al, bh);
+                    tc::mma_m16n8k8(e[t], ah, bl);
+                    tc::mma_m16n8k8(e[t], am, bh);
+                    tc::mma_m16n8k8(e[t], ah, bm);
+                    tc::mma_m16n8k8(hh[t], ah, bh);
+                }
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            d[4][q] = __fadd_rn(
-                __fadd_rn(__fadd_rn(__fadd_rn(d[0][q], d[1][q]), d[2][q]), __fadd_rn(d[3][q], d[4][q])),
-                d[5][q]);
-        float *pt = P + warp * 128;  // unit tile, 16 x 8 row-major
-        pt[g4 * 8 + 2 * t4] = d[4][0];
-        pt[g4 * 8 + 2 * t4 + 1] = d[4][1];
-        pt[(g4 + 8) * 8 + 2 * t4] = d[4][2];
-        pt[(g4 + 8) * 8 + 2 * t4 + 1] = d[4][3];
+        for (int t = 0; t < 3; ++t) {
+            const int jt = jt0 + t;
+            if (jt < jt1) {
+                float *pt = P + (grp * NT8 + jt) * 128;  // tile, 16 x 8 row-major
+                pt[g4 * 8 + 2 * t4] = __fadd_rn(e[t][0], hh[t][0]);
+                pt[g4 * 8 + 2 * t4 + 1] = __fadd_rn(e[t][1], hh[t][1]);
+                pt[(g4 + 8) * 8 + 2 * t4] = __fadd_rn(e[t][2], hh[t][2]);
+                pt[(g4 + 8) * 8 + 2 * t4 + 1] = __fadd_rn(e[t][3], hh[t][3]);
+            }
+        }
     }
     __syncthreads();
 
@@ -603,8 +616,8 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             // (A part, B part), 0 = hi, 1 = mid, 2 = lo; the products below 2^-33 are dropped
             const int terms[6][2] = {{1, 1}, {2, 0}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
             for (int b = 0; b < MB; ++b) {
-                const uint32_t dcol = tm.base + (uint32_t)(64 * b);
-                const uint32_t acol = tm.base + (uint32_t)(64 * MB + 48 * b);
+                const uint32_t dcol = tm.base + (uint32_t)(tmem_dw(n) * b);
+                const uint32_t acol = tm.base + (uint32_t)(tmem_dw(n) * MB + 48 * b);
                 bool acc = false;
                 for (int t = 0; t < 6; ++t)
                     for (int s2 = 0; s2 < 2; ++s2) {
@@ -635,7 +648,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                 const int b = 2 * q + (warp >> 2);
                 for (int c0 = 0; c0 < ntp16; c0 += 8) {
                     float v[8];
-                    tc::tmem_ld8(tm.base + lane_base + (uint32_t)(64 * b + c0), v);
+                    tc::tmem_ld8(tm.base + lane_base + (uint32_t)(tmem_dw(n) * b + c0), v);
                     tc::tmem_ld_wait();
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
@@ -650,10 +663,11 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     __syncthreads();
 }
 
-// One row per thread (256-row chunks): two CTAs per SM (at most 128 registers a thread), so
-// that one CTA's reflector chain runs while the other's waits; two rows: one CTA per SM.
+// Eight warps, ROWS = h / 256 rows per lane in the panel factorization (1 to 4): chunks as tall
+// as shared and tensor memory allow for the width (fewer reflector chains per row).  One row per
+// lane (256-row chunks) allows two CTAs per SM (at most 128 registers a thread).
 template <typename Tin, int ROWS>
-__global__ void __launch_bounds__(kThreads, 3 - ROWS) tsqr_mixed_wy_kernel(const WyArgs2 a) {
+__global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1) tsqr_mixed_wy_kernel(const WyArgs2 a) {
     extern __shared__ __align__(16) unsigned char sm[];
     constexpr int h = 256 * ROWS;
     const F64Args &b = a.base;
@@ -676,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 3 - ROWS) tsqr_mixed_wy_kernel(const
         tc::fence_mbar_init();
     }
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(tbase, tmem_cols(h));
+        tc::tmem_alloc(tbase, tmem_cols(n, h));
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -704,10 +718,10 @@ __global__ void __launch_bounds__(kThreads, 3 - ROWS) tsqr_mixed_wy_kernel(const
         // the mma in flight, release the tensor memory and leave R unwritten
         if (threadIdx.x == 0) tc::mbar_wait(bar, tm.phase, 1LL << 22);
         __syncthreads();
-        if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(h));
+        if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(n, h));
         return;
     }
-    if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(h));
+    if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(n, h));
     __syncthreads();
     // R to FP64 (exact: hi + lo), in place, for the FP64 tree
     double *Rp = reinterpret_cast<double *>(sm + L.R);
@@ -730,12 +744,29 @@ __global__ void __launch_bounds__(kThreads, 3 - ROWS) tsqr_mixed_wy_kernel(const
 namespace {
 template <typename Tin>
 const void *wy_fn(int rows) {
-    return rows == 2 ? (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>
-                     : (const void *)wy::tsqr_mixed_wy_kernel<Tin, 1>;
+    switch (rows) {
+        case 4: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 4>;
+        case 3: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 3>;
+        case 2: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>;
+        default: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 1>;
+    }
+}
+template <typename Tin>
+void wy_launch_t(const wy::WyArgs2 &a, int rows, size_t smem, cudaStream_t stream) {
+    const dim3 grid(a.base.nleaves), block(wy::kThreads);
+    switch (rows) {
+        case 4: wy::tsqr_mixed_wy_kernel<Tin, 4><<<grid, block, smem, stream>>>(a); break;
+        case 3: wy::tsqr_mixed_wy_kernel<Tin, 3><<<grid, block, smem, stream>>>(a); break;
+        case 2: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a); break;
+        default: wy::tsqr_mixed_wy_kernel<Tin, 1><<<grid, block, smem, stream>>>(a); break;
+    }
 }
 }  // namespace
 
 size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total; }
+
+// Whether an h-row chunk (h = 256 .. 1024, a multiple of 256) fits the tensor memory for width n.
+bool mixed_wy_tmem_fits(int n, int h) { return wy::tmem_need(n, h) <= 512; }
 
 // Largest arity (<= 8) whose stacked FP64 triangles fit in the chunk region of an h-row leaf.
 int mixed_wy_arity(int n, int h) {
@@ -750,8 +781,9 @@ bool mixed_wy_tree_fits(int n, int h, int arity) {
 }
 
 cudaError_t mixed_wy_prepare(size_t smem_bytes) {
-    const void *fns[4] = {wy_fn<float>(1), wy_fn<float>(2), wy_fn<__nv_bfloat16>(1),
-                          wy_fn<__nv_bfloat16>(2)};
+    const void *fns[8] = {wy_fn<float>(1), wy_fn<float>(2), wy_fn<float>(3), wy_fn<float>(4),
+                          wy_fn<__nv_bfloat16>(1), wy_fn<__nv_bfloat16>(2),
+                          wy_fn<__nv_bfloat16>(3), wy_fn<__nv_bfloat16>(4)};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes);
@@ -780,17 +812,10 @@ cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int l
     a.vec4 = !bf16 && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (base.lda % 4 == 0);
     const dim3 grid(base.nleaves), block(wy::kThreads);
     const int rows = base.h / 256;
-    if (bf16) {
-        if (rows == 2)
-            wy::tsqr_mixed_wy_kernel<__nv_bfloat16, 2><<<grid, block, smem_bytes, stream>>>(a);
-        else
-            wy::tsqr_mixed_wy_kernel<__nv_bfloat16, 1><<<grid, block, smem_bytes, stream>>>(a);
-    } else {
-        if (rows == 2)
-            wy::tsqr_mixed_wy_kernel<float, 2><<<grid, block, smem_bytes, stream>>>(a);
-        else
-            wy::tsqr_mixed_wy_kernel<float, 1><<<grid, block, smem_bytes, stream>>>(a);
-    }
+    if (bf16)
+        wy_launch_t<__nv_bfloat16>(a, rows, smem_bytes, stream);
+    else
+        wy_launch_t<float>(a, rows, smem_bytes, stream);
     return cudaGetLastError();
 }
 

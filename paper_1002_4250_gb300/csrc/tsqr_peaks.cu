@@ -136,50 +136,38 @@ __global__ void __launch_bounds__(128, 1) tc05_peak_kernel(float *sink, int iter
 // row c mod 8 at 16 bytes each.  A by `variant`:
 //   0: K-major, unswizzled: core matrix (i / 8, k / 4) at (i / 8) 512 + (k / 4) 128, row i mod 8
 //      at 16 bytes each (LBO 128 along K, SBO 512 along M);
-//   1: MN-major, 128-byte swizzle, as a TMA box of 32 rows x 16 columns lays it out: row block
-//      i / 32 at (i / 32) box_stride, column k's 32 rows in one 128-byte line at k 128, 16-byte
-//      unit ((i mod 32) / 4) XOR (k mod 8) (LBO = box_stride between 32-row blocks, SBO = 1024
-//      between 8-column groups);
-//   2: the layout of 1 with LBO and SBO exchanged;
-//   3: K-major, 128-byte swizzle: row i one 128-byte line at (i / 8) 1024 + (i mod 8) 128, unit
+//   1: K-major, 128-byte swizzle: row i one 128-byte line at (i / 8) 1024 + (i mod 8) 128, unit
 //      (k / 4) XOR (i mod 8) (SBO 1024 between 8-row groups; the second K step starts 32 bytes
 //      in);
-//   4: A in tensor memory (row i in lane i, K along 16 columns after D's), written by the
-//      threads with tcgen05.st.
-// The A region is max(4 box_stride, 16384) bytes, the largest extent of any variant (variant
-// 3: 16 groups of 1024 bytes), and B follows it.
-// Before the MMAs every D entry is set to -12345 (tcgen05.st), so a D that comes back as that
-// value was never written.  Two MMAs (K = 8 each); D goes to global memory, row-major.
+//   2: A in tensor memory (row i in lane i, K along 16 columns after D's), written by the
+//      threads with tcgen05.st (the form the blocked mixed leaf's update uses).
+// The A region is 16384 bytes, the largest extent of any variant (variant 1: 16 groups of 1024
+// bytes), and B follows it.  Before the MMAs every D entry is set to -12345 (tcgen05.st), so a D
+// that comes back as that value was never written.  Two MMAs (K = 8 each); D goes to global
+// memory, row-major.
 // ------------------------------------------------------------------------------------------
-__host__ __device__ inline int a_region_bytes(int box_stride) {
-    return 4 * box_stride > 16384 ? 4 * box_stride : 16384;
-}
-__device__ __forceinline__ int a_off(int variant, int i, int k, int box_stride) {
-    switch (variant) {
-        case 0: return (i / 8) * 512 + (k / 4) * 128 + (i % 8) * 16 + (k % 4) * 4;
-        case 3: return (i / 8) * 1024 + (i % 8) * 128 + (((k / 4) ^ (i % 8)) << 4) + (k % 4) * 4;
-        default:
-            return (i / 32) * box_stride + k * 128 + ((((i % 32) >> 2) ^ (k & 7)) << 4) + (i & 3) * 4;
-    }
+constexpr int kSelftestARegion = 16384;
+__device__ __forceinline__ int a_off(int variant, int i, int k) {
+    if (variant == 0) return (i / 8) * 512 + (k / 4) * 128 + (i % 8) * 16 + (k % 4) * 4;
+    return (i / 8) * 1024 + (i % 8) * 128 + (((k / 4) ^ (i % 8)) << 4) + (k % 4) * 4;
 }
 
-__global__ void __launch_bounds__(128, 1) tc05_layout_selftest_kernel(float *D, int N,
-                                                                      int box_stride, int variant,
+__global__ void __launch_bounds__(128, 1) tc05_layout_selftest_kernel(float *D, int N, int variant,
                                                                       int *status,
                                                                       long long wait_limit) {
     extern __shared__ __align__(16) unsigned char dyn_raw[];
     // the 128-byte swizzle pattern repeats every 1024 bytes: operands start on that boundary
     unsigned char *dyn = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *a_s = dyn;                           // a_region_bytes
-    unsigned char *b_s = dyn + a_region_bytes(box_stride);  // (N / 8) x 512 bytes
+    unsigned char *a_s = dyn;                           // kSelftestARegion bytes
+    unsigned char *b_s = dyn + kSelftestARegion;        // (N / 8) x 512 bytes
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tbase;
     __shared__ int ok_s;
-    if (variant != 4)
+    if (variant != 2)
         for (int idx = threadIdx.x; idx < 128 * 16; idx += blockDim.x) {
             const int i = idx % 128, k = idx / 128;
-            *reinterpret_cast<float *>(a_s + a_off(variant, i, k, box_stride)) =
+            *reinterpret_cast<float *>(a_s + a_off(variant, i, k)) =
                 (float)(((7 * i + 3 * k) % 11) - 5);
         }
     for (int idx = threadIdx.x; idx < 16 * N; idx += blockDim.x) {
@@ -207,7 +195,7 @@ __global__ void __launch_bounds__(128, 1) tc05_layout_selftest_kernel(float *D, 
         const float sentinel[8] = {-12345.f, -12345.f, -12345.f, -12345.f,
                                    -12345.f, -12345.f, -12345.f, -12345.f};
         for (int c0 = 0; c0 < N; c0 += 8) tc::tmem_st8(taddr + lane_base + (uint32_t)c0, sentinel);
-        if (variant == 4) {  // this thread's row of A: columns 256 .. 271
+        if (variant == 2) {  // this thread's row of A: columns 256 .. 271
             const int i = 32 * warp + lane;
             for (int k0 = 0; k0 < 16; k0 += 8) {
                 float a[8];
@@ -222,22 +210,16 @@ __global__ void __launch_bounds__(128, 1) tc05_layout_selftest_kernel(float *D, 
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x == 0) {
-        const uint32_t id = tc::instr_desc(tc::kFmtTF32, 128, N, variant == 1 || variant == 2, false);
+        const uint32_t id = tc::instr_desc(tc::kFmtTF32, 128, N, false, false);
         for (int s = 0; s < 2; ++s) {
-            if (variant == 4) {
+            if (variant == 2) {
                 const uint64_t bd = tc::smem_desc(tc::smem_u32(b_s + s * 256), 128, 512, tc::kSwNone);
                 tc::mma_tf32_ts(taddr, taddr + 256u + 8u * s, bd, id, s > 0);
                 continue;
             }
-            uint64_t ad;
-            if (variant == 0)
-                ad = tc::smem_desc(tc::smem_u32(a_s + s * 256), 128, 512, tc::kSwNone);
-            else if (variant == 1)
-                ad = tc::smem_desc(tc::smem_u32(a_s + s * 1024), box_stride, 1024, tc::kSw128);
-            else if (variant == 2)
-                ad = tc::smem_desc(tc::smem_u32(a_s + s * 1024), 1024, box_stride, tc::kSw128);
-            else
-                ad = tc::smem_desc(tc::smem_u32(a_s + s * 32), 16, 1024, tc::kSw128);
+            const uint64_t ad =
+                variant == 0 ? tc::smem_desc(tc::smem_u32(a_s + s * 256), 128, 512, tc::kSwNone)
+                             : tc::smem_desc(tc::smem_u32(a_s + s * 32), 16, 1024, tc::kSw128);
             const uint64_t bd = tc::smem_desc(tc::smem_u32(b_s + s * 256), 128, 512, tc::kSwNone);
             tc::mma_tf32(taddr, ad, bd, id, s > 0);
         }
@@ -333,21 +315,19 @@ extern "C" int tsqr_internal_measure_peaks(double *out, int count) {
 }
 
 // tcgen05 layout self-test (see tc05_layout_selftest_kernel): D is device memory of 128 x N
-// floats, row-major; N a multiple of 16 in [16, 256]; variant 0..3.  Synchronizes the device.
-extern "C" int tsqr_internal_tc_layout_selftest(float *D, int N, int box_stride, int variant) {
-    if (!D || N < 16 || N > 256 || N % 16 || box_stride < 2048 || box_stride % 1024 ||
-        variant < 0 || variant > 4)
-        return TSQR_ERR_INVALID_ARG;
+// floats, row-major; N a multiple of 16 in [16, 256]; variant 0..2.  Synchronizes the device.
+extern "C" int tsqr_internal_tc_layout_selftest(float *D, int N, int variant) {
+    if (!D || N < 16 || N > 256 || N % 16 || variant < 0 || variant > 2) return TSQR_ERR_INVALID_ARG;
     int *status = nullptr;
     if (cudaMalloc((void **)&status, sizeof(int)) != cudaSuccess) return TSQR_ERR_ALLOC;
     cudaMemset(status, 0, sizeof(int));
-    const size_t smem = 1024 + (size_t)a_region_bytes(box_stride) + (size_t)(N / 8) * 512;
+    const size_t smem = 1024 + (size_t)kSelftestARegion + (size_t)(N / 8) * 512;
     if (cudaFuncSetAttribute(tc05_layout_selftest_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaFree(status);
         return TSQR_ERR_CUDA;
     }
-    tc05_layout_selftest_kernel<<<1, 128, smem>>>(D, N, box_stride, variant, status, 1 << 22);
+    tc05_layout_selftest_kernel<<<1, 128, smem>>>(D, N, variant, status, 1 << 22);
     const cudaError_t e = cudaDeviceSynchronize();
     int st = 0;
     cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);

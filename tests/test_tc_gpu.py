@@ -1,7 +1,7 @@
-"""The tensor-core building blocks on the GPU: the tcgen05 operand layouts the mixed-precision
-leaf relies on (an MN-major A with the 128-byte swizzle, laid out as TMA boxes of 32 rows x 16
-columns, times a K-major unswizzled B; D read back from tensor memory), checked exactly
-against numpy on integer inputs, and the peak microbenchmarks' sanity."""
+"""The tensor-core building blocks on the GPU: tcgen05 operand layouts (K-major A unswizzled or
+with the 128-byte swizzle, or A in tensor memory as the mixed-precision leaf's update uses it,
+times a K-major unswizzled B; D read back from tensor memory), checked exactly against numpy on
+integer inputs, and the peak microbenchmarks' sanity."""
 import numpy as np
 import pytest
 
@@ -17,12 +17,12 @@ def T():
     return T
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("N,box_stride", [(16, 2048), (48, 8192), (112, 4096), (256, 2048)])
-def test_tcgen05_layouts(T, N, box_stride, variant):
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("N", [16, 48, 112, 256])
+def test_tcgen05_layouts(T, N, variant):
     import torch
     D = torch.full((128, N), float("nan"), dtype=torch.float32, device="cuda")
-    assert T.capi.tsqr_internal_tc_layout_selftest(D.data_ptr(), N, box_stride, variant) == T.SUCCESS
+    assert T.capi.tsqr_internal_tc_layout_selftest(D.data_ptr(), N, variant) == T.SUCCESS
     i = np.arange(128)[:, None]
     k = np.arange(16)[None, :]
     A = ((7 * i + 3 * k) % 11 - 5).astype(np.float64)

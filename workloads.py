@@ -47,10 +47,19 @@ def haar_orthogonal(n: int, g: torch.Generator) -> torch.Tensor:
 
 
 def conditioned(m: int, n: int, kappa: float, seed: int = 0, dtype=torch.float64,
-                device="cpu") -> torch.Tensor:
-    """(n, m) tensor holding A = G diag(sigma) V^T, sigma geometric from 1 to 1/kappa."""
+                device="cpu", device_draw: bool = False) -> torch.Tensor:
+    """(n, m) tensor holding A = G diag(sigma) V^T, sigma geometric from 1 to 1/kappa.
+
+    With ``device_draw`` and a CUDA ``device``, G is drawn on the device by a device generator
+    seeded with ``seed`` (same distribution, other values; for large sizes), V still from the
+    CPU generator."""
     g = torch.Generator().manual_seed(seed)
-    G = torch.randn(n, m, generator=g, dtype=torch.float64)           # column-major G
+    if device_draw and device != "cpu":
+        gd = torch.Generator(device=device).manual_seed(seed)
+        G = torch.randn(n, m, generator=gd, dtype=torch.float64, device=device)
+        torch.randn(n, 1, generator=g, dtype=torch.float64)  # keep V's draw independent of m
+    else:
+        G = torch.randn(n, m, generator=g, dtype=torch.float64)       # column-major G
     V = haar_orthogonal(n, g)
     if n > 1:
         k = torch.arange(n, dtype=torch.float64)
