@@ -314,7 +314,7 @@ def bench_ours(args, world, rank, local):
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
-        extras = bench_extras(dev, os.cpu_count() or 1)
+        extras = bench_extras(dev, os.cpu_count() or 1, measured)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -355,7 +355,7 @@ def time_call(fn, reps, warmup=2):
     return a.elapsed_time(b) / reps
 
 
-def bench_extras(dev, threads):
+def bench_extras(dev, threads, measured):
     """One entry per workload of the method's configurations, each speed with its error:
     the 10,000 x 16 binary-tree call, 4,194,304 x 32 by tree and at kappa = 1e8, the FP64 width
     sweep at 2^24 rows, the mixed-precision path per kappa (FP32 and BF16) against the FP64 path,
@@ -366,7 +366,7 @@ def bench_extras(dev, threads):
     out["c2_4194304x32"] = bench_c2(dev, threads)
     widths = bench_widths(dev)
     out["c3_widths_2e24"] = widths
-    out["c4_mixed_2e24x64"] = bench_mixed(dev, threads, widths["64"]["ms"])
+    out["c4_mixed_2e24x64"] = bench_mixed(dev, threads, widths["64"]["ms"], measured)
     out["c5_varlen_batch"] = bench_batched(dev, threads)
     out["thin_qr"] = bench_qr(dev)
     out["lstsq"] = bench_lstsq(dev)
@@ -437,11 +437,33 @@ def bench_c2(dev, threads):
     return res
 
 
-def bench_mixed(dev, threads, ms64):
+def mixed_roofline_ms(m, n, elem_bytes, measured, panel=16):
+    """Roofline time (ms) of the blocked mixed leaf: max(bytes(A) / HBM, trailing-update flops
+    as 3xTF32 on the tcgen05 TF32 pipe + the panels' flops on the FFMA pipe), with the pipe
+    peaks measured in this run and the HBM copy bandwidth measured on the pool.  The trailing
+    update of a panel of `panel` columns with t columns right of it costs 4 m panel t flops
+    (Z = X^T C and C -= X Y); the panels take the rest of 2mn^2 - 2n^3/3."""
+    hbm = peaks()["hbm_gbs"] * 1e9
+    tc = measured.get("tf32_tcgen05")
+    ff = measured.get("fp32_ffma")
+    if not tc or not ff:
+        return None
+    trailing = sum(4.0 * m * panel * max(0, n - j - panel) for j in range(0, n, panel))
+    panel_fl = flops(m, n) - trailing
+    t_mem = elem_bytes * m * n / hbm
+    t_pipe = trailing / (tc * 1e12 / 3.0) + panel_fl / (ff * 1e12)
+    return {"roofline_ms": max(t_mem, t_pipe) * 1e3, "hbm_ms": t_mem * 1e3,
+            "pipes_ms": t_pipe * 1e3, "trailing_flops": trailing, "panel_flops": panel_fl,
+            "peaks": "tf32_tcgen05 and fp32_ffma measured in this run (TFLOP/s); HBM: "
+                     + peaks()["source"]}
+
+
+def bench_mixed(dev, threads, ms64, measured):
     """The mixed-precision path at 16,777,216 x 64 on A = G diag(sigma) V^T, kappa in {1e2, 1e4,
     1e6}, FP32 and BF16 storage: time of the AUTO plan (the blocked leaf) and of the fold leaf,
-    the speedup over the FP64 path at 2^24 x 64 (N(0,1), ms64), and the errors against the FP64
-    oracle on the same recipe at 1,048,576 rows (the oracle's time at 2^24 rows is minutes)."""
+    the speedup over the FP64 path at 2^24 x 64 (N(0,1), ms64), the fraction of the blocked
+    leaf's roofline, and the errors against the FP64 oracle on the same recipe at 1,048,576
+    rows (the oracle's time at 2^24 rows is minutes)."""
     import torch
     import paper_1002_4250_gb300 as T
     import oracle
@@ -475,6 +497,10 @@ def bench_mixed(dev, threads, ms64):
                  "errors": _errors(An, Rp, Ro, threads, u32),
                  "fold_errors": _errors(An, Rf, Ro, threads, u32),
                  "gram_tol": 2e-6}
+            roof = mixed_roofline_ms(m, n, 4 if dt == torch.float32 else 2, measured)
+            if roof is not None:
+                roof["frac"] = roof["roofline_ms"] / ms
+                r["roofline"] = roof
             res[f"{name}_kappa_{kappa:.0e}"] = r
         del A64
         torch.cuda.empty_cache()

@@ -256,6 +256,56 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream);
 
+/* Knobs of a varlen batch call: the leaf and tree choices of Section 2 made once per batch
+ * (the paper factorizes one matrix; a batch has many).  A field of 0 takes the library's rule.
+ *   warps          : bulk warps per CTA, 4, 8 or 12 (0: 12 for a batch with widths from 48
+ *                    on whose widest chunk fits with 12 warps, else 4).
+ *   ctas_per_sm    : chunk height: 1 = chunks as tall as fit one CTA per SM, 2 = as fit two
+ *                    (0: 2 when the widest problem's chunk still holds two rows per lane).
+ *                    The grid is as many CTAs per SM as the occupancy allows.
+ *   leaves_per_cta : leaf size: a leaf holds about (sum of max(m_i, 1) n_i^2) / (CTAs x
+ *                    leaves_per_cta) of work, in whole chunks; 1 .. 64 (0: 6).
+ *   arity[b]       : tree arity of the problems in width bucket b (n <= 8, <= 16, <= 32,
+ *                    > 32), 2 .. 8, lowered to what the width's shared memory holds (0: the
+ *                    largest that fits). */
+typedef struct tsqr_batch_plan_t {
+    int32_t warps;
+    int32_t ctas_per_sm;
+    int32_t leaves_per_cta;
+    int32_t arity[4];
+} tsqr_batch_plan_t;
+
+/* tsqr_r_batched with explicit knobs.  plan: NULL or all zero = AUTO (the batch's tuned plan
+ * if tsqr_autotune_batched tuned its shape bucket on this device, else the built-in rules).
+ * Returns TSQR_ERR_INVALID_ARG for a field out of its range, TSQR_ERR_UNSUPPORTED when the
+ * widest problem's chunk does not fit the requested warps and chunk height. */
+tsqr_status_t tsqr_r_batched_ex(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                                const int64_t *offsets, int32_t count, double *R_packed,
+                                int32_t dtype, int32_t prec, const tsqr_batch_plan_t *plan,
+                                tsqr_stream_t stream);
+
+/* Batch autotuning: times knob settings on the caller's batch and caches the fastest for its
+ * shape bucket: the device, the input type, the set of width buckets present, floor(log2
+ * count) and floor(log2 of the work sum max(m_i, 1) n_i^2).  From then on an AUTO batched call
+ * (tsqr_r_batched, or tsqr_r_batched_ex with plan NULL or all zero) in that bucket uses it and
+ * returns the bytes it gives.  The search starts from the built-in rules and moves one knob at a
+ * time: warps x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
+ * (2, 4, 8); each setting is run once to warm up and timed over one call with CUDA events on
+ * `stream`.
+ *   Arguments as for tsqr_r_batched; R_packed is overwritten.  best: optional, receives the
+ *   chosen knobs.  Synchronizes `stream`; not for use under stream capture.  Returns
+ *   TSQR_ERR_INVALID_ARG for count == 0. */
+tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                                    const int64_t *offsets, int32_t count, double *R_packed,
+                                    int32_t dtype, int32_t prec, tsqr_batch_plan_t *best,
+                                    tsqr_stream_t stream);
+
+/* The knobs the last batched call (tsqr_r_batched, tsqr_r_batched_ex) on this host thread ran
+ * with: warps, ctas_per_sm and leaves_per_cta as resolved, arity as given (0 = the largest that
+ * fits).  All zero before any batched call and after one that launched nothing.
+ *   out : host pointer, required.  Returns TSQR_ERR_INVALID_ARG when NULL. */
+tsqr_status_t tsqr_last_batch_plan(tsqr_batch_plan_t *out);
+
 /* Size of the fixed device array tsqr_r_noalloc works in (16 MiB). */
 #define TSQR_NOALLOC_SCRATCH_BYTES (16u << 20)
 
@@ -303,7 +353,8 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
                             int64_t lda, double *R, int64_t ldr, tsqr_plan_t *best,
                             tsqr_stream_t stream);
 
-/* Forgets every tuned plan: AUTO calls go back to the built-in rules. */
+/* Forgets every tuned plan, single-matrix and batched: AUTO calls go back to the built-in
+ * rules. */
 void tsqr_autotune_reset(void);
 
 /* Synchronizes `stream`, returns the device-side status recorded by the calls made on it since

@@ -39,6 +39,21 @@ class Plan(ctypes.Structure):
                 ("leaf", ctypes.c_int32)]
 
 
+class BatchPlan(ctypes.Structure):
+    """tsqr_batch_plan_t: warps, ctas_per_sm, leaves_per_cta, arity[4] (zeros mean "choose")."""
+    _fields_ = [("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("leaves_per_cta", ctypes.c_int32), ("arity", ctypes.c_int32 * 4)]
+
+    def as_tuple(self):
+        return (self.warps, self.ctas_per_sm, self.leaves_per_cta, tuple(self.arity))
+
+
+def make_batch_plan(warps=0, ctas_per_sm=0, leaves_per_cta=0, arity=(0, 0, 0, 0)) -> BatchPlan:
+    """Knobs of a varlen batch call; arity per width bucket (n <= 8, <= 16, <= 32, > 32)."""
+    return BatchPlan(int(warps), int(ctas_per_sm), int(leaves_per_cta),
+                     (ctypes.c_int32 * 4)(*[int(a) for a in arity]))
+
+
 _capi = None
 
 
@@ -63,6 +78,16 @@ def _load():
     capi.tsqr_r_batched.argtypes = [ctypes.POINTER(_p), ctypes.POINTER(_i64), ctypes.POINTER(_i32),
                                     ctypes.POINTER(_i64), _i32, _p, _i32, _i32, _p]
     capi.tsqr_r_batched.restype = _i32
+    capi.tsqr_r_batched_ex.argtypes = [ctypes.POINTER(_p), ctypes.POINTER(_i64),
+                                       ctypes.POINTER(_i32), ctypes.POINTER(_i64), _i32, _p, _i32,
+                                       _i32, ctypes.POINTER(BatchPlan), _p]
+    capi.tsqr_r_batched_ex.restype = _i32
+    capi.tsqr_autotune_batched.argtypes = [ctypes.POINTER(_p), ctypes.POINTER(_i64),
+                                           ctypes.POINTER(_i32), ctypes.POINTER(_i64), _i32, _p,
+                                           _i32, _i32, ctypes.POINTER(BatchPlan), _p]
+    capi.tsqr_autotune_batched.restype = _i32
+    capi.tsqr_last_batch_plan.argtypes = [ctypes.POINTER(BatchPlan)]
+    capi.tsqr_last_batch_plan.restype = _i32
     capi.tsqr_get_device_status.argtypes = [_p]
     capi.tsqr_get_device_status.restype = _i32
     capi.tsqr_release_workspace.argtypes = []
@@ -111,7 +136,8 @@ def __getattr__(name):
 ABI_SYMBOLS = ("tsqr_r", "tsqr_r_ex", "tsqr_qr_uppers", "tsqr_r_batched", "tsqr_get_device_status",
                "tsqr_release_workspace", "tsqr_status_string", "tsqr_resolve_plan",
                "tsqr_last_launch_count", "tsqr_r_noalloc", "tsqr_qr", "tsqr_autotune",
-               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq", "tsqr_caqr_r", "tsqr_last_plan")
+               "tsqr_autotune_reset", "tsqr_r_host", "tsqr_lstsq", "tsqr_caqr_r", "tsqr_last_plan",
+               "tsqr_r_batched_ex", "tsqr_autotune_batched", "tsqr_last_batch_plan")
 
 
 class TsqrError(RuntimeError):
@@ -316,16 +342,47 @@ def tsqr_qr_uppers(R1, R2, normalize=False, R=None, stream=None):
     return R
 
 
-def tsqr_r_batched(ptrs, ms, ns, offsets, R_packed, dtype=F64, prec=PREC_F64, stream=None):
-    """Varlen batch through one launch; ptrs/ms/ns/offsets are host sequences (see tsqr.h)."""
+def _batch_arrays(ptrs, ms, ns, offsets):
     count = len(ms)
     P = (ctypes.c_void_p * max(count, 1))(*[int(p) for p in ptrs])
     M = (ctypes.c_int64 * max(count, 1))(*[int(x) for x in ms])
     N = (ctypes.c_int32 * max(count, 1))(*[int(x) for x in ns])
     O = (ctypes.c_int64 * (count + 1))(*[int(x) for x in offsets])
-    check(_load().tsqr_r_batched(P, M, N, O, count, R_packed.data_ptr(), int(dtype), int(prec),
-                              _stream_ptr(stream)), "tsqr_r_batched")
+    return P, M, N, O, count
+
+
+def tsqr_r_batched(ptrs, ms, ns, offsets, R_packed, dtype=F64, prec=PREC_F64, stream=None,
+                   plan=None):
+    """Varlen batch through one launch; ptrs/ms/ns/offsets are host sequences (see tsqr.h).
+    plan: None (AUTO: the tuned knobs of the batch's bucket, else the built-in rules) or a
+    BatchPlan."""
+    P, M, N, O, count = _batch_arrays(ptrs, ms, ns, offsets)
+    if plan is None:
+        check(_load().tsqr_r_batched(P, M, N, O, count, R_packed.data_ptr(), int(dtype),
+                                     int(prec), _stream_ptr(stream)), "tsqr_r_batched")
+    else:
+        check(_load().tsqr_r_batched_ex(P, M, N, O, count, R_packed.data_ptr(), int(dtype),
+                                        int(prec), ctypes.byref(plan), _stream_ptr(stream)),
+              "tsqr_r_batched_ex")
     return R_packed
+
+
+def tsqr_autotune_batched(ptrs, ms, ns, offsets, R_packed, dtype=F64, prec=PREC_F64,
+                          stream=None) -> BatchPlan:
+    """Time knob settings on this batch, cache the fastest for its shape bucket, return it."""
+    P, M, N, O, count = _batch_arrays(ptrs, ms, ns, offsets)
+    best = BatchPlan()
+    check(_load().tsqr_autotune_batched(P, M, N, O, count, R_packed.data_ptr(), int(dtype),
+                                        int(prec), ctypes.byref(best), _stream_ptr(stream)),
+          "tsqr_autotune_batched")
+    return best
+
+
+def last_batch_plan() -> BatchPlan:
+    """The knobs of the last batched call on this thread (tsqr_last_batch_plan)."""
+    out = BatchPlan()
+    check(_load().tsqr_last_batch_plan(ctypes.byref(out)), "tsqr_last_batch_plan")
+    return out
 
 
 def tsqr_get_device_status(stream=None) -> int:

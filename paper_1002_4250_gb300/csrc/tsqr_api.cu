@@ -35,6 +35,7 @@ namespace {
 
 thread_local int g_last_launches = 0;
 thread_local tsqr_plan_t g_last_plan{};  // the plan of the last call's (first) factorization
+thread_local tsqr_batch_plan_t g_last_batch_plan{};  // the knobs of the last batched call
 
 struct Workspace {
     void *base = nullptr;   // counters + slots (grown on demand)
@@ -1503,31 +1504,84 @@ tsqr_status_t run_mixed(const void *A, bool bf16, int64_t m, int64_t n, int64_t 
 // so that the batch has several leaves per CTA; work items (problem, leaf) ordered by work,
 // largest first, for the persistent kernel's queue.
 // ------------------------------------------------------------------------------------------
+// Width bucket of a batched problem: n <= 8, <= 16, <= 32, > 32.
+int width_bucket(int n) { return n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : 3; }
+
+// Batch plans chosen by tsqr_autotune_batched, per batch shape bucket: device, input type,
+// the width buckets present, floor(log2 count) and floor(log2 of the work sum max(m, 1) n^2).
+struct BatchKey {
+    int dev, dt, widths, clog, wlog;
+    bool operator<(const BatchKey &o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (dt != o.dt) return dt < o.dt;
+        if (widths != o.widths) return widths < o.widths;
+        if (clog != o.clog) return clog < o.clog;
+        return wlog < o.wlog;
+    }
+};
+std::map<BatchKey, tsqr_batch_plan_t> g_batch_tuned;  // guarded by g_tune_mu
+
+BatchKey batch_key(int dev, int dt, const int64_t *ms, const int32_t *ns, int32_t count) {
+    int widths = 0;
+    double work = 0.0;
+    for (int32_t i = 0; i < count; ++i) {
+        widths |= 1 << width_bucket(ns[i]);
+        work += (double)std::max<int64_t>(ms[i], 1) * ns[i] * ns[i];
+    }
+    int wlog = 0;
+    while (wlog < 120 && std::ldexp(1.0, wlog + 1) <= work) ++wlog;
+    return BatchKey{dev, dt, widths, floor_log2(std::max(count, 1)), wlog};
+}
+
+bool batch_plan_is_auto(const tsqr_batch_plan_t *p) {
+    return !p || (p->warps == 0 && p->ctas_per_sm == 0 && p->leaves_per_cta == 0 &&
+                  p->arity[0] == 0 && p->arity[1] == 0 && p->arity[2] == 0 && p->arity[3] == 0);
+}
+
 tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
                           const int64_t *offsets, int32_t count, double *R_packed, int dt,
-                          cudaStream_t stream) {
+                          const tsqr_batch_plan_t *bp_in, cudaStream_t stream) {
     g_last_launches = 0;
     g_last_plan = tsqr_plan_t{};
+    g_last_batch_plan = tsqr_batch_plan_t{};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
     const DeviceInfo di = device_info(dev);
     if (di.sms <= 0) return TSQR_ERR_CUDA;
+    tsqr_batch_plan_t bp{};
+    if (!batch_plan_is_auto(bp_in)) {
+        bp = *bp_in;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_batch_tuned.find(batch_key(dev, dt, ms, ns, count));
+        if (it != g_batch_tuned.end()) bp = it->second;
+    }
+    if ((bp.warps != 0 && bp.warps != 4 && bp.warps != 8 && bp.warps != 12) ||
+        bp.ctas_per_sm < 0 || bp.ctas_per_sm > 2 || bp.leaves_per_cta < 0 ||
+        bp.leaves_per_cta > 64)
+        return TSQR_ERR_INVALID_ARG;
+    for (int b = 0; b < 4; ++b)
+        if (bp.arity[b] != 0 && (bp.arity[b] < 2 || bp.arity[b] > 8)) return TSQR_ERR_INVALID_ARG;
     const bool mixed = dt != 0;
     int nmax = 1;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
     const size_t reserve = 1024 + 256;  // per-CTA reserve plus the kernel's static shared memory
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
-    // bulk warps: 4, or 12 for a batch with widths from 48 on whose widest chunk fits with 12
-    // warps: it runs one CTA per SM and hides the wide problems' reflector chains behind more
-    // warps (the varlen batch of 4096 problems with widths up to 64: FP64 716 ms with 4, 640
-    // with 8, 626 with 12; mixed FP32 304 ms with 4, 224 with 12)
-    const int W = (nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, mixed) >= 1) ? 12 : 4;
-    // two CTAs per SM when the widest problem's chunk fits at two rows per lane (one CTA per
-    // SM with taller chunks measured faster on the varlen batch otherwise: 717 against
-    // 1010 ms for FP64 with widths up to 64)
+    // bulk warps (AUTO): 4, or 12 for a batch with widths from 48 on whose widest chunk fits
+    // with 12 warps: it runs one CTA per SM and hides the wide problems' reflector chains
+    // behind more warps (the varlen batch of 4096 problems with widths up to 64: FP64 716 ms
+    // with 4, 640 with 8, 626 with 12; mixed FP32 304 ms with 4, 224 with 12)
+    const int W = bp.warps ? bp.warps
+                           : (nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, mixed) >= 1)
+                                 ? 12 : 4;
+    // CTAs per SM (AUTO): two when the widest problem's chunk fits at two rows per lane (one
+    // CTA per SM with taller chunks measured faster on the varlen batch otherwise: 717
+    // against 1010 ms for FP64 with widths up to 64)
     size_t budget = two_per_sm;
-    if (good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2) budget = one_per_sm;
+    if (bp.ctas_per_sm == 1 ||
+        (bp.ctas_per_sm == 0 && good_r(max_rows_per_lane_p(nmax, W, two_per_sm, mixed)) < 2))
+        budget = one_per_sm;
     // per width: chunk rows
     std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1), vec_of(TSQR_MAX_N + 1, 1);
     size_t smem = 0;
@@ -1547,14 +1601,15 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         smem = std::max(smem, leaf_smem_bytes(n, hs_of[n], ld_for(hs_of[n], vec_of[n]), W,
                                               mixed));
     }
-    const int kdt = (W == 12) ? dt + 3 : dt;  // the 12-warp kernels
+    const int kdt = (W > 7) ? dt + 3 : dt;  // the kernels for up to 12 bulk warps
     if (batched_prepare(kdt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
     const int per_sm = std::max(1, batched_blocks_per_sm(kdt, W, smem));
     const int64_t ctas = (int64_t)di.sms * per_sm;
-    // leaf size: about 6 leaves per CTA over the whole batch
+    // leaf size: about 6 leaves per CTA over the whole batch (AUTO)
+    const int lpc = bp.leaves_per_cta ? bp.leaves_per_cta : 6;
     double work = 0.0;
     for (int32_t i = 0; i < count; ++i) work += (double)std::max<int64_t>(ms[i], 1) * ns[i] * ns[i];
-    const double target = work / (double)(ctas * 6);
+    const double target = work / (double)(ctas * lpc);
 
     std::vector<BatchProblem> probs(count);
     std::vector<std::pair<double, int2>> items;
@@ -1578,8 +1633,12 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         P.nunits = (m + P.unit - 1) / P.unit;
         if (P.nunits > (1 << 24)) return TSQR_ERR_UNSUPPORTED;
         P.nleaves = (int)P.nunits;
-        P.arity = arity_for(n, mixed ? mixed_s_doubles(n, P.ldS) : P.ldS * n);
-        if (!mixed && tree_ldsd(n, P.arity) > P.ldS) P.arity = 2;
+        // arity: the largest that the width's shared memory holds, or the plan's, lowered to fit
+        const int amax = arity_for(n, mixed ? mixed_s_doubles(n, P.ldS) : P.ldS * n);
+        const int areq = bp.arity[width_bucket(n)];
+        P.arity = areq ? std::min(areq, amax) : amax;
+        if (!mixed)
+            while (P.arity > 2 && tree_ldsd(n, P.arity) > P.ldS) --P.arity;
         TreeShape shape;
         int64_t nodes = 0;
         if (build_tree(P.nleaves, P.arity, &shape, &nodes) != TSQR_SUCCESS) return TSQR_ERR_UNSUPPORTED;
@@ -1631,6 +1690,12 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)items.size());
     if (batched_launch(kdt, b, grid, W, smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
     g_last_launches = 1;
+    tsqr_batch_plan_t used{};
+    used.warps = W;
+    used.ctas_per_sm = budget == one_per_sm ? 1 : 2;
+    used.leaves_per_cta = lpc;
+    for (int b2 = 0; b2 < 4; ++b2) used.arity[b2] = bp.arity[b2];
+    g_last_batch_plan = used;
     return TSQR_SUCCESS;
 }
 
@@ -1782,25 +1847,151 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
     return TSQR_SUCCESS;
 }
 
-tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
-                             const int64_t *offsets, int32_t count, double *R_packed,
-                             int32_t dtype, int32_t prec, tsqr_stream_t stream) {
-    g_last_launches = 0;
-    g_last_plan = tsqr_plan_t{};
+}  // extern "C"
+
+namespace {
+// Argument checks shared by the batched entry points; *dt receives the kernels' input type
+// (0 FP64, 1 FP32, 2 BF16).  count == 0 is valid (nothing to do).
+tsqr_status_t check_batch(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                          const int64_t *offsets, int32_t count, double *R_packed, int32_t dtype,
+                          int32_t prec, int *dt) {
     if (count < 0) return TSQR_ERR_INVALID_ARG;
-    if (count == 0) return TSQR_SUCCESS;
-    if (!ptrs || !ms || !ns || !offsets || !R_packed) return TSQR_ERR_INVALID_ARG;
     const bool f64 = (dtype == TSQR_F64 && prec == TSQR_PREC_F64);
     const bool mixed = (dtype == TSQR_F32 || dtype == TSQR_BF16) && prec == TSQR_PREC_MIXED;
     if (!f64 && !mixed) return TSQR_ERR_INVALID_ARG;
+    *dt = f64 ? 0 : (dtype == TSQR_F32 ? 1 : 2);
+    if (count == 0) return TSQR_SUCCESS;
+    if (!ptrs || !ms || !ns || !offsets || !R_packed) return TSQR_ERR_INVALID_ARG;
     for (int32_t i = 0; i < count; ++i) {
         if (ms[i] < 0 || ns[i] < 1 || offsets[i] < 0) return TSQR_ERR_INVALID_ARG;
         if (ns[i] > TSQR_MAX_N) return TSQR_ERR_UNSUPPORTED;
         if (offsets[i + 1] - offsets[i] < (int64_t)ns[i] * ns[i]) return TSQR_ERR_INVALID_ARG;
         if (ms[i] > 0 && !ptrs[i]) return TSQR_ERR_INVALID_ARG;
     }
-    return run_batched(ptrs, ms, ns, offsets, count, R_packed, f64 ? 0 : (dtype == TSQR_F32 ? 1 : 2),
-                       (cudaStream_t)stream);
+    return TSQR_SUCCESS;
+}
+}  // namespace
+
+extern "C" {
+
+tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                             const int64_t *offsets, int32_t count, double *R_packed,
+                             int32_t dtype, int32_t prec, tsqr_stream_t stream) {
+    return tsqr_r_batched_ex(ptrs, ms, ns, offsets, count, R_packed, dtype, prec, nullptr, stream);
+}
+
+tsqr_status_t tsqr_r_batched_ex(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                                const int64_t *offsets, int32_t count, double *R_packed,
+                                int32_t dtype, int32_t prec, const tsqr_batch_plan_t *plan,
+                                tsqr_stream_t stream) {
+    g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
+    g_last_batch_plan = tsqr_batch_plan_t{};
+    int dt = 0;
+    const tsqr_status_t st = check_batch(ptrs, ms, ns, offsets, count, R_packed, dtype, prec, &dt);
+    if (st != TSQR_SUCCESS || count == 0) return st;
+    return run_batched(ptrs, ms, ns, offsets, count, R_packed, dt, plan, (cudaStream_t)stream);
+}
+
+tsqr_status_t tsqr_last_batch_plan(tsqr_batch_plan_t *out) {
+    if (!out) return TSQR_ERR_INVALID_ARG;
+    *out = g_last_batch_plan;
+    return TSQR_SUCCESS;
+}
+
+tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
+                                    const int64_t *offsets, int32_t count, double *R_packed,
+                                    int32_t dtype, int32_t prec, tsqr_batch_plan_t *best,
+                                    tsqr_stream_t stream) {
+    g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
+    g_last_batch_plan = tsqr_batch_plan_t{};
+    int dt = 0;
+    tsqr_status_t st = check_batch(ptrs, ms, ns, offsets, count, R_packed, dtype, prec, &dt);
+    if (st != TSQR_SUCCESS) return st;
+    if (count == 0) return TSQR_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+    {
+        // the search starts from the built-in rules, which an all-zero plan means once the
+        // bucket has no tuned plan
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_batch_tuned.erase(batch_key(dev, dt, ms, ns, count));
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TSQR_ERR_CUDA;
+    }
+    // time of one plan: one call to warm up (workspace, table upload), then one timed call; a
+    // plan run_batched refuses scores -1
+    auto time_plan = [&](const tsqr_batch_plan_t &c, float *ms_out) -> tsqr_status_t {
+        *ms_out = -1.0f;
+        if (run_batched(ptrs, ms, ns, offsets, count, R_packed, dt, &c, s) != TSQR_SUCCESS)
+            return TSQR_SUCCESS;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return TSQR_ERR_CUDA;
+        const tsqr_status_t r = run_batched(ptrs, ms, ns, offsets, count, R_packed, dt, &c, s);
+        if (r != TSQR_SUCCESS) return r;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms_out, e0, e1) != cudaSuccess)
+            return TSQR_ERR_CUDA;
+        return TSQR_SUCCESS;
+    };
+    // coordinate search from the built-in rules (all fields 0): bulk warps x CTAs per SM, then
+    // leaves per CTA, then the tree arity of each width bucket present
+    tsqr_batch_plan_t cur{};
+    float cur_ms = -1.0f;
+    auto consider = [&](const tsqr_batch_plan_t &c) -> tsqr_status_t {
+        float t = 0.0f;
+        const tsqr_status_t r = time_plan(c, &t);
+        if (r != TSQR_SUCCESS) return r;
+        if (t >= 0.0f && (cur_ms < 0.0f || t < cur_ms)) {
+            cur_ms = t;
+            cur = c;
+        }
+        return TSQR_SUCCESS;
+    };
+    int present = 0;
+    for (int32_t i = 0; i < count; ++i) present |= 1 << width_bucket(ns[i]);
+    st = consider(tsqr_batch_plan_t{});
+    for (int w : {4, 8, 12})
+        for (int k : {1, 2}) {
+            if (st != TSQR_SUCCESS) break;
+            tsqr_batch_plan_t c = cur;
+            c.warps = w;
+            c.ctas_per_sm = k;
+            st = consider(c);
+        }
+    for (int l : {2, 3, 4, 6, 10, 16}) {
+        if (st != TSQR_SUCCESS) break;
+        tsqr_batch_plan_t c = cur;
+        c.leaves_per_cta = l;
+        st = consider(c);
+    }
+    for (int b = 0; b < 4; ++b) {
+        if (!((present >> b) & 1)) continue;
+        for (int a : {2, 4, 8}) {
+            if (st != TSQR_SUCCESS) break;
+            tsqr_batch_plan_t c = cur;
+            c.arity[b] = a;
+            st = consider(c);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_last_launches = 0;
+    g_last_plan = tsqr_plan_t{};
+    g_last_batch_plan = tsqr_batch_plan_t{};
+    if (st != TSQR_SUCCESS) return st;
+    if (cur_ms < 0.0f) return TSQR_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_batch_tuned[batch_key(dev, dt, ms, ns, count)] = cur;
+    }
+    if (best) *best = cur;
+    return TSQR_SUCCESS;
 }
 
 tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream) {
@@ -1968,6 +2159,7 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
 void tsqr_autotune_reset(void) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned.clear();
+    g_batch_tuned.clear();
 }
 
 }  // extern "C"

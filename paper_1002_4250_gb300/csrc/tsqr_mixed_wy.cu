@@ -32,7 +32,10 @@
 // is transformed orthogonally to that accuracy chunk after chunk; the FP32 roundings land in
 // the chunk's rows.  The tails being exactly three TF32 parts makes the V the tensor cores use
 // and the V that S is built from the same matrix: the tails are used exactly as stored.
+#include <cuda.h>  // CUtensorMap and its encoding enums (the driver call is found at run time)
 #include <cuda_bf16.h>
+#include <cstring>
+#include <mutex>
 
 #include "tsqr_fold.cuh"
 #include "tsqr_tc.cuh"
@@ -178,7 +181,8 @@ struct Layout {
     int cc;     // 16 df
     int G;      // 16 x 16 df: x_i . x_J (i < J), scaled by c_i c_J before S is formed
     int S;      // 16 x 16 df (column-major)
-    int bar;    // the mbarrier (8 bytes) and the tensor-memory address (4 bytes)
+    int bar;    // the update's mbarrier (8 bytes), the tensor-memory address (4 bytes), and
+                // from byte 16 one mbarrier per panel for the chunk's TMA loads
     int fsh;    // 16 floats: the factors f_k of the reflector just formed
     int W;      // 16 x ntmax df: W, then Y
     int B;      // diag(c) Y in three TF32 parts, K-major operands of 16 x ntmax16 each
@@ -202,7 +206,7 @@ __host__ __device__ inline Layout layout(int n, int h) {
     L.cc = o;  o += 16 * 8;
     L.G = o;   o += 16 * 16 * 8;
     L.S = o;   o += 16 * 16 * 8;
-    L.bar = o; o += 16;
+    L.bar = o; o += 16 + 8 * 8;
     L.fsh = o; o += 16 * 4;
     const int chunk_end_base = o;
     L.W = o;   o += 16 * ntmax * 8;
@@ -327,11 +331,19 @@ __device__ __forceinline__ void load_chunk(float *C, const Tin *src, int64_t lda
         cp_async_commit();
         cp_async_wait_all();
     } else {
-        for (int idx = threadIdx.x; idx < h * cols; idx += blockDim.x) {
-            const int col = idx / h, i = idx - col * h;
-            float v = 0.f;
-            if (col < n && i < rows) v = __bfloat162float(src[(int64_t)col * lda + i]);
-            C[cidx(i, col, NP)] = v;
+        // eight independent loads in flight per thread (h x cols is a multiple of 8 x 256)
+        for (int idx0 = threadIdx.x; idx0 < h * cols; idx0 += 8 * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = idx0 + u * blockDim.x, col = idx / h, i = idx - col * h;
+                v[u] = (col < n && i < rows) ? __bfloat162float(src[(int64_t)col * lda + i]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = idx0 + u * blockDim.x, col = idx / h, i = idx - col * h;
+                C[cidx(i, col, NP)] = v[u];
+            }
         }
     }
 }
@@ -341,7 +353,75 @@ struct WyArgs2 {
     const void *A;   // FP32 or BF16
     int ldSd;        // leading dimension of the tree's FP64 view of the chunk region
     int vec4;        // FP32 A with 16-byte aligned columns (cp.async of 4 rows)
+    int tma;         // chunks arrive by TMA box loads (FP32, aligned, leaves of whole chunks)
 };
+
+// TMA state of a chunk loop: the tensor map, the next chunk's first row (-1: none), one
+// mbarrier per panel, the parity of the current chunk's phase, and (kept by thread 0, which
+// issues every load) the panels with a load in flight and the parity each such load completes.
+struct Tma {
+    const CUtensorMap *map;
+    int64_t rnext;
+    uint64_t *bar;
+    uint32_t phase;
+    uint32_t pend, ppar;
+};
+
+// TMA loads of panel k (columns 16 k .. 16 k + 15) of the chunk at row r0: h / 32 boxes of 32
+// rows x 16 columns, one per 2 KB box region of the chunk layout; zeros past A's last row and
+// column.  FP32 boxes land as the layout itself (the tensor map's 128-byte swizzle is the
+// layout's XOR); BF16 boxes (1 KB, unswizzled, column after column) land in the upper half of
+// the region and are widened in place by widen_panel.  One thread; completes bar's phase once
+// all bytes have landed.
+template <typename Tin>
+__device__ __forceinline__ void tma_panel(float *C, Tma &t, int64_t r0, int k, int h, int NP,
+                                          uint32_t parity) {
+    constexpr uint32_t box_bytes = 32u * 16u * sizeof(Tin);
+    constexpr int half = sizeof(Tin) == 2 ? 256 : 0;
+    tc::mbar_expect_tx(t.bar + k, (uint32_t)(h / 32) * box_bytes);
+    for (int rb = 0; rb < h / 32; ++rb)
+        tc::tma_load_2d(C + (size_t)(rb * NP + k) * 512 + half, t.map, (int)(r0 + 32 * rb), 16 * k,
+                        t.bar + k);
+    t.pend |= 1u << k;
+    t.ppar = (t.ppar & ~(1u << k)) | (parity << k);
+}
+
+// Panel k's BF16 boxes, staged by tma_panel<__nv_bfloat16>, widened to the FP32 layout in place.
+// Warp w takes boxes 8 q + w (the rows it holds in the factorization): every lane reads its row
+// of the 16 columns before the warp writes any of them back over the staging half.
+template <int ROWS>
+__device__ __forceinline__ void widen_panel(float *C, int k, int NP) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+        const int rb = 8 * q + warp;
+        const __nv_bfloat16 *st =
+            reinterpret_cast<const __nv_bfloat16 *>(C + (size_t)(rb * NP + k) * 512 + 256);
+        float v[kPw];
+#pragma unroll
+        for (int c = 0; c < kPw; ++c) v[c] = __bfloat162float(st[c * 32 + lane]);
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < kPw; ++c) C[cidx(32 * rb + lane, 16 * k + c, NP)] = v[c];
+    }
+}
+
+// Bounded wait for panels k0 .. k1-1 of the current chunk (and their widening for BF16); the
+// CTA agrees on the outcome.  False: a wait gave up (recorded in the status word).
+template <typename Tin, int ROWS>
+__device__ __forceinline__ bool wait_panels(float *C, Tma &t, int k0, int k1, int NP,
+                                            int *status) {
+    bool got = true;
+    for (int k = k0; k < k1; ++k) got = got && tc::mbar_wait(t.bar + k, t.phase, 1LL << 22);
+    if (__syncthreads_and(got ? 1 : 0) == 0) {
+        if (status && threadIdx.x == 0) atomicOr(status, kStatusTimeoutBit);
+        return false;
+    }
+    for (int k = k0; k < k1; ++k) t.pend &= ~(1u << k);
+    if constexpr (sizeof(Tin) == 2)
+        for (int k = k0; k < k1; ++k) widen_panel<ROWS>(C, k, NP);
+    return true;
+}
 
 // ------------------------------------------------------------------------------------------
 // One panel: factorization (reflectors J = 0 .. pw-1 of columns J0 + J), S, and the update of
@@ -365,9 +445,14 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
     return tmem_need(n, h) <= 256 ? 256u : 512u;
 }
 
-template <int ROWS>
+// With TMA loads (t != nullptr): panel 0 has arrived when this is called; panel 0 waits for
+// the other panels before its Z product reads them; and with a next chunk (t->rnext >= 0),
+// panel k's columns of the next chunk are loaded as soon as this chunk no longer reads them:
+// after the Z product (or, for the last panel, after its reflectors).
+template <typename Tin, int ROWS>
 __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, const int n,
-                                           const int NP, const int k, Tmem &tm, int *status) {
+                                           const int NP, const int k, Tmem &tm, int *status,
+                                           Tma *t) {
     constexpr int h = 256 * ROWS;
     float *C = reinterpret_cast<float *>(sm + L.C);
     df *Rd = reinterpret_cast<df *>(sm + L.R);
@@ -469,16 +554,18 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         __syncthreads();
         s_factor(threadIdx.x, pw, G, S, tau_s, c_s);
     }
-    // the tails (unscaled, 22 bits) back to the chunk
-#pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-        const int i = 256 * q + 32 * warp + lane;
-#pragma unroll
-        for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = x[q][kk];
-    }
     const int n8 = round_up_i(n, 8);
     const int T0 = J0 + kPw;           // first trailing column
     const int ntp = n8 - T0;           // trailing columns, padded to 8
+    if (ntp > 0) {
+        // the tails (unscaled) back to the chunk, for the Z product
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+            const int i = 256 * q + 32 * warp + lane;
+#pragma unroll
+            for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = x[q][kk];
+        }
+    }
     if (ntp > 0) {
         // the tails' three TF32 parts, this thread's rows, into tensor memory (the A operand of
         // the update): row 256 q + 32 w + l is lane 32 (w % 4) + l of M-block 2 q + w / 4
@@ -500,8 +587,22 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         }
         tc::tmem_st_wait();
     }
+    if (ntp <= 0) {
+        // the last panel: nothing reads its columns again in this chunk
+        if (t && t->rnext >= 0) {
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (threadIdx.x == 0) tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
+        }
+        __syncthreads();
+        return;
+    }
+    // the Z product reads the trailing panels: with TMA loads, wait for them (and widen BF16)
+    if (t && k == 0 && !wait_panels<Tin, ROWS>(C, *t, 1, NP, NP, status)) {
+        tm.ok = false;
+        return;
+    }
     __syncthreads();
-    if (ntp <= 0) return;
 
     // ---- 2a. Z = X^T C(:, T) on the tensor cores.  The 8 warps are KG row groups x TS sets of
     //          n-tiles (8 columns each): a warp splits its X fragments once per 8 rows and uses
@@ -555,7 +656,10 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             }
         }
     }
+    if (t && t->rnext >= 0) tc::fence_proxy_async();  // the panel's columns are read for the last time
     __syncthreads();
+    if (t && t->rnext >= 0 && threadIdx.x == 0)
+        tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
 
     // ---- 2b. W = R(P, T) + diag(c) Z
     for (int e = threadIdx.x; e < kPw * ntp; e += blockDim.x) {
@@ -667,8 +771,12 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 // as shared and tensor memory allow for the width (fewer reflector chains per row).  One row per
 // lane (256-row chunks) allows two CTAs per SM (at most 128 registers a thread).
 template <typename Tin, int ROWS>
-__global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1) tsqr_mixed_wy_kernel(const WyArgs2 a) {
-    extern __shared__ __align__(16) unsigned char sm[];
+__global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
+    tsqr_mixed_wy_kernel(const WyArgs2 a, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    // the chunk region starts on a 1024-byte boundary (the 128-byte swizzle's period)
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int h = 256 * ROWS;
     const F64Args &b = a.base;
     const int n = b.n;
@@ -685,8 +793,11 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1) tsqr_mixed_wy_ker
     // the update's mbarrier and tensor memory (released before the tree)
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
     uint32_t *tbase = reinterpret_cast<uint32_t *>(sm + L.bar + 8);
+    uint64_t *tbar = reinterpret_cast<uint64_t *>(sm + L.bar + 16);
+    const bool use_tma = a.tma != 0;
     if (threadIdx.x == 0) {
         tc::mbar_init(bar, 1);
+        for (int k = 0; k < NP; ++k) tc::mbar_init(tbar + k, 1);
         tc::fence_mbar_init();
     }
     if (threadIdx.x < 32) {
@@ -703,20 +814,40 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1) tsqr_mixed_wy_ker
     tm.ok = true;
 
     const Tin *A = static_cast<const Tin *>(a.A);
+    float *Cf = reinterpret_cast<float *>(sm + L.C);
+    Tma t{&tmap, -1, tbar, 0u, 0u, 0u};
+    if (use_tma && rbeg < rend && threadIdx.x == 0)
+        for (int k = 0; k < NP; ++k) tma_panel<Tin>(Cf, t, rbeg, k, h, NP, 0u);
     for (int64_t r0 = rbeg; r0 < rend && tm.ok; r0 += h) {
         const int rows = (int)((rend - r0 < h) ? rend - r0 : h);
-        __syncthreads();  // the previous chunk's last reads of C are done
-        load_chunk<Tin>(reinterpret_cast<float *>(sm + L.C), A + r0, b.lda, rows, n, h, NP,
-                        a.vec4 != 0);
-        __syncthreads();
-        for (int k = 0; k < NP && tm.ok; ++k) panel_step<ROWS>(sm, L, n, NP, k, tm, b.status);
+        t.rnext = (r0 + h < rend) ? r0 + h : -1;
+        if (!use_tma) {
+            __syncthreads();  // the previous chunk's last reads of C are done
+            load_chunk<Tin>(Cf, A + r0, b.lda, rows, n, h, NP, a.vec4 != 0);
+            __syncthreads();
+        } else {
+            // panel 0 of this chunk (panel_step waits for the others before they are read)
+            if (!wait_panels<Tin, ROWS>(Cf, t, 0, 1, NP, b.status)) {
+                tm.ok = false;
+                break;
+            }
+            __syncthreads();
+        }
+        for (int k = 0; k < NP && tm.ok; ++k)
+            panel_step<Tin, ROWS>(sm, L, n, NP, k, tm, b.status, use_tma ? &t : nullptr);
+        if (tm.ok) t.phase ^= 1u;
     }
     tc::fence_before_sync();
     __syncthreads();
     if (!tm.ok) {
-        // a tensor-core wait gave up (recorded in the status word): wait once more, bounded, for
-        // the mma in flight, release the tensor memory and leave R unwritten
-        if (threadIdx.x == 0) tc::mbar_wait(bar, tm.phase, 1LL << 22);
+        // a tensor-core or TMA wait gave up (recorded in the status word): wait once more,
+        // bounded, for the mma and the loads in flight, release the tensor memory and leave R
+        // unwritten
+        if (threadIdx.x == 0) {
+            tc::mbar_wait(bar, tm.phase, 1LL << 22);
+            for (int k = 0; k < NP; ++k)
+                if ((t.pend >> k) & 1u) tc::mbar_wait(tbar + k, (t.ppar >> k) & 1u, 1LL << 22);
+        }
         __syncthreads();
         if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(n, h));
         return;
@@ -752,18 +883,62 @@ const void *wy_fn(int rows) {
     }
 }
 template <typename Tin>
-void wy_launch_t(const wy::WyArgs2 &a, int rows, size_t smem, cudaStream_t stream) {
+void wy_launch_t(const wy::WyArgs2 &a, const CUtensorMap &tmap, int rows, size_t smem,
+                 cudaStream_t stream) {
     const dim3 grid(a.base.nleaves), block(wy::kThreads);
     switch (rows) {
-        case 4: wy::tsqr_mixed_wy_kernel<Tin, 4><<<grid, block, smem, stream>>>(a); break;
-        case 3: wy::tsqr_mixed_wy_kernel<Tin, 3><<<grid, block, smem, stream>>>(a); break;
-        case 2: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a); break;
-        default: wy::tsqr_mixed_wy_kernel<Tin, 1><<<grid, block, smem, stream>>>(a); break;
+        case 4: wy::tsqr_mixed_wy_kernel<Tin, 4><<<grid, block, smem, stream>>>(a, tmap); break;
+        case 3: wy::tsqr_mixed_wy_kernel<Tin, 3><<<grid, block, smem, stream>>>(a, tmap); break;
+        case 2: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a, tmap); break;
+        default: wy::tsqr_mixed_wy_kernel<Tin, 1><<<grid, block, smem, stream>>>(a, tmap); break;
     }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the library
+// does not link the driver library itself).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// A (FP32 or BF16) as a 2-D tensor (rows innermost, lda apart) read in boxes of 32 rows x 16
+// columns with zero fill outside: FP32 with the 128-byte swizzle (the chunk layout), BF16
+// unswizzled (staged, then widened).  False where the TMA cannot read A: a base that is not
+// 16-byte aligned, lda x element size not a multiple of 16 bytes, or no encoder.
+bool make_tensor_map(const void *A, bool bf16, int64_t m, int n, int64_t lda, CUtensorMap *tmap) {
+    EncodeTiledFn enc = encode_tiled();
+    const int64_t es = bf16 ? 2 : 4;
+    // box rows are int coordinates up to a chunk past the last row
+    if (!enc || reinterpret_cast<uintptr_t>(A) % 16 != 0 || (lda * es) % 16 != 0 || m < 1 ||
+        m > 0x7fffffffLL - 4096)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
+    const cuuint32_t box[2] = {32, 16};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(tmap, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+               const_cast<void *>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               bf16 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 }  // namespace
 
-size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total; }
+// The layout plus 1024 bytes to align its base to the swizzle period.
+size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total + 1024; }
 
 // Whether an h-row chunk (h = 256 .. 1024, a multiple of 256) fits the tensor memory for width n.
 bool mixed_wy_tmem_fits(int n, int h) { return wy::tmem_need(n, h) <= 512; }
@@ -810,12 +985,16 @@ cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int l
     a.A = A;
     a.ldSd = ldSd;
     a.vec4 = !bf16 && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (base.lda % 4 == 0);
-    const dim3 grid(base.nleaves), block(wy::kThreads);
+    // TMA loads where every leaf's rows are whole chunks (its last chunk then ends at A's last
+    // row, where the TMA fills zeros)
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    a.tma = base.unit % base.h == 0 && make_tensor_map(A, bf16, base.m, base.n, base.lda, &tmap);
     const int rows = base.h / 256;
     if (bf16)
-        wy_launch_t<__nv_bfloat16>(a, rows, smem_bytes, stream);
+        wy_launch_t<__nv_bfloat16>(a, tmap, rows, smem_bytes, stream);
     else
-        wy_launch_t<float>(a, rows, smem_bytes, stream);
+        wy_launch_t<float>(a, tmap, rows, smem_bytes, stream);
     return cudaGetLastError();
 }
 

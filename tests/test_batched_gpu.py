@@ -160,3 +160,112 @@ def test_batched_argument_errors(T):
     with pytest.raises(T.TsqrError) as e:
         T.tsqr_r_batched([A.data_ptr()], [5], [4], [0, 16], Rp, dtype=T.F32, prec=T.PREC_F64)
     assert e.value.status == T.ERR_INVALID_ARG
+
+
+# ---- batch knobs (tsqr_r_batched_ex) and batch autotuning (tsqr_autotune_batched)
+
+def _ptrs_roff(bd, ms, ns, offs):
+    es = bd.element_size()
+    ptrs = [bd.data_ptr() + es * o for o in offs[:-1]]
+    roff = [0]
+    for n in ns:
+        roff.append(roff[-1] + n * n)
+    return ptrs, roff
+
+
+def _check_all(oracle, bn, ms, ns, offs, R, roff, tol):
+    for i, (m, n) in enumerate(zip(ms, ns)):
+        Ri = R[roff[i]:roff[i + 1]].reshape(n, n).T
+        assert np.all(np.tril(Ri, -1) == 0) and np.all(np.diag(Ri) >= 0), i
+        assert oracle.gram_residual(_problem(bn, offs, ms, ns, i), Ri, nthreads=16) <= tol, i
+
+
+@pytest.mark.parametrize("knobs", [dict(warps=4, ctas_per_sm=1), dict(warps=8, ctas_per_sm=1),
+                                   dict(warps=12, ctas_per_sm=1, leaves_per_cta=2),
+                                   dict(leaves_per_cta=16, arity=(2, 2, 2, 2)),
+                                   dict(warps=4, ctas_per_sm=2, arity=(8, 4, 3, 2))])
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_batched_knobs(oracle, T, knobs, prec):
+    """Every knob setting gives a correct R for every problem of a varlen batch, and the knobs
+    the call reports are the ones asked for."""
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(96, 512, 60000, seed=5)
+    if prec == "f64":
+        bd, code, p, tol = buf.cuda(), T.F64, T.PREC_F64, 1e-13
+    else:
+        bd, code, p, tol = buf.to(torch.float32).cuda(), T.F32, T.PREC_MIXED, 2e-6
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    plan = T.make_batch_plan(**knobs)
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=p, plan=plan)
+    used = T.last_batch_plan()
+    for k in ("warps", "ctas_per_sm", "leaves_per_cta"):
+        if knobs.get(k):
+            assert getattr(used, k) == knobs[k], k
+    assert tuple(used.arity) == tuple(knobs.get("arity", (0, 0, 0, 0)))
+    torch.cuda.synchronize()
+    _check_all(oracle, bd.to(torch.float64).cpu().numpy(), ms, ns, offs, Rp.cpu().numpy(), roff,
+               tol)
+
+
+def test_batched_knob_errors(T):
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(4, 512, 2000, seed=6)
+    bd = buf.cuda()
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.zeros(roff[-1], dtype=torch.float64, device="cuda")
+    for bad in (dict(warps=5), dict(ctas_per_sm=3), dict(leaves_per_cta=65),
+                dict(arity=(1, 0, 0, 0)), dict(arity=(0, 0, 9, 0))):
+        with pytest.raises(T.TsqrError) as e:
+            T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, plan=T.make_batch_plan(**bad))
+        assert e.value.status == T.ERR_INVALID_ARG, bad
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_batched_autotune_bucket(oracle, T, prec):
+    """The tuned knobs are cached for the batch's shape bucket: an AUTO call on the same batch,
+    and on another batch of the same bucket, runs with them, is bit-reproducible, and equals
+    the explicit call with the tuned knobs; after a reset AUTO goes back to the built-in
+    rules."""
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(128, 512, 60000, seed=8)
+    if prec == "f64":
+        bd, code, p, tol = buf.cuda(), T.F64, T.PREC_F64, 1e-13
+    else:
+        bd, code, p, tol = buf.to(torch.float32).cuda(), T.F32, T.PREC_MIXED, 2e-6
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.zeros(roff[-1], dtype=torch.float64, device="cuda")
+    T.tsqr_autotune_reset()
+    try:
+        T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=p)
+        builtin = T.last_batch_plan().as_tuple()
+        best = T.tsqr_autotune_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=p)
+        R1 = Rp.clone()
+        T.tsqr_r_batched(ptrs, ms, ns, roff, R1, dtype=code, prec=p)
+        used = T.last_batch_plan()
+        if best.warps:
+            assert used.warps == best.warps
+        if best.ctas_per_sm:
+            assert used.ctas_per_sm == best.ctas_per_sm
+        if best.leaves_per_cta:
+            assert used.leaves_per_cta == best.leaves_per_cta
+        assert tuple(used.arity) == tuple(best.arity)
+        R2 = torch.zeros_like(R1)
+        T.tsqr_r_batched(ptrs, ms, ns, roff, R2, dtype=code, prec=p)
+        R3 = torch.zeros_like(R1)
+        T.tsqr_r_batched(ptrs, ms, ns, roff, R3, dtype=code, prec=p, plan=best)
+        torch.cuda.synchronize()
+        assert torch.equal(R1, R2) and torch.equal(R1, R3)
+        _check_all(oracle, bd.to(torch.float64).cpu().numpy(), ms, ns, offs, R1.cpu().numpy(),
+                   roff, tol)
+        # the same shapes at another address are in the same bucket
+        bd2 = bd.clone()
+        ptrs2, _ = _ptrs_roff(bd2, ms, ns, offs)
+        T.tsqr_r_batched(ptrs2, ms, ns, roff, R2, dtype=code, prec=p)
+        assert T.last_batch_plan().as_tuple() == used.as_tuple()
+        torch.cuda.synchronize()
+        assert torch.equal(R1, R2)
+    finally:
+        T.tsqr_autotune_reset()
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=p)
+    assert T.last_batch_plan().as_tuple() == builtin

@@ -133,6 +133,30 @@ def test_panels_leaf_odd_leading_dimension(oracle, T):
                                oracle.kappa_from_r(Ro) * U32 * np.linalg.norm(Ro))
 
 
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("n", [8, 24, 40, 64])
+def test_panels_leaf_tma_and_thread_loads_agree(oracle, T, dtype, n):
+    """A 16-byte aligned leading dimension takes the TMA box loads (FP32 boxes land swizzled;
+    BF16 boxes are staged and widened); an odd one takes the thread copies.  Both put the same
+    chunk in shared memory, so R is the same to the bit.  m = 50,001 leaves a ragged last chunk
+    (the TMA's zero fill past A's last row)."""
+    import torch
+    m = 50001
+    dt = getattr(torch, dtype)
+    At = workloads.gaussian(m, n, seed=200 + n, dtype=dt)
+
+    def run(ld):
+        big = torch.zeros(n, ld, dtype=dt)
+        big[:, :m] = At
+        return T.tsqr_r_ex(big.cuda().T[:m, :], plan=T.make_plan(leaf="panels")).cpu()
+
+    Ra = run(m + 15)  # 50,016: a multiple of 8 elements (16 bytes of BF16, 32 of FP32)
+    Rb = run(m + 2)   # 50,003: odd
+    assert torch.equal(Ra, Rb)
+    A = oracle.from_torch_colmajor(At.to(torch.float64))
+    assert oracle.gram_residual(A, Ra.numpy()) <= 2e-6
+
+
 def test_panels_leaf_rank_deficient(oracle, T):
     """Zero and repeated columns (identity reflectors, zero pivots): R^T R = A^T A still."""
     import torch
