@@ -601,9 +601,10 @@ def bench_widths(dev):
 def bench_batched(dev, threads):
     """The varlen batch: 4096 problems, m log-uniform in [512, 262144], n uniform in
     {8, 16, 32, 64}, packed in one buffer, one persistent launch per call; FP64 and mixed FP32.
-    Beside each time: the replay of the call captured in a CUDA graph, and the errors of a
-    sample of 24 problems (every 171st) against the oracle (the largest Gram residual and
-    forward error of the sample)."""
+    Each is timed with the built-in knobs and with the knobs tsqr_autotune_batched picks; beside
+    the tuned time: the replay of the call captured in a CUDA graph, and the errors of a sample
+    of 24 problems (every 171st) against the oracle (the largest Gram residual and forward
+    error of the sample)."""
     import numpy as np
     import torch
     import paper_1002_4250_gb300 as T
@@ -621,8 +622,17 @@ def bench_batched(dev, threads):
                                     ("mixed_fp32", torch.float32, T.F32, T.PREC_MIXED, 2.0 ** -24)):
         b = buf if dt == torch.float64 else buf.to(dt)
         ptrs = [b.data_ptr() + b.element_size() * o for o in offs[:-1]]
+        # the built-in knobs, then the knobs tsqr_autotune_batched picks for this batch's
+        # bucket (cached: the AUTO calls below run with them)
+        T.tsqr_autotune_reset()
         call = lambda: T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec)
+        ms_builtin = time_call(call, reps=2 if name == "fp64" else 5, warmup=1)
+        builtin = T.last_batch_plan().as_tuple()
+        t0 = time.perf_counter()
+        tuned = T.tsqr_autotune_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=prec)
+        tune_s = time.perf_counter() - t0
         ms_ = time_call(call, reps=2 if name == "fp64" else 5, warmup=1)
+        used = T.last_batch_plan().as_tuple()
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
             call()  # workspace and problem table in place before the capture
@@ -642,11 +652,15 @@ def bench_batched(dev, threads):
             gram.append(oracle.gram_residual(An, Ri, nthreads=threads))
             ferr.append(oracle.rel_err(Ri, oracle.householder_r(An, nthreads=threads)))
         res[name] = {"ms": ms_, "gflops": fl / ms_ / 1e6, "graph_replay_ms": ms_graph,
+                     "builtin_ms": ms_builtin, "builtin_knobs": builtin,
+                     "tuned_knobs": used, "autotune_s": tune_s,
                      "a_read_gbs": b.element_size() * offs[-1] / ms_ / 1e6,
                      "sample_problems": len(sample), "max_gram_residual": float(np.max(gram)),
                      "max_rel_err_vs_oracle": float(np.max(ferr)),
                      "gram_tol": 1e-13 if name == "fp64" else 2e-6}
         del b
+    T.tsqr_autotune_reset()
+    res["knobs_fields"] = "(warps, ctas_per_sm, leaves_per_cta, arity per width bucket)"
     res["mixed_speedup_vs_fp64"] = res["fp64"]["ms"] / res["mixed_fp32"]["ms"]
     del buf
     torch.cuda.empty_cache()
