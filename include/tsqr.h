@@ -100,7 +100,7 @@ typedef struct {
     int32_t tree;       /* tsqr_tree_t                                                     */
     int32_t tile_rows;  /* rows per tile (slab) b; must fit the kernel's shared memory      */
     int32_t ctas;       /* HYBRID: number of leaf CTAs                                      */
-    int32_t warps;      /* bulk warps per CTA (2, 4, 8 or 12)                                */
+    int32_t warps;      /* bulk warps per CTA (1 .. 12)                                      */
     int32_t arity;      /* children per tree node, 2..8.  BINARY uses 2, the operator of
                            Table 3; a node with c > 2 children folds their c stacked triangles
                            in one sweep (the R factor of [R_1; ...; R_c], equal to a sequence of
@@ -258,8 +258,8 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
 
 /* Knobs of a varlen batch call: the leaf and tree choices of Section 2 made once per batch
  * (the paper factorizes one matrix; a batch has many).  A field of 0 takes the library's rule.
- *   warps          : bulk warps per CTA, 4, 8 or 12 (0: 12 for a batch with widths from 48
- *                    on whose widest chunk fits with 12 warps, else 4).
+ *   warps          : bulk warps per CTA, 1 .. 12 (0: 12 for a batch with widths from 48 on
+ *                    whose widest chunk fits with 12 warps, else 4).
  *   ctas_per_sm    : chunk height: 1 = chunks as tall as fit one CTA per SM, 2 = as fit two
  *                    (0: 2 when the widest problem's chunk still holds two rows per lane).
  *                    The grid is as many CTAs per SM as the occupancy allows.
@@ -289,7 +289,7 @@ tsqr_status_t tsqr_r_batched_ex(const void *const *ptrs, const int64_t *ms, cons
  * count) and floor(log2 of the work sum max(m_i, 1) n_i^2).  From then on an AUTO batched call
  * (tsqr_r_batched, or tsqr_r_batched_ex with plan NULL or all zero) in that bucket uses it and
  * returns the bytes it gives.  The search starts from the built-in rules and moves one knob at a
- * time: warps x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
+ * time: warps (4, 6, 8, 12) x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
  * (2, 4, 8); each setting is run once to warm up and timed over one call with CUDA events on
  * `stream`.
  *   Arguments as for tsqr_r_batched; R_packed is overwritten.  best: optional, receives the
@@ -345,8 +345,10 @@ tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda,
  *   A, m, n, lda, dtype, prec, R, ldr as for tsqr_r_ex; R is overwritten (the last candidate's
  *   result).  best: optional, receives the chosen plan.
  *   Candidates: HYBRID slabs as tall as fit 1, 2 or 3 CTAs per SM, and half as tall, with that
- *   many CTAs per SM on every SM; 4, 8 or 12 bulk warps.
- *   Each is timed over three calls with CUDA events on `stream`.
+ *   many CTAs per SM on every SM; 4, 5, 6, 8 or 12 bulk warps; for FP64 from n = 48 (m >= 8 n) the
+ *   PANELS tree with 16- and 32-column panels; for the mixed path up to n = 64 the blocked
+ *   leaf with 256- and 512-row chunks.  Then the fastest HYBRID plan with tree arity 2, 3, 4, 6
+ *   and 8.  Each is timed over three calls with CUDA events on `stream`.
  *   Synchronizes `stream`; not for use under stream capture.  Returns TSQR_ERR_UNSUPPORTED if
  *   no candidate runs. */
 tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,

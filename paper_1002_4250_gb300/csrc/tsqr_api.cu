@@ -375,8 +375,7 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     // 156.5 against 197.7); FP64 by width
     p->warps = mixed ? (n >= 96 ? 12 : n >= 48 ? 8 : 4) : f64_auto_warps(n);
     if (over && over->warps) {
-        if (over->warps != 2 && over->warps != 4 && over->warps != 8 && over->warps != 12)
-            return TSQR_ERR_INVALID_ARG;
+        if (over->warps < 1 || over->warps > 12) return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
     }
     if (over && (over->tile_rows < 0 || over->ctas < 0 || over->arity < 0))
@@ -1556,7 +1555,7 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         auto it = g_batch_tuned.find(batch_key(dev, dt, ms, ns, count));
         if (it != g_batch_tuned.end()) bp = it->second;
     }
-    if ((bp.warps != 0 && bp.warps != 4 && bp.warps != 8 && bp.warps != 12) ||
+    if (bp.warps < 0 || bp.warps > 12 ||
         bp.ctas_per_sm < 0 || bp.ctas_per_sm > 2 || bp.leaves_per_cta < 0 ||
         bp.leaves_per_cta > 64)
         return TSQR_ERR_INVALID_ARG;
@@ -1956,7 +1955,7 @@ tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, 
     int present = 0;
     for (int32_t i = 0; i < count; ++i) present |= 1 << width_bucket(ns[i]);
     st = consider(tsqr_batch_plan_t{});
-    for (int w : {4, 8, 12})
+    for (int w : {4, 6, 8, 12})
         for (int k : {1, 2}) {
             if (st != TSQR_SUCCESS) break;
             tsqr_batch_plan_t c = cur;
@@ -2076,8 +2075,8 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
     // candidates: HYBRID slabs as tall as fit k CTAs per SM (k = 1, 2, 3), and half as tall,
     // with 4, 12 or 8 bulk warps; k CTAs per SM on every SM
     std::vector<tsqr_plan_t> cands;
-    const int warps_opts[3] = {4, 12, 8};
-    for (int wi = 0; wi < 3; ++wi) {
+    const int warps_opts[5] = {4, 12, 8, 6, 5};
+    for (int wi = 0; wi < 5; ++wi) {
         const int W = warps_opts[wi];
         for (int k = 1; k <= 3; ++k) {
             const size_t reserve = 1024;
@@ -2140,6 +2139,33 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
         if (best_ms < 0.0f || ms < best_ms) {
             best_ms = ms;
             best_plan = c;
+        }
+    }
+    // then the tree arity of the fastest one-reduction plan: 2 (the paper's binary tree) to 8
+    if (st == TSQR_SUCCESS && best_ms >= 0.0f && best_plan.tree == TSQR_TREE_HYBRID) {
+        const tsqr_plan_t base = best_plan;
+        for (int32_t k : {2, 3, 4, 6, 8}) {
+            tsqr_plan_t c = base;
+            c.arity = k;
+            auto call = [&]() {
+                return f64 ? run_f64((const double *)A, m, n, lda, R, ldr, &c, s)
+                           : run_mixed(A, dtype == TSQR_BF16, m, n, lda, R, ldr, &c, s);
+            };
+            if (call() != TSQR_SUCCESS) continue;  // an arity the width's memory cannot hold
+            float ms = 0.0f;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { st = TSQR_ERR_CUDA; break; }
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) ok = (call() == TSQR_SUCCESS);
+            if (!ok || cudaEventRecord(e1, s) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = TSQR_ERR_CUDA;
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_plan = c;
+            }
         }
     }
     cudaEventDestroy(e0);

@@ -27,6 +27,7 @@ def _fields(p):
 
 
 def test_autotune_fp64(oracle, T):
+    import torch
     m, n = 1 << 20, 32
     At = workloads.gaussian(m, n, seed=21)
     Ad = At.cuda().T
@@ -37,7 +38,11 @@ def test_autotune_fp64(oracle, T):
     assert _fields(T.tsqr_resolve_plan(m, n)) == _fields(best)
     assert _fields(T.tsqr_resolve_plan(m + 12345, n)) == _fields(best)  # same log2 bucket
     assert _fields(T.tsqr_resolve_plan(m, 16)) == _fields(other)        # other n untouched
-    R = T.tsqr_r(Ad).cpu().numpy()
+    if best.arity:  # the arity stage picked a tree arity: AUTO resolves to it
+        assert T.tsqr_resolve_plan(m, n).arity == best.arity
+    Rt = T.tsqr_r(Ad)
+    assert torch.equal(Rt, T.tsqr_r_ex(Ad, plan=best))  # AUTO returns the tuned plan's bytes
+    R = Rt.cpu().numpy()
     A = oracle.from_torch_colmajor(At)
     Ro = oracle.householder_r(A, nthreads=16)
     kap = oracle.kappa_from_r(Ro)

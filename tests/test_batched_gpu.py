@@ -214,7 +214,7 @@ def test_batched_knob_errors(T):
     bd = buf.cuda()
     ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
     Rp = torch.zeros(roff[-1], dtype=torch.float64, device="cuda")
-    for bad in (dict(warps=5), dict(ctas_per_sm=3), dict(leaves_per_cta=65),
+    for bad in (dict(warps=13), dict(ctas_per_sm=3), dict(leaves_per_cta=65),
                 dict(arity=(1, 0, 0, 0)), dict(arity=(0, 0, 9, 0))):
         with pytest.raises(T.TsqrError) as e:
             T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, plan=T.make_batch_plan(**bad))

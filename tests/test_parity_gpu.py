@@ -254,3 +254,23 @@ def test_auto_plan_uses_wide_tree_nodes(T):
     p = T.tsqr_resolve_plan(4194304, 32)
     assert p.arity >= 4
     assert T.tsqr_resolve_plan(10000, 16, plan=T.make_plan("binary", tile_rows=256)).arity == 2
+
+
+@pytest.mark.parametrize("warps", [1, 3, 5, 6, 7, 9, 11])
+@pytest.mark.parametrize("n", [5, 32, 64])
+def test_bulk_warp_counts(oracle, T, warps, n):
+    """Any bulk warp count 1 .. 12 (the rows split over the warps, the reducer warp beside
+    them), FP64 and the mixed FP32 fold, with a ragged last chunk."""
+    import torch
+    m = 40001
+    At = workloads.gaussian(m, n, seed=300 + warps)
+    A = oracle.from_torch_colmajor(At)
+    Ro = oracle.householder_r(A, nthreads=8)
+    R = T.tsqr_r_ex(_gpu(At), plan=T.make_plan("hybrid", warps=warps))
+    assert T.last_plan().warps == warps
+    _assert_parity(oracle, A, R, R_ref=Ro)
+    A32 = At.to(torch.float32)
+    R32 = T.tsqr_r_ex(_gpu(A32), plan=T.make_plan("hybrid", warps=warps, leaf="fold"))
+    assert T.last_plan().warps == warps
+    assert oracle.gram_residual(oracle.from_torch_colmajor(A32.to(torch.float64)),
+                                _to_np(R32)) <= 2e-6
