@@ -574,8 +574,10 @@ def bench_qr(dev):
 
 
 def bench_widths(dev):
-    """FP64 at 16,777,216 x n for n in {4, 8, 16, 32, 64, 128}, N(0,1): GFLOP/s, A-read GB/s and
-    the fraction of the roofline time max(bytes(A) / HBM, flops / FP64 peak)."""
+    """FP64 at 16,777,216 x n for n in {4, 8, 16, 32, 64, 128}, N(0,1), with the plan chosen by
+    the autotuner (tsqr_autotune; n = 128 keeps the AUTO panels, whose tuning would take a
+    minute): GFLOP/s, A-read GB/s and the fraction of the roofline time max(bytes(A) / HBM,
+    flops / FP64 peak); beside it the time of the built-in AUTO plan."""
     import torch
     import paper_1002_4250_gb300 as T
     import workloads
@@ -588,13 +590,29 @@ def bench_widths(dev):
         t_roof = max(bytes_a / (pk["hbm_gbs"] * 1e9), fl / (pk["fp64_tflops"] * 1e12)) * 1e3
         A = workloads.gaussian(m, n, seed=0, device=dev).T
         R = T.empty_r(n, dev)
-        ms = time_call(lambda: T.tsqr_r(A, R=R), reps=2 if n >= 64 else 5, warmup=1)
+        T.tsqr_autotune_reset()
+        reps = 2 if n >= 64 else 5
+        ms_builtin = time_call(lambda: T.tsqr_r(A, R=R), reps=reps, warmup=1)
+        builtin = T.last_plan()
+        tune_s = None
+        if n <= 64:
+            t0 = time.perf_counter()
+            T.tsqr_autotune(A, R=R)
+            tune_s = time.perf_counter() - t0
+        ms = time_call(lambda: T.tsqr_r(A, R=R), reps=reps, warmup=1)
+        used = T.last_plan()
+        T.tsqr_autotune_reset()
         del A
         torch.cuda.empty_cache()
+        plan_str = lambda p: (f"{['auto', 'binary', 'flat', 'hybrid', 'panels'][p.tree]} "
+                              f"tile {p.tile_rows} ctas {p.ctas} warps {p.warps} arity {p.arity}")
         res[str(n)] = {"ms": ms, "gflops": fl / ms / 1e6, "a_read_gbs": bytes_a / ms / 1e6,
                        "roofline_ms": t_roof, "frac_of_roofline": t_roof / ms,
                        "bound": "hbm" if bytes_a / (pk["hbm_gbs"] * 1e9) > fl / (pk["fp64_tflops"] * 1e12)
-                       else "alu"}
+                       else "alu",
+                       "plan": plan_str(used), "autotune_s": tune_s,
+                       "builtin_ms": ms_builtin, "builtin_plan": plan_str(builtin),
+                       "builtin_frac_of_roofline": t_roof / ms_builtin}
     return res
 
 

@@ -166,8 +166,9 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
  * of the reduction to the identity, which requires keeping every node's Householder vectors
  * and the shape of the tree.  This call does that: the factorization is tsqr_r's (same plan,
  * same kernels, the same R bit for bit; with the AUTO plan, except at widths where tsqr_r's
- * chunks are too tall for the Q passes' buffers, which take the four-warp plan instead:
- * tsqr_last_plan reports the plan used) with the reflectors of every leaf chunk and tree node
+ * plan runs a number of bulk warps other than 4, 8 or 12, or chunks too tall for the Q passes'
+ * buffers, which take the four-warp plan instead: tsqr_last_plan reports the plan used) with
+ * the reflectors of every leaf chunk and tree node
  * kept, then Q = H [I_n; 0] (with the sign convention applied to Q's columns) is formed top-down
  * through the tree and backwards through each leaf's chunks.  Q is unique for A of full rank
  * (as R is); with Householder reflectors it is then orthonormal to working accuracy however
@@ -179,9 +180,10 @@ tsqr_status_t tsqr_qr_uppers(int64_t n, const double *R1, int64_t ld1, const dou
  *   Q    : device, column-major m x n, ldq >= m; must not overlap A.  It also serves as the
  *          store of the leaf reflectors between the two passes.
  *   R    : device, column-major n x n, ldr >= n.
- *   plan : NULL = AUTO, or as for tsqr_r_ex.  The plan's chunking must put every chunk
- *          boundary at a multiple of its chunk height (AUTO and HYBRID/FLAT plans do; a BINARY
- *          tile taller than one chunk that is not a multiple of it does not).
+ *   plan : NULL = AUTO, or as for tsqr_r_ex with warps 0, 4, 8 or 12 (other counts return
+ *          TSQR_ERR_INVALID_ARG).  The plan's chunking must put every chunk boundary at a
+ *          multiple of its chunk height (AUTO and HYBRID/FLAT plans do; a BINARY tile taller
+ *          than one chunk that is not a multiple of it does not).
  * Every n <= TSQR_MAX_N is supported: where a chunk of tails, the Q rows and the carried block
  * do not fit shared memory together (n above about 64 with the AUTO plan), the passes take Q's
  * columns in groups and the tails go to workspace instead of Q.  Workspace: about (2 + arity)
@@ -207,7 +209,7 @@ tsqr_status_t tsqr_qr(const double *A, int64_t m, int64_t n, int64_t lda, double
  * [A | B] is factorized instead (its R holds R and (Q^T B)(0:n, :) side by side) and one
  * triangular solve follows; R then equals tsqr_r's up to rounding.  Otherwise the columns of B
  * go k_g = min(k, n) at a time (two launches per group after the factorization) and R is
- * tsqr_r's bit for bit.
+ * tsqr_qr's bit for bit (tsqr_r's under the plan tsqr_last_plan reports).
  * Above TSQR_MAX_N columns (AUTO plan only) [A | B] is copied to a buffer allocated for the
  * call (stream-ordered, m (n + k) doubles, plus (n + k)^2 for its R) and factorized by panels
  * as tsqr_caqr_r does; its R holds R and (Q^T B)(0:n, :) side by side, then one triangular

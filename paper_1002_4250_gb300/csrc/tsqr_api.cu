@@ -343,16 +343,39 @@ tsqr_status_t plan_with_r(int64_t m, int n, const tsqr_plan_t *over, bool mixed,
     return build_tree(leaves, p->arity, &p->shape, &p->nodes);
 }
 
-// FP64 bulk warps of the AUTO plan, by width: from a sweep of every n = 2 .. 128 at 4,194,304
-// rows with 4, 8 and 12 bulk warps, a width takes 8 or 12 where that was at least 2% faster
-// than 4 (n = 13: +23%, 49-51: +9%, 80-90: +40%, where four warps drop to one CTA per SM;
-// 56-64 with 12: +4-5%).  Every other width keeps 4, the best or within 2% of it.
-int f64_auto_warps(int n) {
-    if (n == 5 || n == 8 || n == 13 || (n >= 22 && n <= 25) || (n >= 49 && n <= 51) ||
-        (n >= 80 && n <= 90))
-        return 8;
-    if (n == 35 || (n >= 56 && n <= 64)) return 12;
+// FP64 bulk warps of the AUTO plan past 55 columns (one reduction of a matrix too short for
+// the PANELS tree): from a sweep of every n = 2 .. 128 at 4,194,304 rows with 4, 8 and 12 bulk
+// warps, 8 or 12 where that was at least 2% faster than 4 (80-90: +40% with 8, where four
+// warps drop to one CTA per SM; 56-64 with 12: +4-5%).
+int f64_auto_warps_wide(int n) {
+    if (n >= 80 && n <= 90) return 8;
+    if (n >= 56 && n <= 64) return 12;
     return 4;
+}
+
+// FP64 AUTO leaf shape for n <= 55: bulk warps W and resident CTAs per SM k (the chunk as tall
+// as k CTAs per SM allow).  From sweeps of every W = 3 .. 12 and k = 1 .. 3 (with chunks of 1 to
+// 12 rows per lane) for each n = 1 .. 55 at 4,194,304 rows: a width keeps (4, 2) unless a
+// setting was at least 1% faster (ms, (4, 2) against the table's): n = 9: 0.985 / 0.914 (5, 3);
+// 13: 2.00 / 1.85 (5, 2); 18: 3.76 / 3.28 (8, 1); 20: 4.46 / 4.14 (7, 1) (2^24 rows: 17.24 /
+// 15.73); 22: 5.16 / 4.91 (4, 3); 27: 7.60 / 7.23 (5, 2); 36: 14.06 / 13.27 (5, 2) (2^24 rows:
+// 54.70 / 50.76); 40: 16.88 / 16.27 (7, 1); 44: 20.12 / 19.77 (9, 1); 52: 29.55 / 28.19 (6, 2).
+struct LeafShape {
+    int W, k;
+};
+LeafShape f64_auto_shape(int n) {
+    struct Entry {
+        int lo, hi, W, k;
+    };
+    static const Entry kTable[] = {
+        {5, 5, 8, 2},   {7, 7, 9, 2},   {8, 8, 8, 2},   {9, 9, 5, 3},   {13, 14, 5, 2},
+        {18, 18, 8, 1}, {19, 20, 7, 1}, {21, 22, 4, 3}, {23, 23, 6, 2}, {24, 25, 5, 3},
+        {26, 27, 5, 2}, {35, 35, 8, 1}, {36, 39, 5, 2}, {40, 40, 7, 1}, {41, 41, 3, 3},
+        {42, 46, 9, 1}, {49, 51, 8, 1}, {52, 55, 6, 2}};
+    for (const Entry &e : kTable)
+        if (n >= e.lo && n <= e.hi) return LeafShape{e.W, e.k};
+    if (n > 55) return LeafShape{f64_auto_warps_wide(n), 2};
+    return LeafShape{4, 2};
 }
 
 tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F64Plan *p) {
@@ -373,7 +396,8 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     // from two warps per sub-partition (2^24 x 64 FP32: 47.2 against 52.1 ms with 4, 52.1 with
     // 12), and 12 from n = 96 on where they fit (2^24 x 96: FP32 143.6 against 177.4 ms, BF16
     // 156.5 against 197.7); FP64 by width
-    p->warps = mixed ? (n >= 96 ? 12 : n >= 48 ? 8 : 4) : f64_auto_warps(n);
+    const LeafShape shape = f64_auto_shape(n);
+    p->warps = mixed ? (n >= 96 ? 12 : n >= 48 ? 8 : 4) : shape.W;
     if (over && over->warps) {
         if (over->warps < 1 || over->warps > 12) return TSQR_ERR_INVALID_ARG;
         p->warps = over->warps;
@@ -382,6 +406,7 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
         return TSQR_ERR_INVALID_ARG;
     int W = p->warps;
     const size_t reserve = 1024;
+    const size_t three_per_sm = (di.smem_sm > 3 * reserve) ? (di.smem_sm - 3 * reserve) / 3 : 0;
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin, di.smem_sm - reserve);
     int r2 = max_rows_per_lane_p(n, W, two_per_sm, mixed);
@@ -396,10 +421,16 @@ tsqr_status_t plan_leaf(int64_t m, int n, const tsqr_plan_t *over, bool mixed, F
     // the barriers), which pays even at one row per lane (measured at n = 16, 32, 64).
     // Mixed: the FP32 bulk is cheap, so what counts is the number of rows sharing each
     // reflector's serial FP64 work, i.e. the rows held on chip per SM (ties go to two CTAs).
-    const bool two = mixed ? (r2 >= 1 && 2 * good_r(r2) >= good_r(r1)) : (r2 >= 1);
+    // FP64 AUTO widths (n <= 55, bulk warps not given) take the table's CTAs per SM: k = 1 one,
+    // k = 3 three where their chunk holds a row per lane, else two.
+    const bool auto_shape = !mixed && n <= 55 && !(over && over->warps);
+    const bool two = mixed ? (r2 >= 1 && 2 * good_r(r2) >= good_r(r1))
+                           : (r2 >= 1 && !(auto_shape && shape.k == 1));
+    const int r3 = (auto_shape && shape.k == 3) ? max_rows_per_lane_p(n, W, three_per_sm, mixed) : 0;
     // explicit tile rows are honoured up to what one CTA per SM holds
     const bool tile_given = over && over->tile_rows > 0;
-    tsqr_status_t st = plan_with_r(m, n, over, mixed, (two && !tile_given) ? r2 : r1, di, p);
+    const int r_auto = r3 >= 1 ? r3 : two ? r2 : r1;
+    tsqr_status_t st = plan_with_r(m, n, over, mixed, tile_given ? r1 : r_auto, di, p);
     // an explicit arity whose stacked triangles need a taller S region than two CTAs per SM
     // leave room for: one CTA per SM
     if (st == TSQR_ERR_UNSUPPORTED && two && over && over->arity > 0)
@@ -852,17 +883,24 @@ bool plan_wy(int w, const F64Plan &p, const DeviceInfo &di, int *ldX, size_t *wy
 // n where the AUTO plan takes 8 or 12 bulk warps); then the four-warp plan.  tsqr_last_plan
 // reports which.
 tsqr_status_t plan_store(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
+    // the passes that keep and apply the reflectors run 4, 8 or 12 bulk warps
+    if (over && over->warps % 4 != 0) return TSQR_ERR_INVALID_ARG;
     tsqr_status_t st = plan_f64(m, n, over, p);
-    if (st != TSQR_SUCCESS || !plan_is_auto(over) || p->warps == 4) return st;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
-    const DeviceInfo di = device_info(dev);
-    int ldX = 0, kc = 0;
-    size_t wy = 0, qt = 0;
-    if (plan_wy(n, *p, di, &ldX, &wy, &kc, &qt) &&
-        q_leaf_wy_smem_bytes(n, std::min(n, 8), p->ldS, false) <= di.smem_block_optin)
-        return st;
-    tsqr_plan_t w4{};
+    if (st != TSQR_SUCCESS || p->warps == 4) return st;
+    if (p->warps % 4 == 0) {
+        if (!plan_is_auto(over)) return st;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
+        const DeviceInfo di = device_info(dev);
+        int ldX = 0, kc = 0;
+        size_t wy = 0, qt = 0;
+        if (plan_wy(n, *p, di, &ldX, &wy, &kc, &qt) &&
+            q_leaf_wy_smem_bytes(n, std::min(n, 8), p->ldS, false) <= di.smem_block_optin)
+            return st;
+    }
+    // an AUTO (or tuned) width with other warp counts, or 8 / 12 whose blocked Q pass does not
+    // fit: four bulk warps, the plan's other fields kept
+    tsqr_plan_t w4 = plan_is_auto(over) ? tsqr_plan_t{} : *over;
     w4.warps = 4;
     return plan_f64(m, n, &w4, p);
 }
@@ -1780,6 +1818,7 @@ tsqr_status_t tsqr_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, con
         ldb < std::max<int64_t>(1, m) || ldx < n || (R && ldr < n))
         return TSQR_ERR_INVALID_ARG;
     if (!A || (k > 0 && (!B || !X))) return TSQR_ERR_INVALID_ARG;
+    if (plan && plan->warps % 4 != 0) return TSQR_ERR_INVALID_ARG;  // as for tsqr_qr
     if (n > TSQR_MAX_N) {
         if (!plan_is_auto(plan) || n + k > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
         return run_lstsq_panels(A, m, n, lda, B, ldb, k, X, ldx, R, ldr, (cudaStream_t)stream);
@@ -1795,6 +1834,7 @@ tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, do
     if (bad_dims(m, n, lda, ldr) || n < 1 || m < n || panel < 0 || !A || !R)
         return TSQR_ERR_INVALID_ARG;
     if (panel > TSQR_MAX_N || n > 0x7fffffffLL) return TSQR_ERR_UNSUPPORTED;
+    if (plan && plan->warps % 4 != 0) return TSQR_ERR_INVALID_ARG;  // as for tsqr_qr
     const int64_t nb = panel > 0 ? panel : std::min<int64_t>(n, kCaqrPanel);
     return run_caqr(A, m, n, lda, R, ldr, nb, plan, (cudaStream_t)stream);
 }

@@ -58,12 +58,19 @@ def test_caqr_square_and_small(oracle, T):
     _check(oracle, T, workloads.gaussian(1, 1, seed=4))
 
 
-def test_caqr_one_panel_is_tsqr_r(T):
-    """One panel (panel >= n) is the TSQR factorization itself: R is tsqr_r's bit for bit."""
-    At = workloads.gaussian(100003, 24, seed=5)
+@pytest.mark.parametrize("n", [24, 32])
+def test_caqr_one_panel_is_tsqr_r(T, n):
+    """One panel (panel >= n) is the TSQR factorization itself: R is tsqr_r's bit for bit under
+    the plan the call reports (tsqr_r's AUTO plan where it runs 4, 8 or 12 bulk warps: n = 32;
+    else the four-warp plan the reflector-keeping passes take: n = 24)."""
+    At = workloads.gaussian(100003, n, seed=5)
     R = T.tsqr_caqr_r(At.cuda().T, panel=32)
-    assert np.array_equal(R.cpu().numpy(), T.tsqr_r(At.cuda().T).cpu().numpy())
     assert T.capi.tsqr_last_launch_count() == 1
+    used = T.last_plan()
+    assert used.warps % 4 == 0
+    assert np.array_equal(R.cpu().numpy(), T.tsqr_r_ex(At.cuda().T, plan=used).cpu().numpy())
+    if T.tsqr_resolve_plan(100003, n).warps % 4 == 0:
+        assert np.array_equal(R.cpu().numpy(), T.tsqr_r(At.cuda().T).cpu().numpy())
 
 
 def test_caqr_conditioned(oracle, T):

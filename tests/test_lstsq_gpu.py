@@ -41,8 +41,9 @@ def _check(oracle, T, At, Bt, plan=None):
     k = Bn.shape[1]
     X, R = T.tsqr_lstsq(At.cuda().T, Bt.cuda().T, plan=plan)
     augmented = k <= max(1, n // 4) and n + k <= 128
-    # the stored-reflector path's factorization plan gives a bit-identical R
-    used = plan if plan is not None or augmented else T.last_plan()
+    # the stored-reflector path's factorization plan (the plan the call reports) gives a
+    # bit-identical R
+    used = plan if augmented else T.last_plan()
     Rr = T.tsqr_r_ex(At.cuda().T, plan=used).cpu().numpy()
     Xh = X.cpu().numpy()
     Xo = oracle.lstsq(A, Bn, nthreads=16)

@@ -32,8 +32,12 @@ def _check(oracle, T, At, plan=None, nthreads=16):
     m, n = A.shape
     Ad = At.cuda().T
     Q, R = T.tsqr_qr(Ad, plan=plan)
-    used = T.last_plan()  # the AUTO plan, or the four-warp one where its chunks are too tall
-    Rr = T.tsqr_r_ex(Ad, plan=plan if plan is not None else used)
+    # the plan used: the given or AUTO plan, or its four-warp form where that plan runs another
+    # warp count or chunks too tall for the Q passes
+    used = T.last_plan()
+    if plan is not None and plan.warps:
+        assert used.warps == plan.warps
+    Rr = T.tsqr_r_ex(Ad, plan=used)
     Qh, Rh = Q.cpu().numpy(), R.cpu().numpy()
     assert np.array_equal(Rh, Rr.cpu().numpy()), "R differs from tsqr_r's under the same plan"
     Qo, Ro = oracle.householder_qr(A, nthreads=nthreads)
@@ -174,3 +178,17 @@ def test_last_plan(T):
     z = T.last_plan()
     assert (z.tree, z.tile_rows, z.ctas, z.warps, z.arity) == (0, 0, 0, 0, 0)
 
+
+
+@pytest.mark.parametrize("n", [9, 13, 20, 36, 41, 52])
+def test_qr_widths_whose_auto_plan_has_other_warp_counts(oracle, T, n):
+    """Where tsqr_r's AUTO plan runs 3, 5, 6, 7 or 9 bulk warps, tsqr_qr takes four (its passes
+    run 4, 8 or 12) and still equals tsqr_r under that plan; explicit plans with other counts
+    are refused."""
+    m = 60013
+    At = workloads.gaussian(m, n, seed=400 + n)
+    _check(oracle, T, At)
+    assert T.last_plan().warps % 4 == 0
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_qr(At.cuda().T, plan=T.make_plan("hybrid", warps=6))
+    assert e.value.status == T.ERR_INVALID_ARG
