@@ -445,6 +445,21 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
     return tmem_need(n, h) <= 256 ? 256u : 512u;
 }
 
+// Warps that factorize a panel for ROWS = h / 256: four for chunks of up to 512 rows, eight
+// above (h / (32 PW) rows per lane, at most 6).
+__host__ __device__ constexpr int panel_warps(int rows) { return rows <= 2 ? 4 : 8; }
+
+// Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
+// CTA.
+template <int PW>
+__device__ __forceinline__ void panel_sync() {
+    if constexpr (PW == kWarps) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync 1, %0;\n" ::"n"(PW * 32) : "memory");
+    }
+}
+
 // With TMA loads (t != nullptr): panel 0 has arrived when this is called; panel 0 waits for
 // the other panels before its Z product reads them; and with a next chunk (t->rnext >= 0),
 // panel k's columns of the next chunk are loaded as soon as this chunk no longer reads them:
@@ -468,87 +483,100 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     const int J0 = kPw * k;
     const int pw = min(kPw, n - J0);
 
-    // ---- 1. panel factorization in registers
-    float x[ROWS][kPw];
+    // ---- 1. panel factorization in registers, by PW warps (one per sub-partition for chunks
+    //         of up to 512 rows, whose lanes then hold PR = h / (32 PW) rows each: half the
+    //         warp-level reductions per row of eight warps; all eight for taller chunks, whose
+    //         rows would not fit the registers of four)
+    constexpr int PW = panel_warps(ROWS);
+    constexpr int PR = h / (32 * PW);
+    const bool panel_warp = warp < PW;
+    float x[PR][kPw];
+    if (panel_warp) {
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-        const int i = 256 * q + 32 * warp + lane;
+        for (int q = 0; q < PR; ++q) {
+            const int i = 32 * PW * q + 32 * warp + lane;
 #pragma unroll
-        for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
-    }
-    float *fsh = reinterpret_cast<float *>(sm + L.fsh);
-    // The loop over the panel's columns is not unrolled (one copy of its body keeps the
-    // instruction cache warm); the register columns are addressed with static indices and
-    // predicated by the column J.
-    float fv[kPw], xp[ROWS];
+            for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
+        }
+        float *fsh = reinterpret_cast<float *>(sm + L.fsh);
+        // The loop over the panel's columns is not unrolled (one copy of its body keeps the
+        // instruction cache warm); the register columns are addressed with static indices.
+        float fv[kPw], xp[PR];
 #pragma unroll
-    for (int kk = 0; kk < kPw; ++kk) fv[kk] = 0.f;
+        for (int kk = 0; kk < kPw; ++kk) fv[kk] = 0.f;
 #pragma unroll
-    for (int q = 0; q < ROWS; ++q) xp[q] = 0.f;
+        for (int q = 0; q < PR; ++q) xp[q] = 0.f;
 #pragma unroll 1
-    for (int J = 0; J < pw; ++J) {
-        // columns J.. get reflector J-1 (fv = 0 and xp = 0 at J = 0)
+        for (int J = 0; J < pw; ++J) {
+            // columns J.. get reflector J-1; the factors of the columns before J (and of the
+            // padding columns) are zero, so every column takes the same exact FMA
 #pragma unroll
-        for (int kk = 0; kk < kPw; ++kk)
+            for (int kk = 0; kk < kPw; ++kk)
 #pragma unroll
-            for (int q = 0; q < ROWS; ++q)
-                x[q][kk] = (kk >= J) ? __fmaf_rn(-fv[kk], xp[q], x[q][kk]) : x[q][kk];
-        float xj[ROWS];
+                for (int q = 0; q < PR; ++q) x[q][kk] = __fmaf_rn(-fv[kk], xp[q], x[q][kk]);
+            float xj[PR];
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            float t = x[q][0];
+            for (int q = 0; q < PR; ++q) {
+                float tv = x[q][0];
 #pragma unroll
-            for (int kk = 1; kk < kPw; ++kk) t = (kk == J) ? x[q][kk] : t;
-            xj[q] = t;
-        }
-        float v[kPw];
+                for (int kk = 1; kk < kPw; ++kk) tv = (kk == J) ? x[q][kk] : tv;
+                xj[q] = tv;
+            }
+            float v[kPw];
 #pragma unroll
-        for (int kk = 0; kk < kPw; ++kk) {
-            float s = __fmul_rn(xj[0], x[0][kk]);
+            for (int kk = 0; kk < kPw; ++kk) {
+                float sacc = __fmul_rn(xj[0], x[0][kk]);
 #pragma unroll
-            for (int q = 1; q < ROWS; ++q) s = __fmaf_rn(xj[q], x[q][kk], s);
-            v[kk] = s;
-        }
-        const df ws = warp_sum16(v, lane);
-        df *rb = red + (J & 1) * kWarps * 16;
-        if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
-        __syncthreads();
-        if (warp == 0) {
-            // the cross-warp sums (lanes 0-15 over warps 0-3, 16-31 over warps 4-7, for value
-            // lane & 15), reflector J's scalars, row Jg of R and the factors f_k; the other
-            // warps wait for the factors at the next barrier
-            const int vi = lane & 15, half = lane >> 4;
-            const df s01 = dadd(rb[(4 * half) * 16 + vi], rb[(4 * half + 1) * 16 + vi]);
-            const df s23 = dadd(rb[(4 * half + 2) * 16 + vi], rb[(4 * half + 3) * 16 + vi]);
-            const df s = dadd(s01, s23);
-            const df o = shfl_xor_df(s, 16);
-            const df tot = half ? dadd(o, s) : dadd(s, o);  // lane l: value l & 15
-            const int Jg = J0 + J;
-            const df alpha = Rd[rowoff(n, Jg)];
-            const Refl rf = make_refl(alpha, shfl_df(tot, J));
-            float fk = 0.f;
-            if (lane < 16) {
-                if (vi > J && vi < pw && !rf.ident) {
-                    df *rjk = Rd + rowoff(n, Jg) + vi - J;
-                    const df wk = dadd(*rjk, dmul(rf.c, tot));
-                    *rjk = dsub(*rjk, dmul(rf.tau, wk));
-                    const df f = dneg(dmul(wk, rf.ib));
-                    fk = __fadd_rn(f.hi, f.lo);
+                for (int q = 1; q < PR; ++q) sacc = __fmaf_rn(xj[q], x[q][kk], sacc);
+                v[kk] = sacc;
+            }
+            const df ws = warp_sum16(v, lane);
+            df *rb = red + (J & 1) * kWarps * 16;
+            if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
+            panel_sync<PW>();
+            if (warp == 0) {
+                // the cross-warp sums (value lane & 15), reflector J's scalars, row Jg of R and
+                // the factors f_k; the other panel warps wait for the factors at the next barrier
+                const int vi = lane & 15;
+                df tot;
+                if constexpr (PW == 4) {
+                    tot = dadd(dadd(rb[vi], rb[16 + vi]), dadd(rb[32 + vi], rb[48 + vi]));
+                } else {
+                    // lanes 0-15 over warps 0-3, 16-31 over warps 4-7
+                    const int half = lane >> 4;
+                    const df s01 = dadd(rb[(4 * half) * 16 + vi], rb[(4 * half + 1) * 16 + vi]);
+                    const df s23 = dadd(rb[(4 * half + 2) * 16 + vi], rb[(4 * half + 3) * 16 + vi]);
+                    const df s4 = dadd(s01, s23);
+                    const df o = shfl_xor_df(s4, 16);
+                    tot = half ? dadd(o, s4) : dadd(s4, o);
                 }
-                fsh[vi] = fk;
-                if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled by warp 1 later)
-                if (vi == J) {
-                    tau_s[J] = rf.tau;
-                    c_s[J] = rf.c;
-                    Rd[rowoff(n, Jg)] = rf.beta;
+                const int Jg = J0 + J;
+                const df alpha = Rd[rowoff(n, Jg)];
+                const Refl rf = make_refl(alpha, shfl_df(tot, J));
+                float fk = 0.f;
+                if (lane < 16) {
+                    if (vi > J && vi < pw && !rf.ident) {
+                        df *rjk = Rd + rowoff(n, Jg) + vi - J;
+                        const df wk = dadd(*rjk, dmul(rf.c, tot));
+                        *rjk = dsub(*rjk, dmul(rf.tau, wk));
+                        const df f = dneg(dmul(wk, rf.ib));
+                        fk = __fadd_rn(f.hi, f.lo);
+                    }
+                    fsh[vi] = fk;
+                    if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled in s_factor)
+                    if (vi == J) {
+                        tau_s[J] = rf.tau;
+                        c_s[J] = rf.c;
+                        Rd[rowoff(n, Jg)] = rf.beta;
+                    }
                 }
             }
+            panel_sync<PW>();
+#pragma unroll
+            for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
+#pragma unroll
+            for (int q = 0; q < PR; ++q) xp[q] = xj[q];
         }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
-#pragma unroll
-        for (int q = 0; q < ROWS; ++q) xp[q] = xj[q];
     }
     if (J0 + kPw < n) {  // S is needed only where columns right of the panel remain
         __syncthreads();
@@ -557,23 +585,21 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     const int n8 = round_up_i(n, 8);
     const int T0 = J0 + kPw;           // first trailing column
     const int ntp = n8 - T0;           // trailing columns, padded to 8
-    if (ntp > 0) {
+    if (ntp > 0 && panel_warp) {
         // the tails (unscaled) back to the chunk, for the Z product
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int i = 256 * q + 32 * warp + lane;
+        for (int q = 0; q < PR; ++q) {
+            const int i = 32 * PW * q + 32 * warp + lane;
 #pragma unroll
             for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = x[q][kk];
         }
-    }
-    if (ntp > 0) {
         // the tails' three TF32 parts, this thread's rows, into tensor memory (the A operand of
-        // the update): row 256 q + 32 w + l is lane 32 (w % 4) + l of M-block 2 q + w / 4
+        // the update): row 32 PW q + 32 w + l is lane 32 (w % 4) + l of M-block (PW q + w) / 4
         constexpr int MB = h / 128;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll
-        for (int q = 0; q < ROWS; ++q) {
-            const int b = 2 * q + (warp >> 2);
+        for (int q = 0; q < PR; ++q) {
+            const int b = (PW * q + warp) >> 2;
             float hi[8], mid[8], lo[8];
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
