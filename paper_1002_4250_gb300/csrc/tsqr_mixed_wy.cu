@@ -451,13 +451,54 @@ __host__ __device__ constexpr int panel_warps(int rows) { return rows <= 2 ? 4 :
 
 // Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
 // CTA.
-template <int PW>
+// With four panel warps: barrier 1 (the sums are in) also takes the scalar warp, barrier 2
+// (the factors are in) only the panel warps.
+template <int PW, int ID>
 __device__ __forceinline__ void panel_sync() {
     if constexpr (PW == kWarps) {
         __syncthreads();
+    } else if constexpr (ID == 1) {
+        asm volatile("bar.sync 1, %0;\n" ::"n"((PW + 1) * 32) : "memory");
     } else {
-        asm volatile("bar.sync 1, %0;\n" ::"n"(PW * 32) : "memory");
+        asm volatile("bar.sync 2, %0;\n" ::"n"(PW * 32) : "memory");
     }
+}
+
+// Reflector J's double-FP32 scalars from the sums tot (lane l: value l & 15; tot of lane J is
+// the squared norm of the tail) and alpha = R(Jg, Jg): row Jg of R (R(Jg, Jg) = beta and
+// R(Jg, k) -= tau w_k, w_k = R(Jg, k) + c (x_J . x_k)), tau and c for the T factor, the dots
+// with the earlier tails into G.  With want_f, returns this lane's factor f_k = -w_k / beta
+// rounded to FP32 (0 for lanes outside J < k < pw, and for an identity reflector).
+__device__ __forceinline__ float scalar_update(unsigned char *sm, const Layout &L, const int n,
+                                               const int J0, const int J, const int pw,
+                                               const int lane, const df tot, const bool want_f) {
+    df *Rd = reinterpret_cast<df *>(sm + L.R);
+    df *tau_s = reinterpret_cast<df *>(sm + L.tau);
+    df *c_s = reinterpret_cast<df *>(sm + L.cc);
+    df *G = reinterpret_cast<df *>(sm + L.G);
+    const int vi = lane & 15;
+    const int Jg = J0 + J;
+    const df alpha = Rd[rowoff(n, Jg)];
+    const Refl rf = make_refl(alpha, shfl_df(tot, J));
+    float fk = 0.f;
+    if (lane < 16) {
+        if (vi > J && vi < pw && !rf.ident) {
+            df *rjk = Rd + rowoff(n, Jg) + vi - J;
+            const df wk = dadd(*rjk, dmul(rf.c, tot));
+            *rjk = dsub(*rjk, dmul(rf.tau, wk));
+            if (want_f) {
+                const df f = dneg(dmul(wk, rf.ib));
+                fk = __fadd_rn(f.hi, f.lo);
+            }
+        }
+        if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled in s_factor)
+        if (vi == J) {
+            tau_s[J] = rf.tau;
+            c_s[J] = rf.c;
+            Rd[rowoff(n, Jg)] = rf.beta;
+        }
+    }
+    return fk;
 }
 
 // With TMA loads (t != nullptr): panel 0 has arrived when this is called; panel 0 waits for
@@ -530,52 +571,71 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                 for (int q = 1; q < PR; ++q) sacc = __fmaf_rn(xj[q], x[q][kk], sacc);
                 v[kk] = sacc;
             }
+            // row Jg of R (FP32 parts) for the factors below, read before barrier 1: the scalar
+            // warp updates the row after it
+            const int Jg = J0 + J;
+            float a_f = 0.f, r_f = 0.f;
+            if (PW == 4 && warp == 0) {
+                a_f = Rd[rowoff(n, Jg)].hi;
+                const int vi = lane & 15;
+                if (vi > J && vi < pw) r_f = Rd[rowoff(n, Jg) + vi - J].hi;
+            }
             const df ws = warp_sum16(v, lane);
             df *rb = red + (J & 1) * kWarps * 16;
             if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
-            panel_sync<PW>();
-            if (warp == 0) {
-                // the cross-warp sums (value lane & 15), reflector J's scalars, row Jg of R and
-                // the factors f_k; the other panel warps wait for the factors at the next barrier
-                const int vi = lane & 15;
-                df tot;
-                if constexpr (PW == 4) {
-                    tot = dadd(dadd(rb[vi], rb[16 + vi]), dadd(rb[32 + vi], rb[48 + vi]));
-                } else {
-                    // lanes 0-15 over warps 0-3, 16-31 over warps 4-7
-                    const int half = lane >> 4;
+            panel_sync<PW, 1>();
+            if constexpr (PW == 4) {
+                if (warp == 0) {
+                    // the factors f_k of the panel update, in FP32 (the update itself is FP32)
+                    // from the FP32 parts of the sums; the scalar warp forms the reflector's
+                    // double-FP32 scalars and row Jg of R meanwhile
+                    const int vi = lane & 15;
+                    const float tf = __fadd_rn(__fadd_rn(rb[vi].hi, rb[16 + vi].hi),
+                                               __fadd_rn(rb[32 + vi].hi, rb[48 + vi].hi));
+                    const float sig = __shfl_sync(0xffffffffu, tf, J);
+                    float fk = 0.f;
+                    if (sig != 0.f && vi > J && vi < pw) {
+                        const float rt = __fsqrt_rn(__fmaf_rn(a_f, a_f, sig));
+                        const float beta = a_f >= 0.f ? -rt : rt;
+                        const float w = __fmaf_rn(__frcp_rn(__fsub_rn(a_f, beta)), tf, r_f);
+                        fk = -__fmul_rn(w, __frcp_rn(beta));
+                    }
+                    if (lane < 16) fsh[vi] = fk;
+                }
+            } else {
+                if (warp == 0) {
+                    // the cross-warp sums (value lane & 15; lanes 0-15 over warps 0-3, 16-31
+                    // over warps 4-7), reflector J's scalars, row Jg of R and the factors f_k;
+                    // the other panel warps wait for the factors at the next barrier
+                    const int vi = lane & 15, half = lane >> 4;
                     const df s01 = dadd(rb[(4 * half) * 16 + vi], rb[(4 * half + 1) * 16 + vi]);
                     const df s23 = dadd(rb[(4 * half + 2) * 16 + vi], rb[(4 * half + 3) * 16 + vi]);
                     const df s4 = dadd(s01, s23);
                     const df o = shfl_xor_df(s4, 16);
-                    tot = half ? dadd(o, s4) : dadd(s4, o);
-                }
-                const int Jg = J0 + J;
-                const df alpha = Rd[rowoff(n, Jg)];
-                const Refl rf = make_refl(alpha, shfl_df(tot, J));
-                float fk = 0.f;
-                if (lane < 16) {
-                    if (vi > J && vi < pw && !rf.ident) {
-                        df *rjk = Rd + rowoff(n, Jg) + vi - J;
-                        const df wk = dadd(*rjk, dmul(rf.c, tot));
-                        *rjk = dsub(*rjk, dmul(rf.tau, wk));
-                        const df f = dneg(dmul(wk, rf.ib));
-                        fk = __fadd_rn(f.hi, f.lo);
-                    }
-                    fsh[vi] = fk;
-                    if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled in s_factor)
-                    if (vi == J) {
-                        tau_s[J] = rf.tau;
-                        c_s[J] = rf.c;
-                        Rd[rowoff(n, Jg)] = rf.beta;
-                    }
+                    const df tot = half ? dadd(o, s4) : dadd(s4, o);
+                    const float fk = scalar_update(sm, L, n, J0, J, pw, lane, tot, true);
+                    if (lane < 16) fsh[vi] = fk;
                 }
             }
-            panel_sync<PW>();
+            panel_sync<PW, 2>();
 #pragma unroll
             for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
 #pragma unroll
             for (int q = 0; q < PR; ++q) xp[q] = xj[q];
+        }
+    }
+    if (PW == 4 && warp == PW) {
+        // the scalar warp: after each column's first barrier, reflector J's double-FP32
+        // scalars and row Jg of R from the cross-warp sums, while warp 0 forms the factors and
+        // the panel warps go on with the next column (its buffer of sums is rewritten only
+        // after the panel warps have passed the next barrier 1, which waits for this warp)
+#pragma unroll 1
+        for (int J = 0; J < pw; ++J) {
+            panel_sync<PW, 1>();
+            const df *rb = red + (J & 1) * kWarps * 16;
+            const int vi = lane & 15;
+            const df tot = dadd(dadd(rb[vi], rb[16 + vi]), dadd(rb[32 + vi], rb[48 + vi]));
+            scalar_update(sm, L, n, J0, J, pw, lane, tot, false);
         }
     }
     if (J0 + kPw < n) {  // S is needed only where columns right of the panel remain
