@@ -445,9 +445,9 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
     return tmem_need(n, h) <= 256 ? 256u : 512u;
 }
 
-// Warps that factorize a panel for ROWS = h / 256: four for chunks of up to 512 rows, eight
-// above (h / (32 PW) rows per lane, at most 6).
-__host__ __device__ constexpr int panel_warps(int rows) { return rows <= 2 ? 4 : 8; }
+// Warps that factorize a panel for ROWS = h / 256: four, one per sub-partition (h / 128 rows
+// per lane, up to 8, which the registers hold); the eight-warp form is kept for reference.
+__host__ __device__ constexpr int panel_warps(int rows) { return rows > 0 ? 4 : 8; }
 
 // Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
 // CTA.
@@ -595,10 +595,12 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                     const float sig = __shfl_sync(0xffffffffu, tf, J);
                     float fk = 0.f;
                     if (sig != 0.f && vi > J && vi < pw) {
-                        const float rt = __fsqrt_rn(__fmaf_rn(a_f, a_f, sig));
+                        // the hardware's approximate square root and reciprocals (about
+                        // 2^-22): a few FP32 ulps in f_k, the size of the update's own rounding
+                        const float rt = sqrt_approx(__fmaf_rn(a_f, a_f, sig));
                         const float beta = a_f >= 0.f ? -rt : rt;
-                        const float w = __fmaf_rn(__frcp_rn(__fsub_rn(a_f, beta)), tf, r_f);
-                        fk = -__fmul_rn(w, __frcp_rn(beta));
+                        const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
+                        fk = -__fmul_rn(w, rcp_approx(beta));
                     }
                     if (lane < 16) fsh[vi] = fk;
                 }
