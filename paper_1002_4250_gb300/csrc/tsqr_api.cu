@@ -1480,7 +1480,10 @@ tsqr_status_t plan_mixed(int64_t m, int n, bool bf16, const tsqr_plan_t *over, F
         !over || ((over->warps == 0 || over->warps == 8) &&
                   (over->tree == TSQR_TREE_BINARY || over->tile_rows == 0 ||
                    over->tile_rows == 256 || over->tile_rows == 512));
-    const bool wy_auto = n <= kMixedWyMaxN && (bf16 || n > 12);
+    // measured at 2^24 rows: the fold wins up to n = 8 for FP32 (n = 8: 0.81 against 1.04 ms;
+    // n = 9: 1.32 against 1.13) and at n <= 2 for BF16 (n = 2: 0.35 against 0.51 ms; n = 3:
+    // 0.89 against 0.62), the blocked leaf from there to 64 columns
+    const bool wy_auto = n <= kMixedWyMaxN && n > (bf16 ? 2 : 8);
     if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && wy_auto && wy_knobs)) {
         tsqr_plan_t o = over ? *over : tsqr_plan_t{};
         o.leaf = TSQR_LEAF_PANELS;

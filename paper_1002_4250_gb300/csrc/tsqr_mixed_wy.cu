@@ -371,15 +371,18 @@ struct Tma {
 // rows x 16 columns, one per 2 KB box region of the chunk layout; zeros past A's last row and
 // column.  FP32 boxes land as the layout itself (the tensor map's 128-byte swizzle is the
 // layout's XOR); BF16 boxes (1 KB, unswizzled, column after column) land in the upper half of
-// the region and are widened in place by widen_panel.  One thread; completes bar's phase once
+// the region and are widened in place by widen_panel.  One warp: lane 0 arms the barrier with
+// the panel's bytes, then lane l issues boxes l, l + 32, ...; the barrier's phase completes once
 // all bytes have landed.
 template <typename Tin>
 __device__ __forceinline__ void tma_panel(float *C, Tma &t, int64_t r0, int k, int h, int NP,
                                           uint32_t parity) {
     constexpr uint32_t box_bytes = 32u * 16u * sizeof(Tin);
     constexpr int half = sizeof(Tin) == 2 ? 256 : 0;
-    tc::mbar_expect_tx(t.bar + k, (uint32_t)(h / 32) * box_bytes);
-    for (int rb = 0; rb < h / 32; ++rb)
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) tc::mbar_expect_tx(t.bar + k, (uint32_t)(h / 32) * box_bytes);
+    __syncwarp();
+    for (int rb = lane; rb < h / 32; rb += 32)
         tc::tma_load_2d(C + (size_t)(rb * NP + k) * 512 + half, t.map, (int)(r0 + 32 * rb), 16 * k,
                         t.bar + k);
     t.pend |= 1u << k;
@@ -680,7 +683,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         if (t && t->rnext >= 0) {
             tc::fence_proxy_async();
             __syncthreads();
-            if (threadIdx.x == 0) tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
+            if (warp == 0) tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
         }
         __syncthreads();
         return;
@@ -746,8 +749,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     }
     if (t && t->rnext >= 0) tc::fence_proxy_async();  // the panel's columns are read for the last time
     __syncthreads();
-    if (t && t->rnext >= 0 && threadIdx.x == 0)
-        tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
+    if (t && t->rnext >= 0 && warp == 0) tma_panel<Tin>(C, *t, t->rnext, k, h, NP, t->phase ^ 1u);
 
     // ---- 2b. W = R(P, T) + diag(c) Z
     for (int e = threadIdx.x; e < kPw * ntp; e += blockDim.x) {
@@ -904,7 +906,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     const Tin *A = static_cast<const Tin *>(a.A);
     float *Cf = reinterpret_cast<float *>(sm + L.C);
     Tma t{&tmap, -1, tbar, 0u, 0u, 0u};
-    if (use_tma && rbeg < rend && threadIdx.x == 0)
+    if (use_tma && rbeg < rend && threadIdx.x < 32)
         for (int k = 0; k < NP; ++k) tma_panel<Tin>(Cf, t, rbeg, k, h, NP, 0u);
     for (int64_t r0 = rbeg; r0 < rend && tm.ok; r0 += h) {
         const int rows = (int)((rend - r0 < h) ? rend - r0 : h);
