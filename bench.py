@@ -678,7 +678,7 @@ def bench_batched(dev, threads):
                      "gram_tol": 1e-13 if name == "fp64" else 2e-6}
         del b
     T.tsqr_autotune_reset()
-    res["knobs_fields"] = "(warps, ctas_per_sm, leaves_per_cta, arity per width bucket)"
+    res["knobs_fields"] = "(warps, ctas_per_sm, leaves_per_cta, arity per width bucket, leaf)"
     res["mixed_speedup_vs_fp64"] = res["fp64"]["ms"] / res["mixed_fp32"]["ms"]
     del buf
     torch.cuda.empty_cache()

@@ -269,12 +269,19 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
  *                    leaves_per_cta) of work, in whole chunks; 1 .. 64 (0: 6).
  *   arity[b]       : tree arity of the problems in width bucket b (n <= 8, <= 16, <= 32,
  *                    > 32), 2 .. 8, lowered to what the width's shared memory holds (0: the
- *                    largest that fits). */
+ *                    largest that fits).
+ *   leaf           : mixed precision only, a tsqr_leaf_t: FOLD, or PANELS (the blocked
+ *                    tensor-core leaf of tsqr_r_ex, for batches up to 64 columns; chunks of
+ *                    1024, 768 or 512 rows by the widest problem, 8 warps, one CTA per SM, so
+ *                    warps and ctas_per_sm do not apply).  0: PANELS where it applies, else
+ *                    FOLD.  PANELS for an FP64 batch or one wider than 64 columns returns
+ *                    TSQR_ERR_UNSUPPORTED. */
 typedef struct tsqr_batch_plan_t {
     int32_t warps;
     int32_t ctas_per_sm;
     int32_t leaves_per_cta;
     int32_t arity[4];
+    int32_t leaf;
 } tsqr_batch_plan_t;
 
 /* tsqr_r_batched with explicit knobs.  plan: NULL or all zero = AUTO (the batch's tuned plan
@@ -291,7 +298,8 @@ tsqr_status_t tsqr_r_batched_ex(const void *const *ptrs, const int64_t *ms, cons
  * count) and floor(log2 of the work sum max(m_i, 1) n_i^2).  From then on an AUTO batched call
  * (tsqr_r_batched, or tsqr_r_batched_ex with plan NULL or all zero) in that bucket uses it and
  * returns the bytes it gives.  The search starts from the built-in rules and moves one knob at a
- * time: warps (4, 6, 8, 12) x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
+ * time: for a mixed batch up to 64 columns the fold leaf against the blocked one, then (for
+ * the fold) warps (4, 6, 8, 12) x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
  * (2, 4, 8); each setting is run once to warm up and timed over one call with CUDA events on
  * `stream`.
  *   Arguments as for tsqr_r_batched; R_packed is overwritten.  best: optional, receives the
@@ -303,8 +311,8 @@ tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, 
                                     tsqr_stream_t stream);
 
 /* The knobs the last batched call (tsqr_r_batched, tsqr_r_batched_ex) on this host thread ran
- * with: warps, ctas_per_sm and leaves_per_cta as resolved, arity as given (0 = the largest that
- * fits).  All zero before any batched call and after one that launched nothing.
+ * with: warps, ctas_per_sm, leaves_per_cta and leaf as resolved, arity as given (0 = the
+ * largest that fits).  All zero before any batched call and after one that launched nothing.
  *   out : host pointer, required.  Returns TSQR_ERR_INVALID_ARG when NULL. */
 tsqr_status_t tsqr_last_batch_plan(tsqr_batch_plan_t *out);
 

@@ -42,16 +42,21 @@ class Plan(ctypes.Structure):
 class BatchPlan(ctypes.Structure):
     """tsqr_batch_plan_t: warps, ctas_per_sm, leaves_per_cta, arity[4] (zeros mean "choose")."""
     _fields_ = [("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("leaves_per_cta", ctypes.c_int32), ("arity", ctypes.c_int32 * 4)]
+                ("leaves_per_cta", ctypes.c_int32), ("arity", ctypes.c_int32 * 4),
+                ("leaf", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.warps, self.ctas_per_sm, self.leaves_per_cta, tuple(self.arity))
+        return (self.warps, self.ctas_per_sm, self.leaves_per_cta, tuple(self.arity), self.leaf)
 
 
-def make_batch_plan(warps=0, ctas_per_sm=0, leaves_per_cta=0, arity=(0, 0, 0, 0)) -> BatchPlan:
-    """Knobs of a varlen batch call; arity per width bucket (n <= 8, <= 16, <= 32, > 32)."""
+def make_batch_plan(warps=0, ctas_per_sm=0, leaves_per_cta=0, arity=(0, 0, 0, 0),
+                    leaf="auto") -> BatchPlan:
+    """Knobs of a varlen batch call; arity per width bucket (n <= 8, <= 16, <= 32, > 32); leaf
+    "auto", "fold" or "panels" (mixed precision)."""
+    lf = {"auto": LEAF_AUTO, "fold": LEAF_FOLD, "panels": LEAF_PANELS}[leaf] \
+        if isinstance(leaf, str) else int(leaf)
     return BatchPlan(int(warps), int(ctas_per_sm), int(leaves_per_cta),
-                     (ctypes.c_int32 * 4)(*[int(a) for a in arity]))
+                     (ctypes.c_int32 * 4)(*[int(a) for a in arity]), lf)
 
 
 _capi = None

@@ -1575,7 +1575,8 @@ BatchKey batch_key(int dev, int dt, const int64_t *ms, const int32_t *ns, int32_
 
 bool batch_plan_is_auto(const tsqr_batch_plan_t *p) {
     return !p || (p->warps == 0 && p->ctas_per_sm == 0 && p->leaves_per_cta == 0 &&
-                  p->arity[0] == 0 && p->arity[1] == 0 && p->arity[2] == 0 && p->arity[3] == 0);
+                  p->arity[0] == 0 && p->arity[1] == 0 && p->arity[2] == 0 && p->arity[3] == 0 &&
+                  p->leaf == 0);
 }
 
 tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
@@ -1602,9 +1603,25 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         return TSQR_ERR_INVALID_ARG;
     for (int b = 0; b < 4; ++b)
         if (bp.arity[b] != 0 && (bp.arity[b] < 2 || bp.arity[b] > 8)) return TSQR_ERR_INVALID_ARG;
+    if (bp.leaf != 0 && bp.leaf != TSQR_LEAF_FOLD && bp.leaf != TSQR_LEAF_PANELS)
+        return TSQR_ERR_INVALID_ARG;
     const bool mixed = dt != 0;
     int nmax = 1;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
+    if (bp.leaf == TSQR_LEAF_PANELS && (!mixed || nmax > kMixedWyMaxN)) return TSQR_ERR_UNSUPPORTED;
+    // mixed batches up to 64 columns take the blocked leaf unless the plan says fold (4096-problem
+    // varlen batch, FP32: 181 ms with the fold and its tuned knobs, see the design notes)
+    const bool wy = mixed && nmax <= kMixedWyMaxN && bp.leaf != TSQR_LEAF_FOLD;
+    int wy_h = 0, wy_tcols = 0;
+    if (wy) {
+        for (int hh : {1024, 768, 512, 256})
+            if (mixed_wy_smem_bytes(nmax, hh) <= di.smem_block_optin && mixed_wy_tmem_fits(nmax, hh)) {
+                wy_h = hh;
+                break;
+            }
+        if (!wy_h) return TSQR_ERR_UNSUPPORTED;
+        wy_tcols = batched_wy_tmem_cols(nmax, wy_h);
+    }
     const size_t reserve = 1024 + 256;  // per-CTA reserve plus the kernel's static shared memory
     const size_t two_per_sm = (di.smem_sm > 2 * reserve) ? (di.smem_sm - 2 * reserve) / 2 : 0;
     const size_t one_per_sm = std::min(di.smem_block_optin - 256, di.smem_sm - reserve);
@@ -1612,9 +1629,10 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     // with 12 warps: it runs one CTA per SM and hides the wide problems' reflector chains
     // behind more warps (the varlen batch of 4096 problems with widths up to 64: FP64 716 ms
     // with 4, 640 with 8, 626 with 12; mixed FP32 304 ms with 4, 224 with 12)
-    const int W = bp.warps ? bp.warps
-                           : (nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, mixed) >= 1)
-                                 ? 12 : 4;
+    const int W = wy ? 8
+                     : bp.warps ? bp.warps
+                     : (nmax >= 48 && max_rows_per_lane_p(nmax, 12, one_per_sm, mixed) >= 1) ? 12
+                                                                                            : 4;
     // CTAs per SM (AUTO): two when the widest problem's chunk fits at two rows per lane (one
     // CTA per SM with taller chunks measured faster on the varlen batch otherwise: 717
     // against 1010 ms for FP64 with widths up to 64)
@@ -1625,7 +1643,16 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     // per width: chunk rows
     std::vector<int> hs_of(TSQR_MAX_N + 1, 0), blk_of(TSQR_MAX_N + 1, 1), vec_of(TSQR_MAX_N + 1, 1);
     size_t smem = 0;
-    for (int32_t i = 0; i < count; ++i) {
+    for (int32_t i = 0; i < count && wy; ++i) {
+        const int n = ns[i];
+        if (hs_of[n]) continue;
+        hs_of[n] = wy_h;
+        smem = std::max(smem, mixed_wy_smem_bytes(n, wy_h));
+    }
+    // the blocked leaf's CTAs hold their tensor memory for the whole launch: one CTA per SM
+    // (more than half an SM's shared memory), so that no CTA's allocation waits for another's
+    if (wy) smem = std::max(smem, di.smem_sm / 2 + 1024);
+    for (int32_t i = 0; i < count && !wy; ++i) {
         const int n = ns[i];
         if (hs_of[n]) continue;
         int r = good_r(max_rows_per_lane_p(n, W, budget, mixed));
@@ -1642,8 +1669,10 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
                                               mixed));
     }
     const int kdt = (W > 7) ? dt + 3 : dt;  // the kernels for up to 12 bulk warps
-    if (batched_prepare(kdt, smem) != cudaSuccess) return TSQR_ERR_CUDA;
-    const int per_sm = std::max(1, batched_blocks_per_sm(kdt, W, smem));
+    if ((wy ? batched_wy_prepare(dt == 2, wy_h, smem) : batched_prepare(kdt, smem)) != cudaSuccess)
+        return TSQR_ERR_CUDA;
+    const int per_sm = std::max(1, wy ? batched_wy_blocks_per_sm(dt == 2, wy_h, smem)
+                                      : batched_blocks_per_sm(kdt, W, smem));
     const int64_t ctas = (int64_t)di.sms * per_sm;
     // leaf size: about 6 leaves per CTA over the whole batch (AUTO)
     const int lpc = bp.leaves_per_cta ? bp.leaves_per_cta : 6;
@@ -1674,10 +1703,13 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         if (P.nunits > (1 << 24)) return TSQR_ERR_UNSUPPORTED;
         P.nleaves = (int)P.nunits;
         // arity: the largest that the width's shared memory holds, or the plan's, lowered to fit
-        const int amax = arity_for(n, mixed ? mixed_s_doubles(n, P.ldS) : P.ldS * n);
+        const int amax = wy ? mixed_wy_arity(n, wy_h)
+                            : arity_for(n, mixed ? mixed_s_doubles(n, P.ldS) : P.ldS * n);
         const int areq = bp.arity[width_bucket(n)];
         P.arity = areq ? std::min(areq, amax) : amax;
-        if (!mixed)
+        if (wy)
+            while (P.arity > 2 && !mixed_wy_tree_fits(n, wy_h, P.arity)) --P.arity;
+        else if (!mixed)
             while (P.arity > 2 && tree_ldsd(n, P.arity) > P.ldS) --P.arity;
         TreeShape shape;
         int64_t nodes = 0;
@@ -1728,13 +1760,16 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
         cudaSuccess)
         return TSQR_ERR_CUDA;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)items.size());
-    if (batched_launch(kdt, b, grid, W, smem, stream) != cudaSuccess) return TSQR_ERR_CUDA;
+    if ((wy ? batched_wy_launch(b, grid, dt == 2, wy_h, wy_tcols, smem, stream)
+            : batched_launch(kdt, b, grid, W, smem, stream)) != cudaSuccess)
+        return TSQR_ERR_CUDA;
     g_last_launches = 1;
     tsqr_batch_plan_t used{};
     used.warps = W;
-    used.ctas_per_sm = budget == one_per_sm ? 1 : 2;
+    used.ctas_per_sm = wy ? 1 : budget == one_per_sm ? 1 : 2;
     used.leaves_per_cta = lpc;
     for (int b2 = 0; b2 < 4; ++b2) used.arity[b2] = bp.arity[b2];
+    used.leaf = mixed ? (wy ? TSQR_LEAF_PANELS : TSQR_LEAF_FOLD) : 0;
     g_last_batch_plan = used;
     return TSQR_SUCCESS;
 }
@@ -1995,12 +2030,25 @@ tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, 
         }
         return TSQR_SUCCESS;
     };
-    int present = 0;
-    for (int32_t i = 0; i < count; ++i) present |= 1 << width_bucket(ns[i]);
+    int present = 0, nmax = 1;
+    for (int32_t i = 0; i < count; ++i) {
+        present |= 1 << width_bucket(ns[i]);
+        nmax = std::max(nmax, (int)ns[i]);
+    }
     st = consider(tsqr_batch_plan_t{});
+    // mixed batches up to 64 columns: the fold leaf against the blocked one first; the warps and
+    // chunk-height knobs are the fold's
+    if (dt != 0 && nmax <= kMixedWyMaxN)
+        for (int lf : {TSQR_LEAF_FOLD, TSQR_LEAF_PANELS}) {
+            if (st != TSQR_SUCCESS) break;
+            tsqr_batch_plan_t c{};
+            c.leaf = lf;
+            st = consider(c);
+        }
+    const bool fold_knobs = !(dt != 0 && nmax <= kMixedWyMaxN && cur.leaf != TSQR_LEAF_FOLD);
     for (int w : {4, 6, 8, 12})
         for (int k : {1, 2}) {
-            if (st != TSQR_SUCCESS) break;
+            if (st != TSQR_SUCCESS || !fold_knobs) break;
             tsqr_batch_plan_t c = cur;
             c.warps = w;
             c.ctas_per_sm = k;

@@ -53,6 +53,13 @@ cudaError_t mixed_wy_prepare(size_t smem_bytes);
 int mixed_wy_blocks_per_sm(int h, size_t smem_bytes);
 cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int ldSd,
                             size_t smem_bytes, cudaStream_t stream);
+// The same leaf for a varlen batch (one persistent launch; chunks of h rows for every problem;
+// tensor memory of tcols columns held by every CTA).
+int batched_wy_tmem_cols(int nmax, int h);
+cudaError_t batched_wy_prepare(bool bf16, int h, size_t smem_bytes);
+int batched_wy_blocks_per_sm(bool bf16, int h, size_t smem_bytes);
+cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, int tcols,
+                              size_t smem_bytes, cudaStream_t stream);
 
 // Batched path (tsqr_batched.cu); dtype 0 FP64, 1 FP32, 2 BF16; `warps` counts bulk warps.
 cudaError_t batched_prepare(int dtype, size_t smem_bytes);

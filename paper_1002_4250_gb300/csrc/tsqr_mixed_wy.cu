@@ -857,9 +857,65 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     __syncthreads();
 }
 
-// Eight warps, ROWS = h / 256 rows per lane in the panel factorization (1 to 4): chunks as tall
-// as shared and tensor memory allow for the width (fewer reflector chains per row).  One row per
-// lane (256-row chunks) allows two CTAs per SM (at most 128 registers a thread).
+// One leaf: rows [rbeg, rend) of A folded into R chunk by chunk (TMA box loads where t is
+// given, else thread copies), then R converted exactly to FP64 in place at L.R for the tree.
+// Returns false when a wait gave up (recorded in the status word and agreed by the CTA); the
+// caller then waits out what is in flight.
+template <typename Tin, int ROWS>
+__device__ __forceinline__ bool wy_leaf(unsigned char *sm, const Layout &L, const int n,
+                                        const Tin *A, const int64_t lda, const int64_t rbeg,
+                                        const int64_t rend, const bool vec4, Tmem &tm, Tma *t,
+                                        int *status) {
+    constexpr int h = 256 * ROWS;
+    const int NP = (n + kPw - 1) / kPw;
+    df *Rd = reinterpret_cast<df *>(sm + L.R);
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) Rd[e] = mk(0.f);
+    float *Cf = reinterpret_cast<float *>(sm + L.C);
+    if (t && rbeg < rend && threadIdx.x < 32)
+        for (int k = 0; k < NP; ++k) tma_panel<Tin>(Cf, *t, rbeg, k, h, NP, 0u);
+    for (int64_t r0 = rbeg; r0 < rend && tm.ok; r0 += h) {
+        const int rows = (int)((rend - r0 < h) ? rend - r0 : h);
+        if (!t) {
+            __syncthreads();  // the previous chunk's (or leaf's) last reads of C are done
+            load_chunk<Tin>(Cf, A + r0, lda, rows, n, h, NP, vec4);
+            __syncthreads();
+        } else {
+            t->rnext = (r0 + h < rend) ? r0 + h : -1;
+            // panel 0 of this chunk (panel_step waits for the others before they are read)
+            if (!wait_panels<Tin, ROWS>(Cf, *t, 0, 1, NP, status)) {
+                tm.ok = false;
+                break;
+            }
+            __syncthreads();
+        }
+        for (int k = 0; k < NP && tm.ok; ++k) panel_step<Tin, ROWS>(sm, L, n, NP, k, tm, status, t);
+        if (t && tm.ok) t->phase ^= 1u;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (!tm.ok) return false;
+    // R to FP64 (exact: hi + lo), in place, for the FP64 tree
+    double *Rp = reinterpret_cast<double *>(sm + L.R);
+    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
+        const df v = Rd[e];
+        Rp[e] = (double)v.hi + (double)v.lo;
+    }
+    __syncthreads();
+    return true;
+}
+
+// The tree above a leaf's R (FP64 at L.R): the FP64 climb of the one-reduction kernels, with
+// the chunk region as the stacked triangles' buffer.
+__device__ __forceinline__ void wy_climb(unsigned char *sm, const Layout &L, const F64Args &b,
+                                         const int ldSd, const int leaf) {
+    climb_tree<false>(b, reinterpret_cast<double *>(sm + L.C), ldSd,
+                      reinterpret_cast<double *>(sm + L.R), reinterpret_cast<double *>(sm + L.f),
+                      reinterpret_cast<double *>(sm + L.seg),
+                      reinterpret_cast<double *>(sm + L.tot),
+                      reinterpret_cast<unsigned int *>(sm + L.flag), leaf);
+}
+
+// One matrix: CTA = leaf, then the tree.
 template <typename Tin, int ROWS>
 __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     tsqr_mixed_wy_kernel(const WyArgs2 a, const __grid_constant__ CUtensorMap tmap) {
@@ -872,15 +928,13 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     const int n = b.n;
     const int NP = (n + kPw - 1) / kPw;
     const Layout L = layout(n, h);
-    df *Rd = reinterpret_cast<df *>(sm + L.R);
-    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) Rd[e] = mk(0.f);
 
     const int leaf = blockIdx.x;
     const int64_t u0 = ((int64_t)leaf * b.nunits) / b.nleaves;
     const int64_t u1 = ((int64_t)(leaf + 1) * b.nunits) / b.nleaves;
     const int64_t rbeg = u0 * b.unit;
     const int64_t rend = (u1 * b.unit < b.m) ? u1 * b.unit : b.m;
-    // the update's mbarrier and tensor memory (released before the tree)
+    // the update's mbarrier and tensor memory (released before the tree), the TMA's mbarriers
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L.bar);
     uint32_t *tbase = reinterpret_cast<uint32_t *>(sm + L.bar + 8);
     uint64_t *tbar = reinterpret_cast<uint64_t *>(sm + L.bar + 16);
@@ -902,37 +956,12 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     tm.bar = bar;
     tm.phase = 0;
     tm.ok = true;
-
-    const Tin *A = static_cast<const Tin *>(a.A);
-    float *Cf = reinterpret_cast<float *>(sm + L.C);
     Tma t{&tmap, -1, tbar, 0u, 0u, 0u};
-    if (use_tma && rbeg < rend && threadIdx.x < 32)
-        for (int k = 0; k < NP; ++k) tma_panel<Tin>(Cf, t, rbeg, k, h, NP, 0u);
-    for (int64_t r0 = rbeg; r0 < rend && tm.ok; r0 += h) {
-        const int rows = (int)((rend - r0 < h) ? rend - r0 : h);
-        t.rnext = (r0 + h < rend) ? r0 + h : -1;
-        if (!use_tma) {
-            __syncthreads();  // the previous chunk's last reads of C are done
-            load_chunk<Tin>(Cf, A + r0, b.lda, rows, n, h, NP, a.vec4 != 0);
-            __syncthreads();
-        } else {
-            // panel 0 of this chunk (panel_step waits for the others before they are read)
-            if (!wait_panels<Tin, ROWS>(Cf, t, 0, 1, NP, b.status)) {
-                tm.ok = false;
-                break;
-            }
-            __syncthreads();
-        }
-        for (int k = 0; k < NP && tm.ok; ++k)
-            panel_step<Tin, ROWS>(sm, L, n, NP, k, tm, b.status, use_tma ? &t : nullptr);
-        if (tm.ok) t.phase ^= 1u;
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (!tm.ok) {
-        // a tensor-core or TMA wait gave up (recorded in the status word): wait once more,
-        // bounded, for the mma and the loads in flight, release the tensor memory and leave R
-        // unwritten
+    const bool ok = wy_leaf<Tin, ROWS>(sm, L, n, static_cast<const Tin *>(a.A), b.lda, rbeg, rend,
+                                       a.vec4 != 0, tm, use_tma ? &t : nullptr, b.status);
+    if (!ok) {
+        // a tensor-core or TMA wait gave up: wait once more, bounded, for the mma and the loads
+        // in flight, release the tensor memory and leave R unwritten
         if (threadIdx.x == 0) {
             tc::mbar_wait(bar, tm.phase, 1LL << 22);
             for (int k = 0; k < NP; ++k)
@@ -944,17 +973,82 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     }
     if (threadIdx.x < 32) tc::tmem_dealloc(tm.base, tmem_cols(n, h));
     __syncthreads();
-    // R to FP64 (exact: hi + lo), in place, for the FP64 tree
-    double *Rp = reinterpret_cast<double *>(sm + L.R);
-    for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) {
-        const df v = Rd[e];
-        Rp[e] = (double)v.hi + (double)v.lo;
+    wy_climb(sm, L, b, a.ldSd, leaf);
+}
+
+// A varlen batch of mixed-precision problems (n <= 64), one persistent launch: every CTA takes
+// (problem, leaf) items from the queue (largest first), folds the leaf's rows with thread
+// copies and climbs that problem's tree; the chunk height h is the batch's.  The tensor
+// memory (tcols columns, enough for the widest problem) and the update's mbarrier are held for
+// the whole launch.  No CTA ever waits for another.
+template <typename Tin, int ROWS>
+__global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const BatchArgs bt,
+                                                                      const int tcols) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ uint64_t s_bar;
+    __shared__ uint32_t s_tbase;
+    __shared__ int s_item;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int h = 256 * ROWS;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        tc::fence_mbar_init();
     }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&s_tbase, (uint32_t)tcols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
     __syncthreads();
-    climb_tree<false>(b, reinterpret_cast<double *>(sm + L.C), a.ldSd, Rp,
-                      reinterpret_cast<double *>(sm + L.f), reinterpret_cast<double *>(sm + L.seg),
-                      reinterpret_cast<double *>(sm + L.tot),
-                      reinterpret_cast<unsigned int *>(sm + L.flag), leaf);
+    tc::fence_after_sync();
+    Tmem tm;
+    tm.base = s_tbase;
+    tm.bar = &s_bar;
+    tm.phase = 0;
+    tm.ok = true;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(bt.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= bt.nitems) break;
+        const int2 w = bt.items[it];
+        const BatchProblem P = bt.probs[w.x];
+        const int n = P.n;
+        const Layout L = layout(n, h);
+        const int64_t rbeg = (int64_t)w.y * P.unit;
+        const int64_t rend = (rbeg + P.unit < P.m) ? rbeg + P.unit : P.m;
+        const Tin *A = static_cast<const Tin *>(P.A);
+        const bool vec4 = sizeof(Tin) == 4 && (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+                          (P.lda % 4 == 0);
+        if (!wy_leaf<Tin, ROWS>(sm, L, n, A, P.lda, rbeg, rend, vec4, tm, nullptr, bt.status))
+            break;
+        F64Args a{};
+        a.A = nullptr;
+        a.m = P.m;
+        a.lda = P.lda;
+        a.n = n;
+        a.unit = P.unit;
+        a.nunits = P.nunits;
+        a.nleaves = P.nleaves;
+        a.arity = P.arity;
+        a.h = h;
+        a.hs = h;
+        a.blk = 1;
+        a.vec = 1;
+        a.ldS = P.ldS;
+        a.slots = bt.slots + P.slot_off;
+        a.counters = bt.counters + P.cnt_off;
+        a.R = P.R;
+        a.ldr = n;
+        a.status = bt.status;
+        wy_climb(sm, L, a, tree_ldsd(n, P.arity), w.y);
+    }
+    if (!tm.ok && threadIdx.x == 0) tc::mbar_wait(&s_bar, tm.phase, 1LL << 22);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(s_tbase, (uint32_t)tcols);
 }
 
 }  // namespace wy
@@ -1085,6 +1179,63 @@ cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int l
         wy_launch_t<__nv_bfloat16>(a, tmap, rows, smem_bytes, stream);
     else
         wy_launch_t<float>(a, tmap, rows, smem_bytes, stream);
+    return cudaGetLastError();
+}
+
+// ---- the varlen batch (tsqr_r_batched's mixed problems up to 64 columns)
+namespace {
+const void *bwy_fn(bool bf16, int rows) {
+    if (bf16) {
+        switch (rows) {
+            case 4: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 4>;
+            case 3: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 3>;
+            case 2: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2>;
+            default: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 1>;
+        }
+    }
+    switch (rows) {
+        case 4: return (const void *)wy::tsqr_batched_wy_kernel<float, 4>;
+        case 3: return (const void *)wy::tsqr_batched_wy_kernel<float, 3>;
+        case 2: return (const void *)wy::tsqr_batched_wy_kernel<float, 2>;
+        default: return (const void *)wy::tsqr_batched_wy_kernel<float, 1>;
+    }
+}
+}  // namespace
+
+// Tensor-memory columns the batch kernel allocates for chunks of h rows and widths up to nmax.
+int batched_wy_tmem_cols(int nmax, int h) { return (int)wy::tmem_cols(nmax, h); }
+
+cudaError_t batched_wy_prepare(bool bf16, int h, size_t smem_bytes) {
+    return set_smem_attrs(bwy_fn(bf16, h / 256), smem_bytes);
+}
+
+int batched_wy_blocks_per_sm(bool bf16, int h, size_t smem_bytes) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwy_fn(bf16, h / 256), wy::kThreads,
+                                                      smem_bytes) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, int tcols,
+                              size_t smem_bytes, cudaStream_t stream) {
+    const dim3 g(grid), block(wy::kThreads);
+    const int rows = h / 256;
+    if (bf16) {
+        switch (rows) {
+            case 4: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 4><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            case 3: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 3><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            case 2: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            default: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 1><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+        }
+    } else {
+        switch (rows) {
+            case 4: wy::tsqr_batched_wy_kernel<float, 4><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            case 3: wy::tsqr_batched_wy_kernel<float, 3><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            case 2: wy::tsqr_batched_wy_kernel<float, 2><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+            default: wy::tsqr_batched_wy_kernel<float, 1><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+        }
+    }
     return cudaGetLastError();
 }
 

@@ -194,6 +194,7 @@ def test_batched_knobs(oracle, T, knobs, prec):
         bd, code, p, tol = buf.cuda(), T.F64, T.PREC_F64, 1e-13
     else:
         bd, code, p, tol = buf.to(torch.float32).cuda(), T.F32, T.PREC_MIXED, 2e-6
+        knobs = dict(knobs, leaf="fold")  # warps and chunk height are the fold leaf's knobs
     ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
     Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
     plan = T.make_batch_plan(**knobs)
@@ -269,3 +270,83 @@ def test_batched_autotune_bucket(oracle, T, prec):
         T.tsqr_autotune_reset()
     T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=p)
     assert T.last_batch_plan().as_tuple() == builtin
+
+
+# ---- the blocked tensor-core leaf in the mixed batch
+
+def _odd_mixed_batch(dtype, widths=(1, 3, 8, 16, 17, 33, 48, 64)):
+    import torch
+    g = torch.Generator().manual_seed(9)
+    ms = [0, 1, 5, 100, 511, 512, 513, 3000, 40000, 257, 1024, 70001]
+    ns = [widths[i % len(widths)] for i in range(len(ms))]
+    offs = [0]
+    for m, n in zip(ms, ns):
+        offs.append(offs[-1] + m * n)
+    buf = torch.randn(offs[-1], generator=g, dtype=torch.float64).to(dtype)
+    return buf, ms, ns, offs
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("leaf", ["auto", "fold", "panels"])
+def test_batched_mixed_leaves(oracle, T, dtype, leaf):
+    """The mixed batch on either leaf (the blocked one is AUTO up to 64 columns): every
+    problem's R upper triangular with diag >= 0 and R^T R = A^T A within 2e-6, including
+    m = 0, m < n, one row, one column and ragged chunks."""
+    import torch
+    buf, ms, ns, offs = _odd_mixed_batch(getattr(torch, dtype))
+    code = T.F32 if dtype == "float32" else T.BF16
+    bd = buf.cuda()
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=code, prec=T.PREC_MIXED,
+                     plan=T.make_batch_plan(leaf=leaf))
+    assert T.last_batch_plan().leaf == (T.LEAF_FOLD if leaf == "fold" else T.LEAF_PANELS)
+    torch.cuda.synchronize()
+    assert T.tsqr_get_device_status() == T.SUCCESS
+    _check_all(oracle, buf.to(torch.float64).numpy(), ms, ns, offs, Rp.cpu().numpy(), roff, 2e-6)
+
+
+def test_batched_panels_reproducible_and_graph(T):
+    """The blocked-leaf batch is bit-reproducible, and a captured call replays it bit for bit."""
+    import torch
+    buf, ms, ns, offs = workloads.varlen_batch(64, 512, 30000, seed=3, dtype=torch.float32)
+    bd = buf.cuda()
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    plan = T.make_batch_plan(leaf="panels")
+    R1 = torch.zeros(roff[-1], dtype=torch.float64, device="cuda")
+    R2 = torch.zeros_like(R1)
+    T.tsqr_r_batched(ptrs, ms, ns, roff, R1, dtype=T.F32, prec=T.PREC_MIXED, plan=plan)
+    T.tsqr_r_batched(ptrs, ms, ns, roff, R2, dtype=T.F32, prec=T.PREC_MIXED, plan=plan)
+    torch.cuda.synchronize()
+    assert torch.equal(R1, R2)
+    s = torch.cuda.Stream()
+    Rg = torch.full_like(R1, float("nan"))
+    with torch.cuda.stream(s):
+        T.tsqr_r_batched(ptrs, ms, ns, roff, Rg, dtype=T.F32, prec=T.PREC_MIXED, plan=plan,
+                         stream=s)
+    torch.cuda.synchronize()
+    Rg.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        T.tsqr_r_batched(ptrs, ms, ns, roff, Rg, dtype=T.F32, prec=T.PREC_MIXED, plan=plan,
+                         stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Rg, R1)
+
+
+def test_batched_panels_refused(T):
+    """The blocked leaf is mixed precision up to 64 columns: an FP64 batch or a wider problem
+    asks for it in vain."""
+    import torch
+    A = torch.zeros(100 * 80, dtype=torch.float64, device="cuda")
+    Rp = torch.zeros(80 * 80, dtype=torch.float64, device="cuda")
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_r_batched([A.data_ptr()], [100], [8], [0, 64], Rp,
+                         plan=T.make_batch_plan(leaf="panels"))
+    assert e.value.status == T.ERR_UNSUPPORTED
+    A32 = torch.zeros(100 * 80, dtype=torch.float32, device="cuda")
+    with pytest.raises(T.TsqrError) as e:
+        T.tsqr_r_batched([A32.data_ptr()], [100], [80], [0, 6400], Rp, dtype=T.F32,
+                         prec=T.PREC_MIXED, plan=T.make_batch_plan(leaf="panels"))
+    assert e.value.status == T.ERR_UNSUPPORTED
