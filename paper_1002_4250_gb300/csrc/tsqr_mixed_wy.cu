@@ -697,8 +697,8 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 
     // ---- 2a. Z = X^T C(:, T) on the tensor cores.  The 8 warps are KG row groups x TS sets of
     //          n-tiles (8 columns each): a warp splits its X fragments once per 8 rows and uses
-    //          them for every tile of its set.  Per tile two accumulators: the five smaller
-    //          partial products, and X_hi C_hi; partial tiles per row group go to P.
+    //          them for every tile of its set.  Per tile three accumulators (below); partial
+    //          tiles per row group go to P.
     const int NT8 = ntp / 8;
     const int TS = NT8 >= 4 ? 2 : 1;          // tile sets
     const int TPS = (NT8 + TS - 1) / TS;      // tiles per set (<= 3 for n <= 64)
@@ -708,7 +708,9 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         const int grp = warp / TS, set = warp % TS;
         const int jt0 = set * TPS, jt1 = min(NT8, jt0 + TPS);
         const int r0 = grp * (h / KG), r1 = r0 + h / KG;
-        float e[3][4] = {}, hh[3][4] = {};
+        // three accumulators per tile, smallest products first: ea (X_mid C_mid, X_lo C_hi,
+        // X_hi C_lo), eb (X_mid C_hi, X_hi C_mid), hh (X_hi C_hi): shorter dependent mma chains
+        float e[3][4] = {}, eb[3][4] = {}, hh[3][4] = {};
         for (int k0 = r0; k0 < r1; k0 += 8) {
             const float xa[4] = {C[cidx(k0 + t4, J0 + g4, NP)], C[cidx(k0 + t4, J0 + g4 + 8, NP)],
                                  C[cidx(k0 + t4 + 4, J0 + g4, NP)],
@@ -727,11 +729,11 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
                     for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
                     tc::mma_m16n8k8(e[t], am, bm);
-                    tc::mma_m16n8k8(e[t], al, bh);
-                    tc::mma_m16n8k8(e[t], ah, bl);
-                    tc::mma_m16n8k8(e[t], am, bh);
-                    tc::mma_m16n8k8(e[t], ah, bm);
+                    tc::mma_m16n8k8(eb[t], am, bh);
                     tc::mma_m16n8k8(hh[t], ah, bh);
+                    tc::mma_m16n8k8(e[t], al, bh);
+                    tc::mma_m16n8k8(eb[t], ah, bm);
+                    tc::mma_m16n8k8(e[t], ah, bl);
                 }
             }
         }
@@ -740,10 +742,10 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             const int jt = jt0 + t;
             if (jt < jt1) {
                 float *pt = P + (grp * NT8 + jt) * 128;  // tile, 16 x 8 row-major
-                pt[g4 * 8 + 2 * t4] = __fadd_rn(e[t][0], hh[t][0]);
-                pt[g4 * 8 + 2 * t4 + 1] = __fadd_rn(e[t][1], hh[t][1]);
-                pt[(g4 + 8) * 8 + 2 * t4] = __fadd_rn(e[t][2], hh[t][2]);
-                pt[(g4 + 8) * 8 + 2 * t4 + 1] = __fadd_rn(e[t][3], hh[t][3]);
+                pt[g4 * 8 + 2 * t4] = __fadd_rn(__fadd_rn(e[t][0], eb[t][0]), hh[t][0]);
+                pt[g4 * 8 + 2 * t4 + 1] = __fadd_rn(__fadd_rn(e[t][1], eb[t][1]), hh[t][1]);
+                pt[(g4 + 8) * 8 + 2 * t4] = __fadd_rn(__fadd_rn(e[t][2], eb[t][2]), hh[t][2]);
+                pt[(g4 + 8) * 8 + 2 * t4 + 1] = __fadd_rn(__fadd_rn(e[t][3], eb[t][3]), hh[t][3]);
             }
         }
     }
