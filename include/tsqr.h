@@ -89,9 +89,10 @@ typedef enum {
  *         then applied to the columns right of it as one compact WY block (I - V S V^T) whose
  *         two products run on the tensor cores as split-TF32 products with FP32 accumulation
  *         (each as accurate as an FP32 dot product); R in double-FP32 in the leaf, FP64 in the
- *         tree.  n <= 64; chunks of 256, 512, 768 or 1024 rows (tile_rows; AUTO: the
+ *         tree.  n <= 64; chunks of 256, 512, 640, 768 or 1024 rows (tile_rows; AUTO: the
  *         tallest the width's shared and tensor memory allow).
- * AUTO picks PANELS for n <= 64 (FP32: from n = 13 on), where it measured faster, else FOLD. */
+ * AUTO picks PANELS for n <= 64 (FP32 from n = 9, BF16 from n = 3), where it measured faster,
+ * else FOLD. */
 typedef enum { TSQR_LEAF_AUTO = 0, TSQR_LEAF_FOLD = 1, TSQR_LEAF_PANELS = 2 } tsqr_leaf_t;
 
 /* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic
@@ -107,7 +108,7 @@ typedef struct {
                            binary operators by associativity, Section 2).  0 = as many as the
                            kernel's shared memory holds.                                     */
     int32_t leaf;       /* tsqr_leaf_t (mixed path only; 0 elsewhere).  With PANELS,
-                           tile_rows is the chunk height (256, 512, 768 or 1024) of a HYBRID
+                           tile_rows is the chunk height (256, 512, 640, 768 or 1024) of a HYBRID
                            plan, warps is 8 (or 0).                                          */
 } tsqr_plan_t;
 
@@ -253,7 +254,9 @@ tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, do
  *             offsets[i+1] - offsets[i] >= n_i^2; R_i is written column-major with ld n_i at
  *             R_packed + offsets[i].
  *   R_packed: device FP64 buffer of at least offsets[count] elements.
- *   dtype, prec as for tsqr_r_ex.  All problems are factorized by one launch.             */
+ *   dtype, prec as for tsqr_r_ex.  All problems are factorized by one launch: FP64 and wide
+ *   mixed batches by the fold leaf, mixed batches up to 64 columns by the blocked tensor-core
+ *   leaf of TSQR_LEAF_PANELS (see tsqr_batch_plan_t's leaf).                                */
 tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream);

@@ -1394,14 +1394,14 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
     p->warps = 8;
     const int64_t mm = std::max<int64_t>(m, 1);
     const size_t reserve = 1024;
-    // AUTO chunk height: the tallest of 1024, 768, 512 rows that fits one CTA's shared memory
-    // and the SM's tensor memory (fewer reflector chains per row of A: 2^24 x 64 FP32 with
-    // 512-row chunks 24.3 ms, with 256-row chunks (two CTAs per SM) 49 ms)
+    // AUTO chunk height: the tallest of 1024, 768, 640, 512 rows that fits one CTA's shared
+    // memory and the SM's tensor memory (fewer reflector chains per row of A: 2^24 x 64 FP32
+    // with 512-row chunks 24.3 ms, with 256-row chunks (two CTAs per SM) 49 ms)
     auto fits = [&](int hh) {
         return mixed_wy_smem_bytes(n, hh) + reserve <= di.smem_block_optin && mixed_wy_tmem_fits(n, hh);
     };
     int h_auto = 256;
-    for (int hh : {1024, 768, 512})
+    for (int hh : kMixedWyHeights)
         if (fits(hh)) {
             h_auto = hh;
             break;
@@ -1410,14 +1410,15 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
     if (p->tree == TSQR_TREE_BINARY) {
         p->unit = (over && over->tile_rows > 0) ? over->tile_rows : 256;
         h = 256;
-        for (int hh : {1024, 768, 512})
+        for (int hh : kMixedWyHeights)
             if (hh <= h_auto && p->unit % hh == 0) {
                 h = hh;
                 break;
             }
     } else if (over && over->tile_rows > 0) {
-        if (over->tile_rows % 256 != 0 || over->tile_rows > 1024 || !fits(over->tile_rows))
-            return TSQR_ERR_INVALID_ARG;
+        bool known = false;
+        for (int hh : kMixedWyHeights) known |= (over->tile_rows == hh);
+        if (!known || !fits(over->tile_rows)) return TSQR_ERR_INVALID_ARG;
         h = over->tile_rows;
         p->unit = h;
     } else {
@@ -1427,7 +1428,7 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
     p->h = h;
     p->hs = h;
     p->ldS = 0;
-    p->blk = h / 256;
+    p->blk = h / 128;
     (void)reserve;
     p->vec = 1;
     p->smem = mixed_wy_smem_bytes(n, h);
@@ -1614,7 +1615,7 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     const bool wy = mixed && nmax <= kMixedWyMaxN && bp.leaf != TSQR_LEAF_FOLD;
     int wy_h = 0, wy_tcols = 0;
     if (wy) {
-        for (int hh : {1024, 768, 512, 256})
+        for (int hh : kMixedWyHeights)
             if (mixed_wy_smem_bytes(nmax, hh) <= di.smem_block_optin && mixed_wy_tmem_fits(nmax, hh)) {
                 wy_h = hh;
                 break;

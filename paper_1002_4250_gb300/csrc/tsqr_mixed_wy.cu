@@ -390,14 +390,12 @@ __device__ __forceinline__ void tma_panel(float *C, Tma &t, int64_t r0, int k, i
 }
 
 // Panel k's BF16 boxes, staged by tma_panel<__nv_bfloat16>, widened to the FP32 layout in place.
-// Warp w takes boxes 8 q + w (the rows it holds in the factorization): every lane reads its row
-// of the 16 columns before the warp writes any of them back over the staging half.
-template <int ROWS>
+// Warp w takes boxes w, w + 8, ... of the chunk's h / 32: every lane reads its row of the 16
+// columns before the warp writes any of them back over the staging half.
+template <int HB>
 __device__ __forceinline__ void widen_panel(float *C, int k, int NP) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < ROWS; ++q) {
-        const int rb = 8 * q + warp;
+    for (int rb = warp; rb < 4 * HB; rb += kWarps) {
         const __nv_bfloat16 *st =
             reinterpret_cast<const __nv_bfloat16 *>(C + (size_t)(rb * NP + k) * 512 + 256);
         float v[kPw];
@@ -411,7 +409,7 @@ __device__ __forceinline__ void widen_panel(float *C, int k, int NP) {
 
 // Bounded wait for panels k0 .. k1-1 of the current chunk (and their widening for BF16); the
 // CTA agrees on the outcome.  False: a wait gave up (recorded in the status word).
-template <typename Tin, int ROWS>
+template <typename Tin, int HB>
 __device__ __forceinline__ bool wait_panels(float *C, Tma &t, int k0, int k1, int NP,
                                             int *status) {
     bool got = true;
@@ -422,13 +420,13 @@ __device__ __forceinline__ bool wait_panels(float *C, Tma &t, int k0, int k1, in
     }
     for (int k = k0; k < k1; ++k) t.pend &= ~(1u << k);
     if constexpr (sizeof(Tin) == 2)
-        for (int k = k0; k < k1; ++k) widen_panel<ROWS>(C, k, NP);
+        for (int k = k0; k < k1; ++k) widen_panel<HB>(C, k, NP);
     return true;
 }
 
 // ------------------------------------------------------------------------------------------
 // One panel: factorization (reflectors J = 0 .. pw-1 of columns J0 + J), S, and the update of
-// the columns right of it.  ROWS = h / 256 rows per thread in the factorization.
+// the columns right of it.  Chunks of h = 128 HB rows.
 // ------------------------------------------------------------------------------------------
 // Tensor memory of a CTA: for M-block b (rows 128 b .. 128 b + 127) the update's accumulator D_b
 // at columns [DW b, DW b + DW) (DW = the widest trailing block, 16 to 48 columns) and the tails'
@@ -448,9 +446,9 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
     return tmem_need(n, h) <= 256 ? 256u : 512u;
 }
 
-// Warps that factorize a panel for ROWS = h / 256: four, one per sub-partition (h / 128 rows
-// per lane, up to 8, which the registers hold); the eight-warp form is kept for reference.
-__host__ __device__ constexpr int panel_warps(int rows) { return rows > 0 ? 4 : 8; }
+// Warps that factorize a panel of h = 128 HB rows: four, one per sub-partition (HB rows per
+// lane, up to 8, which the registers hold); the eight-warp form is kept for reference.
+__host__ __device__ constexpr int panel_warps(int hb) { return hb > 0 ? 4 : 8; }
 
 // Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
 // CTA.
@@ -508,11 +506,11 @@ __device__ __forceinline__ float scalar_update(unsigned char *sm, const Layout &
 // the other panels before its Z product reads them; and with a next chunk (t->rnext >= 0),
 // panel k's columns of the next chunk are loaded as soon as this chunk no longer reads them:
 // after the Z product (or, for the last panel, after its reflectors).
-template <typename Tin, int ROWS>
+template <typename Tin, int HB>
 __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, const int n,
                                            const int NP, const int k, Tmem &tm, int *status,
                                            Tma *t) {
-    constexpr int h = 256 * ROWS;
+    constexpr int h = 128 * HB;
     float *C = reinterpret_cast<float *>(sm + L.C);
     df *Rd = reinterpret_cast<df *>(sm + L.R);
     df *red = reinterpret_cast<df *>(sm + L.red);
@@ -531,7 +529,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     //         of up to 512 rows, whose lanes then hold PR = h / (32 PW) rows each: half the
     //         warp-level reductions per row of eight warps; all eight for taller chunks, whose
     //         rows would not fit the registers of four)
-    constexpr int PW = panel_warps(ROWS);
+    constexpr int PW = panel_warps(HB);
     constexpr int PR = h / (32 * PW);
     const bool panel_warp = warp < PW;
     float x[PR][kPw];
@@ -689,7 +687,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         return;
     }
     // the Z product reads the trailing panels: with TMA loads, wait for them (and widen BF16)
-    if (t && k == 0 && !wait_panels<Tin, ROWS>(C, *t, 1, NP, NP, status)) {
+    if (t && k == 0 && !wait_panels<Tin, HB>(C, *t, 1, NP, NP, status)) {
         tm.ok = false;
         return;
     }
@@ -838,10 +836,9 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         tc::fence_after_sync();
         if (done) {
             const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll
-            for (int q = 0; q < ROWS; ++q) {
-                const int i = 256 * q + 32 * warp + lane;
-                const int b = 2 * q + (warp >> 2);
+            // M-block b (rows 128 b ..) by warps 0-3 for even b, 4-7 for odd b
+            for (int b = warp >> 2; b < MB; b += 2) {
+                const int i = 128 * b + 32 * (warp & 3) + lane;
                 for (int c0 = 0; c0 < ntp16; c0 += 8) {
                     float v[8];
                     tc::tmem_ld8(tm.base + lane_base + (uint32_t)(tmem_dw(n) * b + c0), v);
@@ -863,12 +860,12 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 // given, else thread copies), then R converted exactly to FP64 in place at L.R for the tree.
 // Returns false when a wait gave up (recorded in the status word and agreed by the CTA); the
 // caller then waits out what is in flight.
-template <typename Tin, int ROWS>
+template <typename Tin, int HB>
 __device__ __forceinline__ bool wy_leaf(unsigned char *sm, const Layout &L, const int n,
                                         const Tin *A, const int64_t lda, const int64_t rbeg,
                                         const int64_t rend, const bool vec4, Tmem &tm, Tma *t,
                                         int *status) {
-    constexpr int h = 256 * ROWS;
+    constexpr int h = 128 * HB;
     const int NP = (n + kPw - 1) / kPw;
     df *Rd = reinterpret_cast<df *>(sm + L.R);
     for (int e = threadIdx.x; e < n * (n + 1) / 2; e += blockDim.x) Rd[e] = mk(0.f);
@@ -884,13 +881,13 @@ __device__ __forceinline__ bool wy_leaf(unsigned char *sm, const Layout &L, cons
         } else {
             t->rnext = (r0 + h < rend) ? r0 + h : -1;
             // panel 0 of this chunk (panel_step waits for the others before they are read)
-            if (!wait_panels<Tin, ROWS>(Cf, *t, 0, 1, NP, status)) {
+            if (!wait_panels<Tin, HB>(Cf, *t, 0, 1, NP, status)) {
                 tm.ok = false;
                 break;
             }
             __syncthreads();
         }
-        for (int k = 0; k < NP && tm.ok; ++k) panel_step<Tin, ROWS>(sm, L, n, NP, k, tm, status, t);
+        for (int k = 0; k < NP && tm.ok; ++k) panel_step<Tin, HB>(sm, L, n, NP, k, tm, status, t);
         if (t && tm.ok) t->phase ^= 1u;
     }
     tc::fence_before_sync();
@@ -918,14 +915,14 @@ __device__ __forceinline__ void wy_climb(unsigned char *sm, const Layout &L, con
 }
 
 // One matrix: CTA = leaf, then the tree.
-template <typename Tin, int ROWS>
-__global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
+template <typename Tin, int HB>
+__global__ void __launch_bounds__(kThreads, HB == 2 ? 2 : 1)
     tsqr_mixed_wy_kernel(const WyArgs2 a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     // the chunk region starts on a 1024-byte boundary (the 128-byte swizzle's period)
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int h = 256 * ROWS;
+    constexpr int h = 128 * HB;
     const F64Args &b = a.base;
     const int n = b.n;
     const int NP = (n + kPw - 1) / kPw;
@@ -959,7 +956,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
     tm.phase = 0;
     tm.ok = true;
     Tma t{&tmap, -1, tbar, 0u, 0u, 0u};
-    const bool ok = wy_leaf<Tin, ROWS>(sm, L, n, static_cast<const Tin *>(a.A), b.lda, rbeg, rend,
+    const bool ok = wy_leaf<Tin, HB>(sm, L, n, static_cast<const Tin *>(a.A), b.lda, rbeg, rend,
                                        a.vec4 != 0, tm, use_tma ? &t : nullptr, b.status);
     if (!ok) {
         // a tensor-core or TMA wait gave up: wait once more, bounded, for the mma and the loads
@@ -983,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 1 ? 2 : 1)
 // copies and climbs that problem's tree; the chunk height h is the batch's.  The tensor
 // memory (tcols columns, enough for the widest problem) and the update's mbarrier are held for
 // the whole launch.  No CTA ever waits for another.
-template <typename Tin, int ROWS>
+template <typename Tin, int HB>
 __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const BatchArgs bt,
                                                                       const int tcols) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -992,7 +989,7 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
     __shared__ int s_item;
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int h = 256 * ROWS;
+    constexpr int h = 128 * HB;
     if (threadIdx.x == 0) {
         tc::mbar_init(&s_bar, 1);
         tc::fence_mbar_init();
@@ -1024,7 +1021,7 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
         const Tin *A = static_cast<const Tin *>(P.A);
         const bool vec4 = sizeof(Tin) == 4 && (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                           (P.lda % 4 == 0);
-        if (!wy_leaf<Tin, ROWS>(sm, L, n, A, P.lda, rbeg, rend, vec4, tm, nullptr, bt.status))
+        if (!wy_leaf<Tin, HB>(sm, L, n, A, P.lda, rbeg, rend, vec4, tm, nullptr, bt.status))
             break;
         F64Args a{};
         a.A = nullptr;
@@ -1060,23 +1057,25 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
 // ------------------------------------------------------------------------------------------
 namespace {
 template <typename Tin>
-const void *wy_fn(int rows) {
-    switch (rows) {
+const void *wy_fn(int hb) {
+    switch (hb) {
+        case 8: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 8>;
+        case 6: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 6>;
+        case 5: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 5>;
         case 4: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 4>;
-        case 3: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 3>;
-        case 2: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>;
-        default: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 1>;
+        default: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>;
     }
 }
 template <typename Tin>
-void wy_launch_t(const wy::WyArgs2 &a, const CUtensorMap &tmap, int rows, size_t smem,
+void wy_launch_t(const wy::WyArgs2 &a, const CUtensorMap &tmap, int hb, size_t smem,
                  cudaStream_t stream) {
     const dim3 grid(a.base.nleaves), block(wy::kThreads);
-    switch (rows) {
+    switch (hb) {
+        case 8: wy::tsqr_mixed_wy_kernel<Tin, 8><<<grid, block, smem, stream>>>(a, tmap); break;
+        case 6: wy::tsqr_mixed_wy_kernel<Tin, 6><<<grid, block, smem, stream>>>(a, tmap); break;
+        case 5: wy::tsqr_mixed_wy_kernel<Tin, 5><<<grid, block, smem, stream>>>(a, tmap); break;
         case 4: wy::tsqr_mixed_wy_kernel<Tin, 4><<<grid, block, smem, stream>>>(a, tmap); break;
-        case 3: wy::tsqr_mixed_wy_kernel<Tin, 3><<<grid, block, smem, stream>>>(a, tmap); break;
-        case 2: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a, tmap); break;
-        default: wy::tsqr_mixed_wy_kernel<Tin, 1><<<grid, block, smem, stream>>>(a, tmap); break;
+        default: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a, tmap); break;
     }
 }
 
@@ -1126,7 +1125,7 @@ bool make_tensor_map(const void *A, bool bf16, int64_t m, int n, int64_t lda, CU
 // The layout plus 1024 bytes to align its base to the swizzle period.
 size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total + 1024; }
 
-// Whether an h-row chunk (h = 256 .. 1024, a multiple of 256) fits the tensor memory for width n.
+// Whether an h-row chunk (h = 256, 512, 640, 768 or 1024) fits the tensor memory for width n.
 bool mixed_wy_tmem_fits(int n, int h) { return wy::tmem_need(n, h) <= 512; }
 
 // Largest arity (<= 8) whose stacked FP64 triangles fit in the chunk region of an h-row leaf.
@@ -1142,9 +1141,10 @@ bool mixed_wy_tree_fits(int n, int h, int arity) {
 }
 
 cudaError_t mixed_wy_prepare(size_t smem_bytes) {
-    const void *fns[8] = {wy_fn<float>(1), wy_fn<float>(2), wy_fn<float>(3), wy_fn<float>(4),
-                          wy_fn<__nv_bfloat16>(1), wy_fn<__nv_bfloat16>(2),
-                          wy_fn<__nv_bfloat16>(3), wy_fn<__nv_bfloat16>(4)};
+    const void *fns[10] = {wy_fn<float>(2), wy_fn<float>(4), wy_fn<float>(5), wy_fn<float>(6),
+                           wy_fn<float>(8), wy_fn<__nv_bfloat16>(2), wy_fn<__nv_bfloat16>(4),
+                           wy_fn<__nv_bfloat16>(5), wy_fn<__nv_bfloat16>(6),
+                           wy_fn<__nv_bfloat16>(8)};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes);
@@ -1158,7 +1158,7 @@ cudaError_t mixed_wy_prepare(size_t smem_bytes) {
 
 int mixed_wy_blocks_per_sm(int h, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wy_fn<float>(h / 256), wy::kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wy_fn<float>(h / 128), wy::kThreads,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
@@ -1176,30 +1176,32 @@ cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int l
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
     a.tma = base.unit % base.h == 0 && make_tensor_map(A, bf16, base.m, base.n, base.lda, &tmap);
-    const int rows = base.h / 256;
+    const int hb = base.h / 128;
     if (bf16)
-        wy_launch_t<__nv_bfloat16>(a, tmap, rows, smem_bytes, stream);
+        wy_launch_t<__nv_bfloat16>(a, tmap, hb, smem_bytes, stream);
     else
-        wy_launch_t<float>(a, tmap, rows, smem_bytes, stream);
+        wy_launch_t<float>(a, tmap, hb, smem_bytes, stream);
     return cudaGetLastError();
 }
 
 // ---- the varlen batch (tsqr_r_batched's mixed problems up to 64 columns)
 namespace {
-const void *bwy_fn(bool bf16, int rows) {
+const void *bwy_fn(bool bf16, int hb) {
     if (bf16) {
-        switch (rows) {
+        switch (hb) {
+            case 8: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 8>;
+            case 6: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 6>;
+            case 5: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 5>;
             case 4: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 4>;
-            case 3: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 3>;
-            case 2: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2>;
-            default: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 1>;
+            default: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2>;
         }
     }
-    switch (rows) {
+    switch (hb) {
+        case 8: return (const void *)wy::tsqr_batched_wy_kernel<float, 8>;
+        case 6: return (const void *)wy::tsqr_batched_wy_kernel<float, 6>;
+        case 5: return (const void *)wy::tsqr_batched_wy_kernel<float, 5>;
         case 4: return (const void *)wy::tsqr_batched_wy_kernel<float, 4>;
-        case 3: return (const void *)wy::tsqr_batched_wy_kernel<float, 3>;
-        case 2: return (const void *)wy::tsqr_batched_wy_kernel<float, 2>;
-        default: return (const void *)wy::tsqr_batched_wy_kernel<float, 1>;
+        default: return (const void *)wy::tsqr_batched_wy_kernel<float, 2>;
     }
 }
 }  // namespace
@@ -1208,12 +1210,12 @@ const void *bwy_fn(bool bf16, int rows) {
 int batched_wy_tmem_cols(int nmax, int h) { return (int)wy::tmem_cols(nmax, h); }
 
 cudaError_t batched_wy_prepare(bool bf16, int h, size_t smem_bytes) {
-    return set_smem_attrs(bwy_fn(bf16, h / 256), smem_bytes);
+    return set_smem_attrs(bwy_fn(bf16, h / 128), smem_bytes);
 }
 
 int batched_wy_blocks_per_sm(bool bf16, int h, size_t smem_bytes) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwy_fn(bf16, h / 256), wy::kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwy_fn(bf16, h / 128), wy::kThreads,
                                                       smem_bytes) != cudaSuccess)
         return 0;
     return nb;
@@ -1222,22 +1224,26 @@ int batched_wy_blocks_per_sm(bool bf16, int h, size_t smem_bytes) {
 cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, int tcols,
                               size_t smem_bytes, cudaStream_t stream) {
     const dim3 g(grid), block(wy::kThreads);
-    const int rows = h / 256;
+    const int hb = h / 128;
+#define TSQR_BWY(T, HBV) wy::tsqr_batched_wy_kernel<T, HBV><<<g, block, smem_bytes, stream>>>(b, tcols)
     if (bf16) {
-        switch (rows) {
-            case 4: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 4><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            case 3: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 3><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            case 2: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            default: wy::tsqr_batched_wy_kernel<__nv_bfloat16, 1><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+        switch (hb) {
+            case 8: TSQR_BWY(__nv_bfloat16, 8); break;
+            case 6: TSQR_BWY(__nv_bfloat16, 6); break;
+            case 5: TSQR_BWY(__nv_bfloat16, 5); break;
+            case 4: TSQR_BWY(__nv_bfloat16, 4); break;
+            default: TSQR_BWY(__nv_bfloat16, 2); break;
         }
     } else {
-        switch (rows) {
-            case 4: wy::tsqr_batched_wy_kernel<float, 4><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            case 3: wy::tsqr_batched_wy_kernel<float, 3><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            case 2: wy::tsqr_batched_wy_kernel<float, 2><<<g, block, smem_bytes, stream>>>(b, tcols); break;
-            default: wy::tsqr_batched_wy_kernel<float, 1><<<g, block, smem_bytes, stream>>>(b, tcols); break;
+        switch (hb) {
+            case 8: TSQR_BWY(float, 8); break;
+            case 6: TSQR_BWY(float, 6); break;
+            case 5: TSQR_BWY(float, 5); break;
+            case 4: TSQR_BWY(float, 4); break;
+            default: TSQR_BWY(float, 2); break;
         }
     }
+#undef TSQR_BWY
     return cudaGetLastError();
 }
 
