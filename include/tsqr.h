@@ -89,10 +89,10 @@ typedef enum {
  *         then applied to the columns right of it as one compact WY block (I - V S V^T) whose
  *         two products run on the tensor cores as split-TF32 products with FP32 accumulation
  *         (each as accurate as an FP32 dot product); R in double-FP32 in the leaf, FP64 in the
- *         tree.  n <= 64; chunks of 256, 512, 640, 768 or 1024 rows (tile_rows; AUTO: the
- *         tallest the width's shared and tensor memory allow).
- * AUTO picks PANELS for n <= 64 (FP32 from n = 9, BF16 from n = 3), where it measured faster,
- * else FOLD. */
+ *         tree.  n <= 112; chunks of 256, 384, 512, 640, 768 or 1024 rows (tile_rows; AUTO:
+ *         the tallest the width's shared and tensor memory allow).
+ * AUTO picks PANELS for n <= 112 (FP32 from n = 9, BF16 from n = 3), where it measured
+ * faster, else FOLD. */
 typedef enum { TSQR_LEAF_AUTO = 0, TSQR_LEAF_FOLD = 1, TSQR_LEAF_PANELS = 2 } tsqr_leaf_t;
 
 /* Optional plan override.  Zero fields mean "choose".  The chosen plan fixes the arithmetic
@@ -108,7 +108,7 @@ typedef struct {
                            binary operators by associativity, Section 2).  0 = as many as the
                            kernel's shared memory holds.                                     */
     int32_t leaf;       /* tsqr_leaf_t (mixed path only; 0 elsewhere).  With PANELS,
-                           tile_rows is the chunk height (256, 512, 640, 768 or 1024) of a HYBRID
+                           tile_rows is the chunk height (256, 384, 512, 640, 768 or 1024) of a HYBRID
                            plan, warps is 8 (or 0).                                          */
 } tsqr_plan_t;
 
@@ -254,9 +254,9 @@ tsqr_status_t tsqr_caqr_r(const double *A, int64_t m, int64_t n, int64_t lda, do
  *             offsets[i+1] - offsets[i] >= n_i^2; R_i is written column-major with ld n_i at
  *             R_packed + offsets[i].
  *   R_packed: device FP64 buffer of at least offsets[count] elements.
- *   dtype, prec as for tsqr_r_ex.  All problems are factorized by one launch: FP64 and wide
- *   mixed batches by the fold leaf, mixed batches up to 64 columns by the blocked tensor-core
- *   leaf of TSQR_LEAF_PANELS (see tsqr_batch_plan_t's leaf).                                */
+ *   dtype, prec as for tsqr_r_ex.  All problems are factorized by one launch: FP64 and wider
+ *   mixed batches by the fold leaf, mixed batches up to 112 columns by the blocked
+ *   tensor-core leaf of TSQR_LEAF_PANELS (see tsqr_batch_plan_t's leaf).                    */
 tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const int32_t *ns,
                              const int64_t *offsets, int32_t count, double *R_packed,
                              int32_t dtype, int32_t prec, tsqr_stream_t stream);
@@ -274,10 +274,10 @@ tsqr_status_t tsqr_r_batched(const void *const *ptrs, const int64_t *ms, const i
  *                    > 32), 2 .. 8, lowered to what the width's shared memory holds (0: the
  *                    largest that fits).
  *   leaf           : mixed precision only, a tsqr_leaf_t: FOLD, or PANELS (the blocked
- *                    tensor-core leaf of tsqr_r_ex, for batches up to 64 columns; chunks of
- *                    1024, 768 or 512 rows by the widest problem, 8 warps, one CTA per SM, so
- *                    warps and ctas_per_sm do not apply).  0: PANELS where it applies, else
- *                    FOLD.  PANELS for an FP64 batch or one wider than 64 columns returns
+ *                    tensor-core leaf of tsqr_r_ex, for batches up to 112 columns; chunks as
+ *                    tall as the widest problem allows, 8 warps, one CTA per SM, so warps and
+ *                    ctas_per_sm do not apply).  0: PANELS up to 112 columns, else FOLD.
+ *                    PANELS for an FP64 batch or one wider than 112 columns returns
  *                    TSQR_ERR_UNSUPPORTED. */
 typedef struct tsqr_batch_plan_t {
     int32_t warps;
@@ -301,7 +301,7 @@ tsqr_status_t tsqr_r_batched_ex(const void *const *ptrs, const int64_t *ms, cons
  * count) and floor(log2 of the work sum max(m_i, 1) n_i^2).  From then on an AUTO batched call
  * (tsqr_r_batched, or tsqr_r_batched_ex with plan NULL or all zero) in that bucket uses it and
  * returns the bytes it gives.  The search starts from the built-in rules and moves one knob at a
- * time: for a mixed batch up to 64 columns the fold leaf against the blocked one, then (for
+ * time: for a mixed batch up to 112 columns the fold leaf against the blocked one, then (for
  * the fold) warps (4, 6, 8, 12) x ctas_per_sm, then leaves_per_cta, then each present width bucket's arity
  * (2, 4, 8); each setting is run once to warm up and timed over one call with CUDA events on
  * `stream`.
@@ -359,8 +359,9 @@ tsqr_status_t tsqr_r_noalloc(const double *A, int64_t m, int64_t n, int64_t lda,
  *   result).  best: optional, receives the chosen plan.
  *   Candidates: HYBRID slabs as tall as fit 1, 2 or 3 CTAs per SM, and half as tall, with that
  *   many CTAs per SM on every SM; 4, 5, 6, 8 or 12 bulk warps; for FP64 from n = 48 (m >= 8 n) the
- *   PANELS tree with 16- and 32-column panels; for the mixed path up to n = 64 the blocked
- *   leaf with 256- and 512-row chunks.  Then the fastest HYBRID plan with tree arity 2, 3, 4, 6
+ *   PANELS tree with 16- and 32-column panels; for the mixed path up to n = 112 the blocked
+ *   leaf with every chunk height (256 to 1024 rows) the width's shared and tensor memory hold,
+ *   1 to as many CTAs per SM as fit.  Then the fastest HYBRID plan with tree arity 2, 3, 4, 6
  *   and 8.  Each is timed over three calls with CUDA events on `stream`.
  *   Synchronizes `stream`; not for use under stream capture.  Returns TSQR_ERR_UNSUPPORTED if
  *   no candidate runs. */

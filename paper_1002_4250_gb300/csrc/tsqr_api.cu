@@ -1375,10 +1375,10 @@ tsqr_status_t run_lstsq_panels(const double *A, int64_t m, int64_t n, int64_t ld
     return st;
 }
 
-// Plan of the blocked mixed leaf (TSQR_LEAF_PANELS): chunks of h = 256 or 512 rows (AUTO: the
-// taller one that keeps two CTAs per SM, for two CTAs' reflector chains to hide each other;
-// else 256), work units of one chunk (HYBRID, FLAT) or one tile (BINARY), the largest tree
-// arity whose stacked FP64 triangles fit the chunk region.
+// Plan of the blocked mixed leaf (TSQR_LEAF_PANELS): chunks of h rows, one of kMixedWyHeights
+// (AUTO: the tallest that the width's shared and tensor memory hold), work units of one chunk
+// (HYBRID, FLAT) or one tile (BINARY), the largest tree arity whose stacked FP64 triangles fit
+// the chunk region.
 tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *p) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -1463,12 +1463,8 @@ tsqr_status_t plan_mixed_wy(int64_t m, int n, const tsqr_plan_t *over, F64Plan *
 }
 
 // The mixed path's plan: the tuned plan of the bucket for AUTO calls, then the blocked leaf
-// where it applies (TSQR_LEAF_PANELS requested, or AUTO with n <= kMixedWyMaxN where it measured
-// faster), else the fold.  Measured at 2^24 rows (ms, FP32 / BF16, fold against panels):
-// n = 8: 0.81 / 1.79 against 1.24 / 1.71; n = 12: 1.63 / 3.07 against 1.79 / 2.37; n = 16:
-// 3.79 / 7.79 against 2.32 / 3.03; n = 32: 11.1 / 14.4 against 6.2 / 7.8; n = 64: 47.6 / 57.4
-// against 24.3 / 27.7.  So AUTO takes the panels from n = 13 on for FP32, and for every n for
-// BF16 (whose fold widens each chunk through registers).
+// where it applies (TSQR_LEAF_PANELS requested, or AUTO where it measured faster, see wy_auto
+// below; up to kMixedWyMaxN columns), else the fold.
 tsqr_status_t plan_mixed(int64_t m, int n, bool bf16, const tsqr_plan_t *over, F64Plan *p) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -1483,7 +1479,9 @@ tsqr_status_t plan_mixed(int64_t m, int n, bool bf16, const tsqr_plan_t *over, F
                    over->tile_rows == 256 || over->tile_rows == 512));
     // measured at 2^24 rows: the fold wins up to n = 8 for FP32 (n = 8: 0.81 against 1.04 ms;
     // n = 9: 1.32 against 1.13) and at n <= 2 for BF16 (n = 2: 0.35 against 0.51 ms; n = 3:
-    // 0.89 against 0.62), the blocked leaf from there to 64 columns
+    // 0.89 against 0.62), the blocked leaf from there to 112 columns (FP32, fold against
+    // panels: n = 65: 48.8 against 25.7 ms; n = 96: 143.8 against 45.2; n = 112: 226.8 against
+    // 73.2; BF16 alike)
     const bool wy_auto = n <= kMixedWyMaxN && n > (bf16 ? 2 : 8);
     if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && wy_auto && wy_knobs)) {
         tsqr_plan_t o = over ? *over : tsqr_plan_t{};
@@ -1610,8 +1608,8 @@ tsqr_status_t run_batched(const void *const *ptrs, const int64_t *ms, const int3
     int nmax = 1;
     for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, (int)ns[i]);
     if (bp.leaf == TSQR_LEAF_PANELS && (!mixed || nmax > kMixedWyMaxN)) return TSQR_ERR_UNSUPPORTED;
-    // mixed batches up to 64 columns take the blocked leaf unless the plan says fold (4096-problem
-    // varlen batch, FP32: 181 ms with the fold and its tuned knobs, see the design notes)
+    // mixed batches up to 112 columns take the blocked leaf unless the plan says fold
+    // (4096-problem varlen batch, FP32: 181 ms with the fold and its tuned knobs against 81)
     const bool wy = mixed && nmax <= kMixedWyMaxN && bp.leaf != TSQR_LEAF_FOLD;
     int wy_h = 0, wy_tcols = 0;
     if (wy) {
@@ -2037,8 +2035,8 @@ tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, 
         nmax = std::max(nmax, (int)ns[i]);
     }
     st = consider(tsqr_batch_plan_t{});
-    // mixed batches up to 64 columns: the fold leaf against the blocked one first; the warps and
-    // chunk-height knobs are the fold's
+    // mixed batches up to 112 columns: the fold leaf against the blocked one first; the warps
+    // and chunk-height knobs are the fold's
     if (dt != 0 && nmax <= kMixedWyMaxN)
         for (int lf : {TSQR_LEAF_FOLD, TSQR_LEAF_PANELS}) {
             if (st != TSQR_SUCCESS) break;
@@ -2192,11 +2190,14 @@ tsqr_status_t tsqr_autotune(const void *A, int32_t dtype, int32_t prec, int64_t 
     }
     if (f64 && n >= 48 && m >= 8 * n)
         for (int32_t nb : {16, 32}) cands.push_back(tsqr_plan_t{TSQR_TREE_PANELS, nb, 0, 0, 0, 0});
-    // the blocked mixed leaf: chunks of 256 or 512 rows with as many CTAs as fit on every SM
+    // the blocked mixed leaf: every chunk height the width's shared and tensor memory hold, with
+    // 1 .. as many CTAs as fit on every SM
     if (mixed && n <= kMixedWyMaxN)
-        for (int32_t hh : {256, 512}) {
+        for (int32_t hh : kMixedWyHeights) {
             const size_t sm_b = mixed_wy_smem_bytes((int)n, hh);
-            if (sm_b > di.smem_block_optin || mixed_wy_prepare(sm_b) != cudaSuccess) continue;
+            if (sm_b + 1024 > di.smem_block_optin || !mixed_wy_tmem_fits((int)n, hh) ||
+                mixed_wy_prepare(sm_b) != cudaSuccess)
+                continue;
             const int per_sm = std::max(1, mixed_wy_blocks_per_sm(hh, sm_b));
             const int64_t units = (m + hh - 1) / hh;
             for (int k = 1; k <= per_sm; ++k)

@@ -43,9 +43,9 @@ cudaError_t mixed_launch(const MixedArgs &a, bool bf16, int warps, size_t smem_b
                          cudaStream_t stream);
 
 // Blocked mixed path (tsqr_mixed_wy.cu): panels of 16 columns, compact WY updates on the
-// tensor cores; n <= kMixedWyMaxN, chunks of h = 256, 512, 640, 768 or 1024 rows, 8 warps.
-constexpr int kMixedWyMaxN = 64;
-constexpr int kMixedWyHeights[5] = {1024, 768, 640, 512, 256};  // tallest first
+// tensor cores; n <= kMixedWyMaxN, chunks of h = 256, 384, 512, 640, 768 or 1024 rows, 8 warps.
+constexpr int kMixedWyMaxN = 112;
+constexpr int kMixedWyHeights[6] = {1024, 768, 640, 512, 384, 256};  // tallest first
 size_t mixed_wy_smem_bytes(int n, int h);
 bool mixed_wy_tmem_fits(int n, int h);
 int mixed_wy_arity(int n, int h);

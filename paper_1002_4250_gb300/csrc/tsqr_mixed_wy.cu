@@ -695,16 +695,19 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 
     // ---- 2a. Z = X^T C(:, T) on the tensor cores.  The 8 warps are KG row groups x TS sets of
     //          n-tiles (8 columns each): a warp splits its X fragments once per 8 rows and uses
-    //          them for every tile of its set.  Per tile three accumulators (below); partial
-    //          tiles per row group go to P.
+    //          them for up to three tiles of its set at a time (a set of more tiles, past 64
+    //          columns, takes several rounds over its rows).  Per tile three accumulators
+    //          (below); partial tiles per row group go to P (KG NT8 <= kMaxPartials).
     const int NT8 = ntp / 8;
-    const int TS = NT8 >= 4 ? 2 : 1;          // tile sets
-    const int TPS = (NT8 + TS - 1) / TS;      // tiles per set (<= 3 for n <= 64)
-    const int KG = kWarps / TS;               // row groups
+    // tile sets: the fewest (1, 2 or 4) whose KG NT8 partial tiles fit P (24 tiles: NT8 <= 3
+    // with 8 row groups, <= 6 with 4, <= 12 with 2)
+    const int TS = NT8 >= 7 ? 4 : NT8 >= 4 ? 2 : 1;
+    const int TPS = (NT8 + TS - 1) / TS;  // tiles per set (<= 3 for n <= 64)
+    const int KG = kWarps / TS;           // row groups
     const int g4 = lane >> 2, t4 = lane & 3;
-    {
-        const int grp = warp / TS, set = warp % TS;
-        const int jt0 = set * TPS, jt1 = min(NT8, jt0 + TPS);
+    const int grp = warp / TS, set = warp % TS;
+    const int jt1 = min(NT8, set * TPS + TPS);
+    for (int jt0 = set * TPS; jt0 < jt1; jt0 += 3) {
         const int r0 = grp * (h / KG), r1 = r0 + h / KG;
         // three accumulators per tile, smallest products first: ea (X_mid C_mid, X_lo C_hi,
         // X_hi C_lo), eb (X_mid C_hi, X_hi C_mid), hh (X_hi C_hi): shorter dependent mma chains
@@ -975,7 +978,7 @@ __global__ void __launch_bounds__(kThreads, HB == 2 ? 2 : 1)
     wy_climb(sm, L, b, a.ldSd, leaf);
 }
 
-// A varlen batch of mixed-precision problems (n <= 64), one persistent launch: every CTA takes
+// A varlen batch of mixed-precision problems (n <= 112), one persistent launch: every CTA takes
 // (problem, leaf) items from the queue (largest first), folds the leaf's rows with thread
 // copies and climbs that problem's tree; the chunk height h is the batch's.  The tensor
 // memory (tcols columns, enough for the widest problem) and the update's mbarrier are held for
@@ -1063,6 +1066,7 @@ const void *wy_fn(int hb) {
         case 6: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 6>;
         case 5: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 5>;
         case 4: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 4>;
+        case 3: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 3>;
         default: return (const void *)wy::tsqr_mixed_wy_kernel<Tin, 2>;
     }
 }
@@ -1075,6 +1079,7 @@ void wy_launch_t(const wy::WyArgs2 &a, const CUtensorMap &tmap, int hb, size_t s
         case 6: wy::tsqr_mixed_wy_kernel<Tin, 6><<<grid, block, smem, stream>>>(a, tmap); break;
         case 5: wy::tsqr_mixed_wy_kernel<Tin, 5><<<grid, block, smem, stream>>>(a, tmap); break;
         case 4: wy::tsqr_mixed_wy_kernel<Tin, 4><<<grid, block, smem, stream>>>(a, tmap); break;
+        case 3: wy::tsqr_mixed_wy_kernel<Tin, 3><<<grid, block, smem, stream>>>(a, tmap); break;
         default: wy::tsqr_mixed_wy_kernel<Tin, 2><<<grid, block, smem, stream>>>(a, tmap); break;
     }
 }
@@ -1125,7 +1130,7 @@ bool make_tensor_map(const void *A, bool bf16, int64_t m, int n, int64_t lda, CU
 // The layout plus 1024 bytes to align its base to the swizzle period.
 size_t mixed_wy_smem_bytes(int n, int h) { return (size_t)wy::layout(n, h).total + 1024; }
 
-// Whether an h-row chunk (h = 256, 512, 640, 768 or 1024) fits the tensor memory for width n.
+// Whether an h-row chunk (h = 256, 384, 512, 640, 768 or 1024) fits the tensor memory for width n.
 bool mixed_wy_tmem_fits(int n, int h) { return wy::tmem_need(n, h) <= 512; }
 
 // Largest arity (<= 8) whose stacked FP64 triangles fit in the chunk region of an h-row leaf.
@@ -1141,8 +1146,9 @@ bool mixed_wy_tree_fits(int n, int h, int arity) {
 }
 
 cudaError_t mixed_wy_prepare(size_t smem_bytes) {
-    const void *fns[10] = {wy_fn<float>(2), wy_fn<float>(4), wy_fn<float>(5), wy_fn<float>(6),
-                           wy_fn<float>(8), wy_fn<__nv_bfloat16>(2), wy_fn<__nv_bfloat16>(4),
+    const void *fns[12] = {wy_fn<float>(2), wy_fn<float>(3), wy_fn<float>(4), wy_fn<float>(5),
+                           wy_fn<float>(6), wy_fn<float>(8), wy_fn<__nv_bfloat16>(2),
+                           wy_fn<__nv_bfloat16>(3), wy_fn<__nv_bfloat16>(4),
                            wy_fn<__nv_bfloat16>(5), wy_fn<__nv_bfloat16>(6),
                            wy_fn<__nv_bfloat16>(8)};
     for (const void *f : fns) {
@@ -1184,7 +1190,7 @@ cudaError_t mixed_wy_launch(const F64Args &base, const void *A, bool bf16, int l
     return cudaGetLastError();
 }
 
-// ---- the varlen batch (tsqr_r_batched's mixed problems up to 64 columns)
+// ---- the varlen batch (tsqr_r_batched's mixed problems up to 112 columns)
 namespace {
 const void *bwy_fn(bool bf16, int hb) {
     if (bf16) {
@@ -1193,6 +1199,7 @@ const void *bwy_fn(bool bf16, int hb) {
             case 6: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 6>;
             case 5: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 5>;
             case 4: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 4>;
+            case 3: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 3>;
             default: return (const void *)wy::tsqr_batched_wy_kernel<__nv_bfloat16, 2>;
         }
     }
@@ -1201,6 +1208,7 @@ const void *bwy_fn(bool bf16, int hb) {
         case 6: return (const void *)wy::tsqr_batched_wy_kernel<float, 6>;
         case 5: return (const void *)wy::tsqr_batched_wy_kernel<float, 5>;
         case 4: return (const void *)wy::tsqr_batched_wy_kernel<float, 4>;
+        case 3: return (const void *)wy::tsqr_batched_wy_kernel<float, 3>;
         default: return (const void *)wy::tsqr_batched_wy_kernel<float, 2>;
     }
 }
@@ -1232,6 +1240,7 @@ cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, in
             case 6: TSQR_BWY(__nv_bfloat16, 6); break;
             case 5: TSQR_BWY(__nv_bfloat16, 5); break;
             case 4: TSQR_BWY(__nv_bfloat16, 4); break;
+            case 3: TSQR_BWY(__nv_bfloat16, 3); break;
             default: TSQR_BWY(__nv_bfloat16, 2); break;
         }
     } else {
@@ -1240,6 +1249,7 @@ cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, in
             case 6: TSQR_BWY(float, 6); break;
             case 5: TSQR_BWY(float, 5); break;
             case 4: TSQR_BWY(float, 4); break;
+            case 3: TSQR_BWY(float, 3); break;
             default: TSQR_BWY(float, 2); break;
         }
     }

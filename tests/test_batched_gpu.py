@@ -289,7 +289,7 @@ def _odd_mixed_batch(dtype, widths=(1, 3, 8, 16, 17, 33, 48, 64)):
 @pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
 @pytest.mark.parametrize("leaf", ["auto", "fold", "panels"])
 def test_batched_mixed_leaves(oracle, T, dtype, leaf):
-    """The mixed batch on either leaf (the blocked one is AUTO up to 64 columns): every
+    """The mixed batch on either leaf (the blocked one is AUTO up to 112 columns): every
     problem's R upper triangular with diag >= 0 and R^T R = A^T A within 2e-6, including
     m = 0, m < n, one row, one column and ragged chunks."""
     import torch
@@ -336,7 +336,7 @@ def test_batched_panels_reproducible_and_graph(T):
 
 
 def test_batched_panels_refused(T):
-    """The blocked leaf is mixed precision up to 64 columns: an FP64 batch or a wider problem
+    """The blocked leaf is mixed precision up to 112 columns: an FP64 batch or a wider problem
     asks for it in vain."""
     import torch
     A = torch.zeros(100 * 80, dtype=torch.float64, device="cuda")
@@ -345,8 +345,38 @@ def test_batched_panels_refused(T):
         T.tsqr_r_batched([A.data_ptr()], [100], [8], [0, 64], Rp,
                          plan=T.make_batch_plan(leaf="panels"))
     assert e.value.status == T.ERR_UNSUPPORTED
-    A32 = torch.zeros(100 * 80, dtype=torch.float32, device="cuda")
+    A32 = torch.zeros(200 * 120, dtype=torch.float32, device="cuda")
+    Rw = torch.zeros(120 * 120, dtype=torch.float64, device="cuda")
     with pytest.raises(T.TsqrError) as e:
-        T.tsqr_r_batched([A32.data_ptr()], [100], [80], [0, 6400], Rp, dtype=T.F32,
+        T.tsqr_r_batched([A32.data_ptr()], [200], [120], [0, 14400], Rw, dtype=T.F32,
                          prec=T.PREC_MIXED, plan=T.make_batch_plan(leaf="panels"))
     assert e.value.status == T.ERR_UNSUPPORTED
+
+
+def test_batched_mixed_wide_problem_takes_the_fold(oracle, T):
+    """A mixed batch with a problem wider than 112 columns runs on the fold leaf as a whole
+    (AUTO), and every problem's R is right."""
+    import torch
+    buf, ms, ns, offs = _odd_mixed_batch(torch.float32, widths=(8, 16, 120, 33, 64))
+    bd = buf.cuda()
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=T.F32, prec=T.PREC_MIXED)
+    assert T.last_batch_plan().leaf == T.LEAF_FOLD
+    torch.cuda.synchronize()
+    _check_all(oracle, buf.to(torch.float64).numpy(), ms, ns, offs, Rp.cpu().numpy(), roff, 2e-6)
+
+
+@pytest.mark.parametrize("leaf", ["auto", "panels"])
+def test_batched_panels_wide(oracle, T, leaf):
+    """A mixed batch up to 112 columns on the blocked leaf, AUTO or asked for."""
+    import torch
+    buf, ms, ns, offs = _odd_mixed_batch(torch.float32, widths=(8, 100, 65, 112, 33))
+    bd = buf.cuda()
+    ptrs, roff = _ptrs_roff(bd, ms, ns, offs)
+    Rp = torch.full((roff[-1],), float("nan"), dtype=torch.float64, device="cuda")
+    T.tsqr_r_batched(ptrs, ms, ns, roff, Rp, dtype=T.F32, prec=T.PREC_MIXED,
+                     plan=T.make_batch_plan(leaf=leaf))
+    assert T.last_batch_plan().leaf == T.LEAF_PANELS
+    torch.cuda.synchronize()
+    _check_all(oracle, buf.to(torch.float64).numpy(), ms, ns, offs, Rp.cpu().numpy(), roff, 2e-6)

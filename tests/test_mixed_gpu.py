@@ -192,3 +192,42 @@ def test_mixed_leaves_conditioned_report(oracle, T, leaf):
     res, err, kap = _check(oracle, T, At, plan=T.make_plan(leaf=leaf))
     print(f"\n{leaf}: gram residual {res:.3e}, |R - R_oracle|/|R_oracle| {err:.3e}, "
           f"50 kappa u32 {50 * kap * U32:.3e}")
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_panels_leaf_nonfinite_input_is_reported(T, dtype, bad):
+    """A NaN or Inf in A propagates into R and sets the non-finite status (no wait gives up);
+    the next clean call is clean again."""
+    import torch
+    dt = getattr(torch, dtype)
+    At = workloads.gaussian(70001, 48, seed=31, dtype=dt)
+    At[17, 40000] = bad
+    T.tsqr_get_device_status()  # clear
+    R = T.tsqr_r_ex(At.cuda().T, plan=T.make_plan(leaf="panels"))
+    assert T.tsqr_get_device_status() == T.STATUS_NONFINITE
+    assert not torch.isfinite(R).all()
+    R = T.tsqr_r_ex(workloads.gaussian(70001, 48, seed=31, dtype=dt).cuda().T,
+                    plan=T.make_plan(leaf="panels"))
+    assert T.tsqr_get_device_status() == T.SUCCESS
+    assert torch.isfinite(R).all()
+
+
+@pytest.mark.parametrize("dtype", ["float32", "bfloat16"])
+@pytest.mark.parametrize("n", [65, 72, 80, 81, 96, 97, 112])
+def test_panels_leaf_wide(oracle, T, dtype, n):
+    """The blocked leaf past 64 columns, at the chunk height the width's memory allows (512 rows
+    to 80 columns, 384 to 96, 256 to 112), with a ragged last chunk; against the oracle.  AUTO
+    takes it too, and its plan passed back gives the same bytes."""
+    import torch
+    m = 30011
+    At = workloads.gaussian(m, n, seed=500 + n, dtype=getattr(torch, dtype))
+    _check(oracle, T, At, plan=T.make_plan(leaf="panels"))
+    used = T.last_plan()
+    assert used.leaf == T.LEAF_PANELS
+    assert used.tile_rows == (512 if n <= 80 else 384 if n <= 96 else 256)
+    Ad = At.cuda().T
+    Ra = T.tsqr_r_ex(Ad)
+    auto = T.last_plan()
+    assert auto.leaf == T.LEAF_PANELS
+    assert torch.equal(T.tsqr_r_ex(Ad, plan=auto), Ra)
