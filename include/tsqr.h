@@ -85,7 +85,7 @@ typedef enum {
  *         every later column by the CUDA cores (FP32 bulk arithmetic, FP64 R and scalars); any
  *         n <= TSQR_MAX_N.
  * PANELS: the same fold by panels of 16 columns: each panel factorized column by column in
- *         registers (the reflector norms, sums and scalars in double-FP32, about 48 bits),
+ *         registers (FP32 dot products; the reflector scalars in double-FP32, about 48 bits),
  *         then applied to the columns right of it as one compact WY block (I - V S V^T) whose
  *         two products run on the tensor cores as split-TF32 products with FP32 accumulation
  *         (each as accurate as an FP32 dot product); R in double-FP32 in the leaf, FP64 in the

@@ -9,11 +9,12 @@
 //      16 dot products of column J with every panel column (its squared norm, the dot
 //      products with the earlier tails that the block's T factor needs, and those with the
 //      later columns).
-//      The per-lane partials are FP32 (one or two rows); every sum across lanes and warps and
-//      every reflector scalar (beta, tau, 1/(alpha - beta)) is in double-FP32 arithmetic
-//      (hi + lo pairs, about 44-48 bits) on the FP32 pipe.  Per reflector: every warp sums its
-//      lanes' partials, one barrier, warp 0 sums the warps' and forms the scalars, row J of R
-//      and the factors of the later columns, a second barrier.
+//      The per-lane partials (up to eight rows) and their sums over a warp's lanes are FP32;
+//      the sums over the warps and every reflector scalar (beta, tau, 1/(alpha - beta)) are in
+//      double-FP32 arithmetic (hi + lo pairs, about 44-48 bits) on the FP32 pipe.  Per
+//      reflector: every panel warp sums its lanes' partials, one barrier, then every panel warp
+//      forms the FP32 factors of the later columns while a scalar warp forms the reflector's
+//      double-FP32 scalars and row J of R.
 //   2. Compact WY form of the panel: with the tails x_J kept UNSCALED in the chunk and
 //      v_J = [e_J; c_J x_J], the product H_0 ... H_15 equals I - V S V^T (LAPACK's dlarft
 //      forward recurrence, S^-1 = diag(1 / tau) + strict_upper(G) in Joffrain et al.'s form),
@@ -30,7 +31,8 @@
 // Why this precision split: everything that multiplies the running triangle R (the reflector
 // scalars, S, the R rows) is accurate to far below FP32 rounding, so R's accumulated content
 // is transformed orthogonally to that accuracy chunk after chunk; the FP32 roundings land in
-// the chunk's rows.  The tails being exactly three TF32 parts makes the V the tensor cores use
+// the chunk's rows.  The dot products carry FP32 rounding (the per-lane partials and the lane
+// sums), an error relative to the chunk's entries like the FP32 update's own.  The tails being exactly three TF32 parts makes the V the tensor cores use
 // and the V that S is built from the same matrix: the tails are used exactly as stored.
 #include <cuda.h>  // CUtensorMap and its encoding enums (the driver call is found at run time)
 #include <cuda_bf16.h>
@@ -224,43 +226,38 @@ __host__ __device__ inline Layout layout(int n, int h) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Warp-wide sums of 16 FP32 partials per lane, in double-FP32: a transposing butterfly (each
-// level halves the values a lane keeps and exchanges the other half with its partner), five
-// levels, 16 exchanges.  Lane l ends with the sum of value idx(l) = 8 b4 + 4 b3 + 2 b2 + b1
-// (bi = bit i of l); lanes l and l ^ 1 hold the same bits.  Fixed order: bit-reproducible.
+// Warp-wide FP32 sums of 16 partials per lane: a transposing butterfly (each level halves the
+// values a lane keeps and exchanges the other half with its partner), five levels, 16
+// exchanges and 16 additions.  Lane l ends with the sum of value idx(l) = 8 b4 + 4 b3 + 2 b2 +
+// b1 (bi = bit i of l); lanes l and l ^ 1 hold the same value.  Fixed order: bit-reproducible.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ df warp_sum16(const float (&v)[16], const int lane) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
-    df a[8];
+__device__ __forceinline__ float warp_sum16_f(const float (&v)[16], const int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const float send = b4 ? v[i] : v[i + 8];
         const float keep = b4 ? v[i + 8] : v[i];
-        const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
-        a[i] = b4 ? two_sum(recv, keep) : two_sum(keep, recv);
+        a[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 16));
     }
-    df b[4];
+    float b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const df send = b3 ? a[i] : a[i + 4];
-        const df keep = b3 ? a[i + 4] : a[i];
-        const df recv = shfl_xor_df(send, 8);
-        b[i] = b3 ? dadd(recv, keep) : dadd(keep, recv);
+        const float send = b3 ? a[i] : a[i + 4];
+        const float keep = b3 ? a[i + 4] : a[i];
+        b[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 8));
     }
-    df c[2];
+    float c[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const df send = b2 ? b[i] : b[i + 2];
-        const df keep = b2 ? b[i + 2] : b[i];
-        const df recv = shfl_xor_df(send, 4);
-        c[i] = b2 ? dadd(recv, keep) : dadd(keep, recv);
+        const float send = b2 ? b[i] : b[i + 2];
+        const float keep = b2 ? b[i + 2] : b[i];
+        c[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 4));
     }
-    const df send = b1 ? c[0] : c[1];
-    const df keep = b1 ? c[1] : c[0];
-    const df recv = shfl_xor_df(send, 2);
-    const df d = b1 ? dadd(recv, keep) : dadd(keep, recv);
-    const df e = shfl_xor_df(d, 1);
-    return b0 ? dadd(e, d) : dadd(d, e);
+    const float send = b1 ? c[0] : c[1];
+    const float keep = b1 ? c[1] : c[0];
+    const float d = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 2));
+    return __fadd_rn(d, __shfl_xor_sync(0xffffffffu, d, 1));  // commutative: l, l ^ 1 agree
 }
 __device__ __forceinline__ int sum16_index(int lane) {
     return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
@@ -451,9 +448,8 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
 __host__ __device__ constexpr int panel_warps(int hb) { return hb > 0 ? 4 : 8; }
 
 // Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
-// CTA.
-// With four panel warps: barrier 1 (the sums are in) also takes the scalar warp, barrier 2
-// (the factors are in) only the panel warps.
+// CTA.  With four panel warps, barrier 1 (the sums are in) also takes the scalar warp and is
+// the column's only barrier; barrier 2 (the factors are in) serves the eight-warp form.
 template <int PW, int ID>
 __device__ __forceinline__ void panel_sync() {
     if constexpr (PW == kWarps) {
@@ -525,10 +521,9 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     const int J0 = kPw * k;
     const int pw = min(kPw, n - J0);
 
-    // ---- 1. panel factorization in registers, by PW warps (one per sub-partition for chunks
-    //         of up to 512 rows, whose lanes then hold PR = h / (32 PW) rows each: half the
-    //         warp-level reductions per row of eight warps; all eight for taller chunks, whose
-    //         rows would not fit the registers of four)
+    // ---- 1. panel factorization in registers, by PW = 4 warps (one per sub-partition, whose
+    //         lanes hold PR = h / 128 rows each, up to 8: half the warp-level reductions per
+    //         row of eight warps)
     constexpr int PW = panel_warps(HB);
     constexpr int PR = h / (32 * PW);
     const bool panel_warp = warp < PW;
@@ -576,35 +571,35 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             // warp updates the row after it
             const int Jg = J0 + J;
             float a_f = 0.f, r_f = 0.f;
-            if (PW == 4 && warp == 0) {
+            if (PW == 4) {
                 a_f = Rd[rowoff(n, Jg)].hi;
                 const int vi = lane & 15;
                 if (vi > J && vi < pw) r_f = Rd[rowoff(n, Jg) + vi - J].hi;
             }
-            const df ws = warp_sum16(v, lane);
+            const df ws = mk(warp_sum16_f(v, lane));  // lo = 0: the scalar warp adds exactly
             df *rb = red + (J & 1) * kWarps * 16;
             if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
             panel_sync<PW, 1>();
             if constexpr (PW == 4) {
-                if (warp == 0) {
-                    // the factors f_k of the panel update, in FP32 (the update itself is FP32)
-                    // from the FP32 parts of the sums; the scalar warp forms the reflector's
-                    // double-FP32 scalars and row Jg of R meanwhile
-                    const int vi = lane & 15;
-                    const float tf = __fadd_rn(__fadd_rn(rb[vi].hi, rb[16 + vi].hi),
-                                               __fadd_rn(rb[32 + vi].hi, rb[48 + vi].hi));
-                    const float sig = __shfl_sync(0xffffffffu, tf, J);
-                    float fk = 0.f;
-                    if (sig != 0.f && vi > J && vi < pw) {
-                        // the hardware's approximate square root and reciprocals (about
-                        // 2^-22): a few FP32 ulps in f_k, the size of the update's own rounding
-                        const float rt = sqrt_approx(__fmaf_rn(a_f, a_f, sig));
-                        const float beta = a_f >= 0.f ? -rt : rt;
-                        const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
-                        fk = -__fmul_rn(w, rcp_approx(beta));
-                    }
-                    if (lane < 16) fsh[vi] = fk;
+                // every panel warp forms the factors f_k of the panel update (lane k & 15
+                // holds f_k), in FP32 (the update itself is FP32) from the FP32 parts of the
+                // sums; the scalar warp forms the reflector's double-FP32 scalars and row Jg of
+                // R meanwhile
+                const int vi = lane & 15;
+                const float tf = __fadd_rn(__fadd_rn(rb[vi].hi, rb[16 + vi].hi),
+                                           __fadd_rn(rb[32 + vi].hi, rb[48 + vi].hi));
+                const float sig = __shfl_sync(0xffffffffu, tf, J);
+                float fk = 0.f;
+                if (sig != 0.f && vi > J && vi < pw) {
+                    // the hardware's approximate square root and reciprocals (about 2^-22): a
+                    // few FP32 ulps in f_k, the size of the update's own rounding
+                    const float rt = sqrt_approx(__fmaf_rn(a_f, a_f, sig));
+                    const float beta = a_f >= 0.f ? -rt : rt;
+                    const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
+                    fk = -__fmul_rn(w, rcp_approx(beta));
                 }
+#pragma unroll
+                for (int kk = 0; kk < kPw; ++kk) fv[kk] = __shfl_sync(0xffffffffu, fk, kk);
             } else {
                 if (warp == 0) {
                     // the cross-warp sums (value lane & 15; lanes 0-15 over warps 0-3, 16-31
@@ -619,19 +614,19 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                     const float fk = scalar_update(sm, L, n, J0, J, pw, lane, tot, true);
                     if (lane < 16) fsh[vi] = fk;
                 }
-            }
-            panel_sync<PW, 2>();
+                panel_sync<PW, 2>();
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
+                for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
+            }
 #pragma unroll
             for (int q = 0; q < PR; ++q) xp[q] = xj[q];
         }
     }
     if (PW == 4 && warp == PW) {
-        // the scalar warp: after each column's first barrier, reflector J's double-FP32
-        // scalars and row Jg of R from the cross-warp sums, while warp 0 forms the factors and
-        // the panel warps go on with the next column (its buffer of sums is rewritten only
-        // after the panel warps have passed the next barrier 1, which waits for this warp)
+        // the scalar warp: after each column's barrier, reflector J's double-FP32 scalars and
+        // row Jg of R from the cross-warp sums, while the panel warps form the factors and go
+        // on with the next column (a buffer of sums is rewritten only after every panel warp
+        // and this warp have passed the next column's barrier, so after their reads of it)
 #pragma unroll 1
         for (int J = 0; J < pw; ++J) {
             panel_sync<PW, 1>();
