@@ -185,7 +185,6 @@ struct Layout {
     int S;      // 16 x 16 df (column-major)
     int bar;    // the update's mbarrier (8 bytes), the tensor-memory address (4 bytes), and
                 // from byte 16 one mbarrier per panel for the chunk's TMA loads
-    int fsh;    // 16 floats: the factors f_k of the reflector just formed
     int W;      // 16 x ntmax df: W, then Y
     int B;      // diag(c) Y in three TF32 parts, K-major operands of 16 x ntmax16 each
     int P;      // kMaxPartials x 16 x 8 floats: partial Z tiles
@@ -209,7 +208,6 @@ __host__ __device__ inline Layout layout(int n, int h) {
     L.G = o;   o += 16 * 16 * 8;
     L.S = o;   o += 16 * 16 * 8;
     L.bar = o; o += 16 + 8 * 8;
-    L.fsh = o; o += 16 * 4;
     const int chunk_end_base = o;
     L.W = o;   o += 16 * ntmax * 8;
     L.B = o;   o += 3 * ntmax16 * 64;
@@ -444,31 +442,22 @@ __host__ __device__ constexpr uint32_t tmem_cols(int n, int h) {
 }
 
 // Warps that factorize a panel of h = 128 HB rows: four, one per sub-partition (HB rows per
-// lane, up to 8, which the registers hold); the eight-warp form is kept for reference.
-__host__ __device__ constexpr int panel_warps(int hb) { return hb > 0 ? 4 : 8; }
+// lane, up to 8, which the registers hold), and warp kPanelWarps, the scalar warp.
+constexpr int kPanelWarps = 4;
 
-// Barrier of the PW panel warps (warps 0 .. PW-1): named barrier 1 when they are not the whole
-// CTA.  With four panel warps, barrier 1 (the sums are in) also takes the scalar warp and is
-// the column's only barrier; barrier 2 (the factors are in) serves the eight-warp form.
-template <int PW, int ID>
+// A column's barrier (named barrier 1): the panel warps and the scalar warp, once the warps'
+// sums are in.
 __device__ __forceinline__ void panel_sync() {
-    if constexpr (PW == kWarps) {
-        __syncthreads();
-    } else if constexpr (ID == 1) {
-        asm volatile("bar.sync 1, %0;\n" ::"n"((PW + 1) * 32) : "memory");
-    } else {
-        asm volatile("bar.sync 2, %0;\n" ::"n"(PW * 32) : "memory");
-    }
+    asm volatile("bar.sync 1, %0;\n" ::"n"((kPanelWarps + 1) * 32) : "memory");
 }
 
 // Reflector J's double-FP32 scalars from the sums tot (lane l: value l & 15; tot of lane J is
 // the squared norm of the tail) and alpha = R(Jg, Jg): row Jg of R (R(Jg, Jg) = beta and
 // R(Jg, k) -= tau w_k, w_k = R(Jg, k) + c (x_J . x_k)), tau and c for the T factor, the dots
-// with the earlier tails into G.  With want_f, returns this lane's factor f_k = -w_k / beta
-// rounded to FP32 (0 for lanes outside J < k < pw, and for an identity reflector).
-__device__ __forceinline__ float scalar_update(unsigned char *sm, const Layout &L, const int n,
-                                               const int J0, const int J, const int pw,
-                                               const int lane, const df tot, const bool want_f) {
+// with the earlier tails into G.
+__device__ __forceinline__ void scalar_update(unsigned char *sm, const Layout &L, const int n,
+                                              const int J0, const int J, const int pw,
+                                              const int lane, const df tot) {
     df *Rd = reinterpret_cast<df *>(sm + L.R);
     df *tau_s = reinterpret_cast<df *>(sm + L.tau);
     df *c_s = reinterpret_cast<df *>(sm + L.cc);
@@ -477,16 +466,11 @@ __device__ __forceinline__ float scalar_update(unsigned char *sm, const Layout &
     const int Jg = J0 + J;
     const df alpha = Rd[rowoff(n, Jg)];
     const Refl rf = make_refl(alpha, shfl_df(tot, J));
-    float fk = 0.f;
     if (lane < 16) {
         if (vi > J && vi < pw && !rf.ident) {
             df *rjk = Rd + rowoff(n, Jg) + vi - J;
             const df wk = dadd(*rjk, dmul(rf.c, tot));
             *rjk = dsub(*rjk, dmul(rf.tau, wk));
-            if (want_f) {
-                const df f = dneg(dmul(wk, rf.ib));
-                fk = __fadd_rn(f.hi, f.lo);
-            }
         }
         if (vi < J) G[vi * 16 + J] = tot;  // x_vi . x_J (scaled in s_factor)
         if (vi == J) {
@@ -495,7 +479,6 @@ __device__ __forceinline__ float scalar_update(unsigned char *sm, const Layout &
             Rd[rowoff(n, Jg)] = rf.beta;
         }
     }
-    return fk;
 }
 
 // With TMA loads (t != nullptr): panel 0 has arrived when this is called; panel 0 waits for
@@ -524,7 +507,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     // ---- 1. panel factorization in registers, by PW = 4 warps (one per sub-partition, whose
     //         lanes hold PR = h / 128 rows each, up to 8: half the warp-level reductions per
     //         row of eight warps)
-    constexpr int PW = panel_warps(HB);
+    constexpr int PW = kPanelWarps;
     constexpr int PR = h / (32 * PW);
     const bool panel_warp = warp < PW;
     float x[PR][kPw];
@@ -535,7 +518,6 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
             for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
         }
-        float *fsh = reinterpret_cast<float *>(sm + L.fsh);
         // The loop over the panel's columns is not unrolled (one copy of its body keeps the
         // instruction cache warm); the register columns are addressed with static indices.
         float fv[kPw], xp[PR];
@@ -567,73 +549,50 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                 for (int q = 1; q < PR; ++q) sacc = __fmaf_rn(xj[q], x[q][kk], sacc);
                 v[kk] = sacc;
             }
-            // row Jg of R (FP32 parts) for the factors below, read before barrier 1: the scalar
-            // warp updates the row after it
+            // row Jg of R (FP32 parts) for the factors below, read before the barrier: the
+            // scalar warp updates the row after it
             const int Jg = J0 + J;
-            float a_f = 0.f, r_f = 0.f;
-            if (PW == 4) {
-                a_f = Rd[rowoff(n, Jg)].hi;
-                const int vi = lane & 15;
-                if (vi > J && vi < pw) r_f = Rd[rowoff(n, Jg) + vi - J].hi;
-            }
-            const df ws = mk(warp_sum16_f(v, lane));  // lo = 0: the scalar warp adds exactly
+            const int vi = lane & 15;
+            const float a_f = Rd[rowoff(n, Jg)].hi;
+            const float r_f = (vi > J && vi < pw) ? Rd[rowoff(n, Jg) + vi - J].hi : 0.f;
+            const float ws = warp_sum16_f(v, lane);
             df *rb = red + (J & 1) * kWarps * 16;
-            if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = ws;
-            panel_sync<PW, 1>();
-            if constexpr (PW == 4) {
-                // every panel warp forms the factors f_k of the panel update (lane k & 15
-                // holds f_k), in FP32 (the update itself is FP32) from the FP32 parts of the
-                // sums; the scalar warp forms the reflector's double-FP32 scalars and row Jg of
-                // R meanwhile
-                const int vi = lane & 15;
-                const float tf = __fadd_rn(__fadd_rn(rb[vi].hi, rb[16 + vi].hi),
-                                           __fadd_rn(rb[32 + vi].hi, rb[48 + vi].hi));
-                const float sig = __shfl_sync(0xffffffffu, tf, J);
-                float fk = 0.f;
-                if (sig != 0.f && vi > J && vi < pw) {
-                    // the hardware's approximate square root and reciprocals (about 2^-22): a
-                    // few FP32 ulps in f_k, the size of the update's own rounding
-                    const float rt = sqrt_approx(__fmaf_rn(a_f, a_f, sig));
-                    const float beta = a_f >= 0.f ? -rt : rt;
-                    const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
-                    fk = -__fmul_rn(w, rcp_approx(beta));
-                }
-#pragma unroll
-                for (int kk = 0; kk < kPw; ++kk) fv[kk] = __shfl_sync(0xffffffffu, fk, kk);
-            } else {
-                if (warp == 0) {
-                    // the cross-warp sums (value lane & 15; lanes 0-15 over warps 0-3, 16-31
-                    // over warps 4-7), reflector J's scalars, row Jg of R and the factors f_k;
-                    // the other panel warps wait for the factors at the next barrier
-                    const int vi = lane & 15, half = lane >> 4;
-                    const df s01 = dadd(rb[(4 * half) * 16 + vi], rb[(4 * half + 1) * 16 + vi]);
-                    const df s23 = dadd(rb[(4 * half + 2) * 16 + vi], rb[(4 * half + 3) * 16 + vi]);
-                    const df s4 = dadd(s01, s23);
-                    const df o = shfl_xor_df(s4, 16);
-                    const df tot = half ? dadd(o, s4) : dadd(s4, o);
-                    const float fk = scalar_update(sm, L, n, J0, J, pw, lane, tot, true);
-                    if (lane < 16) fsh[vi] = fk;
-                }
-                panel_sync<PW, 2>();
-#pragma unroll
-                for (int kk = 0; kk < kPw; ++kk) fv[kk] = fsh[kk];
+            if ((lane & 1) == 0) rb[warp * 16 + sum16_index(lane)] = mk(ws);  // lo = 0: exact adds
+            panel_sync();
+            // every panel warp forms the factors f_k of the panel update (lane k forms f_k), in
+            // FP32 (the update itself is FP32) from the warps' FP32 sums; the scalar warp forms
+            // the reflector's double-FP32 scalars and row Jg of R meanwhile
+            const float tf = __fadd_rn(__fadd_rn(rb[vi].hi, rb[16 + vi].hi),
+                                       __fadd_rn(rb[32 + vi].hi, rb[48 + vi].hi));
+            const float sig = __fadd_rn(__fadd_rn(rb[J].hi, rb[16 + J].hi),
+                                        __fadd_rn(rb[32 + J].hi, rb[48 + J].hi));
+            float fk = 0.f;
+            if (sig != 0.f && vi > J && vi < pw) {
+                // the hardware's approximate square root and reciprocals (about 2^-22): a few
+                // FP32 ulps in f_k, the size of the update's own rounding
+                const float rt = sqrt_approx(__fmaf_rn(a_f, a_f, sig));
+                const float beta = a_f >= 0.f ? -rt : rt;
+                const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
+                fk = -__fmul_rn(w, rcp_approx(beta));
             }
+#pragma unroll
+            for (int kk = 0; kk < kPw; ++kk) fv[kk] = __shfl_sync(0xffffffffu, fk, kk);
 #pragma unroll
             for (int q = 0; q < PR; ++q) xp[q] = xj[q];
         }
     }
-    if (PW == 4 && warp == PW) {
+    if (warp == PW) {
         // the scalar warp: after each column's barrier, reflector J's double-FP32 scalars and
         // row Jg of R from the cross-warp sums, while the panel warps form the factors and go
         // on with the next column (a buffer of sums is rewritten only after every panel warp
         // and this warp have passed the next column's barrier, so after their reads of it)
 #pragma unroll 1
         for (int J = 0; J < pw; ++J) {
-            panel_sync<PW, 1>();
+            panel_sync();
             const df *rb = red + (J & 1) * kWarps * 16;
             const int vi = lane & 15;
             const df tot = dadd(dadd(rb[vi], rb[16 + vi]), dadd(rb[32 + vi], rb[48 + vi]));
-            scalar_update(sm, L, n, J0, J, pw, lane, tot, false);
+            scalar_update(sm, L, n, J0, J, pw, lane, tot);
         }
     }
     if (J0 + kPw < n) {  // S is needed only where columns right of the panel remain
