@@ -145,21 +145,28 @@ __device__ __forceinline__ Refl make_refl(const df alpha, const df sig2) {
 }
 
 // ------------------------------------------------------------------------------------------
-// TF32 parts.  to_tf32 rounds to 11 significant bits (nearest, ties away).
+// TF32 parts: tf32_trunc keeps the top 11 significant bits (the low 13 fraction bits cleared,
+// one logic instruction; rounding with cvt.rna.tf32 instead cost 9% of the leaf's time at
+// n = 64).
 // ------------------------------------------------------------------------------------------
-// x (FP32, 24 bits) = h + m + l exactly
-__device__ __forceinline__ void split3(float x, float &h, float &m, float &l) {
-    h = tc::to_tf32(x);
-    const float r = __fsub_rn(x, h);
-    m = tc::to_tf32(r);
-    l = tc::to_tf32(__fsub_rn(r, m));
+__device__ __forceinline__ float tf32_trunc(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
 }
-// a double-FP32 value to three TF32 parts (33 bits)
+// x (FP32, 24 bits) = h + m + l exactly: h its top 11 significant bits, m the next 11, l the
+// last 2 (both differences exact: each drops bits below the part it removes)
+__device__ __forceinline__ void split3(float x, float &h, float &m, float &l) {
+    h = tf32_trunc(x);
+    const float r = __fsub_rn(x, h);
+    m = tf32_trunc(r);
+    l = __fsub_rn(r, m);
+}
+// a double-FP32 value to three TF32 parts (33 bits), by truncation as split3: h and m exact
+// parts of the leading bits, l the rest truncated to 11 bits (below 2^-33 of the value)
 __device__ __forceinline__ void split3_df(df x, float &h, float &m, float &l) {
-    h = tc::to_tf32(x.hi);
+    h = tf32_trunc(x.hi);
     const df r = two_sum(__fsub_rn(x.hi, h), x.lo);
-    m = tc::to_tf32(r.hi);
-    l = tc::to_tf32(__fadd_rn(__fsub_rn(r.hi, m), r.lo));
+    m = tf32_trunc(r.hi);
+    l = tf32_trunc(__fadd_rn(__fsub_rn(r.hi, m), r.lo));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -662,33 +669,46 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     const int grp = warp / TS, set = warp % TS;
     const int jt1 = min(NT8, set * TPS + TPS);
     for (int jt0 = set * TPS; jt0 < jt1; jt0 += 3) {
-        const int r0 = grp * (h / KG), r1 = r0 + h / KG;
+        const int r0 = grp * (h / KG), r1 = r0 + h / KG;  // multiples of 16
         // three accumulators per tile, smallest products first: ea (X_mid C_mid, X_lo C_hi,
         // X_hi C_lo), eb (X_mid C_hi, X_hi C_mid), hh (X_hi C_hi): shorter dependent mma chains
         float e[3][4] = {}, eb[3][4] = {}, hh[3][4] = {};
-        for (int k0 = r0; k0 < r1; k0 += 8) {
-            const float xa[4] = {C[cidx(k0 + t4, J0 + g4, NP)], C[cidx(k0 + t4, J0 + g4 + 8, NP)],
-                                 C[cidx(k0 + t4 + 4, J0 + g4, NP)],
-                                 C[cidx(k0 + t4 + 4, J0 + g4 + 8, NP)]};
-            float ah[4], am[4], al[4];
+        // chunk addresses (cidx) split into a column part and a row part: every column read
+        // here is g4 mod 8 (J0 and the tiles' first columns are multiples of 8), so a row's
+        // swizzle is ((i % 32) / 4) ^ g4 for all of them
+        const int ox0 = ((J0 >> 4) << 9) + (g4 << 5) + t4;  // column J0 + g4
+        const int ox1 = ox0 + (8 << 5);                     // column J0 + g4 + 8
+        int oc[3];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) split3(xa[q], ah[q], am[q], al[q]);
+        for (int t = 0; t < 3; ++t) {
+            const int c0 = T0 + 8 * (jt0 + t);
+            oc[t] = ((c0 >> 4) << 9) + (((c0 & 15) + g4) << 5) + t4;  // column c0 + g4
+        }
+        for (int k0 = r0; k0 < r1; k0 += 16) {
+            const int rb = ((k0 >> 5) * NP) << 9;
+            const int s0 = (k0 & 31) >> 2;  // 0 or 4
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int jt = jt0 + t;
-                if (jt < jt1) {
-                    const int c0 = T0 + 8 * jt;
-                    const float cb[2] = {C[cidx(k0 + t4, c0 + g4, NP)],
-                                         C[cidx(k0 + t4 + 4, c0 + g4, NP)]};
-                    float bh[2], bm[2], bl[2];
+            for (int half = 0; half < 2; ++half) {  // rows k0 + 8 half + t4 (sa), + 4 (sb)
+                const int sa = rb + (((s0 + 2 * half) ^ g4) << 2);
+                const int sb = rb + (((s0 + 2 * half + 1) ^ g4) << 2);
+                const float xa[4] = {C[sa + ox0], C[sa + ox1], C[sb + ox0], C[sb + ox1]};
+                float ah[4], am[4], al[4];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
-                    tc::mma_m16n8k8(e[t], am, bm);
-                    tc::mma_m16n8k8(eb[t], am, bh);
-                    tc::mma_m16n8k8(hh[t], ah, bh);
-                    tc::mma_m16n8k8(e[t], al, bh);
-                    tc::mma_m16n8k8(eb[t], ah, bm);
-                    tc::mma_m16n8k8(e[t], ah, bl);
+                for (int q = 0; q < 4; ++q) split3(xa[q], ah[q], am[q], al[q]);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    if (jt0 + t < jt1) {
+                        const float cb[2] = {C[sa + oc[t]], C[sb + oc[t]]};
+                        float bh[2], bm[2], bl[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
+                        tc::mma_m16n8k8(e[t], am, bm);
+                        tc::mma_m16n8k8(eb[t], am, bh);
+                        tc::mma_m16n8k8(hh[t], ah, bh);
+                        tc::mma_m16n8k8(e[t], al, bh);
+                        tc::mma_m16n8k8(eb[t], ah, bm);
+                        tc::mma_m16n8k8(e[t], ah, bl);
+                    }
                 }
             }
         }

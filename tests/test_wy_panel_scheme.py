@@ -9,7 +9,9 @@
    the columns right of the panel, W = R(P, T) + diag(c) X^T C, Y = S^T W, R(P, T) -= Y,
    C -= X diag(c) Y, against the reflectors applied one by one.
 2. The TF32 parts (11 significant bits, round to nearest with ties away, as cvt.rna.tf32.f32):
-   a value rounded to 22 bits is exactly two parts, an FP32 value exactly three.
+   a value rounded to 22 bits is exactly two parts, an FP32 value exactly three; and the
+   kernels' split of an FP32 value by truncation (its top 11 significant bits, the next 11, the
+   last 2, each difference taken in FP32) is exact too.
 """
 import numpy as np
 
@@ -101,6 +103,33 @@ def test_tf32_parts_are_exact():
     exact = a.astype(np.float64) * b.astype(np.float64)
     ok = np.isfinite(prod32) & (np.abs(exact) > 1e-30) & (np.abs(exact) < 1e30)
     assert np.all(prod32[ok] == exact[ok])
+
+
+def _tf32_trunc(x):
+    """The top 11 significant bits: the low 13 fraction bits cleared."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32)
+    return (b & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def test_truncated_tf32_parts_are_exact():
+    """x = h + m + l with h = trunc(x), m = trunc(x - h), l = (x - h) - m in FP32: both
+    differences are exact, every part is a TF32 value and l has at most 2 significant bits;
+    the parts' magnitudes fall by 2^-11 and 2^-22 (at most) as with rounding."""
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(200000) * np.exp(rng.uniform(-30, 30, 200000))).astype(np.float32)
+    x[:4] = np.array([0.0, -0.0, 1.0, -3.0], dtype=np.float32)
+    h = _tf32_trunc(x)
+    r = (x - h).astype(np.float32)
+    m = _tf32_trunc(r)
+    l = (r - m).astype(np.float32)
+    x64 = x.astype(np.float64)
+    assert np.all(r.astype(np.float64) == x64 - h.astype(np.float64))
+    assert np.all(h.astype(np.float64) + m.astype(np.float64) + l.astype(np.float64) == x64)
+    for part in (h, m, l):
+        assert np.all(_tf32_trunc(part) == part)
+    assert np.all((l.view(np.uint32) & np.uint32(0x003FFFFF)) == 0)  # <= 2 significant bits
+    assert np.all(np.abs(m.astype(np.float64)) <= 2.0 ** -10 * np.abs(x64))
+    assert np.all(np.abs(l.astype(np.float64)) <= 2.0 ** -21 * np.abs(x64))
 
 
 def test_forward_recurrence_equals_inverse_form():
