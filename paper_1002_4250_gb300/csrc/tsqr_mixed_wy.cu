@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "tsqr_fold.cuh"
 #include "tsqr_tc.cuh"
@@ -525,27 +526,29 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
             for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
         }
-        // The loop over the panel's columns is not unrolled (one copy of its body keeps the
-        // instruction cache warm); the register columns are addressed with static indices.
+        // The loop over the panel's columns is not unrolled (one copy of its body per half keeps
+        // the instruction cache warm); the register columns are addressed with static indices.
+        // Columns 0-7 are final once J >= 8: the second half updates columns 8-15 only, and
+        // each half picks column J among its eight.
         float fv[kPw], xp[PR];
 #pragma unroll
         for (int kk = 0; kk < kPw; ++kk) fv[kk] = 0.f;
 #pragma unroll
         for (int q = 0; q < PR; ++q) xp[q] = 0.f;
-#pragma unroll 1
-        for (int J = 0; J < pw; ++J) {
-            // columns J.. get reflector J-1; the factors of the columns before J (and of the
-            // padding columns) are zero, so every column takes the same exact FMA
+        auto column = [&](const int J, auto lo) {
+            constexpr int LO = decltype(lo)::value;
+            // columns LO.. get reflector J-1; the factors of the columns before J (and of the
+            // padding columns) are zero, so every one of them takes the same exact FMA
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk)
+            for (int kk = LO; kk < kPw; ++kk)
 #pragma unroll
                 for (int q = 0; q < PR; ++q) x[q][kk] = __fmaf_rn(-fv[kk], xp[q], x[q][kk]);
             float xj[PR];
 #pragma unroll
             for (int q = 0; q < PR; ++q) {
-                float tv = x[q][0];
+                float tv = x[q][LO];
 #pragma unroll
-                for (int kk = 1; kk < kPw; ++kk) tv = (kk == J) ? x[q][kk] : tv;
+                for (int kk = LO + 1; kk < LO + 8; ++kk) tv = (kk == J) ? x[q][kk] : tv;
                 xj[q] = tv;
             }
             float v[kPw];
@@ -586,7 +589,11 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
             for (int kk = 0; kk < kPw; ++kk) fv[kk] = __shfl_sync(0xffffffffu, fk, kk);
 #pragma unroll
             for (int q = 0; q < PR; ++q) xp[q] = xj[q];
-        }
+        };
+#pragma unroll 1
+        for (int J = 0; J < min(pw, 8); ++J) column(J, std::integral_constant<int, 0>{});
+#pragma unroll 1
+        for (int J = 8; J < pw; ++J) column(J, std::integral_constant<int, 8>{});
     }
     if (warp == PW) {
         // the scalar warp: after each column's barrier, reflector J's double-FP32 scalars and
