@@ -133,41 +133,42 @@ __device__ __forceinline__ double widen_f32(const float y) {
     return __longlong_as_double(sign | (e << 52) | ((long long)(u & 0x7fffff) << 29));
 }
 
-// 1/sqrt(t) for finite t > 0 by Newton's iteration for the reciprocal square root,
-// y <- y + y (1 - t y^2) / 2, started from the FP32 hardware estimate.  t is first scaled by an
-// even power of two into [1, 4) (exact, on the exponent bits) so that the FP32 estimate cannot
-// overflow or underflow; two steps take its ~2^-22 relative error below FP64 rounding.  Zero,
-// subnormal, infinite and NaN arguments take the library's rsqrt.
+// 1/sqrt(t) for finite t > 0 from the FP32 hardware estimate y by one third-order step of the
+// series (1 - h)^(-1/2) = 1 + h/2 + 3h^2/8 + ..., h = 1 - t y^2: y (1 + h/2 + 3h^2/8), whose
+// error is about 5|h|^3/16, below FP64 rounding for the estimate's ~2^-22 (four dependent FP64
+// operations, against six for two Newton steps: each costs about 65 cycles on the reflector's
+// serial chain).  t is first scaled by an even power of two into [1, 4) (exact, on the exponent
+// bits) so that the FP32 estimate cannot overflow or underflow.  Zero, subnormal, infinite and
+// NaN arguments take the library's rsqrt.
 __device__ __forceinline__ double recip_sqrt(double t) {
     const long long b = __double_as_longlong(t);
     const int e = (int)((b >> 52) & 0x7ff);
     if (e == 0 || e == 0x7ff) return rsqrt(t);
     const int k = (e - 1023) >> 1;  // t = tm 4^k, tm in [1, 4)
     const double tm = __longlong_as_double(b - ((long long)(2 * k) << 52));
-    double y = widen_f32(rsqrtf(seed_f32(tm)));
-    double h = fma(-tm * y, y, 1.0);
-    y = fma(__longlong_as_double(__double_as_longlong(y) - (1LL << 52)), h, y);  // y/2 exactly
-    h = fma(-tm * y, y, 1.0);
-    y = fma(__longlong_as_double(__double_as_longlong(y) - (1LL << 52)), h, y);
-    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));  // y 2^-k
+    const double y = widen_f32(rsqrtf(seed_f32(tm)));
+    const double h = fma(-tm * y, y, 1.0);
+    const double yh = y * h, p = fma(h, 0.375, 0.5);  // independent: one level
+    const double y1 = fma(yh, p, y);
+    return __longlong_as_double(__double_as_longlong(y1) - ((long long)k << 52));  // y1 2^-k
 }
 
-// 1/x for finite nonzero x by Newton's iteration for the reciprocal, y <- y + y (1 - x y),
-// started from the FP32 estimate of 1/xm with x = xm 2^k, |xm| in [1, 2) (exact rescaling);
-// two steps reach FP64 rounding.  Zero, subnormal, infinite and NaN arguments, and |x| >= 2^1022
-// (whose reciprocal is subnormal), divide.
+// 1/x for finite nonzero x from the FP32 estimate y of 1/xm, x = xm 2^k, |xm| in [1, 2) (exact
+// rescaling), by one third-order step y (1 + h + h^2) = y + (y h)(1 + h), h = 1 - xm y (error
+// |h|^3; three dependent FP64 operations, against four for two Newton steps).  Zero,
+// subnormal, infinite and NaN arguments, and |x| >= 2^1022 (whose reciprocal is subnormal),
+// divide.
 __device__ __forceinline__ double recip(double x) {
     const long long b = __double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ff);
     if (e == 0 || e >= 0x7fd) return 1.0 / x;
     const int k = e - 1023;
     const double xm = __longlong_as_double(b - ((long long)k << 52));
-    double y = widen_f32(__fdividef(1.0f, seed_f32(xm)));
-    double h = fma(-xm, y, 1.0);
-    y = fma(y, h, y);
-    h = fma(-xm, y, 1.0);
-    y = fma(y, h, y);
-    return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+    const double y = widen_f32(__fdividef(1.0f, seed_f32(xm)));
+    const double h = fma(-xm, y, 1.0);
+    const double yh = y * h, q = 1.0 + h;  // independent: one level
+    const double y1 = fma(yh, q, y);
+    return __longlong_as_double(__double_as_longlong(y1) - ((long long)k << 52));
 }
 
 // Reflector J's scalars from alpha = R(J,J) and sigma^2 (see the comment above).

@@ -1,4 +1,4 @@
-"""The reflector's scalar routines (Newton iterations for 1/sqrt(t) and 1/x seeded by FP32
+"""The reflector's scalar routines (third-order steps for 1/sqrt(t) and 1/x seeded by FP32
 hardware estimates) against CUDA's own FP64 rsqrt and reciprocal, over the whole exponent
 range: within 2 ulp."""
 import ctypes
