@@ -694,30 +694,26 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
                     seg[lane + kk] = acc;
                 }
             }
-        }
-        __syncthreads();
-
-        if (warp == 0) {
-            // ---- column kk's partials: those of its owner warp's lanes la..lb
-            for (int kk = lane; kk < U; kk += 32) {
-                const int w = ((kk + 1) * Wp - 1) / U;
-                const int kc0 = (w * U) / Wp, kc1 = ((w + 1) * U) / Wp;
-                const int rel = kk - kc0;
-                const int Nw = (kc1 - kc0) * cw;
-                const int la = (32 * (rel * cw + 1) - 1) / Nw;
-                const int lb = (32 * (rel + 1) * cw - 1) / Nw;
-                const double *sg = seg_all + w * ss + rel;
+            // ---- the warp's columns' dot products, while warp 0 forms the reflector: column
+            //      kc0 + rel sums the partials of the warp's lanes la..lb (whose runs touch it)
+            //      in a fixed order
+            __syncwarp();
+            for (int rel = lane; rel < kc1 - kc0; rel += 32) {
+                const int la = (32 * (rel * cw + 1) - 1) / N;
+                const int lb = (32 * (rel + 1) * cw - 1) / N;
+                const double *sg = seg + rel;
                 double d0 = sg[la], d1 = 0.0;
                 for (int l = la + 1; l + 1 <= lb; l += 2) {
                     d0 += sg[l];
                     d1 += sg[l + 1];
                 }
                 if (((lb - la) & 1) == 1) d0 += sg[lb];
-                dk[kk] = d0 + d1;
+                dk[kc0 + rel] = d0 + d1;
             }
-            __syncwarp();
-            apply_reflector(lane, n, J, hr, Rp, f, dk);
         }
+        __syncthreads();
+
+        if (warp == 0) apply_reflector(lane, n, J, hr, Rp, f, dk);
         __syncthreads();
     }
 }
