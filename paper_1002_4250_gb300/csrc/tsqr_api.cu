@@ -2083,6 +2083,21 @@ tsqr_status_t tsqr_autotune_batched(const void *const *ptrs, const int64_t *ms, 
     return TSQR_SUCCESS;
 }
 
+// Test hook (not part of the C ABI in include/tsqr.h): a bounded device wait on an mbarrier,
+// completed (arrive != 0) or left to run out after `limit` polls, which then sets the timeout
+// bit of the stream's status word (read back by tsqr_get_device_status as TSQR_ERR_TIMEOUT).
+// result: device int, 1 if the wait succeeded.
+extern "C" int tsqr_internal_wait_selftest(int64_t limit, int32_t arrive, int32_t *result,
+                                           tsqr_stream_t stream) {
+    if (limit < 1 || limit > (1LL << 20) || !result) return TSQR_ERR_INVALID_ARG;
+    Workspace *ws = nullptr;
+    const tsqr_status_t st = get_workspace((cudaStream_t)stream, 0, &ws);
+    if (st != TSQR_SUCCESS) return st;
+    return tsqr::wait_selftest_launch(limit, arrive, ws->status, result, (cudaStream_t)stream) == 0
+               ? TSQR_SUCCESS
+               : TSQR_ERR_CUDA;
+}
+
 tsqr_status_t tsqr_get_device_status(tsqr_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TSQR_ERR_CUDA;

@@ -88,4 +88,11 @@ tsqr_status_t f64_auto_args(int64_t m, int n, F64Args *a, int *warps, size_t *sm
 // for entry points outside tsqr_api.cu.
 void set_last_call(int launches, const tsqr_plan_t &plan);
 
+// The bounded-wait test kernel (tsqr_selftest.cu): one CTA waits, at most `limit` polls, on an
+// mbarrier that its own arrival completes (arrive != 0) or that nothing completes; a wait that
+// runs out sets kStatusTimeoutBit in *status.  *result: 1 if the wait succeeded.  0 or 3
+// (launch error).
+int wait_selftest_launch(long long limit, int arrive, int *status, int *result,
+                         cudaStream_t stream);
+
 }  // namespace tsqr

@@ -440,6 +440,7 @@ struct Tmem {
     uint64_t *bar;   // mbarrier the update's mma commit arrives on
     uint32_t phase;  // parity of the next commit's phase
     bool ok;         // false once a bounded wait gave up
+    bool pending;    // a commit (of phase `phase`) not yet waited for: its wait gave up
 };
 __host__ __device__ constexpr int tmem_dw(int n) {
     return ((n + 15) / 16) * 16 - 16 > 16 ? ((n + 15) / 16) * 16 - 16 : 16;
@@ -812,9 +813,13 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         // every thread polls (bounded); the CTA agrees on the outcome, so that all its threads
         // take the same path
         const bool done = __syncthreads_and(tc::mbar_wait(tm.bar, tm.phase, 1LL << 22) ? 1 : 0) != 0;
-        tm.phase ^= 1u;
-        if (!done) {
+        if (done) {
+            tm.phase ^= 1u;
+        } else {
+            // the commit stays pending (phase tm.phase): the caller waits for it once more,
+            // bounded, before it releases the tensor memory
             tm.ok = false;
+            tm.pending = true;
             if (status && threadIdx.x == 0) atomicOr(status, kStatusTimeoutBit);
         }
         tc::fence_after_sync();
@@ -939,6 +944,7 @@ __global__ void __launch_bounds__(kThreads, HB == 2 ? 2 : 1)
     tm.bar = bar;
     tm.phase = 0;
     tm.ok = true;
+    tm.pending = false;
     Tma t{&tmap, -1, tbar, 0u, 0u, 0u};
     const bool ok = wy_leaf<Tin, HB>(sm, L, n, static_cast<const Tin *>(a.A), b.lda, rbeg, rend,
                                        a.vec4 != 0, tm, use_tma ? &t : nullptr, b.status);
@@ -946,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, HB == 2 ? 2 : 1)
         // a tensor-core or TMA wait gave up: wait once more, bounded, for the mma and the loads
         // in flight, release the tensor memory and leave R unwritten
         if (threadIdx.x == 0) {
-            tc::mbar_wait(bar, tm.phase, 1LL << 22);
+            if (tm.pending) tc::mbar_wait(bar, tm.phase, 1LL << 22);
             for (int k = 0; k < NP; ++k)
                 if ((t.pend >> k) & 1u) tc::mbar_wait(tbar + k, (t.ppar >> k) & 1u, 1LL << 22);
         }
@@ -990,6 +996,7 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
     tm.bar = &s_bar;
     tm.phase = 0;
     tm.ok = true;
+    tm.pending = false;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = (int)atomicAdd(bt.queue, 1u);
@@ -1028,7 +1035,7 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
         a.status = bt.status;
         wy_climb(sm, L, a, tree_ldsd(n, P.arity), w.y);
     }
-    if (!tm.ok && threadIdx.x == 0) tc::mbar_wait(&s_bar, tm.phase, 1LL << 22);
+    if (tm.pending && threadIdx.x == 0) tc::mbar_wait(&s_bar, tm.phase, 1LL << 22);
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) tc::tmem_dealloc(s_tbase, (uint32_t)tcols);
