@@ -352,7 +352,7 @@ def test_tsqr_tile_shorter_than_n(oracle):
 
 
 # ----------------------------------------------------------------------------------------
-# the checker
+# the Gram-residual check (compensated dot products)
 # ----------------------------------------------------------------------------------------
 def test_dot2_gram_is_compensated(oracle):
     # catastrophic cancellation: exact answer 1, naive summation gives 0
