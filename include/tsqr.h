@@ -58,7 +58,8 @@ typedef enum { TSQR_F64 = 0, TSQR_F32 = 1, TSQR_BF16 = 2 } tsqr_dtype_t;
 /* Arithmetic of the leaf (tile) factorizations.  The tree operator is FP64 in every mode.
  * TSQR_PREC_F64:   FP64 everywhere (A must be TSQR_F64).
  * TSQR_PREC_MIXED: leaf Householder panels in FP32 (A is FP32 or BF16, widened exactly on
- *                  load), reflector norms and tree combines in FP64.                          */
+ *                  load); the reflector scalars and the leaf's R in FP64 (FOLD leaf) or
+ *                  double-FP32, about 48 bits (PANELS leaf); tree combines in FP64.          */
 typedef enum { TSQR_PREC_F64 = 0, TSQR_PREC_MIXED = 1 } tsqr_prec_t;
 
 /* Reduction tree over the row tiles (Section 1: "any reduction tree" works by associativity).
@@ -146,7 +147,8 @@ tsqr_status_t tsqr_r_host(const double *A, int64_t m, int64_t n, int64_t lda, do
  * the tile rows, the leaves, the bulk warps and the arity.
  * (dtype, prec) must be (F64, F64), (F32, MIXED) or (BF16, MIXED).  lda counts elements.
  * MIXED keeps A in its storage type on chip and does the leaves' bulk arithmetic in FP32,
- * with the reflector norms and scalars, R and the tree in FP64; R is always FP64. */
+ * with the reflector scalars and the leaf's R in FP64 (FOLD leaf) or double-FP32 (PANELS leaf,
+ * see tsqr_leaf_t) and the tree in FP64; R is always FP64. */
 tsqr_status_t tsqr_r_ex(const void *A, int32_t dtype, int32_t prec, int64_t m, int64_t n,
                         int64_t lda, double *R, int64_t ldr, const tsqr_plan_t *plan,
                         tsqr_stream_t stream);
