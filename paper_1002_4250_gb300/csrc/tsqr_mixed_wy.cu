@@ -519,46 +519,52 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     constexpr int PW = kPanelWarps;
     constexpr int PR = h / (32 * PW);
     const bool panel_warp = warp < PW;
-    float x[PR][kPw];
+    // the panel's rows in registers as pairs of columns (2 j, 2 j + 1): the update and the dot
+    // products take paired FP32 FMAs (two IEEE FMAs an instruction, the same results)
+    float2 x2[PR][kPw / 2];
+#define TSQR_XE(q, kk) (((kk) & 1) ? x2[q][(kk) >> 1].y : x2[q][(kk) >> 1].x)
     if (panel_warp) {
 #pragma unroll
         for (int q = 0; q < PR; ++q) {
             const int i = 32 * PW * q + 32 * warp + lane;
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk) x[q][kk] = C[cidx(i, J0 + kk, NP)];
+            for (int j = 0; j < kPw / 2; ++j)
+                x2[q][j] = make_float2(C[cidx(i, J0 + 2 * j, NP)], C[cidx(i, J0 + 2 * j + 1, NP)]);
         }
         // The loop over the panel's columns is not unrolled (one copy of its body per half keeps
         // the instruction cache warm); the register columns are addressed with static indices.
         // Columns 0-7 are final once J >= 8: the second half updates columns 8-15 only, and
         // each half picks column J among its eight.
-        float fv[kPw], xp[PR];
+        // nfv: the negated factors -f_k, paired; xp: the previous column J-1's rows, both halves
+        float2 nfv[kPw / 2], xp[PR];
 #pragma unroll
-        for (int kk = 0; kk < kPw; ++kk) fv[kk] = 0.f;
+        for (int j = 0; j < kPw / 2; ++j) nfv[j] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < PR; ++q) xp[q] = 0.f;
+        for (int q = 0; q < PR; ++q) xp[q] = make_float2(0.f, 0.f);
         auto column = [&](const int J, auto lo) {
             constexpr int LO = decltype(lo)::value;
             // columns LO.. get reflector J-1; the factors of the columns before J (and of the
             // padding columns) are zero, so every one of them takes the same exact FMA
 #pragma unroll
-            for (int kk = LO; kk < kPw; ++kk)
+            for (int j = LO / 2; j < kPw / 2; ++j)
 #pragma unroll
-                for (int q = 0; q < PR; ++q) x[q][kk] = __fmaf_rn(-fv[kk], xp[q], x[q][kk]);
-            float xj[PR];
+                for (int q = 0; q < PR; ++q) x2[q][j] = __ffma2_rn(nfv[j], xp[q], x2[q][j]);
+            float2 xj[PR];
 #pragma unroll
             for (int q = 0; q < PR; ++q) {
-                float tv = x[q][LO];
+                float tv = TSQR_XE(q, LO);
 #pragma unroll
-                for (int kk = LO + 1; kk < LO + 8; ++kk) tv = (kk == J) ? x[q][kk] : tv;
-                xj[q] = tv;
+                for (int kk = LO + 1; kk < LO + 8; ++kk) tv = (kk == J) ? TSQR_XE(q, kk) : tv;
+                xj[q] = make_float2(tv, tv);
             }
             float v[kPw];
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk) {
-                float sacc = __fmul_rn(xj[0], x[0][kk]);
+            for (int j = 0; j < kPw / 2; ++j) {
+                float2 sacc = __fmul2_rn(xj[0], x2[0][j]);
 #pragma unroll
-                for (int q = 1; q < PR; ++q) sacc = __fmaf_rn(xj[q], x[q][kk], sacc);
-                v[kk] = sacc;
+                for (int q = 1; q < PR; ++q) sacc = __ffma2_rn(xj[q], x2[q][j], sacc);
+                v[2 * j] = sacc.x;
+                v[2 * j + 1] = sacc.y;
             }
             // row Jg of R (FP32 parts) for the factors below, read before the barrier: the
             // scalar warp updates the row after it
@@ -586,8 +592,11 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                 const float w = __fmaf_rn(rcp_approx(__fsub_rn(a_f, beta)), tf, r_f);
                 fk = -__fmul_rn(w, rcp_approx(beta));
             }
+            const float nfk = -fk;
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk) fv[kk] = __shfl_sync(0xffffffffu, fk, kk);
+            for (int j = 0; j < kPw / 2; ++j)
+                nfv[j] = make_float2(__shfl_sync(0xffffffffu, nfk, 2 * j),
+                                     __shfl_sync(0xffffffffu, nfk, 2 * j + 1));
 #pragma unroll
             for (int q = 0; q < PR; ++q) xp[q] = xj[q];
         };
@@ -623,7 +632,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         for (int q = 0; q < PR; ++q) {
             const int i = 32 * PW * q + 32 * warp + lane;
 #pragma unroll
-            for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = x[q][kk];
+            for (int kk = 0; kk < kPw; ++kk) C[cidx(i, J0 + kk, NP)] = TSQR_XE(q, kk);
         }
         // the tails' three TF32 parts, this thread's rows, into tensor memory (the A operand of
         // the update): row 32 PW q + 32 w + l is lane 32 (w % 4) + l of M-block (PW q + w) / 4
@@ -636,7 +645,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) split3(x[q][8 * half + e], hi[e], mid[e], lo[e]);
+                for (int e = 0; e < 8; ++e) split3(TSQR_XE(q, 8 * half + e), hi[e], mid[e], lo[e]);
                 const uint32_t col = (uint32_t)(tmem_dw(n) * MB + 48 * b + 8 * half);
                 tc::tmem_st8(tm.base + lane_base + col, hi);
                 tc::tmem_st8(tm.base + lane_base + col + 16u, mid);
@@ -645,6 +654,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
         }
         tc::tmem_st_wait();
     }
+#undef TSQR_XE
     if (ntp <= 0) {
         // the last panel: nothing reads its columns again in this chunk
         if (t && t->rnext >= 0) {
