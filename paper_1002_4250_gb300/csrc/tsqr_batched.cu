@@ -40,17 +40,17 @@ __device__ __forceinline__ void batched_body(const BatchArgs &b) {
         const Tin *A = static_cast<const Tin *>(P.A);
         if constexpr (sizeof(T) == 8) {
             switch (P.blk) {
-                case 4: leaf_tree_job<T, Tin, 4, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
-                case 3: leaf_tree_job<T, Tin, 3, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
-                case 2: leaf_tree_job<T, Tin, 2, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
-                default: leaf_tree_job<T, Tin, 1, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y); break;
+                case 4: leaf_tree_job<T, Tin, 4, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y, 0); break;
+                case 3: leaf_tree_job<T, Tin, 3, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y, 0); break;
+                case 2: leaf_tree_job<T, Tin, 2, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y, 0); break;
+                default: leaf_tree_job<T, Tin, 1, 1, false>(a, A, P.ldS, P.ldS * P.n, w.y, 0); break;
             }
         } else {
             const int ldSd = tree_ldsd(P.n, P.arity), sd = mixed_s_doubles_of(P.n, P.ldS, P.arity);
             switch (P.blk * 10 + P.vec) {
-                case 44: leaf_tree_job<T, Tin, 4, 4, true>(a, A, ldSd, sd, w.y); break;
-                case 22: leaf_tree_job<T, Tin, 2, 2, true>(a, A, ldSd, sd, w.y); break;
-                default: leaf_tree_job<T, Tin, 1, 1, true>(a, A, ldSd, sd, w.y); break;
+                case 44: leaf_tree_job<T, Tin, 4, 4, true>(a, A, ldSd, sd, w.y, 0); break;
+                case 22: leaf_tree_job<T, Tin, 2, 2, true>(a, A, ldSd, sd, w.y, 0); break;
+                default: leaf_tree_job<T, Tin, 1, 1, true>(a, A, ldSd, sd, w.y, 0); break;
             }
         }
     }

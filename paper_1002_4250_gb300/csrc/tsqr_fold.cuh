@@ -600,11 +600,16 @@ __device__ __forceinline__ void fold_leaf(T *__restrict__ S, const int ldS, cons
 // sums their partials in a fixed order and updates R and f.  Needs at least two warps.
 // With nsc non-null the reflectors' (tau_J, c_J) go to nsc[2J], nsc[2J+1] (their tails stay
 // in S: rows 0..J of each triangle's column J).
+// worker_sums: every worker warp sums its own columns' dot-product partials right after its
+// sweep, while warp 0 forms the reflector (shorter chain: for a combine that runs alone);
+// otherwise warp 0 sums them all after the barrier (a quarter of the FP64 instructions, whose
+// pipe time counts when many combines run at once).  Both give the same bytes.
 __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldSd, const int c,
                                            double *__restrict__ Rp, double *__restrict__ f,
                                            double *__restrict__ seg_all,
                                            double *__restrict__ dk, const int n,
-                                           double *nsc = nullptr) {
+                                           double *nsc = nullptr,
+                                           const bool worker_sums = true) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int Wp = (blockDim.x >> 5) - 1;  // worker warps 1..Wp
@@ -698,7 +703,7 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
             //      kc0 + rel sums the partials of the warp's lanes la..lb (whose runs touch it)
             //      in a fixed order
             __syncwarp();
-            for (int rel = lane; rel < kc1 - kc0; rel += 32) {
+            for (int rel = lane; worker_sums && rel < kc1 - kc0; rel += 32) {
                 const int la = (32 * (rel * cw + 1) - 1) / N;
                 const int lb = (32 * (rel + 1) * cw - 1) / N;
                 const double *sg = seg + rel;
@@ -713,7 +718,30 @@ __device__ __forceinline__ void fold_stack(double *__restrict__ S, const int ldS
         }
         __syncthreads();
 
-        if (warp == 0) apply_reflector(lane, n, J, hr, Rp, f, dk);
+        if (warp == 0) {
+            if (!worker_sums) {
+                // ---- warp 0 sums column kk's partials: those of its owner warp's lanes la..lb
+                //      (the same sums in the same order as the worker warps')
+                for (int kk = lane; kk < U; kk += 32) {
+                    const int w = ((kk + 1) * Wp - 1) / U;
+                    const int kc0 = (w * U) / Wp, kc1 = ((w + 1) * U) / Wp;
+                    const int rel = kk - kc0;
+                    const int Nw = (kc1 - kc0) * cw;
+                    const int la = (32 * (rel * cw + 1) - 1) / Nw;
+                    const int lb = (32 * (rel + 1) * cw - 1) / Nw;
+                    const double *sg = seg_all + w * ss + rel;
+                    double d0 = sg[la], d1 = 0.0;
+                    for (int l = la + 1; l + 1 <= lb; l += 2) {
+                        d0 += sg[l];
+                        d1 += sg[l + 1];
+                    }
+                    if (((lb - la) & 1) == 1) d0 += sg[lb];
+                    dk[kk] = d0 + d1;
+                }
+                __syncwarp();
+            }
+            apply_reflector(lane, n, J, hr, Rp, f, dk);
+        }
         __syncthreads();
     }
 }
@@ -778,10 +806,19 @@ __device__ __forceinline__ void store_normalized(const double *__restrict__ Rp, 
 // last child to arrive stacks the children in index order (the lowest on top), folds them and
 // climbs on; the others return.  The root writes the sign-normalized R.  Rp holds the leaf's
 // R; Sd (leading dimension ldSd) must hold arity-1 stacked n x n triangles.
+// Tree levels of at most this many nodes combine with fold_stack's worker sums: few combines
+// run at once there, each bound by its serial chain (the binary tree over 4,194,304 x 32,
+// 16,384 leaves, ran 2.7% slower with worker sums at every level; the 10,000 x 16 one, 40
+// leaves, 12% faster).
+constexpr int kWorkerSumNodes = 152;
+
 template <bool kStore>
+// worker_sum_nodes: levels with at most this many nodes combine with fold_stack's worker sums
+// (0 for the batch kernels, whose problems' combines run many at once).
 __device__ __forceinline__ void climb_tree(const F64Args &a, double *Sd, const int ldSd,
                                            double *Rp, double *f, double *seg, double *tot,
-                                           unsigned int *flag, const int leaf) {
+                                           unsigned int *flag, const int leaf,
+                                           const int worker_sum_nodes = kWorkerSumNodes) {
     const int n = a.n;
     // k-ary tree: node t of level l+1 has children k t .. k t + k-1 of level l
     const int k = a.arity;
@@ -821,7 +858,7 @@ __device__ __forceinline__ void climb_tree(const F64Args &a, double *Sd, const i
             const size_t id = (size_t)next_off + parent;
             const int ldv = (k - 1) * n;
             fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n,
-                       a.q.node_sc + id * 2 * n);
+                       a.q.node_sc + id * 2 * n, next_cnt <= worker_sum_nodes);
             // the node's tails: rows 0..(nchild-1) n - 1 of S (zero below each diagonal)
             double *dst = a.q.node_V + id * (size_t)ldv * n;
             const int rows = (nchild - 1) * n;
@@ -830,7 +867,8 @@ __device__ __forceinline__ void climb_tree(const F64Args &a, double *Sd, const i
                 dst[row + (size_t)col * ldv] = Sd[row + (size_t)col * ldSd];
             }
         } else {
-            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n);
+            fold_stack(Sd, ldSd, nchild - 1, Rp, f, seg, tot + seg_stride(n), n, nullptr,
+                       next_cnt <= worker_sum_nodes);
         }
         off = next_off;
         cnt = next_cnt;
@@ -849,7 +887,8 @@ __device__ __forceinline__ void climb_tree(const F64Args &a, double *Sd, const i
 // signs, are kept in a.q for forming Q (tsqr_qr); chunk boundaries are then multiples of a.h.
 template <typename T, typename Tin, int B, int V, bool kPipe, bool kStore = false>
 __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, const int ldSd,
-                                              const int s_doubles, const int leaf) {
+                                              const int s_doubles, const int leaf,
+                                              const int worker_sum_nodes = kWorkerSumNodes) {
     extern __shared__ __align__(16) double smem[];
     const int n = a.n;
     const SmemLayout L = smem_layout_s(n, s_doubles, blockDim.x >> 5);
@@ -914,7 +953,7 @@ __device__ __forceinline__ void leaf_tree_job(const F64Args &a, const Tin *A, co
         }
     }
 
-    climb_tree<kStore>(a, Sd, ldSd, Rp, f, seg, tot, flag, leaf);
+    climb_tree<kStore>(a, Sd, ldSd, Rp, f, seg, tot, flag, leaf, worker_sum_nodes);
 }
 
 

@@ -905,12 +905,13 @@ __device__ __forceinline__ bool wy_leaf(unsigned char *sm, const Layout &L, cons
 // The tree above a leaf's R (FP64 at L.R): the FP64 climb of the one-reduction kernels, with
 // the chunk region as the stacked triangles' buffer.
 __device__ __forceinline__ void wy_climb(unsigned char *sm, const Layout &L, const F64Args &b,
-                                         const int ldSd, const int leaf) {
+                                         const int ldSd, const int leaf,
+                                         const int worker_sum_nodes = kWorkerSumNodes) {
     climb_tree<false>(b, reinterpret_cast<double *>(sm + L.C), ldSd,
                       reinterpret_cast<double *>(sm + L.R), reinterpret_cast<double *>(sm + L.f),
                       reinterpret_cast<double *>(sm + L.seg),
                       reinterpret_cast<double *>(sm + L.tot),
-                      reinterpret_cast<unsigned int *>(sm + L.flag), leaf);
+                      reinterpret_cast<unsigned int *>(sm + L.flag), leaf, worker_sum_nodes);
 }
 
 // One matrix: CTA = leaf, then the tree.
@@ -1043,7 +1044,7 @@ __global__ void __launch_bounds__(kThreads, 1) tsqr_batched_wy_kernel(const Batc
         a.R = P.R;
         a.ldr = n;
         a.status = bt.status;
-        wy_climb(sm, L, a, tree_ldsd(n, P.arity), w.y);
+        wy_climb(sm, L, a, tree_ldsd(n, P.arity), w.y, 0);
     }
     if (tm.pending && threadIdx.x == 0) tc::mbar_wait(&s_bar, tm.phase, 1LL << 22);
     tc::fence_before_sync();
