@@ -23,17 +23,19 @@
 //      chunk): Z = X^T C(:, T) (tensor cores), W = R(P, T) + diag(c) Z, Y = S^T W,
 //      R(P, T) -= Y, C(:, T) -= X (diag(c) Y) (tensor cores).
 // The tensor-core products are split-TF32 (compensated) products with FP32 accumulation: every
-// FP32 operand is exactly three TF32 parts (11 + 11 + 2 significant bits), diag(c) Y is split
-// into three too, and the six partial products down to 2^-22 of the leading one are summed
-// (the smallest first), so each product is as accurate as an FP32 dot product.  R is held in double-FP32 during the leaf and converted (exactly) to
-// FP64 for the FP64 tree (climb_tree / fold_stack, the paper's operator).
+// FP32 operand is exactly three TF32 parts (11 + 11 + 2 significant bits, split by truncation),
+// diag(c) Y is split into three too, and the six partial products down to 2^-22 of the leading
+// one are summed (the smallest first), so each product is as accurate as an FP32 dot product.
+// R is held in double-FP32 during the leaf and converted (exactly) to FP64 for the FP64 tree
+// (climb_tree / fold_stack, the paper's operator).
 //
 // Why this precision split: everything that multiplies the running triangle R (the reflector
 // scalars, S, the R rows) is accurate to far below FP32 rounding, so R's accumulated content
 // is transformed orthogonally to that accuracy chunk after chunk; the FP32 roundings land in
 // the chunk's rows.  The dot products carry FP32 rounding (the per-lane partials and the lane
-// sums), an error relative to the chunk's entries like the FP32 update's own.  The tails being exactly three TF32 parts makes the V the tensor cores use
-// and the V that S is built from the same matrix: the tails are used exactly as stored.
+// sums), an error relative to the chunk's entries like the FP32 update's own.  The tails being
+// exactly three TF32 parts makes the V the tensor cores use and the V that S is built from the
+// same matrix: the tails are used exactly as stored.
 #include <cuda.h>  // CUtensorMap and its encoding enums (the driver call is found at run time)
 #include <cuda_bf16.h>
 #include <cstring>
