@@ -163,6 +163,20 @@ __device__ __forceinline__ void split3(float x, float &h, float &m, float &l) {
     m = tf32_trunc(r);
     l = __fsub_rn(r, m);
 }
+// split3 of two values at once: the two differences as paired FMAs x + (-1) h (exact, the
+// same results as split3's subtractions)
+__device__ __forceinline__ void split3x2(float x0, float x1, float &h0, float &h1, float &m0,
+                                         float &m1, float &l0, float &l1) {
+    h0 = tf32_trunc(x0);
+    h1 = tf32_trunc(x1);
+    const float2 mone = make_float2(-1.f, -1.f);
+    const float2 r = __ffma2_rn(make_float2(h0, h1), mone, make_float2(x0, x1));
+    m0 = tf32_trunc(r.x);
+    m1 = tf32_trunc(r.y);
+    const float2 l = __ffma2_rn(make_float2(m0, m1), mone, r);
+    l0 = l.x;
+    l1 = l.y;
+}
 // a double-FP32 value to three TF32 parts (33 bits), by truncation as split3: h and m exact
 // parts of the leading bits, l the rest truncated to 11 bits (below 2^-33 of the value)
 __device__ __forceinline__ void split3_df(df x, float &h, float &m, float &l) {
@@ -714,14 +728,16 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                 const float xa[4] = {C[sa + ox0], C[sa + ox1], C[sb + ox0], C[sb + ox1]};
                 float ah[4], am[4], al[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) split3(xa[q], ah[q], am[q], al[q]);
+                for (int q = 0; q < 4; q += 2)
+                    split3x2(xa[q], xa[q + 1], ah[q], ah[q + 1], am[q], am[q + 1], al[q],
+                             al[q + 1]);
 #pragma unroll
                 for (int t = 0; t < 3; ++t) {
                     if (jt0 + t < jt1) {
                         const float cb[2] = {C[sa + oc[t]], C[sb + oc[t]]};
                         float bh[2], bm[2], bl[2];
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) split3(cb[q], bh[q], bm[q], bl[q]);
+                        split3x2(cb[0], cb[1], bh[0], bh[1], bm[0], bm[1], bl[0], bl[1]);
                         tc::mma_m16n8k8(e[t], am, bm);
                         tc::mma_m16n8k8(eb[t], am, bh);
                         tc::mma_m16n8k8(hh[t], ah, bh);
@@ -845,9 +861,14 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
                     tc::tmem_ld8(tm.base + lane_base + (uint32_t)(tmem_dw(n) * b + c0), v);
                     tc::tmem_ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        float *pc = C + cidx(i, T0 + c0 + e, NP);
-                        *pc = __fsub_rn(*pc, v[e]);
+                    for (int e = 0; e < 8; e += 2) {  // C - D as paired FMAs C + (-1) D: exact
+                        float *pc0 = C + cidx(i, T0 + c0 + e, NP);
+                        float *pc1 = C + cidx(i, T0 + c0 + e + 1, NP);
+                        const float2 d = __ffma2_rn(make_float2(v[e], v[e + 1]),
+                                                    make_float2(-1.f, -1.f),
+                                                    make_float2(*pc0, *pc1));
+                        *pc0 = d.x;
+                        *pc1 = d.y;
                     }
                 }
             }
