@@ -155,16 +155,9 @@ __device__ __forceinline__ Refl make_refl(const df alpha, const df sig2) {
 __device__ __forceinline__ float tf32_trunc(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
 }
-// x (FP32, 24 bits) = h + m + l exactly: h its top 11 significant bits, m the next 11, l the
-// last 2 (both differences exact: each drops bits below the part it removes)
-__device__ __forceinline__ void split3(float x, float &h, float &m, float &l) {
-    h = tf32_trunc(x);
-    const float r = __fsub_rn(x, h);
-    m = tf32_trunc(r);
-    l = __fsub_rn(r, m);
-}
-// split3 of two values at once: the two differences as paired FMAs x + (-1) h (exact, the
-// same results as split3's subtractions)
+// Two FP32 values (24 bits) each = h + m + l exactly: h its top 11 significant bits, m the next
+// 11, l the last 2 (both differences exact: each drops bits below the part it removes), the
+// differences taken two at a time as paired FMAs x + (-1) h (the same results as subtractions)
 __device__ __forceinline__ void split3x2(float x0, float x1, float &h0, float &h1, float &m0,
                                          float &m1, float &l0, float &l1) {
     h0 = tf32_trunc(x0);
@@ -177,7 +170,7 @@ __device__ __forceinline__ void split3x2(float x0, float x1, float &h0, float &h
     l0 = l.x;
     l1 = l.y;
 }
-// a double-FP32 value to three TF32 parts (33 bits), by truncation as split3: h and m exact
+// a double-FP32 value to three TF32 parts (33 bits), by truncation as split3x2: h and m exact
 // parts of the leading bits, l the rest truncated to 11 bits (below 2^-33 of the value)
 __device__ __forceinline__ void split3_df(df x, float &h, float &m, float &l) {
     h = tf32_trunc(x.hi);
@@ -661,7 +654,9 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) split3(TSQR_XE(q, 8 * half + e), hi[e], mid[e], lo[e]);
+                for (int e = 0; e < 8; e += 2)
+                    split3x2(TSQR_XE(q, 8 * half + e), TSQR_XE(q, 8 * half + e + 1), hi[e],
+                             hi[e + 1], mid[e], mid[e + 1], lo[e], lo[e + 1]);
                 const uint32_t col = (uint32_t)(tmem_dw(n) * MB + 48 * b + 8 * half);
                 tc::tmem_st8(tm.base + lane_base + col, hi);
                 tc::tmem_st8(tm.base + lane_base + col + 16u, mid);
