@@ -1477,11 +1477,11 @@ tsqr_status_t plan_mixed(int64_t m, int n, bool bf16, const tsqr_plan_t *over, F
         !over || ((over->warps == 0 || over->warps == 8) &&
                   (over->tree == TSQR_TREE_BINARY || over->tile_rows == 0 ||
                    over->tile_rows == 256 || over->tile_rows == 512));
-    // measured at 2^24 rows: the fold wins up to n = 8 for FP32 (n = 8: 0.81 against 1.04 ms;
-    // n = 9: 1.32 against 1.13) and at n <= 2 for BF16 (n = 2: 0.35 against 0.51 ms; n = 3:
-    // 0.89 against 0.62), the blocked leaf from there to 112 columns (FP32, fold against
-    // panels: n = 65: 48.8 against 25.7 ms; n = 96: 143.8 against 45.2; n = 112: 226.8 against
-    // 73.2; BF16 alike)
+    // measured at 2^24 rows: the fold wins up to n = 8 for FP32 (n = 8: 0.80 against 0.82 ms;
+    // n = 9: 1.31 against 0.90; n = 7 alone goes the other way, 0.85 against 0.75) and at
+    // n <= 2 for BF16 (n = 2: 0.34 against 0.44 ms; n = 3: 0.84 against 0.53), the blocked leaf
+    // from there to 112 columns (FP32, fold against panels: n = 65: 48.8 against 25.7 ms;
+    // n = 96: 143.8 against 45.2; n = 112: 226.8 against 73.2; BF16 alike)
     const bool wy_auto = n <= kMixedWyMaxN && n > (bf16 ? 2 : 8);
     if (leaf == TSQR_LEAF_PANELS || (leaf == 0 && wy_auto && wy_knobs)) {
         tsqr_plan_t o = over ? *over : tsqr_plan_t{};
