@@ -54,6 +54,11 @@ constexpr int kWarps = 8;
 constexpr int kPw = 16;       // panel width
 constexpr int kMaxPartials = 24;  // partial Z tiles (row group x n-tile) in shared memory
 
+// The Z product's tile sets for nt8 8-column tiles: the fewest (1, 2 or 4) whose
+// (8 / sets) row groups x nt8 partial tiles fit kMaxPartials (nt8 <= 3 with 8 row groups, <= 6
+// with 4, <= 12 with 2: n <= 112).
+__host__ __device__ constexpr int z_tile_sets(int nt8) { return nt8 >= 7 ? 4 : nt8 >= 4 ? 2 : 1; }
+
 // ------------------------------------------------------------------------------------------
 // Double-FP32 ("df") arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2.  Error-free
 // transformations (Knuth's TwoSum, Dekker's fast TwoSum, TwoProduct by FMA) in round-to-nearest
@@ -689,9 +694,7 @@ __device__ __forceinline__ void panel_step(unsigned char *sm, const Layout &L, c
     //          columns, takes several rounds over its rows).  Per tile three accumulators
     //          (below); partial tiles per row group go to P (KG NT8 <= kMaxPartials).
     const int NT8 = ntp / 8;
-    // tile sets: the fewest (1, 2 or 4) whose KG NT8 partial tiles fit P (24 tiles: NT8 <= 3
-    // with 8 row groups, <= 6 with 4, <= 12 with 2)
-    const int TS = NT8 >= 7 ? 4 : NT8 >= 4 ? 2 : 1;
+    const int TS = z_tile_sets(NT8);
     const int TPS = (NT8 + TS - 1) / TS;  // tiles per set (<= 3 for n <= 64)
     const int KG = kWarps / TS;           // row groups
     const int g4 = lane >> 2, t4 = lane & 3;
@@ -1275,3 +1278,23 @@ cudaError_t batched_wy_launch(const BatchArgs &b, int grid, bool bf16, int h, in
 }
 
 }  // namespace tsqr
+
+// Test hook (not part of the C ABI in include/tsqr.h; host only, no device call): the blocked
+// leaf's shared-memory bytes for width n and chunk height h (out[0]), its tensor-memory columns
+// (out[1]), and the most partial Z tiles any of its panels keeps (out[2]) against the slots
+// (out[3]).  Returns 0.
+extern "C" int tsqr_internal_wy_layout(int n, int h, int64_t *out) {
+    out[0] = (int64_t)tsqr::mixed_wy_smem_bytes(n, h);
+    out[1] = tsqr::wy::tmem_need(n, h);
+    int most = 0;
+    const int n8 = tsqr::wy::round_up_i(n, 8);
+    for (int j0 = 0; j0 < n; j0 += tsqr::wy::kPw) {
+        const int nt8 = (n8 - (j0 + tsqr::wy::kPw)) / 8;
+        if (nt8 <= 0) continue;
+        const int kg = tsqr::wy::kWarps / tsqr::wy::z_tile_sets(nt8);
+        most = kg * nt8 > most ? kg * nt8 : most;
+    }
+    out[2] = most;
+    out[3] = tsqr::wy::kMaxPartials;
+    return 0;
+}
